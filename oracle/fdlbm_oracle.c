@@ -1,0 +1,501 @@
+/*
+ * CPU oracle for the T2S2-FDLBM D2Q9 step (Chen, Chai, Wang, Shi,
+ * "A finite-difference lattice Boltzmann model with second-order accuracy of
+ * time and space for incompressible flow", arXiv 1911.12913).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, obviously correct FP64
+ * reference that the CUDA library is checked against.  Only the tests, the
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or constant with the CUDA library.
+ *
+ * Style: whole-field passes in the order of the paper's computational sequence
+ * (Sec. 2D, Steps 1-3), one formula per loop, no fusion, no blocking.  Every
+ * function names the equation it follows.  Readings of passages that are silent
+ * or garbled in the paper:
+ *   - the blend weight `beta` multiplies the second-order UPWIND difference,
+ *     D_m = (1-beta) D_c + beta D_u (Eq. 2.36 prints the weights the other way
+ *     round; the symbol of Eq. 4.8 and the errors of Table 1 fit this reading).
+ *     `beta_is_central = 1` selects the literal print (tests only);
+ *   - the c < 0 branch of the upwind difference (Eq. 2.38) is the mirror image
+ *     of the c >= 0 branch;
+ *   - on a stretched tensor-product grid, d/dx = (d zeta/dx) d/d zeta with the
+ *     differences of Eqs. 2.37-2.38 taken in the unit-spaced index coordinate;
+ *   - the force terms of Eqs. 2.20, 2.32, 2.34 are kept in every transform, and
+ *     the moment of the half-step variable is rho u = sum xi fbar + (h/2) rho F
+ *     (the analogue of Eq. 3.3 for the variable of Eq. 2.31);
+ *   - walls use the non-equilibrium extrapolation of Eq. 3.10 with the density
+ *     of the nearest interior node; the intermediate f* at wall nodes is set the
+ *     same way; interior nodes whose upwind stencil would leave the domain use
+ *     the central difference alone.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* D2Q9 lattice of Sec. 3 with xi = 1: velocity columns and weights, cs^2 = 1/3. */
+static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WQ[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double CS2 = 1.0 / 3.0;
+
+typedef struct {
+    int nx, ny;
+    int periodic_x, periodic_y;   /* 1 periodic, 0 walls at both ends */
+    const double *mx, *my;        /* d zeta/dx per column, d mu/dy per row (> 0) */
+    double tau, dt, A, beta;      /* relaxation time, time step, t* = tn + A dt, upwind weight */
+    int beta_is_central;          /* 1: literal Eq. 2.36 (beta weights the central part) */
+    int scheme;                   /* 1: T2S2-FDLBM1 (Eq. 2.23), 2: T2S2-FDLBM2 (Eq. 5.23) */
+    const double *force;          /* [2][ny][nx] body acceleration, or NULL */
+    double wall_u[4][2];          /* velocity of the W, E, S, N walls */
+    int nthreads;
+} oracle_cfg;
+
+#define IDX(c, x, y) ((size_t)(y) * (size_t)(c)->nx + (size_t)(x))
+#define POP(c, i) ((size_t)(i) * (size_t)(c)->nx * (size_t)(c)->ny)
+
+static int nthreads_of(const oracle_cfg *c) { return c->nthreads > 0 ? c->nthreads : 1; }
+
+/* Eq. 3.2: second-order equilibrium. */
+void oracle_feq(double rho, double ux, double uy, double *feq)
+{
+    double uu = ux * ux + uy * uy;
+    for (int i = 0; i < 9; ++i) {
+        double eu = EX[i] * ux + EY[i] * uy;
+        /* uu:(xi xi - cs^2 I) = (xi.u)^2 - cs^2 u.u */
+        feq[i] = WQ[i] * rho * (1.0 + eu / CS2 + (eu * eu - CS2 * uu) / (2.0 * CS2 * CS2));
+    }
+}
+
+/* Eq. 3.12: forcing term F_i = Fbar.(xi_i - u) f_i^eq / RT with RT = cs^2. */
+void oracle_force_term(const double *feq, double ux, double uy, double Fx, double Fy,
+                       double *F)
+{
+    for (int i = 0; i < 9; ++i)
+        F[i] = ((EX[i] - ux) * Fx + (EY[i] - uy) * Fy) * feq[i] / CS2;
+}
+
+static void force_at(const oracle_cfg *c, size_t n, double *Fx, double *Fy)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    *Fx = c->force ? c->force[n] : 0.0;
+    *Fy = c->force ? c->force[N + n] : 0.0;
+}
+
+/* Eq. 3.3 applied to a distribution whose first moment lacks `shift * rho * F`:
+ * rho = sum f_i, rho u = sum xi_i f_i + shift rho F.  shift = dt/2 for f~,
+ * h/2 for fbar (Eq. 2.31), 0 for the physical f. */
+static void moments_node(const oracle_cfg *c, const double *f, size_t n, double shift,
+                         double *rho, double *ux, double *uy)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    double r = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        double v = f[i * N + n];
+        r += v;
+        jx += EX[i] * v;
+        jy += EY[i] * v;
+    }
+    double Fx, Fy;
+    force_at(c, n, &Fx, &Fy);
+    jx += shift * r * Fx;
+    jy += shift * r * Fy;
+    *rho = r;
+    *ux = jx / r;
+    *uy = jy / r;
+}
+
+/* Eq. 3.3: density and velocity from f~. */
+void oracle_moments(const oracle_cfg *c, const double *f, double *rho, double *ux, double *uy)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    for (size_t n = 0; n < N; ++n)
+        moments_node(c, f, n, 0.5 * c->dt, &rho[n], &ux[n], &uy[n]);
+}
+
+/* Eq. 3.5 (coefficient read as rho0 w_i (2 tau + dt) / (2 cs^2), see the
+ * module header of the Python wrapper) or Eq. 3.2 alone when grad is NULL.
+ * grad = [dudx, dudy, dvdx, dvdy], each [ny][nx]. */
+void oracle_init(const oracle_cfg *c, const double *rho, const double *ux, const double *uy,
+                 const double *grad, double rho0, double *f)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    for (size_t n = 0; n < N; ++n) {
+        double feq[9];
+        oracle_feq(rho[n], ux[n], uy[n], feq);
+        for (int i = 0; i < 9; ++i) {
+            double v = feq[i];
+            if (grad) {
+                double xx = EX[i] * EX[i], xy = EX[i] * EY[i], yy = EY[i] * EY[i];
+                double ddot = xx * grad[n] + xy * (grad[N + n] + grad[2 * N + n]) +
+                              yy * grad[3 * N + n];
+                v -= rho0 * WQ[i] * (2.0 * c->tau + c->dt) / (2.0 * CS2) * ddot;
+            }
+            f[i * N + n] = v;
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Space discretisation, Eqs. 2.36-2.38, in the index coordinate k (unit step),
+ * scaled by the metric.  Returns d f / d chi_alpha for velocity sign `s`.
+ * ------------------------------------------------------------------------- */
+static int wrap(int k, int n)
+{
+    while (k < 0) k += n;
+    while (k >= n) k -= n;
+    return k;
+}
+
+static double sample(const oracle_cfg *c, const double *fld, int x, int y)
+{
+    if (c->periodic_x) x = wrap(x, c->nx);
+    if (c->periodic_y) y = wrap(y, c->ny);
+    return fld[IDX(c, x, y)];
+}
+
+/* Central difference, Eq. 2.37 (index space). */
+static double d_central(const oracle_cfg *c, const double *f, int x, int y, int ax)
+{
+    int dx = ax == 0, dy = ax == 1;
+    return (sample(c, f, x + dx, y + dy) - sample(c, f, x - dx, y - dy)) / 2.0;
+}
+
+/* Second-order upwind difference, Eq. 2.38 (index space), sign s of xi_alpha. */
+static double d_upwind(const oracle_cfg *c, const double *f, int x, int y, int ax, int s)
+{
+    int dx = ax == 0, dy = ax == 1;
+    if (s >= 0)
+        return (3.0 * sample(c, f, x, y) - 4.0 * sample(c, f, x - dx, y - dy) +
+                sample(c, f, x - 2 * dx, y - 2 * dy)) / 2.0;
+    return -(3.0 * sample(c, f, x, y) - 4.0 * sample(c, f, x + dx, y + dy) +
+             sample(c, f, x + 2 * dx, y + 2 * dy)) / 2.0;
+}
+
+/* Mixed difference, Eq. 2.36, with the metric: d f/d x_alpha at node (x, y). */
+static double d_mixed(const oracle_cfg *c, const double *f, int x, int y, int ax, int s)
+{
+    double m = ax == 0 ? c->mx[x] : c->my[y];
+    int k = ax == 0 ? x : y, n = ax == 0 ? c->nx : c->ny;
+    int per = ax == 0 ? c->periodic_x : c->periodic_y;
+    double dc = d_central(c, f, x, y, ax);
+    /* upwind stencil leaves a walled domain: central difference alone */
+    int upwind_ok = per || (s >= 0 ? k - 2 >= 0 : k + 2 <= n - 1);
+    if (!upwind_ok) return m * dc;
+    double du = d_upwind(c, f, x, y, ax, s);
+    double wu = c->beta_is_central ? 1.0 - c->beta : c->beta;
+    return m * ((1.0 - wu) * dc + wu * du);
+}
+
+/* Eq. 2.27: L(f_i) = -xi_i . grad f_i, evaluated at one node for population i. */
+static double advection(const oracle_cfg *c, const double *fi, int x, int y, int i)
+{
+    double L = 0.0;
+    if (EX[i]) L -= EX[i] * d_mixed(c, fi, x, y, 0, EX[i]);
+    if (EY[i]) L -= EY[i] * d_mixed(c, fi, x, y, 1, EY[i]);
+    return L;
+}
+
+static int is_wall(const oracle_cfg *c, int x, int y)
+{
+    return (!c->periodic_x && (x == 0 || x == c->nx - 1)) ||
+           (!c->periodic_y && (y == 0 || y == c->ny - 1));
+}
+
+/* Nearest interior node along the inward normal (diagonal at corners). */
+static void wall_partner(const oracle_cfg *c, int x, int y, int *px, int *py, double *uw)
+{
+    int jx = x, jy = y;
+    if (!c->periodic_x) { if (x == 0) jx = 1; else if (x == c->nx - 1) jx = c->nx - 2; }
+    if (!c->periodic_y) { if (y == 0) jy = 1; else if (y == c->ny - 1) jy = c->ny - 2; }
+    *px = jx;
+    *py = jy;
+    /* wall velocity: the W/E walls own the corners (a moving lid stops at the side walls) */
+    int side = -1;
+    if (!c->periodic_x && x == 0) side = 0;
+    else if (!c->periodic_x && x == c->nx - 1) side = 1;
+    else if (!c->periodic_y && y == 0) side = 2;
+    else if (!c->periodic_y && y == c->ny - 1) side = 3;
+    uw[0] = side >= 0 ? c->wall_u[side][0] : 0.0;
+    uw[1] = side >= 0 ? c->wall_u[side][1] : 0.0;
+}
+
+/* Eq. 3.10: non-equilibrium extrapolation onto every wall node of f.
+ * `shift` selects the first-moment convention of f (see moments_node). */
+static void apply_nee(const oracle_cfg *c, double *f, double shift)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    for (int y = 0; y < c->ny; ++y)
+        for (int x = 0; x < c->nx; ++x) {
+            if (!is_wall(c, x, y)) continue;
+            int jx, jy;
+            double uw[2];
+            wall_partner(c, x, y, &jx, &jy, uw);
+            size_t nb = IDX(c, x, y), nj = IDX(c, jx, jy);
+            double rj, uxj, uyj, feqj[9], feqb[9];
+            moments_node(c, f, nj, shift, &rj, &uxj, &uyj);
+            oracle_feq(rj, uxj, uyj, feqj);
+            oracle_feq(rj, uw[0], uw[1], feqb);
+            for (int i = 0; i < 9; ++i)
+                f[i * N + nb] = feqb[i] + (f[i * N + nj] - feqj[i]);
+        }
+}
+
+typedef struct {
+    double *rho, *ux, *uy, *feq, *F, *fphys, *fbar_plus, *fbar_star, *fstar, *ftil_plus, *L;
+} work_t;
+
+static int work_alloc(const oracle_cfg *c, work_t *w)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    memset(w, 0, sizeof(*w));
+    w->rho = malloc(N * sizeof(double));
+    w->ux = malloc(N * sizeof(double));
+    w->uy = malloc(N * sizeof(double));
+    double **big[] = {&w->feq, &w->F, &w->fphys, &w->fbar_plus, &w->fbar_star,
+                      &w->fstar, &w->ftil_plus, &w->L};
+    for (int k = 0; k < 8; ++k) *big[k] = malloc(9 * N * sizeof(double));
+    int ok = w->rho && w->ux && w->uy;
+    for (int k = 0; k < 8; ++k) ok = ok && *big[k];
+    return ok ? 0 : -1;
+}
+
+static void work_free(work_t *w)
+{
+    free(w->rho); free(w->ux); free(w->uy); free(w->feq); free(w->F); free(w->fphys);
+    free(w->fbar_plus); free(w->fbar_star); free(w->fstar); free(w->ftil_plus); free(w->L);
+}
+
+/* Node-local pass: rho, u (Eq. 3.3), f^eq (Eq. 3.2), F (Eq. 3.12) of a
+ * distribution g whose first moment lacks `shift rho F`. */
+static void macro_pass(const oracle_cfg *c, const double *g, double shift, work_t *w)
+{
+    size_t N = (size_t)c->nx * c->ny;
+#pragma omp parallel for num_threads(nthreads_of(c)) schedule(static)
+    for (long long n = 0; n < (long long)N; ++n) {
+        double fe[9], Fi[9], Fx, Fy;
+        moments_node(c, g, (size_t)n, shift, &w->rho[n], &w->ux[n], &w->uy[n]);
+        oracle_feq(w->rho[n], w->ux[n], w->uy[n], fe);
+        force_at(c, (size_t)n, &Fx, &Fy);
+        oracle_force_term(fe, w->ux[n], w->uy[n], Fx, Fy, Fi);
+        for (int i = 0; i < 9; ++i) {
+            w->feq[i * N + n] = fe[i];
+            w->F[i * N + n] = Fi[i];
+        }
+    }
+}
+
+/* Eq. 2.20: post-collision f~+ from f~, f^eq, F. */
+static void post_collision_pass(const oracle_cfg *c, const double *f, work_t *w)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    double tau = c->tau, dt = c->dt;
+#pragma omp parallel for num_threads(nthreads_of(c)) schedule(static)
+    for (long long k = 0; k < (long long)(9 * N); ++k)
+        w->ftil_plus[k] = ((2 * tau - dt) * f[k] + 2 * dt * w->feq[k] + 2 * tau * dt * w->F[k]) /
+                          (2 * tau + dt);
+}
+
+/* Inverse of Eq. 2.31 for the step s (Eq. 2.32): physical f from the
+ * half-variable fb = f - (s/2) Omega-bar. */
+static void physical_pass(const oracle_cfg *c, const double *fb, double s, work_t *w)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    double tau = c->tau;
+#pragma omp parallel for num_threads(nthreads_of(c)) schedule(static)
+    for (long long k = 0; k < (long long)(9 * N); ++k)
+        w->fphys[k] = (2 * tau * fb[k] + s * w->feq[k] + s * tau * w->F[k]) / (2 * tau + s);
+}
+
+/* out = f + (h/2) Omega-bar(f) = (1 - h/2tau) f + (h/2tau) f^eq + (h/2) F
+ * (Eq. 2.34, left-hand definition) for the physical f in w->fphys. */
+static void plus_half_pass(const oracle_cfg *c, double h, work_t *w, double *out)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    double tau = c->tau;
+#pragma omp parallel for num_threads(nthreads_of(c)) schedule(static)
+    for (long long k = 0; k < (long long)(9 * N); ++k)
+        out[k] = w->fphys[k] - h / (2 * tau) * (w->fphys[k] - w->feq[k]) + 0.5 * h * w->F[k];
+}
+
+/* Characteristic estimate, Eqs. 2.33 and 2.35: out = in - h xi_i . grad in
+ * at interior nodes (wall nodes are filled later). */
+static void characteristic_pass(const oracle_cfg *c, const double *in, double h, double *out)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    for (int i = 0; i < 9; ++i) {
+#pragma omp parallel for num_threads(nthreads_of(c)) schedule(static)
+        for (int y = 0; y < c->ny; ++y)
+            for (int x = 0; x < c->nx; ++x) {
+                size_t n = IDX(c, x, y);
+                if (is_wall(c, x, y)) { out[i * N + n] = in[i * N + n]; continue; }
+                /* -h xi.grad = +h L (Eq. 2.27) */
+                out[i * N + n] = in[i * N + n] + h * advection(c, in + i * N, x, y, i);
+            }
+    }
+}
+
+/* Eq. 2.27 with Eq. 2.36 at interior nodes. */
+static void advection_pass(const oracle_cfg *c, const double *fin, double *L)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    for (int i = 0; i < 9; ++i) {
+#pragma omp parallel for num_threads(nthreads_of(c)) schedule(static)
+        for (int y = 0; y < c->ny; ++y)
+            for (int x = 0; x < c->nx; ++x) {
+                size_t n = IDX(c, x, y);
+                L[i * N + n] = is_wall(c, x, y) ? 0.0 : advection(c, fin + i * N, x, y, i);
+            }
+    }
+}
+
+/* One T2S2-FDLBM1 step (Sec. 2D Steps 1-3; A = 0 gives T1S2, Remark I). */
+static void step_scheme1(const oracle_cfg *c, double *f, work_t *w)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    double dt = c->dt, tau = c->tau, h = c->A * dt;
+    /* Step 1a: f~ -> (rho, u, f^eq, F) -> physical f -> fbar^{+,h} (Eqs. 3.3, 2.19, 2.34) */
+    macro_pass(c, f, 0.5 * dt, w);
+    physical_pass(c, f, dt, w);
+    plus_half_pass(c, h, w, w->fbar_plus);
+    /* Step 2 (node-local, uses the same f^eq and F): f~+ (Eq. 2.20) */
+    post_collision_pass(c, f, w);
+    /* Step 1b: fbar(t*) by the characteristic estimate (Eqs. 2.33, 2.35) */
+    characteristic_pass(c, w->fbar_plus, h, w->fbar_star);
+    /* Step 1c: moments of fbar*, then f* (Eq. 2.52 with the force term of Eq. 2.32) */
+    macro_pass(c, w->fbar_star, 0.5 * h, w);
+    physical_pass(c, w->fbar_star, h, w);
+    memcpy(w->fstar, w->fphys, 9 * N * sizeof(double));
+    if (!c->periodic_x || !c->periodic_y) apply_nee(c, w->fstar, 0.0);
+    /* Step 1d: L(f*) (Eqs. 2.27, 2.36) */
+    advection_pass(c, w->fstar, w->L);
+    /* Step 3: f~^{n+1} = f~+ + dt L(f*) (Eq. 2.23), then walls (Eq. 3.10) */
+    for (size_t k = 0; k < 9 * N; ++k) f[k] = w->ftil_plus[k] + dt * w->L[k];
+    if (!c->periodic_x || !c->periodic_y) apply_nee(c, f, 0.5 * dt);
+    (void)tau;
+}
+
+/* One T2S2-FDLBM2 step (Sec. 2D, second sequence; Eq. 5.23, h = dt). */
+static void step_scheme2(const oracle_cfg *c, double *f, work_t *w)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    double dt = c->dt;
+    /* Step 1: f~ -> f^n (Eq. 2.52 with h = dt) -> L(f^n) */
+    macro_pass(c, f, 0.5 * dt, w);
+    physical_pass(c, f, dt, w);
+    memcpy(w->fstar, w->fphys, 9 * N * sizeof(double));
+    if (!c->periodic_x || !c->periodic_y) apply_nee(c, w->fstar, 0.0);
+    advection_pass(c, w->fstar, w->L);
+    /* Step 2: f~ -> f~+ (Eq. 2.20) -> fbar(t_{n+1}) (Eqs. 2.33, 2.35 with h = dt,
+     * fbar^{+,h} = f~+) -> f^{n+1} (Eq. 2.52) -> L(f^{n+1}) */
+    post_collision_pass(c, f, w);
+    characteristic_pass(c, w->ftil_plus, dt, w->fbar_star);
+    macro_pass(c, w->fbar_star, 0.5 * dt, w);
+    physical_pass(c, w->fbar_star, dt, w);
+    if (!c->periodic_x || !c->periodic_y) apply_nee(c, w->fphys, 0.0);
+    /* w->fbar_plus is free here: reuse it for L(f^{n+1}) */
+    advection_pass(c, w->fphys, w->fbar_plus);
+    /* Step 3: Eq. 5.23 */
+    for (size_t k = 0; k < 9 * N; ++k)
+        f[k] = w->ftil_plus[k] + 0.5 * dt * (w->L[k] + w->fbar_plus[k]);
+    if (!c->periodic_x || !c->periodic_y) apply_nee(c, f, 0.5 * dt);
+}
+
+/* Advance f~ (layout [9][ny][nx]) by nsteps.  Returns 0, or -1 on allocation failure. */
+int oracle_step(const oracle_cfg *c, double *f, int nsteps)
+{
+    work_t w;
+    if (work_alloc(c, &w)) { work_free(&w); return -1; }
+    for (int s = 0; s < nsteps; ++s) {
+        if (c->scheme == 2) step_scheme2(c, f, &w);
+        else step_scheme1(c, f, &w);
+    }
+    work_free(&w);
+    return 0;
+}
+
+/* T1S2-FDLBM of Guo et al. written directly from Eqs. 2.18-2.20, independent of
+ * step_scheme1: f~^{n+1} = f~+ + dt L(f^n), with f^n recovered from f~ by
+ * inverting Eq. 2.19. */
+int oracle_step_t1s2(const oracle_cfg *c, double *f, int nsteps)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    double dt = c->dt, tau = c->tau;
+    double *fn = malloc(9 * N * sizeof(double));
+    double *fp = malloc(9 * N * sizeof(double));
+    double *rho = malloc(N * sizeof(double)), *ux = malloc(N * sizeof(double)),
+           *uy = malloc(N * sizeof(double));
+    if (!fn || !fp || !rho || !ux || !uy) {
+        free(fn); free(fp); free(rho); free(ux); free(uy);
+        return -1;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        for (size_t n = 0; n < N; ++n) {
+            double fe[9], Fi[9], Fx, Fy;
+            moments_node(c, f, n, 0.5 * dt, &rho[n], &ux[n], &uy[n]);
+            oracle_feq(rho[n], ux[n], uy[n], fe);
+            force_at(c, n, &Fx, &Fy);
+            oracle_force_term(fe, ux[n], uy[n], Fx, Fy, Fi);
+            for (int i = 0; i < 9; ++i) {
+                size_t k = i * N + n;
+                /* f~ = f - (dt/2)[-(f - feq)/tau + F]  =>  f = (f~ + dt/(2tau) feq + dt/2 F)/(1 + dt/(2tau)) */
+                fn[k] = (f[k] + dt / (2 * tau) * fe[i] + 0.5 * dt * Fi[i]) / (1 + dt / (2 * tau));
+                /* f~+ = f + (dt/2) Omega-bar(f) */
+                fp[k] = fn[k] - dt / (2 * tau) * (fn[k] - fe[i]) + 0.5 * dt * Fi[i];
+            }
+        }
+        if (!c->periodic_x || !c->periodic_y) apply_nee(c, fn, 0.0);
+        for (int i = 0; i < 9; ++i)
+            for (int y = 0; y < c->ny; ++y)
+                for (int x = 0; x < c->nx; ++x) {
+                    size_t k = i * N + IDX(c, x, y);
+                    f[k] = fp[k] + (is_wall(c, x, y) ? 0.0 : dt * advection(c, fn + i * N, x, y, i));
+                }
+        if (!c->periodic_x || !c->periodic_y) apply_nee(c, f, 0.5 * dt);
+    }
+    free(fn); free(fp); free(rho); free(ux); free(uy);
+    return 0;
+}
+
+/* Stand-alone difference operators for the tests of Eqs. 2.36-2.38:
+ * out[y][x] = d fld / d x_alpha (with metric) at interior nodes, for sign s. */
+void oracle_derivative(const oracle_cfg *c, const double *fld, int axis, int s, double *out)
+{
+    for (int y = 0; y < c->ny; ++y)
+        for (int x = 0; x < c->nx; ++x)
+            out[IDX(c, x, y)] = is_wall(c, x, y) ? 0.0 : d_mixed(c, fld, x, y, axis, s);
+}
+
+/* The intermediate quantities of one T2S2 step for inspection by the tests:
+ * fbar^{+,h}, fbar*, f*, f~+ and L(f*) (each [9][ny][nx]). */
+int oracle_stages(const oracle_cfg *c, const double *f, double *fbar_plus, double *fbar_star,
+                  double *fstar, double *ftil_plus, double *L)
+{
+    size_t N = (size_t)c->nx * c->ny;
+    work_t w;
+    double *tmp = malloc(9 * N * sizeof(double));
+    if (!tmp || work_alloc(c, &w)) { free(tmp); work_free(&w); return -1; }
+    memcpy(tmp, f, 9 * N * sizeof(double));
+    double h = c->A * c->dt;
+    macro_pass(c, tmp, 0.5 * c->dt, &w);
+    physical_pass(c, tmp, c->dt, &w);
+    plus_half_pass(c, h, &w, w.fbar_plus);
+    post_collision_pass(c, tmp, &w);
+    characteristic_pass(c, w.fbar_plus, h, w.fbar_star);
+    macro_pass(c, w.fbar_star, 0.5 * h, &w);
+    physical_pass(c, w.fbar_star, h, &w);
+    memcpy(w.fstar, w.fphys, 9 * N * sizeof(double));
+    if (!c->periodic_x || !c->periodic_y) apply_nee(c, w.fstar, 0.0);
+    advection_pass(c, w.fstar, w.L);
+    memcpy(fbar_plus, w.fbar_plus, 9 * N * sizeof(double));
+    memcpy(fbar_star, w.fbar_star, 9 * N * sizeof(double));
+    memcpy(fstar, w.fstar, 9 * N * sizeof(double));
+    memcpy(ftil_plus, w.ftil_plus, 9 * N * sizeof(double));
+    memcpy(L, w.L, 9 * N * sizeof(double));
+    free(tmp);
+    work_free(&w);
+    return 0;
+}
