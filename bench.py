@@ -1,0 +1,352 @@
+"""Throughput benchmark of the T2S2-FDLBM D2Q9 step on GB300.
+
+Workload: Taylor-vortex throughput case on a 4096 x 4096 periodic uniform grid
+of [0, 2pi)^2, random-phase sinusoidal initial velocity of amplitude 0.01
+(seeded), nu = 0.01, CFL = 0.5, blend 0.1, FP32-deviation storage.  One bench
+step = one time step of the whole grid (one launch of the fused kernel).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is the whole-job cell-update rate (MLUPS)
+measured with CUDA events on the stream the kernels are launched on, with the
+state already resident in HBM.  ``e2e`` is the same metric through the C ABI
+with pinned host buffers: initial fields in, K steps, mass/residual and
+moments out, all inside the timed region.  With N > 1 (torchrun) every rank
+runs an independent replica (the step has no exchange across replicas).
+``--impl reference`` times the CPU FP64 oracle on a bounded sample of the same
+workload (a 512 x 512 grid) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "D2Q9 T2S2-FDLBM MLUPS & % HBM roofline, FP32 vs FP64; adjoint/forward cost"
+N_GRID = 4096
+NU, CFL, BLEND, U0, SEED = 0.01, 0.5, 0.1, 0.01, 2026
+BYTES_PER_CELL = {"fp32": 72, "fp64": 144}   # 9 populations read once + written once
+SAMPLE_N = 512                                # oracle sample grid
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_GRID)
+    p.add_argument("--fp64-steps", type=int, default=100)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload_fields(n):
+    import inputs as I
+    import numpy as np
+    rng = np.random.default_rng(SEED)
+    phase = tuple(float(v) for v in rng.uniform(0.0, 2 * math.pi, size=2))
+    ax = I.periodic_axis(n, 0.0, 2 * math.pi)
+    f = I.taylor_green(ax, ax, u0=U0, phase=phase)
+    return ax, f, phase
+
+
+def config(n, precision, steps):
+    return {"workload": f"taylor-green throughput {n}x{n} periodic uniform, {precision} "
+                        f"(random-phase u0={U0}, nu={NU}, CFL={CFL}, blend={BLEND})",
+            "nx": n, "ny": n, "precision": precision, "bench_steps": steps,
+            "l2": "inputs larger than L2 (state 2 x %.0f MB)" % (9 * n * n * (4 if precision == 'fp32' else 8) / 1e6)}
+
+
+# ----------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            cmd = ["nvidia-smi", f"--id={self.uuid}", f"--query-gpu={self.Q}",
+                   "--format=csv,noheader,nounits", "-lms", "200"]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------- helpers
+def kernel_traffic(precision):
+    """Per-launch DRAM bytes of the fused kernel from the committed ncu summary,
+    valid only while the kernel source is unchanged."""
+    f = ROOT / "profiles" / f"fused_{precision}_traffic.json"
+    if not f.exists():
+        return None
+    d = json.loads(f.read_text())
+    src = (ROOT / "paper_1911_12913_gb300" / "csrc" / "step_fused.cu").read_bytes()
+    if d.get("kernel_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return d.get("dram_bytes_per_launch_full")
+
+
+def peaks():
+    try:
+        return json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_oracle_rate(n, target_s=12.0, nthreads=None, steps=None):
+    """Time the FP64 oracle (as it stands) on an n x n sample of the workload."""
+    import oracle as O
+    ax, f, phase = workload_fields(n)
+    nthreads = nthreads or (os.cpu_count() or 1)
+    o = O.Oracle(ax, ax, nu=NU, dt=O.time_step(CFL, ax, ax), beta=BLEND, nthreads=nthreads)
+    o.init_fields(f["rho"], f["ux"], f["uy"], [f["dudx"], f["dudy"], f["dvdx"], f["dvdy"]])
+    if steps is None:
+        t0 = time.perf_counter()
+        o.step(2)
+        per = (time.perf_counter() - t0) / 2
+        steps = max(2, int(target_s / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t0
+    return n * n * steps / el / 1e6, steps, el, nthreads
+
+
+# ----------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    ax, f, phase = workload_fields(SAMPLE_N)
+    nthreads = os.cpu_count() or 1
+    o = O.Oracle(ax, ax, nu=NU, dt=O.time_step(CFL, ax, ax), beta=BLEND, nthreads=nthreads)
+    o.init_fields(f["rho"], f["ux"], f["uy"], [f["dudx"], f["dudy"], f["dvdx"], f["dvdy"]])
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    el = time.perf_counter() - t0
+    mlups = SAMPLE_N * SAMPLE_N * args.steps / el / 1e6
+    sample = (f"{SAMPLE_N}x{SAMPLE_N} sample of the {N_GRID}x{N_GRID} workload (same nu, CFL, "
+              f"blend, phase), FP64 oracle, {args.steps} steps")
+    out = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config(N_GRID, "fp32", args.steps),
+           "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": nthreads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_1911_12913_gb300.solver import FDLBM
+
+    n = args.n
+    N = n * n
+    ax, f, phase = workload_fields(n)
+    grad = [f["dudx"], f["dudy"], f["dvdx"], f["dvdy"]]
+    stream = torch.cuda.current_stream(dev)
+
+    # ---------------- device-resident timing (FP32 deviation, the headline)
+    s = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream)
+    s.init_fields(f["rho"], f["ux"], f["uy"], grad)
+    m0, _ = s.reduce()
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(uuid) as clk:
+        ev0.record(stream)
+        s.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms)
+    m1, _ = s.reduce()
+    mass_drift = abs(m1 - m0) / abs(m0)
+    launches = args.steps * s.kernels_per_step
+    per_launch_s = ms / 1e3 / args.steps
+    value = world * N * args.steps / (ms_max / 1e3) / 1e6
+
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    peak_note = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    achieved = BYTES_PER_CELL["fp32"] * N / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": kernel_traffic("fp32"),
+                "peak_source": peak_note + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+                "bytes_per_cell": BYTES_PER_CELL["fp32"], "kernel": "k_step_fused<float>"}
+    del s
+    torch.cuda.empty_cache()
+
+    # ---------------- FP64 beside it (same workload, shorter run)
+    fp64 = None
+    if args.fp64_steps > 0:
+        s64 = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp64", stream=stream)
+        s64.init_fields(f["rho"], f["ux"], f["uy"], grad)
+        s64.step(3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.step(args.fp64_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        t64 = ms64 / 1e3 / args.fp64_steps
+        fp64 = {"value": N / t64 / 1e6, "unit": "MLUPS", "ms_per_step": ms64 / args.fp64_steps,
+                "steps": args.fp64_steps,
+                "hbm_achieved_gbs": BYTES_PER_CELL["fp64"] * N / t64 / 1e9,
+                "hbm_frac": BYTES_PER_CELL["fp64"] * N / t64 / 1e9 / hbm}
+        del s64
+        torch.cuda.empty_cache()
+
+    # ---------------- end to end through the C ABI with pinned host buffers
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in f.items()}
+    out_host = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(3)]
+    s = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream)
+    L, h = s._L, s._h
+    gpin = torch.stack([pin["dudx"], pin["dudy"], pin["dvdx"], pin["dvdy"]]).pin_memory()
+    import ctypes
+    mass, resid = ctypes.c_double(), ctypes.c_double()
+
+    def e2e_job(k):
+        rc = L.fdlbm_init_fields(h, pin["rho"].data_ptr(), pin["ux"].data_ptr(),
+                                 pin["uy"].data_ptr(), gpin.data_ptr(), 0)
+        rc |= L.fdlbm_step(h, k)
+        rc |= L.fdlbm_reduce(h, ctypes.byref(mass), ctypes.byref(resid))
+        rc |= L.fdlbm_moments(h, *(o.data_ptr() for o in out_host), 0)
+        assert rc == 0, L.fdlbm_last_error(h)
+
+    e2e_job(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_job(args.steps)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_s = max_over_ranks(e2e_s)
+    e2e = {"value": world * N * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 7 * N * 8 / args.steps,
+           "d2h_bytes_per_step": (3 * N * 8 + 3 * 8) / args.steps,
+           "job": "init_fields(host rho,u,grad u) + K steps + reduce + moments(host), per rank"}
+    del s
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            rate, st, el, th = cpu_oracle_rate(SAMPLE_N)
+            cpu = {"value": rate, "unit": "MLUPS", "cores": th, "kind": "oracle",
+                   "sample": f"{SAMPLE_N}x{SAMPLE_N} sample of the workload, FP64 oracle, "
+                             f"{st} steps in {el:.1f} s"}
+        out = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32", "data": "synthetic",
+               "config": config(n, "fp32", args.steps), "clocks": clk.summary(),
+               "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+               "cpu_baseline": cpu, "fp64": fp64, "mass_drift_rel": mass_drift,
+               "parallelism": "replicas" if world > 1 else "single"}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

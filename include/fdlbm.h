@@ -1,0 +1,163 @@
+/*
+ * fdlbm.h - C ABI of the GB300 library for the D2Q9 T2S2-FDLBM time step
+ * (Chen, Chai, Wang, Shi, "A finite-difference lattice Boltzmann model with
+ * second-order accuracy of time and space for incompressible flow",
+ * arXiv 1911.12913).
+ *
+ * One handle = one grid, one parameter set and the distribution state f~ of
+ * every node, resident in device memory.  All compute runs in CUDA kernels on
+ * the handle's stream; the host only marshals arguments.
+ *
+ * Conventions for every entry point:
+ *  - Return an fdlbm_status; no C++ exception crosses this boundary.  The text
+ *    of the last failure of a handle is available from fdlbm_last_error().
+ *  - Arrays are row-major [ny][nx] (x fastest); distributions are [9][ny][nx]
+ *    with the population order of Sec. 3 of the paper:
+ *      i :  0  1  2  3  4  5  6  7  8
+ *      xi: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+ *  - Arguments tagged `where` are host pointers (FDLBM_MEM_HOST) or device
+ *    pointers (FDLBM_MEM_DEVICE) of FP64 values.  They are borrowed for the call
+ *    only: host arrays are copied before the call returns, device arrays are
+ *    read by work enqueued on the handle's stream (keep them alive until that
+ *    work completes).
+ *  - fdlbm_step() is asynchronous.  Calls that return host data (get_state and
+ *    moments with FDLBM_MEM_HOST, reduce) synchronise the stream.
+ */
+#ifndef FDLBM_H
+#define FDLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDLBM_ABI_VERSION 1
+
+typedef struct fdlbm_ctx *fdlbm_t;
+
+typedef enum {
+    FDLBM_OK = 0,
+    FDLBM_EINVAL = -1,        /* invalid argument (sizes, metrics <= 0, NULL, ...) */
+    FDLBM_ENOMEM = -2,        /* workspace too small, or device allocation failed */
+    FDLBM_ECUDA = -3,         /* CUDA runtime error; see fdlbm_last_error() */
+    FDLBM_ENONFINITE = -4,    /* a reduction met NaN or Inf (the run diverged) */
+    FDLBM_EUNSUPPORTED = -5   /* option combination not available */
+} fdlbm_status;
+
+enum { FDLBM_PERIODIC = 0, FDLBM_WALL = 1 };            /* boundary kind of an axis */
+enum { FDLBM_FP64 = 0, FDLBM_FP32_DEV = 1 };            /* storage / arithmetic precision */
+enum { FDLBM_PATH_AUTO = 0, FDLBM_PATH_FUSED = 1, FDLBM_PATH_STAGED = 2 };
+enum { FDLBM_MEM_HOST = 0, FDLBM_MEM_DEVICE = 1 };
+enum { FDLBM_WALL_W = 0, FDLBM_WALL_E = 1, FDLBM_WALL_S = 2, FDLBM_WALL_N = 3 };
+
+/* Tensor-product grid (Sec. 3, Eqs. 3.9 and 3.11).  A periodic axis stores its
+ * n unique nodes (node n is node 0 shifted by the period); a walled axis stores
+ * both wall nodes.  Coordinates are host arrays, strictly increasing. */
+typedef struct {
+    int nx, ny;
+    const double *x, *y;      /* host, length nx / ny */
+    double lx, ly;            /* period of a periodic axis; 0: n * (x[1] - x[0]) */
+    int bc_x, bc_y;           /* FDLBM_PERIODIC or FDLBM_WALL */
+    double wall_u[4][2];      /* (u, v) of the W, E, S, N walls (Eq. 3.10 boundary data) */
+} fdlbm_grid;
+
+/* 1-D grid metrics: d(zeta)/dx at every column and d(mu)/dy at every row, where
+ * zeta, mu are the node indices (unit spacing).  d/dx = (dzeta/dx) d/dzeta is
+ * applied to the differences of Eqs. 2.36-2.38.  Host arrays, every entry > 0.
+ * NULL for an axis means uniform spacing: 1 / (x[1] - x[0]). */
+typedef struct {
+    const double *dzeta_dx;   /* length nx or NULL */
+    const double *dmu_dy;     /* length ny or NULL */
+} fdlbm_metrics;
+
+typedef struct {
+    double A;                 /* t* = t_n + A dt (Eq. 2.9): 0.5 = T2S2-FDLBM1 (Eq. 2.21), 0 = T1S2 (Eq. 2.16) */
+    double rho0;              /* reference density; FP32 storage keeps f~_i - w_i rho0 */
+    int precision;            /* FDLBM_FP64 or FDLBM_FP32_DEV */
+    int has_force;            /* 1: reserve a body-acceleration field (fdlbm_set_force), Eq. 3.12 */
+    int path;                 /* FDLBM_PATH_AUTO: fused kernel for periodic grids, staged otherwise */
+    int rows_per_cta;         /* fused kernel tile height; 0 = automatic */
+    void *stream;             /* cudaStream_t used for all work; NULL = default stream */
+    void *workspace;          /* caller-owned device memory of fdlbm_workspace_bytes() bytes,
+                                 256-byte aligned; NULL = the library allocates its own */
+    size_t workspace_bytes;
+} fdlbm_opts;
+
+/* Fill *o with the defaults: A = 0.5, rho0 = 1, FP64, no force, automatic path,
+ * default stream, library-owned workspace. */
+void fdlbm_default_opts(fdlbm_opts *o);
+
+/* Eq. 3.1: dt = CFL * dx_min / xi with xi = 1 (lattice speed) and dx_min the
+ * smallest node spacing over both axes.  Host only.  Returns a negative value
+ * for an invalid grid or cfl <= 0. */
+double fdlbm_time_step(const fdlbm_grid *grid, double cfl);
+
+/* Device bytes a handle needs for this grid and options (0 if invalid).  Host only. */
+size_t fdlbm_workspace_bytes(const fdlbm_grid *grid, const fdlbm_opts *opts);
+
+/* Create a handle.  nu: kinematic viscosity (tau = nu / cs^2, cs^2 = 1/3);
+ * cfl: Eq. 3.1; blend: weight beta of the second-order upwind difference in the
+ * mixed difference, D_m = (1 - beta) D_central + beta D_upwind (Eq. 2.36 with the
+ * blend read as the upwind weight; see Eq. 4.8).  opts may be NULL (defaults).
+ * The state is zero (f~ = w_i rho0, fluid at rest) until initialised.
+ * Errors: EINVAL (sizes < 3, non-increasing coordinates, metric <= 0, nu <= 0,
+ * cfl <= 0, blend outside [0, 1], A outside [0, 1]), ENOMEM (workspace too
+ * small or cudaMalloc failed), ECUDA. */
+fdlbm_status fdlbm_create(const fdlbm_grid *grid, const fdlbm_metrics *metrics, double nu,
+                          double cfl, double blend, const fdlbm_opts *opts, fdlbm_t *out);
+
+/* Release the handle and any memory the library allocated.  NULL-safe. */
+void fdlbm_destroy(fdlbm_t h);
+
+/* Initialise f~ from macroscopic fields: Eq. 3.2 (f~ = f^eq(rho, u)), or with
+ * grad != NULL the non-equilibrium start of Eq. 3.5,
+ *   f~_i = f_i^eq - rho0 w_i (2 tau + dt) / (2 cs^2) xi_i xi_i : grad u,
+ * grad = 4 consecutive [ny][nx] fields du/dx, du/dy, dv/dx, dv/dy.
+ * rho, ux, uy: [ny][nx] FP64 at `where`. */
+fdlbm_status fdlbm_init_fields(fdlbm_t h, const double *rho, const double *ux, const double *uy,
+                               const double *grad, int where);
+
+/* Copy f~ ([9][ny][nx] FP64 at `where`) into / out of the handle. */
+fdlbm_status fdlbm_set_state(fdlbm_t h, const double *f, int where);
+fdlbm_status fdlbm_get_state(fdlbm_t h, double *f, int where);
+
+/* Body acceleration Fbar ([2][ny][nx] FP64 at `where`: x then y component),
+ * used by Eqs. 3.3 and 3.12.  Needs opts.has_force. */
+fdlbm_status fdlbm_set_force(fdlbm_t h, const double *force, int where);
+
+/* Advance n >= 0 time steps of the scheme (Sec. 2D, Steps 1-3; Eq. 2.23), with
+ * the non-equilibrium extrapolation of Eq. 3.10 on walled sides.  Enqueued on
+ * the stream; returns ECUDA if a launch fails. */
+fdlbm_status fdlbm_step(fdlbm_t h, int n);
+
+/* Density and velocity of Eq. 3.3 into [ny][nx] FP64 arrays at `where`. */
+fdlbm_status fdlbm_moments(fdlbm_t h, double *rho, double *ux, double *uy, int where);
+
+/* FP64 reductions (warp shuffles, fixed order): *mass = sum rho / (m_x m_y) over all
+ * nodes (the Jacobian-weighted mass, exactly conserved on periodic grids), and
+ * *resid = the successive-state residual of the cavity section,
+ * sqrt(sum |u - u_prev|^2 / sum |u|^2), against the velocity of the previous
+ * fdlbm_reduce call (-1 on the first call).  Synchronises the stream.  Returns
+ * ENONFINITE if either value is NaN/Inf.  Either pointer may be NULL. */
+fdlbm_status fdlbm_reduce(fdlbm_t h, double *mass, double *resid);
+
+/* Bind the handle to another stream (cudaStream_t). */
+fdlbm_status fdlbm_set_stream(fdlbm_t h, void *stream);
+
+/* Wait for the handle's stream; reports asynchronous CUDA errors as ECUDA. */
+fdlbm_status fdlbm_sync(fdlbm_t h);
+
+double fdlbm_dt(fdlbm_t h);              /* the dt of Eq. 3.1 used by the handle */
+double fdlbm_tau(fdlbm_t h);             /* nu / cs^2 */
+long long fdlbm_steps_done(fdlbm_t h);   /* steps enqueued since creation */
+int fdlbm_path(fdlbm_t h);               /* FDLBM_PATH_FUSED or FDLBM_PATH_STAGED */
+int fdlbm_kernels_per_step(fdlbm_t h);   /* kernel launches fdlbm_step makes per step */
+const char *fdlbm_last_error(fdlbm_t h); /* never NULL */
+const char *fdlbm_status_string(fdlbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDLBM_H */

@@ -1,0 +1,535 @@
+// C ABI of the T2S2-FDLBM library (declared in include/fdlbm.h): argument
+// checks, workspace layout, host<->device staging and kernel dispatch.  No
+// arithmetic of the method runs here; every step runs in the kernels of
+// step_fused.cu, step_staged.cu and fields.cu.
+#include <algorithm>
+#include <cstdint>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace fdlbm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kStagingBytes = size_t(64) << 20;  // host<->device staging chunk
+constexpr int kRedBlocks = 152 * 4;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+fdlbm_status fail(fdlbm_ctx *h, fdlbm_status s, const char *what)
+{
+    if (h) h->err = what;
+    return s;
+}
+
+fdlbm_status cuda_fail(fdlbm_ctx *h, cudaError_t e, const char *where)
+{
+    if (h) {
+        h->err = std::string(where) + ": " + cudaGetErrorString(e);
+    }
+    return FDLBM_ECUDA;
+}
+
+bool valid_axis(const double *c, int n)
+{
+    if (!c || n < 3) return false;
+    for (int i = 1; i < n; ++i)
+        if (!(c[i] > c[i - 1]) || !std::isfinite(c[i])) return false;
+    return std::isfinite(c[0]);
+}
+
+double period(const double *c, int n, double l)
+{
+    return l > 0 ? l : n * (c[1] - c[0]);
+}
+
+double min_spacing(const double *c, int n, bool periodic, double l)
+{
+    double m = INFINITY;
+    for (int i = 1; i < n; ++i) m = std::min(m, c[i] - c[i - 1]);
+    if (periodic) m = std::min(m, c[0] + period(c, n, l) - c[n - 1]);
+    return m;
+}
+
+bool grid_ok(const fdlbm_grid *g)
+{
+    if (!g) return false;
+    if (g->bc_x != FDLBM_PERIODIC && g->bc_x != FDLBM_WALL) return false;
+    if (g->bc_y != FDLBM_PERIODIC && g->bc_y != FDLBM_WALL) return false;
+    if (!valid_axis(g->x, g->nx) || !valid_axis(g->y, g->ny)) return false;
+    if (g->bc_x == FDLBM_PERIODIC && !(g->x[0] + period(g->x, g->nx, g->lx) > g->x[g->nx - 1]))
+        return false;
+    if (g->bc_y == FDLBM_PERIODIC && !(g->y[0] + period(g->y, g->ny, g->ly) > g->y[g->ny - 1]))
+        return false;
+    return true;
+}
+
+int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+
+bool fused_ok(const fdlbm_grid *g)
+{
+    return g->bc_x == FDLBM_PERIODIC && g->bc_y == FDLBM_PERIODIC && g->nx >= 4 && g->ny >= 4;
+}
+
+int choose_path(const fdlbm_grid *g, const fdlbm_opts *o)
+{
+    if (o->path == FDLBM_PATH_STAGED) return FDLBM_PATH_STAGED;
+    if (o->path == FDLBM_PATH_FUSED) return fused_ok(g) ? FDLBM_PATH_FUSED : -1;
+    return fused_ok(g) ? FDLBM_PATH_FUSED : FDLBM_PATH_STAGED;
+}
+
+// Rows per CTA of the fused kernel: enough CTAs for several waves on 152 SMs.
+int choose_rows(int nx, int ny)
+{
+    const int strips = (nx + 119) / 120;
+    const int target = 152 * 3 * 4;
+    int rows = (int)((long long)ny * strips / target);
+    rows = std::max(16, std::min(128, rows / 8 * 8));
+    return std::min(rows, ny);
+}
+
+template <class R>
+StepArgs<R> step_args(fdlbm_ctx *h)
+{
+    StepArgs<R> a{};
+    a.gin = reinterpret_cast<const R *>(h->ws + h->lay.state[h->cur]);
+    a.gout = reinterpret_cast<R *>(h->ws + h->lay.state[1 - h->cur]);
+    a.mx = reinterpret_cast<const R *>(h->ws + h->lay.mx);
+    a.my = reinterpret_cast<const R *>(h->ws + h->lay.my);
+    a.force = h->has_force ? reinterpret_cast<const R *>(h->ws + h->lay.force) : nullptr;
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    a.bc_x = h->bc_x;
+    a.bc_y = h->bc_y;
+    for (int s = 0; s < 4; ++s)
+        for (int k = 0; k < 2; ++k) a.wall_u[s][k] = R(h->wall_u[s][k]);
+    a.c = make_coeffs<R>(h->tau, h->dt, h->A, h->rho0);
+    a.st = make_stencil<R>(h->beta);
+    a.stc = make_stencil<R>(0.0);
+    a.rows = h->rows;
+    if (h->path == FDLBM_PATH_STAGED) {
+        a.P = reinterpret_cast<R *>(h->ws + h->lay.P);
+        a.Q = reinterpret_cast<R *>(h->ws + h->lay.Q);
+        a.S = reinterpret_cast<R *>(h->ws + h->lay.S);
+    }
+    return a;
+}
+
+// Copy `nfields` host or device fields ([ny][nx] FP64 each) through the staging
+// area in row chunks and hand each chunk to `kernel(ptr, row0, nrows, fstride)`.
+template <class K>
+fdlbm_status staged_in(fdlbm_ctx *h, const double *const *fields, int nfields, int where,
+                       K kernel, const char *what)
+{
+    const size_t row_bytes = (size_t)h->nx * sizeof(double);
+    if (where == FDLBM_MEM_DEVICE) {
+        // device fields: consecutive pointers are expected for multi-field args
+        cudaError_t e = kernel(fields, h->ny, (size_t)h->nx * h->ny, 0);
+        return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, what);
+    }
+    double *stage = reinterpret_cast<double *>(h->ws + h->lay.staging);
+    const int rows = (int)std::max<size_t>(1, h->lay.staging_elems / ((size_t)nfields * h->nx));
+    for (int r0 = 0; r0 < h->ny; r0 += rows) {
+        const int nr = std::min(rows, h->ny - r0);
+        const size_t fstride = (size_t)nr * h->nx;
+        std::vector<const double *> ptrs(nfields);
+        for (int k = 0; k < nfields; ++k) {
+            if (!fields[k]) {
+                ptrs[k] = nullptr;
+                continue;
+            }
+            cudaError_t e = cudaMemcpyAsync(stage + k * fstride, fields[k] + (size_t)r0 * h->nx,
+                                            nr * row_bytes, cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, what);
+            ptrs[k] = stage + k * fstride;
+        }
+        cudaError_t e = kernel(ptrs.data(), nr, fstride, r0);
+        if (e != cudaSuccess) return cuda_fail(h, e, what);
+        // the staging area is reused by the next chunk
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, what);
+    }
+    return FDLBM_OK;
+}
+
+}  // namespace
+
+namespace fdlbm {
+
+size_t real_size(int precision) { return precision == FDLBM_FP32_DEV ? 4 : 8; }
+
+Layout make_layout(int nx, int ny, int pitch, int precision, int has_force, bool staged)
+{
+    Layout L{};
+    const size_t rs = real_size(precision);
+    const size_t plane = (size_t)pitch * ny;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, kAlign);
+        return o;
+    };
+    L.state[0] = take(9 * plane * rs);
+    L.state[1] = take(9 * plane * rs);
+    L.mx = take(nx * rs);
+    L.my = take(ny * rs);
+    L.mxd = take(nx * sizeof(double));
+    L.myd = take(ny * sizeof(double));
+    L.force = has_force ? take(2 * plane * rs) : 0;
+    if (staged) {
+        L.P = take(9 * plane * rs);
+        L.Q = take(9 * plane * rs);
+        L.S = take(9 * plane * rs);
+    }
+    L.uprev = take(2 * (size_t)nx * ny * sizeof(double));
+    L.nblocks_red = kRedBlocks;
+    L.partials = take((size_t)kRedBlocks * 3 * sizeof(double));
+    L.red = take(4 * sizeof(double));
+    const size_t need_rows = (size_t)9 * nx * sizeof(double);  // one row of 9 fields
+    const size_t sbytes = std::max(std::min(kStagingBytes, 9 * (size_t)nx * ny * sizeof(double)),
+                                   need_rows);
+    L.staging = take(sbytes);
+    L.staging_elems = sbytes / sizeof(double);
+    L.total = off;
+    return L;
+}
+
+}  // namespace fdlbm
+
+extern "C" {
+
+void fdlbm_default_opts(fdlbm_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->A = 0.5;
+    o->rho0 = 1.0;
+    o->precision = FDLBM_FP64;
+    o->path = FDLBM_PATH_AUTO;
+}
+
+double fdlbm_time_step(const fdlbm_grid *g, double cfl)
+{
+    if (!grid_ok(g) || !(cfl > 0)) return -1.0;
+    const double dx = std::min(min_spacing(g->x, g->nx, g->bc_x == FDLBM_PERIODIC, g->lx),
+                               min_spacing(g->y, g->ny, g->bc_y == FDLBM_PERIODIC, g->ly));
+    return cfl * dx / 1.0;  // xi = 1
+}
+
+size_t fdlbm_workspace_bytes(const fdlbm_grid *g, const fdlbm_opts *opts)
+{
+    fdlbm_opts o;
+    fdlbm_default_opts(&o);
+    if (opts) o = *opts;
+    if (!grid_ok(g)) return 0;
+    const int path = choose_path(g, &o);
+    if (path < 0) return 0;
+    return make_layout(g->nx, g->ny, pitch_of(g->nx), o.precision, o.has_force,
+                       path == FDLBM_PATH_STAGED)
+        .total;
+}
+
+fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, double nu,
+                          double cfl, double blend, const fdlbm_opts *opts, fdlbm_t *out)
+{
+    if (!out) return FDLBM_EINVAL;
+    *out = nullptr;
+    fdlbm_opts o;
+    fdlbm_default_opts(&o);
+    if (opts) o = *opts;
+    if (!grid_ok(g) || !(nu > 0) || !(cfl > 0) || !(blend >= 0 && blend <= 1) ||
+        !(o.A >= 0 && o.A <= 1) || !(o.rho0 > 0) ||
+        (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0)
+        return FDLBM_EINVAL;
+    const int path = choose_path(g, &o);
+    if (path < 0) return FDLBM_EUNSUPPORTED;
+    std::vector<double> mx(g->nx), my(g->ny);
+    for (int i = 0; i < g->nx; ++i)
+        mx[i] = (metrics && metrics->dzeta_dx) ? metrics->dzeta_dx[i] : 1.0 / (g->x[1] - g->x[0]);
+    for (int j = 0; j < g->ny; ++j)
+        my[j] = (metrics && metrics->dmu_dy) ? metrics->dmu_dy[j] : 1.0 / (g->y[1] - g->y[0]);
+    for (double v : mx)
+        if (!(v > 0) || !std::isfinite(v)) return FDLBM_EINVAL;
+    for (double v : my)
+        if (!(v > 0) || !std::isfinite(v)) return FDLBM_EINVAL;
+
+    fdlbm_ctx *h = new (std::nothrow) fdlbm_ctx();
+    if (!h) return FDLBM_ENOMEM;
+    h->nx = g->nx;
+    h->ny = g->ny;
+    h->pitch = pitch_of(g->nx);
+    h->plane = (size_t)h->pitch * h->ny;
+    h->bc_x = g->bc_x;
+    h->bc_y = g->bc_y;
+    std::memcpy(h->wall_u, g->wall_u, sizeof(h->wall_u));
+    h->precision = o.precision;
+    h->nu = nu;
+    h->tau = nu * 3.0;  // tau = nu / cs^2
+    h->cfl = cfl;
+    h->dt = fdlbm_time_step(g, cfl);
+    h->beta = blend;
+    h->A = o.A;
+    h->rho0 = o.rho0;
+    h->has_force = o.has_force ? 1 : 0;
+    h->path = path;
+    h->rows = o.rows_per_cta > 0 ? std::min(o.rows_per_cta, g->ny) : choose_rows(g->nx, g->ny);
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    h->lay = make_layout(h->nx, h->ny, h->pitch, h->precision, h->has_force,
+                         path == FDLBM_PATH_STAGED);
+    cudaGetDevice(&h->device);
+    if (o.workspace) {
+        if (o.workspace_bytes < h->lay.total ||
+            (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0) {
+            delete h;
+            return FDLBM_ENOMEM;
+        }
+        h->ws = static_cast<char *>(o.workspace);
+        h->ws_bytes = o.workspace_bytes;
+    } else {
+        cudaError_t e = cudaMalloc(&h->ws, h->lay.total);
+        if (e != cudaSuccess) {
+            delete h;
+            return FDLBM_ENOMEM;
+        }
+        h->owns_ws = true;
+        h->ws_bytes = h->lay.total;
+    }
+    // zero state (fluid at rest), metrics in both precisions
+    cudaError_t e = cudaMemsetAsync(h->ws + h->lay.state[0], 0,
+                                    h->lay.state[1] - h->lay.state[0], h->stream);
+    if (e == cudaSuccess && h->has_force)
+        e = cudaMemsetAsync(h->ws + h->lay.force, 0, 2 * h->plane * real_size(h->precision),
+                            h->stream);
+    if (e == cudaSuccess) {
+        if (h->precision == FDLBM_FP32_DEV) {
+            std::vector<float> fx(mx.begin(), mx.end()), fy(my.begin(), my.end());
+            e = cudaMemcpy(h->ws + h->lay.mx, fx.data(), fx.size() * 4, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(h->ws + h->lay.my, fy.data(), fy.size() * 4, cudaMemcpyHostToDevice);
+        } else {
+            e = cudaMemcpy(h->ws + h->lay.mx, mx.data(), mx.size() * 8, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(h->ws + h->lay.my, my.data(), my.size() * 8, cudaMemcpyHostToDevice);
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->ws + h->lay.mxd, mx.data(), mx.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->ws + h->lay.myd, my.data(), my.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        fdlbm_destroy(h);
+        return FDLBM_ECUDA;
+    }
+    *out = h;
+    return FDLBM_OK;
+}
+
+void fdlbm_destroy(fdlbm_t h)
+{
+    if (!h) return;
+    if (h->owns_ws && h->ws) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->ws);
+    }
+    delete h;
+}
+
+fdlbm_status fdlbm_init_fields(fdlbm_t h, const double *rho, const double *ux, const double *uy,
+                               const double *grad, int where)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (!rho || !ux || !uy || (where != FDLBM_MEM_HOST && where != FDLBM_MEM_DEVICE))
+        return fail(h, FDLBM_EINVAL, "init_fields: NULL field or bad `where`");
+    const size_t N = (size_t)h->nx * h->ny;
+    const double *f[7] = {rho, ux, uy, grad, grad ? grad + N : nullptr,
+                          grad ? grad + 2 * N : nullptr, grad ? grad + 3 * N : nullptr};
+    h->have_uprev = false;
+    return staged_in(
+        h, f, grad ? 7 : 3, where,
+        [&](const double *const *p, int nr, size_t fstride, int r0) {
+            return launch_init_fields(h, p[0], p[1], p[2], grad ? p[3] : nullptr, r0, nr, fstride);
+        },
+        "init_fields");
+}
+
+fdlbm_status fdlbm_set_state(fdlbm_t h, const double *f, int where)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (!f || (where != FDLBM_MEM_HOST && where != FDLBM_MEM_DEVICE))
+        return fail(h, FDLBM_EINVAL, "set_state: NULL or bad `where`");
+    const size_t N = (size_t)h->nx * h->ny;
+    const double *p[9];
+    for (int i = 0; i < 9; ++i) p[i] = f + i * N;
+    h->have_uprev = false;
+    return staged_in(
+        h, p, 9, where,
+        [&](const double *const *q, int nr, size_t fstride, int r0) {
+            return launch_convert_in(h, q[0], r0, nr, fstride);
+        },
+        "set_state");
+}
+
+fdlbm_status fdlbm_set_force(fdlbm_t h, const double *force, int where)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (!h->has_force) return fail(h, FDLBM_EUNSUPPORTED, "set_force: created without has_force");
+    if (!force || (where != FDLBM_MEM_HOST && where != FDLBM_MEM_DEVICE))
+        return fail(h, FDLBM_EINVAL, "set_force: NULL or bad `where`");
+    const size_t N = (size_t)h->nx * h->ny;
+    const double *p[2] = {force, force + N};
+    return staged_in(
+        h, p, 2, where,
+        [&](const double *const *q, int nr, size_t fstride, int r0) {
+            return launch_set_force(h, q[0], r0, nr, fstride);
+        },
+        "set_force");
+}
+
+fdlbm_status fdlbm_get_state(fdlbm_t h, double *f, int where)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (!f || (where != FDLBM_MEM_HOST && where != FDLBM_MEM_DEVICE))
+        return fail(h, FDLBM_EINVAL, "get_state: NULL or bad `where`");
+    const size_t N = (size_t)h->nx * h->ny;
+    cudaError_t e;
+    if (where == FDLBM_MEM_DEVICE) {
+        e = launch_convert_out(h, f, 0, h->ny, N);
+        return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "get_state");
+    }
+    double *stage = reinterpret_cast<double *>(h->ws + h->lay.staging);
+    const int rows = (int)std::max<size_t>(1, h->lay.staging_elems / (9 * (size_t)h->nx));
+    for (int r0 = 0; r0 < h->ny; r0 += rows) {
+        const int nr = std::min(rows, h->ny - r0);
+        const size_t fstride = (size_t)nr * h->nx;
+        e = launch_convert_out(h, stage, r0, nr, fstride);
+        if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+        for (int i = 0; i < 9; ++i) {
+            e = cudaMemcpyAsync(f + i * N + (size_t)r0 * h->nx, stage + i * fstride,
+                                fstride * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+        }
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+    }
+    return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_step(fdlbm_t h, int n)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (n < 0) return fail(h, FDLBM_EINVAL, "step: n < 0");
+    for (int k = 0; k < n; ++k) {
+        cudaError_t e;
+        if (h->precision == FDLBM_FP32_DEV) {
+            auto a = step_args<float>(h);
+            e = h->path == FDLBM_PATH_FUSED ? launch_fused(a, h->stream) : launch_staged(a, h->stream);
+        } else {
+            auto a = step_args<double>(h);
+            e = h->path == FDLBM_PATH_FUSED ? launch_fused(a, h->stream) : launch_staged(a, h->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "step");
+        h->cur = 1 - h->cur;
+        ++h->steps;
+    }
+    return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_moments(fdlbm_t h, double *rho, double *ux, double *uy, int where)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (!rho || !ux || !uy || (where != FDLBM_MEM_HOST && where != FDLBM_MEM_DEVICE))
+        return fail(h, FDLBM_EINVAL, "moments: NULL or bad `where`");
+    const size_t N = (size_t)h->nx * h->ny;
+    cudaError_t e;
+    if (where == FDLBM_MEM_DEVICE) {
+        e = launch_moments(h, rho, ux, uy, 0, h->ny, N);
+        return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "moments");
+    }
+    double *stage = reinterpret_cast<double *>(h->ws + h->lay.staging);
+    const int rows = (int)std::max<size_t>(1, h->lay.staging_elems / (3 * (size_t)h->nx));
+    for (int r0 = 0; r0 < h->ny; r0 += rows) {
+        const int nr = std::min(rows, h->ny - r0);
+        const size_t fs = (size_t)nr * h->nx;
+        e = launch_moments(h, stage, stage + fs, stage + 2 * fs, r0, nr, fs);
+        if (e != cudaSuccess) return cuda_fail(h, e, "moments");
+        double *dst[3] = {rho, ux, uy};
+        for (int k = 0; k < 3; ++k) {
+            e = cudaMemcpyAsync(dst[k] + (size_t)r0 * h->nx, stage + k * fs, fs * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "moments");
+        }
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "moments");
+    }
+    return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_reduce(fdlbm_t h, double *mass, double *resid)
+{
+    if (!h) return FDLBM_EINVAL;
+    cudaError_t e = launch_reduce(h, h->have_uprev ? 1 : 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduce");
+    double r[4];
+    e = cudaMemcpyAsync(r, h->ws + h->lay.red, 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "reduce");
+    const double res = h->have_uprev ? std::sqrt(r[2] / r[1]) : -1.0;
+    h->have_uprev = true;
+    if (mass) *mass = r[0];
+    if (resid) *resid = res;
+    if (!std::isfinite(r[0]) || !std::isfinite(r[1]) || !std::isfinite(r[2]))
+        return fail(h, FDLBM_ENONFINITE, "reduce: non-finite mass or velocity (diverged)");
+    return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_set_stream(fdlbm_t h, void *stream)
+{
+    if (!h) return FDLBM_EINVAL;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_sync(fdlbm_t h)
+{
+    if (!h) return FDLBM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "sync");
+}
+
+double fdlbm_dt(fdlbm_t h) { return h ? h->dt : -1.0; }
+double fdlbm_tau(fdlbm_t h) { return h ? h->tau : -1.0; }
+long long fdlbm_steps_done(fdlbm_t h) { return h ? h->steps : -1; }
+int fdlbm_path(fdlbm_t h) { return h ? h->path : -1; }
+int fdlbm_kernels_per_step(fdlbm_t h)
+{
+    if (!h) return -1;
+    if (h->path == FDLBM_PATH_FUSED) return 1;
+    return (h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL) ? 5 : 3;
+}
+
+const char *fdlbm_last_error(fdlbm_t h) { return h ? h->err.c_str() : "NULL handle"; }
+
+const char *fdlbm_status_string(fdlbm_status s)
+{
+    switch (s) {
+    case FDLBM_OK: return "ok";
+    case FDLBM_EINVAL: return "invalid argument";
+    case FDLBM_ENOMEM: return "out of memory / workspace too small";
+    case FDLBM_ECUDA: return "CUDA error";
+    case FDLBM_ENONFINITE: return "non-finite result";
+    case FDLBM_EUNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,278 @@
+// Kernels that move data between the caller's FP64 fields and the stored
+// deviations g_i = f~_i - w_i rho0 (in FP64 or FP32), plus the moments of
+// Eq. 3.3 and the FP64 mass / residual reductions.
+//
+// Every kernel here handles the rows [row0, row0 + nrows) of the grid; the
+// caller-side arrays hold exactly those rows, x fastest, and multi-field
+// arrays place field k at offset k * fstride elements.
+#include "internal.h"
+
+namespace fdlbm {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+template <class R>
+__global__ void k_init(StepArgs<R> a, const double *rho, const double *ux, const double *uy,
+                       const double *grad, size_t fstride, int row0, int nrows, double tau,
+                       double dt, double rho0)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || j >= nrows) return;
+    const size_t l = (size_t)j * a.nx + x;
+    const double r = rho[l], u = ux[l], v = uy[l];
+    double geq[9];
+    equilibrium_dev<double>(r - rho0, r, u, v, geq);
+    // Eq. 3.5 with the coefficient rho0 w_i (2 tau + dt) / (2 cs^2)
+    const double k = rho0 * (2.0 * tau + dt) * 1.5;
+    const size_t o = (size_t)(row0 + j) * a.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        double val = geq[i];
+        if (grad) {
+            const double gxx = grad[l], gxy = grad[fstride + l], gyx = grad[2 * fstride + l],
+                         gyy = grad[3 * fstride + l];
+            const double d = double(cx(i) * cx(i)) * gxx + double(cx(i) * cy(i)) * (gxy + gyx) +
+                             double(cy(i) * cy(i)) * gyy;
+            val -= k * wq<double>(i) * d;
+        }
+        a.gout[i * a.plane + o] = R(val);
+    }
+}
+
+template <class R>
+__global__ void k_convert_in(StepArgs<R> a, const double *f, size_t fstride, int row0, int nrows,
+                             double rho0)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || j >= nrows) return;
+    const size_t l = (size_t)j * a.nx + x, o = (size_t)(row0 + j) * a.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) a.gout[i * a.plane + o] = R(f[i * fstride + l] - wq<double>(i) * rho0);
+}
+
+template <class R>
+__global__ void k_convert_out(StepArgs<R> a, double *f, size_t fstride, int row0, int nrows,
+                              double rho0)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || j >= nrows) return;
+    const size_t l = (size_t)j * a.nx + x, o = (size_t)(row0 + j) * a.pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i * fstride + l] = double(a.gin[i * a.plane + o]) + wq<double>(i) * rho0;
+}
+
+template <class R>
+__global__ void k_set_force(StepArgs<R> a, R *force, const double *src, size_t fstride, int row0,
+                            int nrows)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || j >= nrows) return;
+    const size_t l = (size_t)j * a.nx + x, o = (size_t)(row0 + j) * a.pitch + x;
+    force[o] = R(src[l]);
+    force[a.plane + o] = R(src[fstride + l]);
+}
+
+// Eq. 3.3 in FP64 from the stored deviations.
+template <class R>
+__device__ void node_moments(const StepArgs<R> &a, const R *force, size_t o, double rho0,
+                             double half_dt, double &rho, double &ux, double &uy)
+{
+    double g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = double(a.gin[i * a.plane + o]);
+    double drho, jx, jy;
+    moments_dev<double>(g, drho, jx, jy);
+    rho = rho0 + drho;
+    if (force) {
+        jx += half_dt * rho * double(force[o]);
+        jy += half_dt * rho * double(force[a.plane + o]);
+    }
+    ux = jx / rho;
+    uy = jy / rho;
+}
+
+template <class R>
+__global__ void k_moments(StepArgs<R> a, const R *force, double *rho, double *ux, double *uy,
+                          int row0, int nrows, double rho0, double half_dt)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || j >= nrows) return;
+    const size_t l = (size_t)j * a.nx + x, o = (size_t)(row0 + j) * a.pitch + x;
+    double r, u, v;
+    node_moments(a, force, o, rho0, half_dt, r, u, v);
+    rho[l] = r;
+    ux[l] = u;
+    uy[l] = v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Per-block partial sums of  J rho,  |u|^2,  |u - u_prev|^2  (J = 1/(m_x m_y)),
+// then u_prev <- u.  Grid-stride over nodes; fixed block count -> fixed order.
+template <class R>
+__global__ void __launch_bounds__(kRedThreads)
+    k_reduce_partial(StepArgs<R> a, const R *force, const double *mxd, const double *myd,
+                     double *uprev, int use_prev, double rho0, double half_dt, double *partials)
+{
+    __shared__ double red[3][kRedThreads / 32];
+    const size_t N = (size_t)a.nx * a.ny;
+    double m = 0.0, uu = 0.0, du = 0.0;
+    for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(n / a.nx), x = (int)(n % a.nx);
+        const size_t o = (size_t)y * a.pitch + x;
+        double r, u, v;
+        node_moments(a, force, o, rho0, half_dt, r, u, v);
+        m += r / (mxd[x] * myd[y]);
+        uu += u * u + v * v;
+        if (use_prev) {
+            const double eu = u - uprev[n], ev = v - uprev[N + n];
+            du += eu * eu + ev * ev;
+        }
+        uprev[n] = u;
+        uprev[N + n] = v;
+    }
+    m = warp_sum(m);
+    uu = warp_sum(uu);
+    du = warp_sum(du);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = m;
+        red[1][wid] = uu;
+        red[2][wid] = du;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) s += red[threadIdx.x][w];
+        partials[(size_t)blockIdx.x * 3 + threadIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_reduce_final(const double *partials, int nblocks, double *out)
+{
+    __shared__ double red[3][kRedThreads / 32];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int k = 0; k < 3; ++k) s[k] += partials[(size_t)b * 3 + k];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < 3; ++k) {
+        s[k] = warp_sum(s[k]);
+        if (lane == 0) red[k][wid] = s[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) t += red[threadIdx.x][w];
+        out[threadIdx.x] = t;
+    }
+}
+
+template <class R>
+StepArgs<R> view(fdlbm_ctx *h)
+{
+    StepArgs<R> a{};
+    a.nx = h->nx;
+    a.ny = h->ny;
+    a.pitch = h->pitch;
+    a.plane = h->plane;
+    a.gin = reinterpret_cast<const R *>(h->ws + h->lay.state[h->cur]);
+    a.gout = reinterpret_cast<R *>(h->ws + h->lay.state[h->cur]);
+    return a;
+}
+
+inline dim3 grid2(int nx, int nrows, dim3 blk)
+{
+    return dim3((nx + blk.x - 1) / blk.x, (nrows + blk.y - 1) / blk.y);
+}
+
+}  // namespace
+
+#define DISPATCH(h, R, ...)                           \
+    do {                                              \
+        if ((h)->precision == FDLBM_FP32_DEV) {       \
+            using R = float;                          \
+            __VA_ARGS__;                              \
+        } else {                                      \
+            using R = double;                         \
+            __VA_ARGS__;                              \
+        }                                             \
+    } while (0)
+
+cudaError_t launch_init_fields(fdlbm_ctx *h, const double *rho, const double *ux,
+                               const double *uy, const double *grad, int row0, int nrows,
+                               size_t fstride)
+{
+    const dim3 blk(32, 8);
+    DISPATCH(h, R, k_init<R><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
+                       view<R>(h), rho, ux, uy, grad, fstride, row0, nrows, h->tau, h->dt, h->rho0));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_in(fdlbm_ctx *h, const double *f, int row0, int nrows, size_t fstride)
+{
+    const dim3 blk(32, 8);
+    DISPATCH(h, R, k_convert_in<R><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
+                       view<R>(h), f, fstride, row0, nrows, h->rho0));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_out(fdlbm_ctx *h, double *f, int row0, int nrows, size_t fstride)
+{
+    const dim3 blk(32, 8);
+    DISPATCH(h, R, k_convert_out<R><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
+                       view<R>(h), f, fstride, row0, nrows, h->rho0));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_force(fdlbm_ctx *h, const double *force, int row0, int nrows,
+                             size_t fstride)
+{
+    const dim3 blk(32, 8);
+    DISPATCH(h, R, k_set_force<R><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
+                       view<R>(h), reinterpret_cast<R *>(h->ws + h->lay.force), force, fstride,
+                       row0, nrows));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(fdlbm_ctx *h, double *rho, double *ux, double *uy, int row0,
+                           int nrows, size_t /*fstride*/)
+{
+    const dim3 blk(32, 8);
+    DISPATCH(h, R,
+             const R *force = h->has_force ? reinterpret_cast<const R *>(h->ws + h->lay.force)
+                                           : nullptr;
+             k_moments<R><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
+                 view<R>(h), force, rho, ux, uy, row0, nrows, h->rho0, 0.5 * h->dt));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(fdlbm_ctx *h, int use_prev)
+{
+    double *partials = reinterpret_cast<double *>(h->ws + h->lay.partials);
+    double *out = reinterpret_cast<double *>(h->ws + h->lay.red);
+    const double *mxd = reinterpret_cast<const double *>(h->ws + h->lay.mxd);
+    const double *myd = reinterpret_cast<const double *>(h->ws + h->lay.myd);
+    double *uprev = reinterpret_cast<double *>(h->ws + h->lay.uprev);
+    DISPATCH(h, R,
+             const R *force = h->has_force ? reinterpret_cast<const R *>(h->ws + h->lay.force)
+                                           : nullptr;
+             k_reduce_partial<R><<<h->lay.nblocks_red, kRedThreads, 0, h->stream>>>(
+                 view<R>(h), force, mxd, myd, uprev, use_prev, h->rho0, 0.5 * h->dt, partials));
+    k_reduce_final<<<1, kRedThreads, 0, h->stream>>>(partials, h->lay.nblocks_red, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fdlbm

@@ -1,0 +1,87 @@
+// Host-side state of a handle and the launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <string>
+
+#include "fdlbm.h"
+#include "lattice.cuh"
+
+namespace fdlbm {
+
+// Everything a step kernel needs, passed by value.
+template <class R>
+struct StepArgs {
+    const R *gin;        // [9][ny][pitch] deviations at t_n
+    R *gout;             // [9][ny][pitch] deviations at t_{n+1}
+    const R *mx, *my;    // metrics d zeta/dx (nx), d mu/dy (ny)
+    const R *force;      // [2][ny][pitch] or nullptr
+    int nx, ny, pitch;
+    size_t plane;        // ny * pitch
+    int bc_x, bc_y;      // FDLBM_PERIODIC / FDLBM_WALL
+    R wall_u[4][2];
+    Coeffs<R> c;
+    Stencil<R> st;       // mixed weights
+    Stencil<R> stc;      // central-only weights (next to walls)
+    int rows;            // fused kernel: rows per CTA
+    // staged path scratch, [9][ny][pitch] each
+    R *P, *Q, *S;
+};
+
+struct Layout {
+    size_t state[2], mx, my, mxd, myd, force, P, Q, S, uprev, partials, red, staging;
+    size_t staging_elems, total;
+    int nblocks_red;
+};
+
+}  // namespace fdlbm
+
+struct fdlbm_ctx {
+    int nx = 0, ny = 0, pitch = 0;
+    size_t plane = 0;
+    int bc_x = 0, bc_y = 0;
+    double wall_u[4][2] = {};
+    int precision = FDLBM_FP64;
+    double nu = 0, tau = 0, dt = 0, cfl = 0, beta = 0, A = 0.5, rho0 = 1;
+    int has_force = 0;
+    int path = FDLBM_PATH_FUSED;
+    int rows = 64;
+    cudaStream_t stream = nullptr;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool owns_ws = false;
+    int device = 0;
+    fdlbm::Layout lay{};
+    int cur = 0;
+    bool have_uprev = false;
+    long long steps = 0;
+    std::string err;
+};
+
+namespace fdlbm {
+
+size_t real_size(int precision);
+Layout make_layout(int nx, int ny, int pitch, int precision, int has_force, bool staged);
+
+// step_fused.cu
+template <class R>
+cudaError_t launch_fused(const StepArgs<R> &a, cudaStream_t s);
+// step_staged.cu
+template <class R>
+cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s);
+// fields.cu
+cudaError_t launch_init_fields(fdlbm_ctx *h, const double *rho, const double *ux,
+                               const double *uy, const double *grad, int row0, int nrows,
+                               size_t src_pitch_rows);
+cudaError_t launch_convert_in(fdlbm_ctx *h, const double *f, int row0, int nrows,
+                              size_t src_plane);
+cudaError_t launch_convert_out(fdlbm_ctx *h, double *f, int row0, int nrows, size_t dst_plane);
+cudaError_t launch_set_force(fdlbm_ctx *h, const double *force, int row0, int nrows,
+                             size_t src_plane);
+cudaError_t launch_moments(fdlbm_ctx *h, double *rho, double *ux, double *uy, int row0,
+                           int nrows, size_t dst_plane);
+cudaError_t launch_reduce(fdlbm_ctx *h, int use_prev);
+
+}  // namespace fdlbm

@@ -1,0 +1,179 @@
+"""Python handle on one libfdlbm solver (the same calls as the C ABI).
+
+Device memory for the handle's workspace comes from PyTorch; the handle uses
+torch's current CUDA stream unless another stream is given.  Fields can be
+passed as numpy arrays (host, copied through the library's staging area) or as
+CUDA torch tensors (read in place on the stream).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+def _check(L, h, rc, what):
+    if rc != 0:
+        msg = L.fdlbm_last_error(h).decode() if h else ""
+        raise B.FdlbmError(rc, f"{what}: {msg}")
+
+
+class FDLBM:
+    """One grid, one parameter set, one distribution state on the GPU.
+
+    ``xa, ya``: axes with ``coords``, ``metric`` (d zeta/dx), ``periodic`` and
+    ``length`` (see ``inputs.Axis``).  ``blend``: upwind weight of the mixed
+    difference.  ``precision``: ``"fp64"`` or ``"fp32"`` (FP32 deviation storage).
+    """
+
+    def __init__(self, xa, ya, *, nu: float, cfl: float, blend: float, A: float = 0.5,
+                 precision: str = "fp64", rho0: float = 1.0, has_force: bool = False,
+                 wall_u=None, path: str = "auto", rows_per_cta: int = 0, stream=None,
+                 device=None):
+        self._L = L = B.load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.nx, self.ny = xa.n, ya.n
+        self._grid, self._keep = B.make_grid(xa, ya, wall_u)
+        self._mx = np.ascontiguousarray(xa.metric, dtype=np.float64)
+        self._my = np.ascontiguousarray(ya.metric, dtype=np.float64)
+        m = B.Metrics()
+        m.dzeta_dx, m.dmu_dy = B._dptr(self._mx), B._dptr(self._my)
+        o = B.Opts()
+        L.fdlbm_default_opts(ctypes.byref(o))
+        o.A, o.rho0 = A, rho0
+        o.precision = {"fp64": B.FP64, "fp32": B.FP32_DEV}[precision]
+        o.has_force = int(has_force)
+        o.path = {"auto": B.PATH_AUTO, "fused": B.PATH_FUSED, "staged": B.PATH_STAGED}[path]
+        o.rows_per_cta = rows_per_cta
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        o.stream = self.stream.cuda_stream
+        nbytes = L.fdlbm_workspace_bytes(ctypes.byref(self._grid), ctypes.byref(o))
+        if nbytes == 0:
+            raise B.FdlbmError(-1, "invalid grid/options (workspace size 0)")
+        # torch allocations are 512-byte aligned
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        o.workspace, o.workspace_bytes = self._ws.data_ptr(), nbytes
+        h = ctypes.c_void_p()
+        rc = L.fdlbm_create(ctypes.byref(self._grid), ctypes.byref(m), nu, cfl, blend,
+                            ctypes.byref(o), ctypes.byref(h))
+        _check(L, None, rc, "fdlbm_create")
+        self._h = h
+        self.precision = precision
+
+    # ----------------------------------------------------------- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.fdlbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------- properties
+    @property
+    def dt(self) -> float:
+        return self._L.fdlbm_dt(self._h)
+
+    @property
+    def tau(self) -> float:
+        return self._L.fdlbm_tau(self._h)
+
+    @property
+    def path(self) -> str:
+        return {B.PATH_FUSED: "fused", B.PATH_STAGED: "staged"}[self._L.fdlbm_path(self._h)]
+
+    @property
+    def kernels_per_step(self) -> int:
+        return self._L.fdlbm_kernels_per_step(self._h)
+
+    @property
+    def steps_done(self) -> int:
+        return self._L.fdlbm_steps_done(self._h)
+
+    # ----------------------------------------------------------- marshalling
+    def _arg(self, a, shape):
+        """(pointer, where, keepalive) for a numpy array or CUDA tensor of FP64."""
+        if a is None:
+            return None, B.MEM_HOST, None
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda:
+                t = a.detach().to(torch.float64).contiguous()
+                assert tuple(t.shape) == shape, (t.shape, shape)
+                return t.data_ptr(), B.MEM_DEVICE, t
+            a = a.detach().cpu().numpy()
+        arr = np.ascontiguousarray(a, dtype=np.float64)
+        assert arr.shape == shape, (arr.shape, shape)
+        return arr.ctypes.data, B.MEM_HOST, arr
+
+    def init_fields(self, rho, ux, uy, grad=None):
+        """Eq. 3.2 (or Eq. 3.5 with the velocity gradient [dudx, dudy, dvdx, dvdy])."""
+        sh = (self.ny, self.nx)
+        args = [self._arg(v, sh) for v in (rho, ux, uy)]
+        g = None
+        if grad is not None:
+            gs = torch.stack([torch.as_tensor(v) for v in grad]) if isinstance(grad[0], torch.Tensor) \
+                else np.stack(grad)
+            g = self._arg(gs, (4,) + sh)
+        wheres = {w for _, w, _ in args} | ({g[1]} if g else set())
+        if len(wheres) != 1:
+            raise ValueError("all fields must live on the same side (host or device)")
+        rc = self._L.fdlbm_init_fields(self._h, args[0][0], args[1][0], args[2][0],
+                                       g[0] if g else None, wheres.pop())
+        _check(self._L, self._h, rc, "init_fields")
+        return self
+
+    def set_state(self, f):
+        p, where, keep = self._arg(f, (9, self.ny, self.nx))
+        _check(self._L, self._h, self._L.fdlbm_set_state(self._h, p, where), "set_state")
+        if where == B.MEM_DEVICE:
+            self.stream.synchronize()
+        return self
+
+    def get_state(self, device: bool = False):
+        if device:
+            out = torch.empty((9, self.ny, self.nx), dtype=torch.float64, device=self.device)
+            _check(self._L, self._h, self._L.fdlbm_get_state(self._h, out.data_ptr(), B.MEM_DEVICE),
+                   "get_state")
+            return out
+        out = np.empty((9, self.ny, self.nx))
+        _check(self._L, self._h, self._L.fdlbm_get_state(self._h, out.ctypes.data, B.MEM_HOST),
+               "get_state")
+        return out
+
+    def set_force(self, force):
+        p, where, keep = self._arg(force, (2, self.ny, self.nx))
+        _check(self._L, self._h, self._L.fdlbm_set_force(self._h, p, where), "set_force")
+        if where == B.MEM_DEVICE:
+            self.stream.synchronize()
+        return self
+
+    def step(self, n: int = 1):
+        _check(self._L, self._h, self._L.fdlbm_step(self._h, int(n)), "step")
+        return self
+
+    def moments(self, device: bool = False):
+        sh = (self.ny, self.nx)
+        if device:
+            outs = [torch.empty(sh, dtype=torch.float64, device=self.device) for _ in range(3)]
+            rc = self._L.fdlbm_moments(self._h, *(o.data_ptr() for o in outs), B.MEM_DEVICE)
+        else:
+            outs = [np.empty(sh) for _ in range(3)]
+            rc = self._L.fdlbm_moments(self._h, *(o.ctypes.data for o in outs), B.MEM_HOST)
+        _check(self._L, self._h, rc, "moments")
+        return tuple(outs)
+
+    def reduce(self):
+        """(Jacobian-weighted mass, successive-state residual or -1)."""
+        m, r = ctypes.c_double(), ctypes.c_double()
+        rc = self._L.fdlbm_reduce(self._h, ctypes.byref(m), ctypes.byref(r))
+        _check(self._L, self._h, rc, "reduce")
+        return m.value, r.value
+
+    def sync(self):
+        _check(self._L, self._h, self._L.fdlbm_sync(self._h), "sync")

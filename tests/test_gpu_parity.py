@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle,
+element by element on the same seeded inputs.
+
+Tolerances: FP64 paths must match the oracle's f~ to 1e-12 relative L2 (the
+only differences are rounding order; one step changes f~ by a few ulps).  The
+FP32-deviation path reports its error against the FP64 oracle; its bound here
+is derived from FP32 rounding of deviations of size |u| ~ 1e-2 (relative
+rounding 6e-8 per operation, a few hundred operations per step, errors that
+random-walk over the steps).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs as I
+import oracle as O
+from conftest import oracle_threads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1911_12913_gb300.solver import FDLBM  # noqa: E402
+
+FP64_TOL = 1e-12
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _pair(xa, ya, *, nu, cfl, beta, A=0.5, precision="fp64", force=None, wall_u=None,
+          path="auto", rows=0, nthreads=1):
+    s = FDLBM(xa, ya, nu=nu, cfl=cfl, blend=beta, A=A, precision=precision,
+              has_force=force is not None, wall_u=wall_u, path=path, rows_per_cta=rows)
+    o = O.Oracle(xa, ya, nu=nu, dt=s.dt, beta=beta, A=A, force=force, wall_u=wall_u,
+                 nthreads=nthreads)
+    if force is not None:
+        s.set_force(force)
+    return s, o
+
+
+def _init_both(s, o, fields, grad=True):
+    g = [fields["dudx"], fields["dudy"], fields["dvdx"], fields["dvdy"]] if grad else None
+    s.init_fields(fields["rho"], fields["ux"], fields["uy"], g)
+    o.init_fields(fields["rho"], fields["ux"], fields["uy"], g)
+
+
+# ------------------------------------------------------------------ Taylor vortex 64^2
+@pytest.mark.parametrize("path", ["fused", "staged"])
+def test_taylor_green_64_fp64_1000_steps(path):
+    """Taylor vortex, 64x64 on [0,2pi)^2, u0 = 0.01, nu = 0.01, CFL 0.5, 1000 steps."""
+    xa = I.periodic_axis(64, 0.0, 2 * math.pi)
+    ya = I.periodic_axis(64, 0.0, 2 * math.pi)
+    s, o = _pair(xa, ya, nu=0.01, cfl=0.5, beta=0.1, path=path, nthreads=oracle_threads())
+    assert s.path == path
+    f = I.taylor_green(xa, ya, u0=0.01)
+    _init_both(s, o, f)
+    assert rel(s.get_state(), o.f) < 1e-15
+    s.step(1000)
+    o.step(1000)
+    assert rel(s.get_state(), o.f) <= FP64_TOL
+    _, ux, uy = s.moments()
+    _, oux, ouy = o.moments()
+    assert O.gre(ux, uy, oux, ouy) <= 1e-10
+    ua, va = I.taylor_green_velocity(xa, ya, 1000 * s.dt, u0=0.01, nu=0.01)
+    assert O.gre(ux, uy, ua, va) < 2e-4
+
+
+def test_taylor_green_64_fp32_error_vs_fp64_oracle():
+    """FP32-deviation storage: error against the FP64 oracle after 1000 steps."""
+    xa = I.periodic_axis(64, 0.0, 2 * math.pi)
+    ya = I.periodic_axis(64, 0.0, 2 * math.pi)
+    s, o = _pair(xa, ya, nu=0.01, cfl=0.5, beta=0.1, precision="fp32", nthreads=oracle_threads())
+    f = I.taylor_green(xa, ya, u0=0.01)
+    _init_both(s, o, f)
+    s.step(1000)
+    o.step(1000)
+    _, ux, uy = s.moments()
+    _, oux, ouy = o.moments()
+    err_u = O.gre(ux, uy, oux, ouy)
+    err_f = rel(s.get_state(), o.f)
+    print(f"FP32-deviation vs FP64 oracle after 1000 steps: rel L2 u = {err_u:.3e}, f~ = {err_f:.3e}")
+    assert err_u < 1e-4 and err_f < 1e-6
+
+
+# ------------------------------------------------------------------ ragged, forced, stretched
+@pytest.mark.parametrize("path,rows", [("fused", 0), ("fused", 5), ("fused", 1), ("staged", 0)])
+@pytest.mark.parametrize("nx,ny", [(133, 37), (4, 9), (250, 21)])
+def test_random_state_force_stretched_fp64(path, rows, nx, ny):
+    """Seeded non-equilibrium state, body-force field, random positive metrics,
+    sizes that leave ragged strips and row segments: 25 steps."""
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 0.7)
+    xa.metric = I.random_metric(nx, 31, base=nx, spread=0.4)
+    ya.metric = I.random_metric(ny, 32, base=ny / 0.7, spread=0.4)
+    rng = np.random.default_rng(7)
+    force = 1e-3 * rng.uniform(-1, 1, size=(2, ny, nx))
+    s, o = _pair(xa, ya, nu=0.02, cfl=0.4, beta=0.2, force=force, path=path, rows=rows)
+    _init_both(s, o, I.random_fields(nx, ny, 17))
+    s.step(25)
+    o.step(25)
+    assert rel(s.get_state(), o.f) <= FP64_TOL
+
+
+def test_t1s2_special_case_fp64():
+    """A = 0 in the fused kernel equals the oracle's separately written T1S2 routine."""
+    xa = I.periodic_axis(96, 0.0, 2 * math.pi)
+    ya = I.periodic_axis(40, 0.0, 2 * math.pi)
+    s, o = _pair(xa, ya, nu=0.01, cfl=0.2, beta=0.1, A=0.0)
+    _init_both(s, o, I.random_fields(96, 40, 3, smooth=True))
+    s.step(50)
+    o.step_t1s2(50)
+    assert rel(s.get_state(), o.f) <= FP64_TOL
+
+
+# ------------------------------------------------------------------ walls (Eq. 3.10)
+def test_poiseuille_stretched_walls_fp64():
+    """Channel: periodic x, tanh-stretched walled y (Eq. 3.9, 10 x 20 cells), body force."""
+    F = 0.01
+    nu = math.sqrt(F / 80.0)
+    xa = I.periodic_axis(10, 0.0, 1.0)
+    ya = I.tanh_axis(20, 1.5)
+    force = np.zeros((2, ya.n, xa.n))
+    force[0] = F
+    s, o = _pair(xa, ya, nu=nu, cfl=0.9, beta=0.1, force=force)
+    assert s.path == "staged"
+    one = np.ones((ya.n, xa.n))
+    s.init_fields(one, 0 * one, 0 * one)
+    o.init_fields(one, 0 * one, 0 * one)
+    s.step(300)
+    o.step(300)
+    assert rel(s.get_state(), o.f) <= FP64_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 2e-6)])
+def test_cavity_stretched_walls(precision, tol):
+    """Lid-driven cavity on a tanh grid (walls on all sides, lid U = 0.1)."""
+    n = 24
+    ax = I.tanh_axis(n, 1.5)
+    wall_u = [(0, 0), (0, 0), (0, 0), (0.1, 0.0)]
+    s, o = _pair(ax, ax, nu=0.1 / 100.0, cfl=0.9, beta=0.1, wall_u=wall_u, precision=precision)
+    one = np.ones((ax.n, ax.n))
+    s.init_fields(one, 0 * one, 0 * one)
+    o.init_fields(one, 0 * one, 0 * one)
+    s.step(400)
+    o.step(400)
+    assert rel(s.get_state(), o.f) <= tol
+
+
+# ------------------------------------------------------------------ reductions, misc
+def test_reduce_mass_and_residual():
+    """FP64 reductions: Jacobian-weighted mass (exact invariant) and the
+    successive-state residual against the oracle's velocities."""
+    nx, ny = 70, 50
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 1.0)
+    xa.metric = I.random_metric(nx, 1, base=nx)
+    s, o = _pair(xa, ya, nu=0.02, cfl=0.4, beta=0.1)
+    _init_both(s, o, I.random_fields(nx, ny, 5))
+    m0, r0 = s.reduce()
+    assert r0 == -1.0
+    assert m0 == pytest.approx(o.mass(), rel=1e-14)
+    _, ux0, uy0 = o.moments()
+    s.step(1)
+    o.step(1)
+    m1, r1 = s.reduce()
+    assert m1 == pytest.approx(m0, rel=1e-13)
+    _, ux1, uy1 = o.moments()
+    want = math.sqrt(np.sum((ux1 - ux0) ** 2 + (uy1 - uy0) ** 2) / np.sum(ux1 ** 2 + uy1 ** 2))
+    assert r1 == pytest.approx(want, rel=1e-9)
+
+
+def test_device_side_arguments_and_zero_steps():
+    n = 40
+    xa = I.periodic_axis(n, 0.0, 1.0)
+    s, o = _pair(xa, xa, nu=0.01, cfl=0.5, beta=0.1)
+    fld = I.random_fields(n, n, 9)
+    dev = {k: torch.tensor(v, device="cuda") for k, v in fld.items()}
+    s.init_fields(dev["rho"], dev["ux"], dev["uy"], [dev["dudx"], dev["dudy"], dev["dvdx"], dev["dvdy"]])
+    o.init_fields(fld["rho"], fld["ux"], fld["uy"], [fld["dudx"], fld["dudy"], fld["dvdx"], fld["dvdy"]])
+    before = s.get_state(device=True).cpu().numpy()
+    assert rel(before, o.f) < 1e-15
+    s.step(0)
+    assert np.array_equal(s.get_state(), before)
+    s.set_state(torch.tensor(o.f, device="cuda"))
+    s.step(3)
+    o.step(3)
+    r, ux, uy = s.moments(device=True)
+    orr, oux, ouy = o.moments()
+    assert rel(r.cpu().numpy(), orr) < 1e-14
+    assert O.gre(ux.cpu().numpy(), uy.cpu().numpy(), oux, ouy) < 1e-11
+
+
+# ------------------------------------------------------------------ full size, sampled
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-7), ("fp64", FP64_TOL)])
+def test_full_size_4096_sampled_patches(precision, tol):
+    """4096^2 periodic grid in the launch configuration the benchmark times
+    (automatic tile height): after 2 steps, sampled 40x40 patches are checked
+    against the oracle run on the same patch.  One step reaches 4 nodes, so the
+    central 24x24 nodes of each patch are exact for the oracle."""
+    n, steps, P = 4096, 2, 40
+    xa = I.periodic_axis(n, 0.0, 2 * math.pi)
+    s = FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision=precision)
+    assert s.path == "fused"
+    fld = I.taylor_green(xa, xa, u0=0.01, phase=(0.7, 2.1))
+    pert = I.random_fields(n, n, 77, du=0.002, drho=0.001, dgrad=0.001)
+    for k in fld:
+        fld[k] = fld[k] + (pert[k] - (1.0 if k == "rho" else 0.0))
+    grad = [fld["dudx"], fld["dudy"], fld["dvdx"], fld["dvdy"]]
+    s.init_fields(fld["rho"], fld["ux"], fld["uy"], grad)
+    s.step(steps)
+    g = s.get_state(device=True)
+    rng = np.random.default_rng(4096)
+    m = 4 * steps
+    errs = []
+    for _ in range(12):
+        x0, y0 = (int(v) for v in rng.integers(0, n, size=2))
+        xs = (x0 + np.arange(P)) % n
+        ys = (y0 + np.arange(P)) % n
+        pa = I.periodic_axis(P, 0.0, P * 2 * math.pi / n)
+        o = O.Oracle(pa, pa, nu=0.01, dt=s.dt, beta=0.1)
+        sub = {k: v[np.ix_(ys, xs)] for k, v in fld.items()}
+        o.init_fields(sub["rho"], sub["ux"], sub["uy"],
+                      [sub["dudx"], sub["dudy"], sub["dvdx"], sub["dvdy"]])
+        o.step(steps)
+        want = o.f[:, m:P - m, m:P - m]
+        iy = torch.tensor(ys[m:P - m], device=g.device)
+        ix = torch.tensor(xs[m:P - m], device=g.device)
+        got = g[:, iy][:, :, ix].cpu().numpy()
+        errs.append(rel(got, want))
+    print(f"{precision} 4096^2 sampled patches: max rel L2(f~) = {max(errs):.3e}")
+    assert max(errs) <= tol
