@@ -35,7 +35,9 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "D2Q9 T2S2-FDLBM MLUPS & % HBM roofline, FP32 vs FP64; adjoint/forward cost"
 N_GRID = 4096
-NU, CFL, BLEND, U0, SEED = 0.01, 0.5, 0.1, 0.01, 2026
+# nu = 0.001 (the Taylor-vortex viscosity of Sec. 3A): with nu = 0.01 the scheme is
+# unstable at the 4096^2 spacing (dt/tau = 0.026, nearly collisionless transport).
+NU, CFL, BLEND, U0, SEED = 0.001, 0.5, 0.1, 0.01, 2026
 BYTES_PER_CELL = {"fp32": 72, "fp64": 144}   # 9 populations read once + written once
 SAMPLE_N = 512                                # oracle sample grid
 
@@ -49,6 +51,9 @@ def parse():
     p.add_argument("--n", type=int, default=N_GRID)
     p.add_argument("--fp64-steps", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--variant", default="auto", choices=["auto", "scalar", "packed", "tma"],
+                   help="FP32 fused kernel variant for the headline timing")
+    p.add_argument("--no-variants", action="store_true", help="skip timing the other variant")
     return p.parse_args()
 
 
@@ -231,7 +236,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     # ---------------- device-resident timing (FP32 deviation, the headline)
-    s = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream)
+    s = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream,
+              variant=args.variant)
+    kernel_desc = s.describe
     s.init_fields(f["rho"], f["ux"], f["uy"], grad)
     m0, _ = s.reduce()
     s.step(args.warmup)
@@ -262,9 +269,36 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": kernel_traffic("fp32"),
                 "peak_source": peak_note + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
-                "bytes_per_cell": BYTES_PER_CELL["fp32"], "kernel": "k_step_fused<float>"}
+                "bytes_per_cell": BYTES_PER_CELL["fp32"], "kernel": kernel_desc}
     del s
     torch.cuda.empty_cache()
+
+    # ---------------- both FP32 fused variants, same workload, shorter runs
+    variants = {}
+    if not args.no_variants:
+        for var in ("scalar", "tma", "packed"):
+            try:
+                sv = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream,
+                           variant=var)
+            except Exception as exc:  # variant not applicable to this grid
+                variants[var] = {"unavailable": str(exc)}
+                continue
+            sv.init_fields(f["rho"], f["ux"], f["uy"], grad)
+            sv.step(5)
+            kv = max(100, args.steps // 4)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            sv.step(kv)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sv.sync()
+            tv = e0.elapsed_time(e1) / 1e3 / kv
+            variants[var] = {"kernel": sv.describe, "MLUPS": N / tv / 1e6,
+                             "ms_per_step": tv * 1e3, "hbm_frac": BYTES_PER_CELL["fp32"] * N / tv / 1e9 / hbm,
+                             "steps": kv}
+            del sv
+            torch.cuda.empty_cache()
 
     # ---------------- FP64 beside it (same workload, shorter run)
     fp64 = None
@@ -333,7 +367,8 @@ def run_ours(args):
                "dtype": "f32", "data": "synthetic",
                "config": config(n, "fp32", args.steps), "clocks": clk.summary(),
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-               "cpu_baseline": cpu, "fp64": fp64, "mass_drift_rel": mass_drift,
+               "cpu_baseline": cpu, "fp64": fp64, "fp32_variants": variants,
+               "mass_drift_rel": mass_drift,
                "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(out), flush=True)
     if world > 1:

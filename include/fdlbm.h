@@ -49,6 +49,17 @@ enum { FDLBM_PERIODIC = 0, FDLBM_WALL = 1 };            /* boundary kind of an a
 enum { FDLBM_FP64 = 0, FDLBM_FP32_DEV = 1 };            /* storage / arithmetic precision */
 enum { FDLBM_PATH_AUTO = 0, FDLBM_PATH_FUSED = 1, FDLBM_PATH_STAGED = 2 };
 enum { FDLBM_MEM_HOST = 0, FDLBM_MEM_DEVICE = 1 };
+/* Fused-kernel variant (periodic grids):
+ *  SCALAR  one column per thread, rows loaded through registers (any nx >= 4);
+ *  TMA     one column per thread, rows streamed into shared memory by bulk
+ *          copies (nx a multiple of 16 bytes worth of values, nx >= 128);
+ *  PACKED  FP32 only, two strips per thread in packed f32x2 arithmetic, bulk
+ *          copies (no force field, nx % 4 == 0, nx >= 256).
+ * AUTO picks SCALAR (the fastest measured on GB300 for the periodic 4096^2
+ * throughput case).  Asking for a variant that does not apply returns
+ * FDLBM_EUNSUPPORTED. */
+enum { FDLBM_VARIANT_AUTO = 0, FDLBM_VARIANT_SCALAR = 1, FDLBM_VARIANT_PACKED = 2,
+       FDLBM_VARIANT_TMA = 3 };
 enum { FDLBM_WALL_W = 0, FDLBM_WALL_E = 1, FDLBM_WALL_S = 2, FDLBM_WALL_N = 3 };
 
 /* Tensor-product grid (Sec. 3, Eqs. 3.9 and 3.11).  A periodic axis stores its
@@ -78,6 +89,7 @@ typedef struct {
     int has_force;            /* 1: reserve a body-acceleration field (fdlbm_set_force), Eq. 3.12 */
     int path;                 /* FDLBM_PATH_AUTO: fused kernel for periodic grids, staged otherwise */
     int rows_per_cta;         /* fused kernel tile height; 0 = automatic */
+    int variant;              /* FDLBM_VARIANT_*; PACKED where it does not apply -> EUNSUPPORTED */
     void *stream;             /* cudaStream_t used for all work; NULL = default stream */
     void *workspace;          /* caller-owned device memory of fdlbm_workspace_bytes() bytes,
                                  256-byte aligned; NULL = the library allocates its own */
@@ -154,6 +166,9 @@ long long fdlbm_steps_done(fdlbm_t h);   /* steps enqueued since creation */
 int fdlbm_path(fdlbm_t h);               /* FDLBM_PATH_FUSED or FDLBM_PATH_STAGED */
 int fdlbm_kernels_per_step(fdlbm_t h);   /* kernel launches fdlbm_step makes per step */
 const char *fdlbm_last_error(fdlbm_t h); /* never NULL */
+/* Short description of the kernel the handle runs per step, e.g.
+ * "fused-f32x2 rows=121" (never NULL; valid until the handle is destroyed). */
+const char *fdlbm_describe(fdlbm_t h);
 const char *fdlbm_status_string(fdlbm_status s);
 
 #ifdef __cplusplus

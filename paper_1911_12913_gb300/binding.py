@@ -18,6 +18,7 @@ PERIODIC, WALL = 0, 1
 FP64, FP32_DEV = 0, 1
 PATH_AUTO, PATH_FUSED, PATH_STAGED = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
+VARIANT_AUTO, VARIANT_SCALAR, VARIANT_PACKED, VARIANT_TMA = 0, 1, 2, 3
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EUNSUPPORTED"}
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -37,7 +38,7 @@ class Metrics(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("A", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("precision", ctypes.c_int), ("has_force", ctypes.c_int),
-                ("path", ctypes.c_int), ("rows_per_cta", ctypes.c_int),
+                ("path", ctypes.c_int), ("rows_per_cta", ctypes.c_int), ("variant", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -69,6 +70,7 @@ SIGNATURES = [
     ("fdlbm_path", ctypes.c_int, [_H]),
     ("fdlbm_kernels_per_step", ctypes.c_int, [_H]),
     ("fdlbm_last_error", ctypes.c_char_p, [_H]),
+    ("fdlbm_describe", ctypes.c_char_p, [_H]),
     ("fdlbm_status_string", ctypes.c_char_p, [ctypes.c_int]),
 ]
 

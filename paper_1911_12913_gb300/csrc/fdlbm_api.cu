@@ -84,14 +84,38 @@ int choose_path(const fdlbm_grid *g, const fdlbm_opts *o)
     return fused_ok(g) ? FDLBM_PATH_FUSED : FDLBM_PATH_STAGED;
 }
 
-// Rows per CTA of the fused kernel: enough CTAs for several waves on 152 SMs.
-int choose_rows(int nx, int ny)
+// Rows per CTA of the fused kernel.  Each CTA recomputes 8 halo rows, so tall
+// tiles waste less; the grid should also fill whole waves of resident CTAs.
+// Pick the height that minimises (waves) x (rows + 8), the modelled sweep time.
+int choose_rows(int nx, int ny, int precision, int variant)
 {
-    const int strips = (nx + 119) / 120;
-    const int target = 152 * 3 * 4;
-    int rows = (int)((long long)ny * strips / target);
-    rows = std::max(16, std::min(128, rows / 8 * 8));
-    return std::min(rows, ny);
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool f32 = precision == FDLBM_FP32_DEV;
+    int per_sm;
+    if (variant == FDLBM_VARIANT_PACKED)
+        per_sm = fused_x2_blocks_per_sm();
+    else if (variant == FDLBM_VARIANT_TMA)
+        per_sm = f32 ? fused_tma_blocks_per_sm<float>() : fused_tma_blocks_per_sm<double>();
+    else
+        per_sm = f32 ? fused_blocks_per_sm<float>() : fused_blocks_per_sm<double>();
+    if (per_sm <= 0) per_sm = 1;
+    const long long slots = (long long)per_sm * sms;
+    const int W = variant == FDLBM_VARIANT_PACKED ? fused_x2_tile_width() : fused_tile_width();
+    const long long strips = (nx + W - 1) / W;
+    int best = std::min(ny, 64);
+    double best_cost = 1e300;
+    for (int rows = 8; rows <= std::min(ny, 512); ++rows) {
+        const long long ctas = strips * ((ny + rows - 1) / rows);
+        const long long waves = (ctas + slots - 1) / slots;
+        const double cost = (double)waves * (rows + 8);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = rows;
+        }
+    }
+    return std::max(1, std::min(best, ny));
 }
 
 template <class R>
@@ -115,6 +139,7 @@ StepArgs<R> step_args(fdlbm_ctx *h)
     a.st = make_stencil<R>(h->beta);
     a.stc = make_stencil<R>(0.0);
     a.rows = h->rows;
+    a.err = reinterpret_cast<int *>(h->ws + h->lay.err);
     if (h->path == FDLBM_PATH_STAGED) {
         a.P = reinterpret_cast<R *>(h->ws + h->lay.P);
         a.Q = reinterpret_cast<R *>(h->ws + h->lay.Q);
@@ -160,6 +185,18 @@ fdlbm_status staged_in(fdlbm_ctx *h, const double *const *fields, int nfields, i
     return FDLBM_OK;
 }
 
+// Kernel-side failure flag (a bounded wait that gave up).  Synchronises.
+fdlbm_status check_flag(fdlbm_ctx *h)
+{
+    int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, h->ws + h->lay.err, sizeof(int), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "error flag");
+    if (flag) return fail(h, FDLBM_ECUDA, "a step kernel timed out waiting for its row copies");
+    return FDLBM_OK;
+}
+
 }  // namespace
 
 namespace fdlbm {
@@ -193,6 +230,7 @@ Layout make_layout(int nx, int ny, int pitch, int precision, int has_force, bool
     L.nblocks_red = kRedBlocks;
     L.partials = take((size_t)kRedBlocks * 3 * sizeof(double));
     L.red = take(4 * sizeof(double));
+    L.err = take(sizeof(int) * 4);
     const size_t need_rows = (size_t)9 * nx * sizeof(double);  // one row of 9 fields
     const size_t sbytes = std::max(std::min(kStagingBytes, 9 * (size_t)nx * ny * sizeof(double)),
                                    need_rows);
@@ -247,10 +285,21 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
     if (opts) o = *opts;
     if (!grid_ok(g) || !(nu > 0) || !(cfl > 0) || !(blend >= 0 && blend <= 1) ||
         !(o.A >= 0 && o.A <= 1) || !(o.rho0 > 0) ||
-        (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0)
+        (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0 ||
+        o.variant < FDLBM_VARIANT_AUTO || o.variant > FDLBM_VARIANT_TMA)
         return FDLBM_EINVAL;
     const int path = choose_path(g, &o);
     if (path < 0) return FDLBM_EUNSUPPORTED;
+    const bool fused = path == FDLBM_PATH_FUSED;
+    const bool f32 = o.precision == FDLBM_FP32_DEV;
+    const bool packed_ok = fused && f32 && !o.has_force && fused_x2_ok(g->nx, g->ny);
+    const bool tma_ok = fused && (f32 ? fused_tma_ok<float>(g->nx, g->ny)
+                                      : fused_tma_ok<double>(g->nx, g->ny));
+    if ((o.variant == FDLBM_VARIANT_PACKED && !packed_ok) ||
+        (o.variant == FDLBM_VARIANT_TMA && !tma_ok))
+        return FDLBM_EUNSUPPORTED;
+    int variant = o.variant;
+    if (variant == FDLBM_VARIANT_AUTO) variant = FDLBM_VARIANT_SCALAR;
     std::vector<double> mx(g->nx), my(g->ny);
     for (int i = 0; i < g->nx; ++i)
         mx[i] = (metrics && metrics->dzeta_dx) ? metrics->dzeta_dx[i] : 1.0 / (g->x[1] - g->x[0]);
@@ -280,7 +329,11 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
     h->rho0 = o.rho0;
     h->has_force = o.has_force ? 1 : 0;
     h->path = path;
-    h->rows = o.rows_per_cta > 0 ? std::min(o.rows_per_cta, g->ny) : choose_rows(g->nx, g->ny);
+    h->rows = 1;
+    h->variant = variant;
+    if (path == FDLBM_PATH_FUSED)
+        h->rows = o.rows_per_cta > 0 ? std::min(o.rows_per_cta, g->ny)
+                                     : choose_rows(g->nx, g->ny, o.precision, variant);
     h->stream = static_cast<cudaStream_t>(o.stream);
     h->lay = make_layout(h->nx, h->ny, h->pitch, h->precision, h->has_force,
                          path == FDLBM_PATH_STAGED);
@@ -305,6 +358,7 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
     // zero state (fluid at rest), metrics in both precisions
     cudaError_t e = cudaMemsetAsync(h->ws + h->lay.state[0], 0,
                                     h->lay.state[1] - h->lay.state[0], h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->lay.err, 0, sizeof(int) * 4, h->stream);
     if (e == cudaSuccess && h->has_force)
         e = cudaMemsetAsync(h->ws + h->lay.force, 0, 2 * h->plane * real_size(h->precision),
                             h->stream);
@@ -431,10 +485,22 @@ fdlbm_status fdlbm_step(fdlbm_t h, int n)
         cudaError_t e;
         if (h->precision == FDLBM_FP32_DEV) {
             auto a = step_args<float>(h);
-            e = h->path == FDLBM_PATH_FUSED ? launch_fused(a, h->stream) : launch_staged(a, h->stream);
+            if (h->path == FDLBM_PATH_STAGED)
+                e = launch_staged(a, h->stream);
+            else if (h->variant == FDLBM_VARIANT_PACKED)
+                e = launch_fused_x2(a, a.err, h->stream);
+            else if (h->variant == FDLBM_VARIANT_TMA)
+                e = launch_fused_tma(a, h->stream);
+            else
+                e = launch_fused(a, h->stream);
         } else {
             auto a = step_args<double>(h);
-            e = h->path == FDLBM_PATH_FUSED ? launch_fused(a, h->stream) : launch_staged(a, h->stream);
+            if (h->path == FDLBM_PATH_STAGED)
+                e = launch_staged(a, h->stream);
+            else if (h->variant == FDLBM_VARIANT_TMA)
+                e = launch_fused_tma(a, h->stream);
+            else
+                e = launch_fused(a, h->stream);
         }
         if (e != cudaSuccess) return cuda_fail(h, e, "step");
         h->cur = 1 - h->cur;
@@ -483,6 +549,8 @@ fdlbm_status fdlbm_reduce(fdlbm_t h, double *mass, double *resid)
                         h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce");
+    fdlbm_status fs = check_flag(h);
+    if (fs != FDLBM_OK) return fs;
     const double res = h->have_uprev ? std::sqrt(r[2] / r[1]) : -1.0;
     h->have_uprev = true;
     if (mass) *mass = r[0];
@@ -503,7 +571,8 @@ fdlbm_status fdlbm_sync(fdlbm_t h)
 {
     if (!h) return FDLBM_EINVAL;
     cudaError_t e = cudaStreamSynchronize(h->stream);
-    return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "sync");
+    if (e != cudaSuccess) return cuda_fail(h, e, "sync");
+    return check_flag(h);
 }
 
 double fdlbm_dt(fdlbm_t h) { return h ? h->dt : -1.0; }
@@ -518,6 +587,18 @@ int fdlbm_kernels_per_step(fdlbm_t h)
 }
 
 const char *fdlbm_last_error(fdlbm_t h) { return h ? h->err.c_str() : "NULL handle"; }
+
+const char *fdlbm_describe(fdlbm_t h)
+{
+    if (!h) return "NULL handle";
+    const char *prec = h->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64";
+    const char *kern = h->path == FDLBM_PATH_STAGED        ? "staged"
+                       : h->variant == FDLBM_VARIANT_PACKED ? "fused-f32x2"
+                       : h->variant == FDLBM_VARIANT_TMA    ? "fused-tma"
+                                                            : "fused";
+    h->desc = std::string(kern) + " " + prec + " rows=" + std::to_string(h->rows);
+    return h->desc.c_str();
+}
 
 const char *fdlbm_status_string(fdlbm_status s)
 {

@@ -26,12 +26,13 @@ struct StepArgs {
     Stencil<R> st;       // mixed weights
     Stencil<R> stc;      // central-only weights (next to walls)
     int rows;            // fused kernel: rows per CTA
+    int *err;            // kernel-side failure flag (bounded waits that gave up)
     // staged path scratch, [9][ny][pitch] each
     R *P, *Q, *S;
 };
 
 struct Layout {
-    size_t state[2], mx, my, mxd, myd, force, P, Q, S, uprev, partials, red, staging;
+    size_t state[2], mx, my, mxd, myd, force, P, Q, S, uprev, partials, red, err, staging;
     size_t staging_elems, total;
     int nblocks_red;
 };
@@ -47,6 +48,7 @@ struct fdlbm_ctx {
     double nu = 0, tau = 0, dt = 0, cfl = 0, beta = 0, A = 0.5, rho0 = 1;
     int has_force = 0;
     int path = FDLBM_PATH_FUSED;
+    int variant = FDLBM_VARIANT_SCALAR;  // fused kernel actually used
     int rows = 64;
     cudaStream_t stream = nullptr;
     char *ws = nullptr;
@@ -58,6 +60,7 @@ struct fdlbm_ctx {
     bool have_uprev = false;
     long long steps = 0;
     std::string err;
+    std::string desc;
 };
 
 namespace fdlbm {
@@ -68,6 +71,21 @@ Layout make_layout(int nx, int ny, int pitch, int precision, int has_force, bool
 // step_fused.cu
 template <class R>
 cudaError_t launch_fused(const StepArgs<R> &a, cudaStream_t s);
+int fused_tile_width();
+template <class R>
+int fused_blocks_per_sm();
+// step_fused_tma.cu (scalar sweep with bulk-copy row loads)
+template <class R>
+bool fused_tma_ok(int nx, int ny);
+template <class R>
+cudaError_t launch_fused_tma(const StepArgs<R> &a, cudaStream_t s);
+template <class R>
+int fused_tma_blocks_per_sm();
+// step_fused_x2.cu (FP32, two strips per CTA in packed f32x2, bulk-copy loads)
+bool fused_x2_ok(int nx, int ny);
+cudaError_t launch_fused_x2(const StepArgs<float> &a, int *err, cudaStream_t s);
+int fused_x2_tile_width();
+int fused_x2_blocks_per_sm();
 // step_staged.cu
 template <class R>
 cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s);

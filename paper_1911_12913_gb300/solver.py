@@ -31,8 +31,8 @@ class FDLBM:
 
     def __init__(self, xa, ya, *, nu: float, cfl: float, blend: float, A: float = 0.5,
                  precision: str = "fp64", rho0: float = 1.0, has_force: bool = False,
-                 wall_u=None, path: str = "auto", rows_per_cta: int = 0, stream=None,
-                 device=None):
+                 wall_u=None, path: str = "auto", rows_per_cta: int = 0, variant: str = "auto",
+                 stream=None, device=None):
         self._L = L = B.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.nx, self.ny = xa.n, ya.n
@@ -48,6 +48,8 @@ class FDLBM:
         o.has_force = int(has_force)
         o.path = {"auto": B.PATH_AUTO, "fused": B.PATH_FUSED, "staged": B.PATH_STAGED}[path]
         o.rows_per_cta = rows_per_cta
+        o.variant = {"auto": B.VARIANT_AUTO, "scalar": B.VARIANT_SCALAR,
+                     "packed": B.VARIANT_PACKED, "tma": B.VARIANT_TMA}[variant]
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         o.stream = self.stream.cuda_stream
         nbytes = L.fdlbm_workspace_bytes(ctypes.byref(self._grid), ctypes.byref(o))
@@ -87,6 +89,10 @@ class FDLBM:
     @property
     def path(self) -> str:
         return {B.PATH_FUSED: "fused", B.PATH_STAGED: "staged"}[self._L.fdlbm_path(self._h)]
+
+    @property
+    def describe(self) -> str:
+        return self._L.fdlbm_describe(self._h).decode()
 
     @property
     def kernels_per_step(self) -> int:

@@ -44,13 +44,31 @@ def test_every_declared_symbol_is_exported(B):
     assert set(names) == bound, set(names) ^ bound
 
 
-def test_struct_layouts_match_header(B):
-    # sizes of the C structs as laid out by the compiler (x86-64 / aarch64 LP64)
-    assert ctypes.sizeof(B.Grid) == 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4 + 64
-    assert ctypes.sizeof(B.Opts) == 8 + 8 + 4 * 4 + 8 + 8 + 8
+def test_struct_layouts_match_header(B, tmp_path):
+    """The ctypes mirrors have the size and field offsets the C compiler gives
+    the structs of include/fdlbm.h (a C program compiled against the header)."""
+    import subprocess
+    fields = {"fdlbm_grid": B.Grid, "fdlbm_metrics": B.Metrics, "fdlbm_opts": B.Opts}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fdlbm.h"', "int main(void){"]
+    for cname, py in fields.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", f"-I{ROOT / 'include'}", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in fields.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
     o = B.Opts()
     B.load().fdlbm_default_opts(ctypes.byref(o))
-    assert (o.A, o.rho0, o.precision, o.path, o.workspace) == (0.5, 1.0, B.FP64, B.PATH_AUTO, None)
+    assert (o.A, o.rho0, o.precision, o.path, o.variant, o.workspace) == \
+        (0.5, 1.0, B.FP64, B.PATH_AUTO, B.VARIANT_AUTO, None)
 
 
 def test_time_step_matches_paper_tables(B):

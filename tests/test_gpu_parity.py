@@ -106,6 +106,74 @@ def test_random_state_force_stretched_fp64(path, rows, nx, ny):
     assert rel(s.get_state(), o.f) <= FP64_TOL
 
 
+@pytest.mark.parametrize("variant", ["packed", "tma", "scalar"])
+@pytest.mark.parametrize("nx,ny,rows", [(500, 37, 0), (256, 21, 7), (964, 40, 0), (4096, 9, 0),
+                                        (260, 12, 1)])
+def test_fp32_fused_variants(variant, nx, ny, rows):
+    """FP32 fused kernels (scalar; bulk-copy rows; packed two-strip f32x2):
+    ragged strips, a strip beyond the domain, wrapped halos, stretched metrics;
+    25 steps against the FP64 oracle, with the error flag checked."""
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 0.7)
+    xa.metric = I.random_metric(nx, 41, base=nx, spread=0.3)
+    ya.metric = I.random_metric(ny, 42, base=ny / 0.7, spread=0.3)
+    s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, precision="fp32", rows_per_cta=rows,
+              variant=variant)
+    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2)
+    assert s.describe.split()[0] == {"packed": "fused-f32x2", "tma": "fused-tma",
+                                     "scalar": "fused"}[variant], s.describe
+    _init_both(s, o, I.random_fields(nx, ny, 23))
+    s.step(25)
+    o.step(25)
+    s.sync()
+    err = rel(s.get_state(), o.f)
+    print(f"{s.describe} {nx}x{ny}: rel L2(f~) = {err:.3e}")
+    assert err <= 1e-6
+
+
+@pytest.mark.parametrize("nx,ny,rows", [(256, 37, 0), (132, 21, 3), (130, 9, 1)])
+def test_fp64_tma_variant_force_stretched(nx, ny, rows):
+    """FP64 bulk-copy variant with a force field and stretched metrics."""
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 0.7)
+    xa.metric = I.random_metric(nx, 51, base=nx, spread=0.4)
+    ya.metric = I.random_metric(ny, 52, base=ny / 0.7, spread=0.4)
+    force = 1e-3 * np.random.default_rng(11).uniform(-1, 1, size=(2, ny, nx))
+    s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, has_force=True, rows_per_cta=rows,
+              variant="tma")
+    assert s.describe.startswith("fused-tma fp64"), s.describe
+    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force)
+    s.set_force(force)
+    _init_both(s, o, I.random_fields(nx, ny, 19))
+    s.step(25)
+    o.step(25)
+    s.sync()
+    assert rel(s.get_state(), o.f) <= FP64_TOL
+
+
+def test_variant_not_applicable_is_rejected():
+    xa = I.periodic_axis(130, 0.0, 1.0)   # 130 % 4 != 0: no 16-byte FP32 row pieces
+    with pytest.raises(Exception, match="EUNSUPPORTED"):
+        FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="tma")
+    with pytest.raises(Exception, match="EUNSUPPORTED"):
+        FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="packed")
+
+
+def test_scalar_fp32_fused_with_force():
+    """FP32 fused scalar kernel (body force present) against the FP64 oracle."""
+    nx, ny = 300, 33
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 0.7)
+    force = 1e-3 * np.random.default_rng(3).uniform(-1, 1, size=(2, ny, nx))
+    s, o = _pair(xa, ya, nu=0.02, cfl=0.4, beta=0.2, precision="fp32", force=force)
+    assert s.describe.startswith("fused fp32dev"), s.describe
+    _init_both(s, o, I.random_fields(nx, ny, 29))
+    s.step(25)
+    o.step(25)
+    s.sync()
+    assert rel(s.get_state(), o.f) <= 1e-6
+
+
 def test_t1s2_special_case_fp64():
     """A = 0 in the fused kernel equals the oracle's separately written T1S2 routine."""
     xa = I.periodic_axis(96, 0.0, 2 * math.pi)
@@ -206,6 +274,7 @@ def test_full_size_4096_sampled_patches(precision, tol):
     xa = I.periodic_axis(n, 0.0, 2 * math.pi)
     s = FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision=precision)
     assert s.path == "fused"
+    print(s.describe)
     fld = I.taylor_green(xa, xa, u0=0.01, phase=(0.7, 2.1))
     pert = I.random_fields(n, n, 77, du=0.002, drho=0.001, dgrad=0.001)
     for k in fld:
@@ -213,6 +282,7 @@ def test_full_size_4096_sampled_patches(precision, tol):
     grad = [fld["dudx"], fld["dudy"], fld["dvdx"], fld["dvdy"]]
     s.init_fields(fld["rho"], fld["ux"], fld["uy"], grad)
     s.step(steps)
+    s.sync()
     g = s.get_state(device=True)
     rng = np.random.default_rng(4096)
     m = 4 * steps
