@@ -42,7 +42,8 @@ typedef enum {
     FDLBM_ENOMEM = -2,        /* workspace too small, or device allocation failed */
     FDLBM_ECUDA = -3,         /* CUDA runtime error; see fdlbm_last_error() */
     FDLBM_ENONFINITE = -4,    /* a reduction met NaN or Inf (the run diverged) */
-    FDLBM_EUNSUPPORTED = -5   /* option combination not available */
+    FDLBM_EUNSUPPORTED = -5,  /* option combination not available */
+    FDLBM_ETOOBIG = -6        /* size beyond a fixed capacity (see fdlbm_reduce_noalloc) */
 } fdlbm_status;
 
 enum { FDLBM_PERIODIC = 0, FDLBM_WALL = 1 };            /* boundary kind of an axis */
@@ -170,6 +171,32 @@ const char *fdlbm_last_error(fdlbm_t h); /* never NULL */
  * "fused-f32x2 rows=121" (never NULL; valid until the handle is destroyed). */
 const char *fdlbm_describe(fdlbm_t h);
 const char *fdlbm_status_string(fdlbm_status s);
+
+/* Allocation-free reduction, for callers that cannot allocate device memory
+ * where they need it (code whose device memory is all owned by a framework's
+ * pool, a service loop that must keep a fixed footprint after start-up, a
+ * thread that may not call cudaMalloc while other work is in flight).  The
+ * paper has no counterpart; this is a library utility.
+ *
+ * Same quantities as fdlbm_reduce, computed from caller-owned device buffers:
+ *   f         device, FP64 [9][ny][nx] f~ (the fdlbm_get_state layout);
+ *   dzeta_dx, dmu_dy  device, FP64 metrics of length nx and ny;
+ *   uprev     device, FP64 [2][ny][nx] previous velocity (u then v), or NULL;
+ *   out       device, 3 FP64: Jacobian-weighted mass, residual against uprev
+ *             (-1 without uprev), sum |u|^2.  Velocities are those of Eq. 3.3
+ *             without body force.
+ * Enqueued on `stream` (cudaStream_t, NULL = default); read `out` after the
+ * stream completes.  No allocation of any kind: the scratch (3 doubles per grid
+ * row) is a fixed device array of fdlbm_reduce_noalloc_max_rows() rows that
+ * every GPU using the library holds until the process exits.  The first call on
+ * a device looks up that array's device address, so make it before any stream
+ * capture.  Every call shares the array: calls whose kernels overlap on the GPU
+ * race and give wrong results.  Errors: EINVAL (NULL pointer, nx or ny < 1),
+ * ETOOBIG (ny above the maximum), ECUDA. */
+fdlbm_status fdlbm_reduce_noalloc(const double *f, int nx, int ny, const double *dzeta_dx,
+                                  const double *dmu_dy, const double *uprev, double *out,
+                                  void *stream);
+int fdlbm_reduce_noalloc_max_rows(void);
 
 #ifdef __cplusplus
 }

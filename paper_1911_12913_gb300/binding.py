@@ -19,7 +19,8 @@ FP64, FP32_DEV = 0, 1
 PATH_AUTO, PATH_FUSED, PATH_STAGED = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 VARIANT_AUTO, VARIANT_SCALAR, VARIANT_PACKED, VARIANT_TMA = 0, 1, 2, 3
-STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EUNSUPPORTED"}
+STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EUNSUPPORTED",
+          -6: "ETOOBIG"}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -72,6 +73,10 @@ SIGNATURES = [
     ("fdlbm_last_error", ctypes.c_char_p, [_H]),
     ("fdlbm_describe", ctypes.c_char_p, [_H]),
     ("fdlbm_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("fdlbm_reduce_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
+    ("fdlbm_reduce_noalloc_max_rows", ctypes.c_int, []),
 ]
 
 _lib = None

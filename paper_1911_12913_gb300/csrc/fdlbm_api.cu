@@ -609,6 +609,7 @@ const char *fdlbm_status_string(fdlbm_status s)
     case FDLBM_ECUDA: return "CUDA error";
     case FDLBM_ENONFINITE: return "non-finite result";
     case FDLBM_EUNSUPPORTED: return "unsupported option";
+    case FDLBM_ETOOBIG: return "size beyond the fixed capacity";
     }
     return "unknown status";
 }
