@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--n", type=int, default=N_GRID)
     p.add_argument("--fp64-steps", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--variant", default="auto", choices=["auto", "scalar", "packed", "tma"],
+    p.add_argument("--variant", default="auto", choices=["auto", "scalar", "packed", "tma", "async"],
                    help="FP32 fused kernel variant for the headline timing")
     p.add_argument("--no-variants", action="store_true", help="skip timing the other variant")
     return p.parse_args()
@@ -276,7 +276,7 @@ def run_ours(args):
     # ---------------- both FP32 fused variants, same workload, shorter runs
     variants = {}
     if not args.no_variants:
-        for var in ("scalar", "tma", "packed"):
+        for var in ("scalar", "async", "tma", "packed"):
             try:
                 sv = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream,
                            variant=var)

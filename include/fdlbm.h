@@ -55,13 +55,21 @@ enum { FDLBM_MEM_HOST = 0, FDLBM_MEM_DEVICE = 1 };
  *  TMA     one column per thread, rows streamed into shared memory by bulk
  *          copies (nx a multiple of 16 bytes worth of values, nx >= 128);
  *  PACKED  FP32 only, two strips per thread in packed f32x2 arithmetic, bulk
- *          copies (no force field, nx % 4 == 0, nx >= 256).
+ *          copies (no force field, nx % 4 == 0, nx >= 256);
+ *  ASYNC   one column per thread, each thread prefetching its own column two
+ *          rows ahead with cp.async (any nx >= 4).
  * AUTO picks SCALAR (the fastest measured on GB300 for the periodic 4096^2
  * throughput case).  Asking for a variant that does not apply returns
  * FDLBM_EUNSUPPORTED. */
 enum { FDLBM_VARIANT_AUTO = 0, FDLBM_VARIANT_SCALAR = 1, FDLBM_VARIANT_PACKED = 2,
-       FDLBM_VARIANT_TMA = 3 };
+       FDLBM_VARIANT_TMA = 3, FDLBM_VARIANT_ASYNC = 4 };
 enum { FDLBM_WALL_W = 0, FDLBM_WALL_E = 1, FDLBM_WALL_S = 2, FDLBM_WALL_N = 3 };
+/* Time-marching scheme (Sec. 2A):
+ *  T2S2_1  f~(n+1) = f~+ + dt L(f*), f* at t_n + A dt (Eq. 2.23; A = 0 gives T1S2);
+ *  T2S2_2  f~(n+1) = f~+ + dt/2 [L(f^n) + L(f^{n+1})] with the characteristic
+ *          estimate of f^{n+1} over h = dt (Eq. 5.23, second sequence of Sec. 2D).
+ *          Runs on the staged kernels; A is ignored. */
+enum { FDLBM_SCHEME_T2S2_1 = 0, FDLBM_SCHEME_T2S2_2 = 1 };
 
 /* Tensor-product grid (Sec. 3, Eqs. 3.9 and 3.11).  A periodic axis stores its
  * n unique nodes (node n is node 0 shifted by the period); a walled axis stores
@@ -91,6 +99,7 @@ typedef struct {
     int path;                 /* FDLBM_PATH_AUTO: fused kernel for periodic grids, staged otherwise */
     int rows_per_cta;         /* fused kernel tile height; 0 = automatic */
     int variant;              /* FDLBM_VARIANT_*; PACKED where it does not apply -> EUNSUPPORTED */
+    int scheme;               /* FDLBM_SCHEME_T2S2_1 (default) or FDLBM_SCHEME_T2S2_2 */
     void *stream;             /* cudaStream_t used for all work; NULL = default stream */
     void *workspace;          /* caller-owned device memory of fdlbm_workspace_bytes() bytes,
                                  256-byte aligned; NULL = the library allocates its own */

@@ -18,7 +18,8 @@ PERIODIC, WALL = 0, 1
 FP64, FP32_DEV = 0, 1
 PATH_AUTO, PATH_FUSED, PATH_STAGED = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
-VARIANT_AUTO, VARIANT_SCALAR, VARIANT_PACKED, VARIANT_TMA = 0, 1, 2, 3
+SCHEME_T2S2_1, SCHEME_T2S2_2 = 0, 1
+VARIANT_AUTO, VARIANT_SCALAR, VARIANT_PACKED, VARIANT_TMA, VARIANT_ASYNC = 0, 1, 2, 3, 4
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EUNSUPPORTED",
           -6: "ETOOBIG"}
 
@@ -40,6 +41,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("A", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("precision", ctypes.c_int), ("has_force", ctypes.c_int),
                 ("path", ctypes.c_int), ("rows_per_cta", ctypes.c_int), ("variant", ctypes.c_int),
+                ("scheme", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 

@@ -79,9 +79,10 @@ bool fused_ok(const fdlbm_grid *g)
 
 int choose_path(const fdlbm_grid *g, const fdlbm_opts *o)
 {
+    const bool can_fuse = fused_ok(g) && o->scheme == FDLBM_SCHEME_T2S2_1;
     if (o->path == FDLBM_PATH_STAGED) return FDLBM_PATH_STAGED;
-    if (o->path == FDLBM_PATH_FUSED) return fused_ok(g) ? FDLBM_PATH_FUSED : -1;
-    return fused_ok(g) ? FDLBM_PATH_FUSED : FDLBM_PATH_STAGED;
+    if (o->path == FDLBM_PATH_FUSED) return can_fuse ? FDLBM_PATH_FUSED : -1;
+    return can_fuse ? FDLBM_PATH_FUSED : FDLBM_PATH_STAGED;
 }
 
 // Rows per CTA of the fused kernel.  Each CTA recomputes 8 halo rows, so tall
@@ -98,6 +99,8 @@ int choose_rows(int nx, int ny, int precision, int variant)
         per_sm = fused_x2_blocks_per_sm();
     else if (variant == FDLBM_VARIANT_TMA)
         per_sm = f32 ? fused_tma_blocks_per_sm<float>() : fused_tma_blocks_per_sm<double>();
+    else if (variant == FDLBM_VARIANT_ASYNC)
+        per_sm = f32 ? fused_async_blocks_per_sm<float>() : fused_async_blocks_per_sm<double>();
     else
         per_sm = f32 ? fused_blocks_per_sm<float>() : fused_blocks_per_sm<double>();
     if (per_sm <= 0) per_sm = 1;
@@ -135,7 +138,9 @@ StepArgs<R> step_args(fdlbm_ctx *h)
     a.bc_y = h->bc_y;
     for (int s = 0; s < 4; ++s)
         for (int k = 0; k < 2; ++k) a.wall_u[s][k] = R(h->wall_u[s][k]);
-    a.c = make_coeffs<R>(h->tau, h->dt, h->A, h->rho0);
+    // T2S2-FDLBM2 marches its characteristic estimate over h = dt
+    a.c = make_coeffs<R>(h->tau, h->dt, h->scheme == FDLBM_SCHEME_T2S2_2 ? 1.0 : h->A, h->rho0);
+    a.scheme = h->scheme;
     a.st = make_stencil<R>(h->beta);
     a.stc = make_stencil<R>(0.0);
     a.rows = h->rows;
@@ -286,7 +291,8 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
     if (!grid_ok(g) || !(nu > 0) || !(cfl > 0) || !(blend >= 0 && blend <= 1) ||
         !(o.A >= 0 && o.A <= 1) || !(o.rho0 > 0) ||
         (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0 ||
-        o.variant < FDLBM_VARIANT_AUTO || o.variant > FDLBM_VARIANT_TMA)
+        o.variant < FDLBM_VARIANT_AUTO || o.variant > FDLBM_VARIANT_ASYNC ||
+        (o.scheme != FDLBM_SCHEME_T2S2_1 && o.scheme != FDLBM_SCHEME_T2S2_2))
         return FDLBM_EINVAL;
     const int path = choose_path(g, &o);
     if (path < 0) return FDLBM_EUNSUPPORTED;
@@ -296,7 +302,8 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
     const bool tma_ok = fused && (f32 ? fused_tma_ok<float>(g->nx, g->ny)
                                       : fused_tma_ok<double>(g->nx, g->ny));
     if ((o.variant == FDLBM_VARIANT_PACKED && !packed_ok) ||
-        (o.variant == FDLBM_VARIANT_TMA && !tma_ok))
+        (o.variant == FDLBM_VARIANT_TMA && !tma_ok) ||
+        (o.variant == FDLBM_VARIANT_ASYNC && !fused))
         return FDLBM_EUNSUPPORTED;
     int variant = o.variant;
     if (variant == FDLBM_VARIANT_AUTO) variant = FDLBM_VARIANT_SCALAR;
@@ -320,6 +327,7 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
     h->bc_y = g->bc_y;
     std::memcpy(h->wall_u, g->wall_u, sizeof(h->wall_u));
     h->precision = o.precision;
+    h->scheme = o.scheme;
     h->nu = nu;
     h->tau = nu * 3.0;  // tau = nu / cs^2
     h->cfl = cfl;
@@ -491,6 +499,8 @@ fdlbm_status fdlbm_step(fdlbm_t h, int n)
                 e = launch_fused_x2(a, a.err, h->stream);
             else if (h->variant == FDLBM_VARIANT_TMA)
                 e = launch_fused_tma(a, h->stream);
+            else if (h->variant == FDLBM_VARIANT_ASYNC)
+                e = launch_fused_async(a, h->stream);
             else
                 e = launch_fused(a, h->stream);
         } else {
@@ -499,6 +509,8 @@ fdlbm_status fdlbm_step(fdlbm_t h, int n)
                 e = launch_staged(a, h->stream);
             else if (h->variant == FDLBM_VARIANT_TMA)
                 e = launch_fused_tma(a, h->stream);
+            else if (h->variant == FDLBM_VARIANT_ASYNC)
+                e = launch_fused_async(a, h->stream);
             else
                 e = launch_fused(a, h->stream);
         }
@@ -583,7 +595,9 @@ int fdlbm_kernels_per_step(fdlbm_t h)
 {
     if (!h) return -1;
     if (h->path == FDLBM_PATH_FUSED) return 1;
-    return (h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL) ? 5 : 3;
+    const bool walls = h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL;
+    if (h->scheme == FDLBM_SCHEME_T2S2_2) return walls ? 6 : 3;
+    return walls ? 5 : 3;
 }
 
 const char *fdlbm_last_error(fdlbm_t h) { return h ? h->err.c_str() : "NULL handle"; }
@@ -592,9 +606,14 @@ const char *fdlbm_describe(fdlbm_t h)
 {
     if (!h) return "NULL handle";
     const char *prec = h->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64";
+    if (h->scheme == FDLBM_SCHEME_T2S2_2) {
+        h->desc = std::string("staged-scheme2 ") + prec;
+        return h->desc.c_str();
+    }
     const char *kern = h->path == FDLBM_PATH_STAGED        ? "staged"
                        : h->variant == FDLBM_VARIANT_PACKED ? "fused-f32x2"
                        : h->variant == FDLBM_VARIANT_TMA    ? "fused-tma"
+                       : h->variant == FDLBM_VARIANT_ASYNC  ? "fused-async"
                                                             : "fused";
     h->desc = std::string(kern) + " " + prec + " rows=" + std::to_string(h->rows);
     return h->desc.c_str();

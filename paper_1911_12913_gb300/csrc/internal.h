@@ -27,6 +27,7 @@ struct StepArgs {
     Stencil<R> stc;      // central-only weights (next to walls)
     int rows;            // fused kernel: rows per CTA
     int *err;            // kernel-side failure flag (bounded waits that gave up)
+    int scheme;          // FDLBM_SCHEME_T2S2_1 / _2 (the second only on the staged path)
     // staged path scratch, [9][ny][pitch] each
     R *P, *Q, *S;
 };
@@ -45,6 +46,7 @@ struct fdlbm_ctx {
     int bc_x = 0, bc_y = 0;
     double wall_u[4][2] = {};
     int precision = FDLBM_FP64;
+    int scheme = FDLBM_SCHEME_T2S2_1;
     double nu = 0, tau = 0, dt = 0, cfl = 0, beta = 0, A = 0.5, rho0 = 1;
     int has_force = 0;
     int path = FDLBM_PATH_FUSED;
@@ -81,6 +83,11 @@ template <class R>
 cudaError_t launch_fused_tma(const StepArgs<R> &a, cudaStream_t s);
 template <class R>
 int fused_tma_blocks_per_sm();
+// step_fused_async.cu (scalar sweep, per-thread cp.async row prefetch)
+template <class R>
+cudaError_t launch_fused_async(const StepArgs<R> &a, cudaStream_t s);
+template <class R>
+int fused_async_blocks_per_sm();
 // step_fused_x2.cu (FP32, two strips per CTA in packed f32x2, bulk-copy loads)
 bool fused_x2_ok(int nx, int ny);
 cudaError_t launch_fused_x2(const StepArgs<float> &a, int *err, cudaStream_t s);

@@ -121,6 +121,7 @@ struct Coeffs {
     R b_bar, c_bar;     // fbar^{+,h} from f~ (Eq. 2.19 inverted, then Eq. 2.34)
     R b_til, c_til;     // f~+ (Eq. 2.20)
     R b_star, c_star;   // f* from fbar* (Eq. 2.32)
+    R b_phys, c_phys;   // physical f from f~ (Eq. 2.19 inverted; Eq. 2.32 with h = dt)
     R half_dt, half_h;  // force shifts of the first moment (Eq. 3.3 and its h analogue)
 };
 
@@ -141,6 +142,8 @@ __host__ inline Coeffs<R> make_coeffs(double tau, double dt, double A, double rh
     c.c_til = R(2.0 * tau * dt / (2.0 * tau + dt));
     c.b_star = R(h / (2.0 * tau + h));
     c.c_star = R(h * tau / (2.0 * tau + h));
+    c.b_phys = R(dt / (2.0 * tau + dt));
+    c.c_phys = R(tau * dt / (2.0 * tau + dt));
     c.half_dt = R(0.5 * dt);
     c.half_h = R(0.5 * h);
     return c;

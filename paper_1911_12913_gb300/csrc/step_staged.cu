@@ -9,6 +9,11 @@
 //   k_update      interior nodes   out = Q - dt xi.grad S (Eq. 2.23)
 //   k_wall_nee    wall nodes of out, Eq. 3.10 (moments of Eq. 3.3)
 //
+// T2S2-FDLBM2 (Eq. 5.23, second sequence of Sec. 2D) reuses the kernels with
+// h = dt: P holds the physical f^n (with its wall nodes extrapolated), the
+// characteristic estimate runs on f~+ (fbar^{+,h} = f~+ when h = dt), S is
+// f^{n+1}, and the update is out = Q - dt/2 xi.grad (P + S).
+//
 // Next to a wall, where the second-order upwind difference would need a node
 // outside the domain, the central difference is used alone.
 #include "internal.h"
@@ -106,13 +111,15 @@ __global__ void k_prepare(const StepArgs<R> a)
     macro<R, FORCE>(a, g, a.c.half_dt, o, drho, rho, ux, uy, Fx, Fy);
     equilibrium_dev(drho, rho, ux, uy, geq);
     if (FORCE) force_terms(a.c.rho0, geq, ux, uy, Fx, Fy, F);
+    const bool s2 = a.scheme == FDLBM_SCHEME_T2S2_2;
+    const R bP = s2 ? a.c.b_phys : a.c.b_bar, cP = s2 ? a.c.c_phys : a.c.c_bar;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const R neq = geq[i] - g[i];
-        R gb = g[i] + a.c.b_bar * neq;
+        R gb = g[i] + bP * neq;
         R gt = g[i] + a.c.b_til * neq;
         if (FORCE) {
-            gb += a.c.c_bar * F[i];
+            gb += cP * F[i];
             gt += a.c.c_til * F[i];
         }
         a.P[i * a.plane + o] = gb;
@@ -128,10 +135,12 @@ __global__ void k_star(const StepArgs<R> a)
     if (x >= a.nx || y >= a.ny) return;
     if (View<R>{a}.wall(x, y)) return;
     const size_t o = (size_t)y * a.pitch + x;
+    // source of the characteristic estimate: fbar^{+,h} (scheme 1) or f~+ (scheme 2)
+    const R *src = a.scheme == FDLBM_SCHEME_T2S2_2 ? a.Q : a.P;
     R gs[9], geq[9], F[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-        gs[i] = a.P[i * a.plane + o] - a.c.h * xi_grad(a, a.P + i * a.plane, i, x, y);
+        gs[i] = src[i * a.plane + o] - a.c.h * xi_grad(a, src + i * a.plane, i, x, y);
     R drho, rho, ux, uy, Fx, Fy;
     macro<R, FORCE>(a, gs, a.c.half_h, o, drho, rho, ux, uy, Fx, Fy);
     equilibrium_dev(drho, rho, ux, uy, geq);
@@ -152,6 +161,14 @@ __global__ void k_update(const StepArgs<R> a)
     if (x >= a.nx || y >= a.ny) return;
     if (View<R>{a}.wall(x, y)) return;
     const size_t o = (size_t)y * a.pitch + x;
+    if (a.scheme == FDLBM_SCHEME_T2S2_2) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            a.gout[i * a.plane + o] =
+                a.Q[i * a.plane + o] - a.c.half_dt * (xi_grad(a, a.P + i * a.plane, i, x, y) +
+                                                      xi_grad(a, a.S + i * a.plane, i, x, y));
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i)
         a.gout[i * a.plane + o] = a.Q[i * a.plane + o] - a.c.dt * xi_grad(a, a.S + i * a.plane, i, x, y);
@@ -207,6 +224,8 @@ cudaError_t run(const StepArgs<R> &a, cudaStream_t s)
     const int nwall = (a.bc_y == FDLBM_WALL ? 2 * a.nx : 0) +
                       (a.bc_x == FDLBM_WALL ? 2 * a.ny : 0);
     k_prepare<R, FORCE><<<grd, blk, 0, s>>>(a);
+    if (walls && a.scheme == FDLBM_SCHEME_T2S2_2)
+        k_wall_nee<R, false><<<(nwall + 127) / 128, 128, 0, s>>>(a, a.P, R(0));
     k_star<R, FORCE><<<grd, blk, 0, s>>>(a);
     if (walls) k_wall_nee<R, false><<<(nwall + 127) / 128, 128, 0, s>>>(a, a.S, R(0));
     k_update<R><<<grd, blk, 0, s>>>(a);

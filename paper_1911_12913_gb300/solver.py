@@ -27,12 +27,13 @@ class FDLBM:
     ``xa, ya``: axes with ``coords``, ``metric`` (d zeta/dx), ``periodic`` and
     ``length`` (see ``inputs.Axis``).  ``blend``: upwind weight of the mixed
     difference.  ``precision``: ``"fp64"`` or ``"fp32"`` (FP32 deviation storage).
+    ``scheme``: 1 = T2S2-FDLBM1 (Eq. 2.23, A = 0 gives T1S2), 2 = T2S2-FDLBM2 (Eq. 5.23).
     """
 
     def __init__(self, xa, ya, *, nu: float, cfl: float, blend: float, A: float = 0.5,
                  precision: str = "fp64", rho0: float = 1.0, has_force: bool = False,
                  wall_u=None, path: str = "auto", rows_per_cta: int = 0, variant: str = "auto",
-                 stream=None, device=None):
+                 scheme: int = 1, stream=None, device=None):
         self._L = L = B.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.nx, self.ny = xa.n, ya.n
@@ -48,8 +49,10 @@ class FDLBM:
         o.has_force = int(has_force)
         o.path = {"auto": B.PATH_AUTO, "fused": B.PATH_FUSED, "staged": B.PATH_STAGED}[path]
         o.rows_per_cta = rows_per_cta
+        o.scheme = {1: B.SCHEME_T2S2_1, 2: B.SCHEME_T2S2_2}[scheme]
         o.variant = {"auto": B.VARIANT_AUTO, "scalar": B.VARIANT_SCALAR,
-                     "packed": B.VARIANT_PACKED, "tma": B.VARIANT_TMA}[variant]
+                     "packed": B.VARIANT_PACKED, "tma": B.VARIANT_TMA,
+                     "async": B.VARIANT_ASYNC}[variant]
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         o.stream = self.stream.cuda_stream
         nbytes = L.fdlbm_workspace_bytes(ctypes.byref(self._grid), ctypes.byref(o))

@@ -106,7 +106,7 @@ def test_random_state_force_stretched_fp64(path, rows, nx, ny):
     assert rel(s.get_state(), o.f) <= FP64_TOL
 
 
-@pytest.mark.parametrize("variant", ["packed", "tma", "scalar"])
+@pytest.mark.parametrize("variant", ["packed", "tma", "scalar", "async"])
 @pytest.mark.parametrize("nx,ny,rows", [(500, 37, 0), (256, 21, 7), (964, 40, 0), (4096, 9, 0),
                                         (260, 12, 1)])
 def test_fp32_fused_variants(variant, nx, ny, rows):
@@ -121,7 +121,7 @@ def test_fp32_fused_variants(variant, nx, ny, rows):
               variant=variant)
     o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2)
     assert s.describe.split()[0] == {"packed": "fused-f32x2", "tma": "fused-tma",
-                                     "scalar": "fused"}[variant], s.describe
+                                     "scalar": "fused", "async": "fused-async"}[variant], s.describe
     _init_both(s, o, I.random_fields(nx, ny, 23))
     s.step(25)
     o.step(25)
@@ -131,17 +131,18 @@ def test_fp32_fused_variants(variant, nx, ny, rows):
     assert err <= 1e-6
 
 
+@pytest.mark.parametrize("variant", ["tma", "async"])
 @pytest.mark.parametrize("nx,ny,rows", [(256, 37, 0), (132, 21, 3), (130, 9, 1)])
-def test_fp64_tma_variant_force_stretched(nx, ny, rows):
-    """FP64 bulk-copy variant with a force field and stretched metrics."""
+def test_fp64_tma_variant_force_stretched(variant, nx, ny, rows):
+    """FP64 bulk-copy and cp.async variants with a force field and stretched metrics."""
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.periodic_axis(ny, 0.0, 0.7)
     xa.metric = I.random_metric(nx, 51, base=nx, spread=0.4)
     ya.metric = I.random_metric(ny, 52, base=ny / 0.7, spread=0.4)
     force = 1e-3 * np.random.default_rng(11).uniform(-1, 1, size=(2, ny, nx))
     s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, has_force=True, rows_per_cta=rows,
-              variant="tma")
-    assert s.describe.startswith("fused-tma fp64"), s.describe
+              variant=variant)
+    assert s.describe.startswith(f"fused-{variant} fp64"), s.describe
     o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force)
     s.set_force(force)
     _init_both(s, o, I.random_fields(nx, ny, 19))
@@ -149,6 +150,25 @@ def test_fp64_tma_variant_force_stretched(nx, ny, rows):
     o.step(25)
     s.sync()
     assert rel(s.get_state(), o.f) <= FP64_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-6), ("fp64", FP64_TOL)])
+@pytest.mark.parametrize("nx,ny,rows", [(133, 37, 0), (4, 9, 0), (250, 21, 1)])
+def test_async_variant_odd_sizes_with_force(precision, tol, nx, ny, rows):
+    """cp.async variant on sizes the bulk-copy kernels reject, with a force field."""
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 0.7)
+    xa.metric = I.random_metric(nx, 61, base=nx, spread=0.3)
+    force = 1e-3 * np.random.default_rng(13).uniform(-1, 1, size=(2, ny, nx))
+    s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, has_force=True, rows_per_cta=rows,
+              precision=precision, variant="async")
+    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force)
+    s.set_force(force)
+    _init_both(s, o, I.random_fields(nx, ny, 31))
+    s.step(25)
+    o.step(25)
+    s.sync()
+    assert rel(s.get_state(), o.f) <= tol
 
 
 def test_variant_not_applicable_is_rejected():
@@ -172,6 +192,45 @@ def test_scalar_fp32_fused_with_force():
     o.step(25)
     s.sync()
     assert rel(s.get_state(), o.f) <= 1e-6
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 1e-6)])
+def test_t2s2_fdlbm2_periodic_force_metrics(precision, tol):
+    """T2S2-FDLBM2 (Eq. 5.23) on the staged kernels against the oracle's second
+    sequence: random state, force field, stretched metrics."""
+    nx, ny = 70, 45
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 0.7)
+    xa.metric = I.random_metric(nx, 71, base=nx, spread=0.3)
+    ya.metric = I.random_metric(ny, 72, base=ny / 0.7, spread=0.3)
+    force = 1e-3 * np.random.default_rng(17).uniform(-1, 1, size=(2, ny, nx))
+    s = FDLBM(xa, ya, nu=0.02, cfl=0.3, blend=0.2, has_force=True, precision=precision, scheme=2)
+    assert s.describe.startswith("staged-scheme2"), s.describe
+    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force, scheme=2)
+    s.set_force(force)
+    _init_both(s, o, I.random_fields(nx, ny, 37))
+    s.step(25)
+    o.step(25)
+    assert rel(s.get_state(), o.f) <= tol
+
+
+def test_t2s2_fdlbm2_channel_walls_fp64():
+    """T2S2-FDLBM2 with Eq. 3.10 walls on the stretched channel grid of Eq. 3.9."""
+    F = 0.01
+    nu = math.sqrt(F / 80.0)
+    xa = I.periodic_axis(10, 0.0, 1.0)
+    ya = I.tanh_axis(20, 1.5)
+    force = np.zeros((2, ya.n, xa.n))
+    force[0] = F
+    s = FDLBM(xa, ya, nu=nu, cfl=0.5, blend=0.1, has_force=True, scheme=2)
+    o = O.Oracle(xa, ya, nu=nu, dt=s.dt, beta=0.1, force=force, scheme=2)
+    s.set_force(force)
+    one = np.ones((ya.n, xa.n))
+    s.init_fields(one, 0 * one, 0 * one)
+    o.init_fields(one, 0 * one, 0 * one)
+    s.step(200)
+    o.step(200)
+    assert rel(s.get_state(), o.f) <= FP64_TOL
 
 
 def test_t1s2_special_case_fp64():
