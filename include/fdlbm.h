@@ -181,6 +181,48 @@ const char *fdlbm_last_error(fdlbm_t h); /* never NULL */
 const char *fdlbm_describe(fdlbm_t h);
 const char *fdlbm_status_string(fdlbm_status s);
 
+/* ---------------------------------------------------------------------------
+ * Batched mode: many independent cases (uneven sizes, walls, forces, Reynolds
+ * numbers) advanced together.  Every case is an ordinary handle whose memory
+ * lies inside one batch workspace: the per-case calls (fdlbm_init_fields,
+ * fdlbm_set_force, fdlbm_get_state, fdlbm_moments, fdlbm_reduce, fdlbm_dt) work
+ * on fdlbm_batch_case(b, c); stepping, the stream and destruction belong to the
+ * batch (fdlbm_step / fdlbm_set_stream on a case return EUNSUPPORTED,
+ * fdlbm_destroy ignores it).  All cases run the staged kernels of their own
+ * scheme (Sec. 2D), each with its own dt (Eq. 3.1); one batch step advances
+ * every case by one of its own time steps.
+ * ------------------------------------------------------------------------- */
+typedef struct fdlbm_batch_ctx *fdlbm_batch_t;
+
+/* Device bytes of the batch workspace (0 if any case is invalid).  opts may be
+ * NULL (defaults) or an array of ncases option blocks. */
+size_t fdlbm_batch_workspace_bytes(int ncases, const fdlbm_grid *grids, const fdlbm_opts *opts);
+
+/* Create a batch.  grids, nu, cfl, blend: arrays of ncases; metrics and opts:
+ * arrays of ncases or NULL.  All cases must share one precision.  The stream is
+ * opts[0].stream, or a private non-blocking stream when NULL (graph capture
+ * needs a non-legacy stream).  graph_steps > 0: fdlbm_batch_step replays a CUDA
+ * graph of that many steps (rounded up to even) captured on first use, and
+ * launches any remainder directly.  autotune != 0: time a few block shapes of
+ * the node kernels on this batch and keep the fastest (cached per batch
+ * signature for the process); the states are reset to rest afterwards.
+ * workspace: caller device memory of fdlbm_batch_workspace_bytes() bytes,
+ * 256-byte aligned, or NULL (the library allocates). */
+fdlbm_status fdlbm_batch_create(int ncases, const fdlbm_grid *grids, const fdlbm_metrics *metrics,
+                                const double *nu, const double *cfl, const double *blend,
+                                const fdlbm_opts *opts, int graph_steps, int autotune,
+                                void *workspace, size_t workspace_bytes, fdlbm_batch_t *out);
+fdlbm_t fdlbm_batch_case(fdlbm_batch_t b, int c);    /* NULL if out of range */
+int fdlbm_batch_size(fdlbm_batch_t b);
+long long fdlbm_batch_cells(fdlbm_batch_t b);        /* nodes of all cases */
+/* Advance every case by n steps (asynchronous on the batch stream). */
+fdlbm_status fdlbm_batch_step(fdlbm_batch_t b, int n);
+fdlbm_status fdlbm_batch_sync(fdlbm_batch_t b);
+void *fdlbm_batch_stream(fdlbm_batch_t b);           /* cudaStream_t of the batch */
+const char *fdlbm_batch_describe(fdlbm_batch_t b);
+const char *fdlbm_batch_last_error(fdlbm_batch_t b);
+void fdlbm_batch_destroy(fdlbm_batch_t b);           /* NULL-safe; releases every case */
+
 /* Allocation-free reduction, for callers that cannot allocate device memory
  * where they need it (code whose device memory is all owned by a framework's
  * pool, a service loop that must keep a fixed footprint after start-up, a

@@ -24,7 +24,7 @@ __all__ = [
     "Axis", "periodic_axis", "wall_axis", "tanh_axis", "min_spacing",
     "taylor_green", "taylor_green_velocity", "poiseuille_velocity",
     "random_fields", "random_metric", "spectral_vorticity_velocity",
-    "batched_cases",
+    "batched_cases", "batched_problem",
 ]
 
 
@@ -222,6 +222,30 @@ class Case:
     re: float
     stretched: bool
     extra: dict = field(default_factory=dict)
+
+
+def batched_problem(case: "Case", *, U: float = 0.1, c: float = 1.5) -> dict:
+    """Problem data of one batched case: axes, viscosity from the Reynolds
+    number, wall velocities, and the uniform driving acceleration of a channel.
+
+    cavity: unit square, walls on all sides, lid (north wall) speed U,
+    nu = U / Re; tanh-clustered at the walls when ``stretched`` (Eq. 3.11 with
+    the symmetric parameterisation), else uniform.
+    channel: unit-height channel, periodic x with n nodes over the same length,
+    walls in y (tanh map of Eq. 3.9 when ``stretched``), centre-line speed U,
+    nu = U / Re, acceleration F = 8 nu U / H^2 (from Eq. 3.7).
+    """
+    n = case.n
+    if case.kind == "cavity":
+        ax = tanh_axis(n, c) if case.stretched else wall_axis(n, 0.0, 1.0)
+        return dict(xa=ax, ya=ax, nu=U / case.re, wall_u=[(0.0, 0.0)] * 3 + [(U, 0.0)],
+                    force=None)
+    xa = periodic_axis(n, 0.0, 1.0)
+    ya = tanh_axis(n, c) if case.stretched else wall_axis(n, 0.0, 1.0)
+    nu = U / case.re
+    force = np.zeros((2, ya.n, xa.n))
+    force[0] = 8.0 * nu * U
+    return dict(xa=xa, ya=ya, nu=nu, wall_u=None, force=force)
 
 
 def batched_cases(count: int, seed: int, *, nmin: int = 33, nmax: int = 513,

@@ -9,7 +9,7 @@ from .binding import FdlbmError, load  # noqa: F401
 
 
 def __getattr__(name):
-    if name == "FDLBM":
-        from .solver import FDLBM
-        return FDLBM
+    if name in ("FDLBM", "FDLBMBatch"):
+        from . import solver
+        return getattr(solver, name)
     raise AttributeError(name)

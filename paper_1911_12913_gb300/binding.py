@@ -75,6 +75,21 @@ SIGNATURES = [
     ("fdlbm_last_error", ctypes.c_char_p, [_H]),
     ("fdlbm_describe", ctypes.c_char_p, [_H]),
     ("fdlbm_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("fdlbm_batch_workspace_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(Grid),
+                                                      ctypes.POINTER(Opts)]),
+    ("fdlbm_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Grid), ctypes.POINTER(Metrics),
+                                          _dp, _dp, _dp, ctypes.POINTER(Opts), ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.POINTER(_H)]),
+    ("fdlbm_batch_case", _H, [_H, ctypes.c_int]),
+    ("fdlbm_batch_size", ctypes.c_int, [_H]),
+    ("fdlbm_batch_cells", ctypes.c_longlong, [_H]),
+    ("fdlbm_batch_step", ctypes.c_int, [_H, ctypes.c_int]),
+    ("fdlbm_batch_sync", ctypes.c_int, [_H]),
+    ("fdlbm_batch_stream", ctypes.c_void_p, [_H]),
+    ("fdlbm_batch_describe", ctypes.c_char_p, [_H]),
+    ("fdlbm_batch_last_error", ctypes.c_char_p, [_H]),
+    ("fdlbm_batch_destroy", None, [_H]),
     ("fdlbm_reduce_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p]),

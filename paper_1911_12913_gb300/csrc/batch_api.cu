@@ -1,0 +1,449 @@
+// Batched mode of the C ABI (fdlbm_batch_*, declared in include/fdlbm.h):
+// many independent cases in one workspace, advanced together by the batched
+// staged kernels, with a fixed number of steps captured once into a CUDA graph
+// and replayed, and a small autotuner for the block shape of the node kernels.
+//
+// Each case is an ordinary handle (fdlbm_t) whose memory lies inside the batch
+// workspace, so the per-case calls (init_fields, set_force, get_state,
+// moments, reduce) work unchanged on fdlbm_batch_case(b, c); only stepping is
+// reserved to the batch, which keeps every case on the same ping-pong parity.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "staged_nodes.cuh"
+
+using namespace fdlbm;
+
+struct fdlbm_batch_ctx {
+    std::vector<fdlbm_ctx *> cases;
+    std::vector<size_t> off;
+    int precision = FDLBM_FP64;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool owns_ws = false;
+    cudaStream_t stream = nullptr;
+    bool owns_stream = false;
+    void *d_args = nullptr;    // 2 x ncases argument blocks
+    int *d_ints = nullptr;     // blk_case | blk_start | tiles_x | wall_start
+    size_t d_ints_cap = 0;
+    BatchTables tab{};
+    dim3 blk{32, 8, 1};
+    int graph_steps = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long steps = 0;
+    bool tuned = false;
+    double tuned_ms = -1.0;
+    std::string err, desc;
+};
+
+namespace {
+
+constexpr size_t kAlignB = 256;
+size_t align_b(size_t v) { return (v + kAlignB - 1) / kAlignB * kAlignB; }
+
+size_t args_size(int precision)
+{
+    return precision == FDLBM_FP32_DEV ? sizeof(StepArgs<float>) : sizeof(StepArgs<double>);
+}
+
+fdlbm_status bfail(fdlbm_batch_ctx *b, fdlbm_status s, const std::string &what)
+{
+    b->err = what;
+    return s;
+}
+
+// Host-side tables for block shape `blk`, uploaded to the device.
+fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk)
+{
+    const int n = (int)b->cases.size();
+    std::vector<int> blk_start(n), tiles_x(n), wall_start(n), blk_case;
+    int total_wall = 0;
+    bool any2 = false;
+    for (int c = 0; c < n; ++c) {
+        const fdlbm_ctx *h = b->cases[c];
+        const int tx = (h->nx + (int)blk.x - 1) / (int)blk.x;
+        const int ty = (h->ny + (int)blk.y - 1) / (int)blk.y;
+        blk_start[c] = (int)blk_case.size();
+        tiles_x[c] = tx;
+        blk_case.insert(blk_case.end(), (size_t)tx * ty, c);
+        wall_start[c] = total_wall;
+        const bool wy = h->bc_y == FDLBM_WALL, wx = h->bc_x == FDLBM_WALL;
+        total_wall += (wy ? 2 * h->nx : 0) + (wx ? 2 * (wy ? h->ny - 2 : h->ny) : 0);
+        any2 = any2 || h->scheme == FDLBM_SCHEME_T2S2_2;
+    }
+    const size_t nints = blk_case.size() + 3 * (size_t)n;
+    if (nints > b->d_ints_cap) {
+        if (b->d_ints) cudaFree(b->d_ints);
+        b->d_ints = nullptr;
+        if (cudaMalloc(&b->d_ints, nints * sizeof(int)) != cudaSuccess)
+            return bfail(b, FDLBM_ENOMEM, "batch: table allocation failed");
+        b->d_ints_cap = nints;
+    }
+    std::vector<int> all;
+    all.reserve(nints);
+    all.insert(all.end(), blk_case.begin(), blk_case.end());
+    all.insert(all.end(), blk_start.begin(), blk_start.end());
+    all.insert(all.end(), tiles_x.begin(), tiles_x.end());
+    all.insert(all.end(), wall_start.begin(), wall_start.end());
+    if (cudaMemcpy(b->d_ints, all.data(), nints * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bfail(b, FDLBM_ECUDA, "batch: table upload failed");
+    // argument blocks for both parities (every case at cur = 0 for even steps)
+    const size_t as = args_size(b->precision);
+    std::vector<unsigned char> host(2 * n * as);
+    for (int p = 0; p < 2; ++p)
+        for (int c = 0; c < n; ++c) {
+            fdlbm_ctx *h = b->cases[c];
+            const int saved = h->cur;
+            h->cur = p;
+            if (b->precision == FDLBM_FP32_DEV) {
+                StepArgs<float> a = handle_step_args<float>(h);
+                std::memcpy(&host[(p * n + c) * as], &a, as);
+            } else {
+                StepArgs<double> a = handle_step_args<double>(h);
+                std::memcpy(&host[(p * n + c) * as], &a, as);
+            }
+            h->cur = saved;
+        }
+    if (cudaMemcpy(b->d_args, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bfail(b, FDLBM_ECUDA, "batch: argument upload failed");
+    const int nb = (int)blk_case.size();
+    b->tab.args[0] = b->d_args;
+    b->tab.args[1] = static_cast<char *>(b->d_args) + n * as;
+    b->tab.blk_case = b->d_ints;
+    b->tab.blk_start = b->d_ints + nb;
+    b->tab.tiles_x = b->d_ints + nb + n;
+    b->tab.wall_start = b->d_ints + nb + 2 * n;
+    b->tab.ncases = n;
+    b->tab.total_blocks = nb;
+    b->tab.total_wall = total_wall;
+    b->tab.any_scheme2 = any2;
+    b->blk = blk;
+    return FDLBM_OK;
+}
+
+cudaError_t launch_one(fdlbm_batch_ctx *b, int parity)
+{
+    return b->precision == FDLBM_FP32_DEV ? launch_batched<float>(b->tab, parity, b->blk, b->stream)
+                                          : launch_batched<double>(b->tab, parity, b->blk, b->stream);
+}
+
+void advance_bookkeeping(fdlbm_batch_ctx *b, long long n)
+{
+    b->steps += n;
+    for (fdlbm_ctx *h : b->cases) {
+        if (n & 1) h->cur = 1 - h->cur;
+        h->steps += n;
+    }
+}
+
+fdlbm_status step_direct(fdlbm_batch_ctx *b, int n)
+{
+    for (int k = 0; k < n; ++k) {
+        cudaError_t e = launch_one(b, (int)(b->steps & 1));
+        if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, std::string("batch step: ") + cudaGetErrorString(e));
+        advance_bookkeeping(b, 1);
+    }
+    return FDLBM_OK;
+}
+
+void drop_graph(fdlbm_batch_ctx *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Capture graph_steps batch steps starting from an even step.
+fdlbm_status capture(fdlbm_batch_ctx *b)
+{
+    drop_graph(b);
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+    cudaError_t el = cudaSuccess;
+    for (int k = 0; k < b->graph_steps && el == cudaSuccess; ++k) el = launch_one(b, k & 1);
+    e = cudaStreamEndCapture(b->stream, &b->graph);
+    if (el != cudaSuccess || e != cudaSuccess) {
+        drop_graph(b);
+        return bfail(b, FDLBM_ECUDA, "capture failed");
+    }
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        drop_graph(b);
+        return bfail(b, FDLBM_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return FDLBM_OK;
+}
+
+std::string signature(const fdlbm_batch_ctx *b)
+{
+    std::ostringstream os;
+    os << b->precision;
+    for (const fdlbm_ctx *h : b->cases)
+        os << ';' << h->nx << 'x' << h->ny << ':' << h->bc_x << h->bc_y << h->has_force << h->scheme;
+    return os.str();
+}
+
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<dim3, double>> g_tune_cache;
+
+// Reset every case to fluid at rest (after tuning runs on the state).
+fdlbm_status reset_states(fdlbm_batch_ctx *b)
+{
+    for (fdlbm_ctx *h : b->cases) {
+        const size_t sz = h->lay.state[1] - h->lay.state[0];
+        cudaError_t e = cudaMemsetAsync(h->ws + h->lay.state[0], 0, 2 * sz, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->lay.err, 0, 4 * sizeof(int), b->stream);
+        if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, "reset");
+        h->cur = 0;
+        h->steps = 0;
+        h->have_uprev = false;
+    }
+    b->steps = 0;
+    return cudaStreamSynchronize(b->stream) == cudaSuccess ? FDLBM_OK
+                                                           : bfail(b, FDLBM_ECUDA, "reset sync");
+}
+
+// Time each candidate block shape on the batch as created and keep the fastest.
+fdlbm_status autotune(fdlbm_batch_ctx *b)
+{
+    const std::string key = signature(b);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            b->tuned = true;
+            b->tuned_ms = it->second.second;
+            return build_tables(b, it->second.first);
+        }
+    }
+    const dim3 cand[] = {dim3(32, 8), dim3(64, 4), dim3(128, 2), dim3(32, 4), dim3(16, 16), dim3(256, 1)};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    dim3 best = cand[0];
+    float best_ms = 1e30f;
+    for (const dim3 &c : cand) {
+        fdlbm_status st = build_tables(b, c);
+        if (st == FDLBM_OK) st = step_direct(b, 2);
+        if (st != FDLBM_OK) break;
+        cudaEventRecord(e0, b->stream);
+        st = step_direct(b, 6);
+        cudaEventRecord(e1, b->stream);
+        if (st != FDLBM_OK || cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tuned = true;
+    b->tuned_ms = best_ms / 6.0;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = {best, b->tuned_ms};
+    }
+    fdlbm_status st = build_tables(b, best);
+    if (st != FDLBM_OK) return st;
+    return reset_states(b);
+}
+
+void release(fdlbm_batch_ctx *b)
+{
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    for (fdlbm_ctx *h : b->cases) delete h;
+    if (b->d_args) cudaFree(b->d_args);
+    if (b->d_ints) cudaFree(b->d_ints);
+    if (b->owns_ws && b->ws) cudaFree(b->ws);
+    if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fdlbm_batch_workspace_bytes(int ncases, const fdlbm_grid *grids, const fdlbm_opts *opts)
+{
+    if (ncases <= 0 || !grids) return 0;
+    size_t total = 0;
+    for (int c = 0; c < ncases; ++c) {
+        fdlbm_opts o;
+        fdlbm_default_opts(&o);
+        if (opts) o = opts[c];
+        o.path = FDLBM_PATH_STAGED;
+        const size_t s = fdlbm_workspace_bytes(&grids[c], &o);
+        if (s == 0) return 0;
+        total += align_b(s);
+    }
+    return total;
+}
+
+fdlbm_status fdlbm_batch_create(int ncases, const fdlbm_grid *grids, const fdlbm_metrics *metrics,
+                                const double *nu, const double *cfl, const double *blend,
+                                const fdlbm_opts *opts, int graph_steps, int autotune_blocks,
+                                void *workspace, size_t workspace_bytes, fdlbm_batch_t *out)
+{
+    if (!out || ncases <= 0 || !grids || !nu || !cfl || !blend || graph_steps < 0)
+        return FDLBM_EINVAL;
+    *out = nullptr;
+    fdlbm_batch_ctx *b = new (std::nothrow) fdlbm_batch_ctx();
+    if (!b) return FDLBM_ENOMEM;
+    std::vector<std::vector<double>> mxs(ncases), mys(ncases);
+    size_t total = 0;
+    for (int c = 0; c < ncases; ++c) {
+        fdlbm_opts o;
+        fdlbm_default_opts(&o);
+        if (opts) o = opts[c];
+        o.workspace = nullptr;
+        if (c > 0 && o.precision != b->precision) {
+            release(b);
+            return FDLBM_EINVAL;  // one precision per batch
+        }
+        b->precision = o.precision;
+        fdlbm_ctx *h = nullptr;
+        fdlbm_status st = handle_prepare(&grids[c], metrics ? &metrics[c] : nullptr, nu[c], cfl[c],
+                                         blend[c], o, true, &h, mxs[c], mys[c]);
+        if (st != FDLBM_OK) {
+            release(b);
+            return st;
+        }
+        h->in_batch = true;
+        b->cases.push_back(h);
+        b->off.push_back(total);
+        total += align_b(h->lay.total);
+    }
+    // stream: the caller's, or a private one (graph capture needs a non-legacy stream)
+    fdlbm_opts o0;
+    fdlbm_default_opts(&o0);
+    if (opts) o0 = opts[0];
+    b->stream = static_cast<cudaStream_t>(o0.stream);
+    if (!b->stream) {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            release(b);
+            return FDLBM_ECUDA;
+        }
+        b->owns_stream = true;
+    }
+    if (workspace) {
+        if (workspace_bytes < total || reinterpret_cast<uintptr_t>(workspace) % kAlignB) {
+            release(b);
+            return FDLBM_ENOMEM;
+        }
+        b->ws = static_cast<char *>(workspace);
+        b->ws_bytes = workspace_bytes;
+    } else {
+        if (cudaMalloc(&b->ws, total) != cudaSuccess) {
+            release(b);
+            return FDLBM_ENOMEM;
+        }
+        b->owns_ws = true;
+        b->ws_bytes = total;
+    }
+    for (int c = 0; c < ncases; ++c) {
+        fdlbm_ctx *h = b->cases[c];
+        h->ws = b->ws + b->off[c];
+        h->ws_bytes = h->lay.total;
+        h->stream = b->stream;
+        if (handle_upload(h, mxs[c], mys[c]) != FDLBM_OK) {
+            release(b);
+            return FDLBM_ECUDA;
+        }
+    }
+    if (cudaMalloc(&b->d_args, 2 * ncases * args_size(b->precision)) != cudaSuccess) {
+        release(b);
+        return FDLBM_ENOMEM;
+    }
+    b->graph_steps = graph_steps + (graph_steps & 1);  // even: starts and ends on the same parity
+    fdlbm_status st = autotune_blocks ? autotune(b) : build_tables(b, dim3(32, 8));
+    if (st != FDLBM_OK) {
+        release(b);
+        return st;
+    }
+    *out = b;
+    return FDLBM_OK;
+}
+
+fdlbm_t fdlbm_batch_case(fdlbm_batch_t b, int c)
+{
+    if (!b || c < 0 || c >= (int)b->cases.size()) return nullptr;
+    return b->cases[c];
+}
+
+int fdlbm_batch_size(fdlbm_batch_t b) { return b ? (int)b->cases.size() : -1; }
+
+long long fdlbm_batch_cells(fdlbm_batch_t b)
+{
+    if (!b) return -1;
+    long long n = 0;
+    for (const fdlbm_ctx *h : b->cases) n += (long long)h->nx * h->ny;
+    return n;
+}
+
+fdlbm_status fdlbm_batch_step(fdlbm_batch_t b, int n)
+{
+    if (!b) return FDLBM_EINVAL;
+    if (n < 0) return bfail(b, FDLBM_EINVAL, "batch step: n < 0");
+    if ((b->steps & 1) && n > 0) {  // realign on an even step for the graph
+        fdlbm_status st = step_direct(b, 1);
+        if (st != FDLBM_OK) return st;
+        --n;
+    }
+    if (b->graph_steps > 0 && n >= b->graph_steps) {
+        if (!b->exec) {
+            fdlbm_status st = capture(b);
+            if (st != FDLBM_OK) return st;
+        }
+        while (n >= b->graph_steps) {
+            cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+            if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+            advance_bookkeeping(b, b->graph_steps);
+            n -= b->graph_steps;
+        }
+    }
+    return step_direct(b, n);
+}
+
+fdlbm_status fdlbm_batch_sync(fdlbm_batch_t b)
+{
+    if (!b) return FDLBM_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? FDLBM_OK : bfail(b, FDLBM_ECUDA, cudaGetErrorString(e));
+}
+
+void *fdlbm_batch_stream(fdlbm_batch_t b) { return b ? (void *)b->stream : nullptr; }
+
+const char *fdlbm_batch_describe(fdlbm_batch_t b)
+{
+    if (!b) return "NULL batch";
+    std::ostringstream os;
+    os << "batched-staged " << (b->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64")
+       << " cases=" << b->cases.size() << " block=" << b->blk.x << "x" << b->blk.y
+       << " graph_steps=" << b->graph_steps << " launches_per_step="
+       << (3 + (b->tab.total_wall > 0 ? 2 : 0) + (b->tab.total_wall > 0 && b->tab.any_scheme2 ? 1 : 0));
+    if (b->tuned) os << " tuned_ms_per_step=" << b->tuned_ms;
+    b->desc = os.str();
+    return b->desc.c_str();
+}
+
+const char *fdlbm_batch_last_error(fdlbm_batch_t b) { return b ? b->err.c_str() : "NULL batch"; }
+
+void fdlbm_batch_destroy(fdlbm_batch_t b)
+{
+    if (b) release(b);
+}
+
+}  // extern "C"

@@ -245,6 +245,115 @@ Layout make_layout(int nx, int ny, int pitch, int precision, int has_force, bool
     return L;
 }
 
+// Validate the arguments and fill a new handle (no device work).  With
+// force_staged the staged kernels are used whatever the grid (batched cases).
+fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, double nu,
+                            double cfl, double blend, const fdlbm_opts &o, bool force_staged,
+                            fdlbm_ctx **out, std::vector<double> &mx, std::vector<double> &my)
+{
+    if (!grid_ok(g) || !(nu > 0) || !(cfl > 0) || !(blend >= 0 && blend <= 1) ||
+        !(o.A >= 0 && o.A <= 1) || !(o.rho0 > 0) ||
+        (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0 ||
+        o.variant < FDLBM_VARIANT_AUTO || o.variant > FDLBM_VARIANT_ASYNC ||
+        (o.scheme != FDLBM_SCHEME_T2S2_1 && o.scheme != FDLBM_SCHEME_T2S2_2))
+        return FDLBM_EINVAL;
+    const int path = force_staged ? FDLBM_PATH_STAGED : choose_path(g, &o);
+    if (path < 0) return FDLBM_EUNSUPPORTED;
+    const bool fused = path == FDLBM_PATH_FUSED;
+    const bool f32 = o.precision == FDLBM_FP32_DEV;
+    const bool packed_ok = fused && f32 && !o.has_force && fused_x2_ok(g->nx, g->ny);
+    const bool tma_ok = fused && (f32 ? fused_tma_ok<float>(g->nx, g->ny)
+                                      : fused_tma_ok<double>(g->nx, g->ny));
+    if ((o.variant == FDLBM_VARIANT_PACKED && !packed_ok) ||
+        (o.variant == FDLBM_VARIANT_TMA && !tma_ok) ||
+        (o.variant == FDLBM_VARIANT_ASYNC && !fused))
+        return FDLBM_EUNSUPPORTED;
+    int variant = o.variant;
+    if (variant == FDLBM_VARIANT_AUTO) variant = FDLBM_VARIANT_SCALAR;
+    mx.assign(g->nx, 0.0);
+    my.assign(g->ny, 0.0);
+    for (int i = 0; i < g->nx; ++i)
+        mx[i] = (metrics && metrics->dzeta_dx) ? metrics->dzeta_dx[i] : 1.0 / (g->x[1] - g->x[0]);
+    for (int j = 0; j < g->ny; ++j)
+        my[j] = (metrics && metrics->dmu_dy) ? metrics->dmu_dy[j] : 1.0 / (g->y[1] - g->y[0]);
+    for (double v : mx)
+        if (!(v > 0) || !std::isfinite(v)) return FDLBM_EINVAL;
+    for (double v : my)
+        if (!(v > 0) || !std::isfinite(v)) return FDLBM_EINVAL;
+
+    fdlbm_ctx *h = new (std::nothrow) fdlbm_ctx();
+    if (!h) return FDLBM_ENOMEM;
+    h->nx = g->nx;
+    h->ny = g->ny;
+    h->pitch = pitch_of(g->nx);
+    h->plane = (size_t)h->pitch * h->ny;
+    h->bc_x = g->bc_x;
+    h->bc_y = g->bc_y;
+    std::memcpy(h->wall_u, g->wall_u, sizeof(h->wall_u));
+    h->precision = o.precision;
+    h->scheme = o.scheme;
+    h->nu = nu;
+    h->tau = nu * 3.0;  // tau = nu / cs^2
+    h->cfl = cfl;
+    h->dt = fdlbm_time_step(g, cfl);
+    h->beta = blend;
+    h->A = o.A;
+    h->rho0 = o.rho0;
+    h->has_force = o.has_force ? 1 : 0;
+    h->path = path;
+    h->rows = 1;
+    h->variant = variant;
+    if (path == FDLBM_PATH_FUSED)
+        h->rows = o.rows_per_cta > 0 ? std::min(o.rows_per_cta, g->ny)
+                                     : choose_rows(g->nx, g->ny, o.precision, variant);
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    h->lay = make_layout(h->nx, h->ny, h->pitch, h->precision, h->has_force,
+                         path == FDLBM_PATH_STAGED);
+    cudaGetDevice(&h->device);
+    *out = h;
+    return FDLBM_OK;
+}
+
+// Zero the state (fluid at rest) and the force, clear the error flag, upload
+// the metrics in both precisions.  h->ws must be attached.  Synchronises.
+fdlbm_status handle_upload(fdlbm_ctx *h, const std::vector<double> &mx, const std::vector<double> &my)
+{
+    cudaError_t e = cudaMemsetAsync(h->ws + h->lay.state[0], 0,
+                                    h->lay.state[1] - h->lay.state[0], h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->ws + h->lay.state[1], 0, h->lay.state[1] - h->lay.state[0], h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->lay.err, 0, sizeof(int) * 4, h->stream);
+    if (e == cudaSuccess && h->has_force)
+        e = cudaMemsetAsync(h->ws + h->lay.force, 0, 2 * h->plane * real_size(h->precision),
+                            h->stream);
+    if (e == cudaSuccess) {
+        if (h->precision == FDLBM_FP32_DEV) {
+            std::vector<float> fx(mx.begin(), mx.end()), fy(my.begin(), my.end());
+            e = cudaMemcpy(h->ws + h->lay.mx, fx.data(), fx.size() * 4, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(h->ws + h->lay.my, fy.data(), fy.size() * 4, cudaMemcpyHostToDevice);
+        } else {
+            e = cudaMemcpy(h->ws + h->lay.mx, mx.data(), mx.size() * 8, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(h->ws + h->lay.my, my.data(), my.size() * 8, cudaMemcpyHostToDevice);
+        }
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->ws + h->lay.mxd, mx.data(), mx.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h->ws + h->lay.myd, my.data(), my.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? FDLBM_OK : FDLBM_ECUDA;
+}
+
+template <class R>
+StepArgs<R> handle_step_args(fdlbm_ctx *h)
+{
+    return step_args<R>(h);
+}
+template StepArgs<float> handle_step_args<float>(fdlbm_ctx *);
+template StepArgs<double> handle_step_args<double>(fdlbm_ctx *);
+
 }  // namespace fdlbm
 
 extern "C" {
@@ -288,64 +397,10 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
     fdlbm_opts o;
     fdlbm_default_opts(&o);
     if (opts) o = *opts;
-    if (!grid_ok(g) || !(nu > 0) || !(cfl > 0) || !(blend >= 0 && blend <= 1) ||
-        !(o.A >= 0 && o.A <= 1) || !(o.rho0 > 0) ||
-        (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0 ||
-        o.variant < FDLBM_VARIANT_AUTO || o.variant > FDLBM_VARIANT_ASYNC ||
-        (o.scheme != FDLBM_SCHEME_T2S2_1 && o.scheme != FDLBM_SCHEME_T2S2_2))
-        return FDLBM_EINVAL;
-    const int path = choose_path(g, &o);
-    if (path < 0) return FDLBM_EUNSUPPORTED;
-    const bool fused = path == FDLBM_PATH_FUSED;
-    const bool f32 = o.precision == FDLBM_FP32_DEV;
-    const bool packed_ok = fused && f32 && !o.has_force && fused_x2_ok(g->nx, g->ny);
-    const bool tma_ok = fused && (f32 ? fused_tma_ok<float>(g->nx, g->ny)
-                                      : fused_tma_ok<double>(g->nx, g->ny));
-    if ((o.variant == FDLBM_VARIANT_PACKED && !packed_ok) ||
-        (o.variant == FDLBM_VARIANT_TMA && !tma_ok) ||
-        (o.variant == FDLBM_VARIANT_ASYNC && !fused))
-        return FDLBM_EUNSUPPORTED;
-    int variant = o.variant;
-    if (variant == FDLBM_VARIANT_AUTO) variant = FDLBM_VARIANT_SCALAR;
-    std::vector<double> mx(g->nx), my(g->ny);
-    for (int i = 0; i < g->nx; ++i)
-        mx[i] = (metrics && metrics->dzeta_dx) ? metrics->dzeta_dx[i] : 1.0 / (g->x[1] - g->x[0]);
-    for (int j = 0; j < g->ny; ++j)
-        my[j] = (metrics && metrics->dmu_dy) ? metrics->dmu_dy[j] : 1.0 / (g->y[1] - g->y[0]);
-    for (double v : mx)
-        if (!(v > 0) || !std::isfinite(v)) return FDLBM_EINVAL;
-    for (double v : my)
-        if (!(v > 0) || !std::isfinite(v)) return FDLBM_EINVAL;
-
-    fdlbm_ctx *h = new (std::nothrow) fdlbm_ctx();
-    if (!h) return FDLBM_ENOMEM;
-    h->nx = g->nx;
-    h->ny = g->ny;
-    h->pitch = pitch_of(g->nx);
-    h->plane = (size_t)h->pitch * h->ny;
-    h->bc_x = g->bc_x;
-    h->bc_y = g->bc_y;
-    std::memcpy(h->wall_u, g->wall_u, sizeof(h->wall_u));
-    h->precision = o.precision;
-    h->scheme = o.scheme;
-    h->nu = nu;
-    h->tau = nu * 3.0;  // tau = nu / cs^2
-    h->cfl = cfl;
-    h->dt = fdlbm_time_step(g, cfl);
-    h->beta = blend;
-    h->A = o.A;
-    h->rho0 = o.rho0;
-    h->has_force = o.has_force ? 1 : 0;
-    h->path = path;
-    h->rows = 1;
-    h->variant = variant;
-    if (path == FDLBM_PATH_FUSED)
-        h->rows = o.rows_per_cta > 0 ? std::min(o.rows_per_cta, g->ny)
-                                     : choose_rows(g->nx, g->ny, o.precision, variant);
-    h->stream = static_cast<cudaStream_t>(o.stream);
-    h->lay = make_layout(h->nx, h->ny, h->pitch, h->precision, h->has_force,
-                         path == FDLBM_PATH_STAGED);
-    cudaGetDevice(&h->device);
+    fdlbm_ctx *h = nullptr;
+    std::vector<double> mx, my;
+    fdlbm_status st = handle_prepare(g, metrics, nu, cfl, blend, o, false, &h, mx, my);
+    if (st != FDLBM_OK) return st;
     if (o.workspace) {
         if (o.workspace_bytes < h->lay.total ||
             (reinterpret_cast<uintptr_t>(o.workspace) % kAlign) != 0) {
@@ -363,33 +418,10 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
         h->owns_ws = true;
         h->ws_bytes = h->lay.total;
     }
-    // zero state (fluid at rest), metrics in both precisions
-    cudaError_t e = cudaMemsetAsync(h->ws + h->lay.state[0], 0,
-                                    h->lay.state[1] - h->lay.state[0], h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + h->lay.err, 0, sizeof(int) * 4, h->stream);
-    if (e == cudaSuccess && h->has_force)
-        e = cudaMemsetAsync(h->ws + h->lay.force, 0, 2 * h->plane * real_size(h->precision),
-                            h->stream);
-    if (e == cudaSuccess) {
-        if (h->precision == FDLBM_FP32_DEV) {
-            std::vector<float> fx(mx.begin(), mx.end()), fy(my.begin(), my.end());
-            e = cudaMemcpy(h->ws + h->lay.mx, fx.data(), fx.size() * 4, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess)
-                e = cudaMemcpy(h->ws + h->lay.my, fy.data(), fy.size() * 4, cudaMemcpyHostToDevice);
-        } else {
-            e = cudaMemcpy(h->ws + h->lay.mx, mx.data(), mx.size() * 8, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess)
-                e = cudaMemcpy(h->ws + h->lay.my, my.data(), my.size() * 8, cudaMemcpyHostToDevice);
-        }
-    }
-    if (e == cudaSuccess)
-        e = cudaMemcpy(h->ws + h->lay.mxd, mx.data(), mx.size() * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(h->ws + h->lay.myd, my.data(), my.size() * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) {
+    st = handle_upload(h, mx, my);
+    if (st != FDLBM_OK) {
         fdlbm_destroy(h);
-        return FDLBM_ECUDA;
+        return st;
     }
     *out = h;
     return FDLBM_OK;
@@ -397,7 +429,7 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
 
 void fdlbm_destroy(fdlbm_t h)
 {
-    if (!h) return;
+    if (!h || h->in_batch) return;  // batch cases are released by fdlbm_batch_destroy
     if (h->owns_ws && h->ws) {
         cudaStreamSynchronize(h->stream);
         cudaFree(h->ws);
@@ -489,6 +521,8 @@ fdlbm_status fdlbm_step(fdlbm_t h, int n)
 {
     if (!h) return FDLBM_EINVAL;
     if (n < 0) return fail(h, FDLBM_EINVAL, "step: n < 0");
+    if (h->in_batch)
+        return fail(h, FDLBM_EUNSUPPORTED, "step: a batch case advances with fdlbm_batch_step");
     for (int k = 0; k < n; ++k) {
         cudaError_t e;
         if (h->precision == FDLBM_FP32_DEV) {
@@ -575,6 +609,7 @@ fdlbm_status fdlbm_reduce(fdlbm_t h, double *mass, double *resid)
 fdlbm_status fdlbm_set_stream(fdlbm_t h, void *stream)
 {
     if (!h) return FDLBM_EINVAL;
+    if (h->in_batch) return fail(h, FDLBM_EUNSUPPORTED, "set_stream: batch cases use the batch stream");
     h->stream = static_cast<cudaStream_t>(stream);
     return FDLBM_OK;
 }

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <string>
+#include <vector>
 
 #include "fdlbm.h"
 #include "lattice.cuh"
@@ -32,6 +33,17 @@ struct StepArgs {
     R *P, *Q, *S;
 };
 
+// Device tables of a batch (see step_batched.cu).
+struct BatchTables {
+    const void *args[2];   // StepArgs<R>[ncases] for even / odd steps (ping-pong)
+    const int *blk_case;   // [total_blocks]
+    const int *blk_start;  // [ncases]
+    const int *tiles_x;    // [ncases]
+    const int *wall_start; // [ncases]
+    int ncases, total_blocks, total_wall;
+    bool any_scheme2;
+};
+
 struct Layout {
     size_t state[2], mx, my, mxd, myd, force, P, Q, S, uprev, partials, red, err, staging;
     size_t staging_elems, total;
@@ -51,6 +63,7 @@ struct fdlbm_ctx {
     int has_force = 0;
     int path = FDLBM_PATH_FUSED;
     int variant = FDLBM_VARIANT_SCALAR;  // fused kernel actually used
+    bool in_batch = false;               // owned by a batch: stepped by fdlbm_batch_step
     int rows = 64;
     cudaStream_t stream = nullptr;
     char *ws = nullptr;
@@ -68,6 +81,13 @@ struct fdlbm_ctx {
 namespace fdlbm {
 
 size_t real_size(int precision);
+fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, double nu,
+                            double cfl, double blend, const fdlbm_opts &o, bool force_staged,
+                            fdlbm_ctx **out, std::vector<double> &mx, std::vector<double> &my);
+fdlbm_status handle_upload(fdlbm_ctx *h, const std::vector<double> &mx,
+                           const std::vector<double> &my);
+template <class R>
+StepArgs<R> handle_step_args(fdlbm_ctx *h);
 Layout make_layout(int nx, int ny, int pitch, int precision, int has_force, bool staged);
 
 // step_fused.cu
@@ -96,6 +116,9 @@ int fused_x2_blocks_per_sm();
 // step_staged.cu
 template <class R>
 cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s);
+// step_batched.cu
+template <class R>
+cudaError_t launch_batched(const BatchTables &t, int parity, dim3 blk, cudaStream_t s);
 // fields.cu
 cudaError_t launch_init_fields(fdlbm_ctx *h, const double *rho, const double *ux,
                                const double *uy, const double *grad, int row0, int nrows,

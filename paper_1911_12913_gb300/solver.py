@@ -68,11 +68,25 @@ class FDLBM:
         self._h = h
         self.precision = precision
 
+    @classmethod
+    def _case_view(cls, L, handle, xa, ya, stream, device, precision, batch):
+        """A non-owning view of case handle `handle` of a batch."""
+        self = cls.__new__(cls)
+        self._L = L
+        self._h = handle
+        self._owned = False
+        self._batch = batch  # keeps the batch (and its memory) alive
+        self.nx, self.ny = xa.n, ya.n
+        self.stream = stream
+        self.device = device
+        self.precision = precision
+        return self
+
     # ----------------------------------------------------------- lifetime
     def close(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and getattr(self, "_owned", True):
             self._L.fdlbm_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
@@ -186,3 +200,89 @@ class FDLBM:
 
     def sync(self):
         _check(self._L, self._h, self._L.fdlbm_sync(self._h), "sync")
+
+
+class FDLBMBatch:
+    """Many independent cases stepped together (batched staged kernels, CUDA
+    graph replay, autotuned block shape).  ``cases``: list of dicts with keys
+    ``xa, ya, nu, cfl, blend`` and optional ``wall_u, has_force, A, scheme``.
+    ``batch.case(c)`` returns an ``FDLBM`` view of case c for initialisation and
+    read-back; ``batch.step(n)`` advances every case."""
+
+    def __init__(self, cases, *, precision: str = "fp32", graph_steps: int = 50,
+                 autotune: bool = True, device=None):
+        self._L = L = B.load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        n = len(cases)
+        grids = (B.Grid * n)()
+        mets = (B.Metrics * n)()
+        opts = (B.Opts * n)()
+        self._keep = []
+        for c, cs in enumerate(cases):
+            g, keep = B.make_grid(cs["xa"], cs["ya"], cs.get("wall_u"))
+            grids[c] = g
+            mx = np.ascontiguousarray(cs["xa"].metric, dtype=np.float64)
+            my = np.ascontiguousarray(cs["ya"].metric, dtype=np.float64)
+            mets[c].dzeta_dx, mets[c].dmu_dy = B._dptr(mx), B._dptr(my)
+            self._keep += [keep, mx, my]
+            L.fdlbm_default_opts(ctypes.byref(opts[c]))
+            opts[c].precision = {"fp64": B.FP64, "fp32": B.FP32_DEV}[precision]
+            opts[c].has_force = int(cs.get("has_force", False))
+            opts[c].A = cs.get("A", 0.5)
+            opts[c].scheme = {1: B.SCHEME_T2S2_1, 2: B.SCHEME_T2S2_2}[cs.get("scheme", 1)]
+        nu = np.ascontiguousarray([cs["nu"] for cs in cases], dtype=np.float64)
+        cfl = np.ascontiguousarray([cs["cfl"] for cs in cases], dtype=np.float64)
+        blend = np.ascontiguousarray([cs["blend"] for cs in cases], dtype=np.float64)
+        nbytes = L.fdlbm_batch_workspace_bytes(n, grids, opts)
+        if nbytes == 0:
+            raise B.FdlbmError(-1, "invalid batch (workspace size 0)")
+        self._ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        rc = L.fdlbm_batch_create(n, grids, mets, B._dptr(nu), B._dptr(cfl), B._dptr(blend), opts,
+                                  graph_steps, int(autotune), self._ws.data_ptr(), nbytes,
+                                  ctypes.byref(h))
+        if rc != 0:
+            raise B.FdlbmError(rc, "fdlbm_batch_create")
+        self._h = h
+        self.stream = torch.cuda.ExternalStream(L.fdlbm_batch_stream(h), device=self.device)
+        self._cases = [FDLBM._case_view(L, L.fdlbm_batch_case(h, c), cs["xa"], cs["ya"], self.stream,
+                                        self.device, precision, self)
+                       for c, cs in enumerate(cases)]
+
+    def case(self, c: int) -> FDLBM:
+        return self._cases[c]
+
+    def __len__(self):
+        return len(self._cases)
+
+    @property
+    def cells(self) -> int:
+        return self._L.fdlbm_batch_cells(self._h)
+
+    @property
+    def describe(self) -> str:
+        return self._L.fdlbm_batch_describe(self._h).decode()
+
+    def step(self, n: int = 1):
+        rc = self._L.fdlbm_batch_step(self._h, int(n))
+        if rc != 0:
+            raise B.FdlbmError(rc, self._L.fdlbm_batch_last_error(self._h).decode())
+        return self
+
+    def sync(self):
+        rc = self._L.fdlbm_batch_sync(self._h)
+        if rc != 0:
+            raise B.FdlbmError(rc, self._L.fdlbm_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for cv in self._cases:
+                cv._h = None
+            self._L.fdlbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

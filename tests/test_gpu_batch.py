@@ -1,0 +1,148 @@
+"""Batched mode (many independent cases, batched staged kernels, CUDA-graph
+replay, autotuned block shape) against the CPU oracle, case by case."""
+import math
+
+import numpy as np
+import pytest
+
+import inputs as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1911_12913_gb300 import binding as B  # noqa: E402
+from paper_1911_12913_gb300.solver import FDLBMBatch  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _mixed_cases():
+    """Cavity (tanh and uniform), channel with force, periodic with force and
+    metrics, periodic without force, and one T2S2-FDLBM2 case."""
+    F = 0.01
+    cav = I.tanh_axis(16, 1.5)
+    per_x = I.periodic_axis(33, 0.0, 1.0)
+    per_y = I.periodic_axis(29, 0.0, 0.8)
+    per_x.metric = I.random_metric(33, 5, base=33)
+    chan_y = I.tanh_axis(20, 1.5)
+    lid = [(0, 0), (0, 0), (0, 0), (0.1, 0.0)]
+    cases = [
+        dict(xa=cav, ya=cav, nu=0.1 / 100, cfl=0.5, blend=0.1, wall_u=lid, init="rest"),
+        dict(xa=I.periodic_axis(10, 0.0, 1.0), ya=chan_y, nu=math.sqrt(F / 80), cfl=0.5,
+             blend=0.1, has_force=True, force="channel", init="rest"),
+        dict(xa=per_x, ya=per_y, nu=0.02, cfl=0.4, blend=0.2, has_force=True, force="random",
+             init="random"),
+        dict(xa=I.periodic_axis(40, 0.0, 2 * math.pi), ya=I.periodic_axis(40, 0.0, 2 * math.pi),
+             nu=0.01, cfl=0.5, blend=0.1, init="tg"),
+        dict(xa=I.wall_axis(20, 0.0, 1.0), ya=I.wall_axis(18, 0.0, 1.0), nu=0.001, cfl=0.5,
+             blend=0.1, wall_u=lid, init="rest"),
+        dict(xa=I.periodic_axis(24, 0.0, 1.0), ya=I.periodic_axis(20, 0.0, 1.0), nu=0.02,
+             cfl=0.3, blend=0.2, scheme=2, init="random"),
+    ]
+    return cases
+
+
+def _setup(batch, cases):
+    oracles = []
+    for c, cs in enumerate(cases):
+        view = batch.case(c)
+        xa, ya = cs["xa"], cs["ya"]
+        force = None
+        if cs.get("force") == "channel":
+            force = np.zeros((2, ya.n, xa.n))
+            force[0] = 0.01
+        elif cs.get("force") == "random":
+            force = 1e-3 * np.random.default_rng(c).uniform(-1, 1, size=(2, ya.n, xa.n))
+        o = O.Oracle(xa, ya, nu=cs["nu"], dt=view.dt, beta=cs["blend"], force=force,
+                     wall_u=cs.get("wall_u"), scheme=cs.get("scheme", 1))
+        if force is not None:
+            view.set_force(force)
+        if cs["init"] == "rest":
+            one = np.ones((ya.n, xa.n))
+            fld = dict(rho=one, ux=0 * one, uy=0 * one)
+            g = None
+        elif cs["init"] == "tg":
+            fld = I.taylor_green(xa, ya, u0=0.01)
+            g = [fld["dudx"], fld["dudy"], fld["dvdx"], fld["dvdy"]]
+        else:
+            fld = I.random_fields(xa.n, ya.n, 100 + c)
+            g = [fld["dudx"], fld["dudy"], fld["dvdx"], fld["dvdy"]]
+        view.init_fields(fld["rho"], fld["ux"], fld["uy"], g)
+        o.init_fields(fld["rho"], fld["ux"], fld["uy"], g)
+        oracles.append(o)
+    return oracles
+
+
+@pytest.mark.parametrize("precision,tol,autotune", [("fp64", 1e-12, False), ("fp32", 2e-6, True)])
+def test_mixed_batch_matches_oracle(precision, tol, autotune):
+    cases = _mixed_cases()
+    batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=autotune)
+    assert "cases=6" in batch.describe
+    oracles = _setup(batch, cases)
+    # 11 steps: 4 + 4 by graph replay, 3 launched directly; then 1 more
+    # (odd parity) and 5 more (realignment + graph + direct)
+    for n in (11, 1, 5):
+        batch.step(n)
+        for o in oracles:
+            o.step(n)
+    batch.sync()
+    for c, o in enumerate(oracles):
+        err = rel(batch.case(c).get_state(), o.f)
+        assert err <= tol, (c, err, batch.describe)
+    print(batch.describe)
+
+
+def test_batch_case_restrictions():
+    cases = _mixed_cases()[:2]
+    batch = FDLBMBatch(cases, precision="fp64", graph_steps=0, autotune=False)
+    L = B.load()
+    h = batch.case(0)._h
+    assert L.fdlbm_step(h, 1) == -5          # only the batch steps its cases
+    assert L.fdlbm_set_stream(h, None) == -5
+    L.fdlbm_destroy(h)                        # ignored for batch-owned cases
+    batch.step(3)
+    batch.sync()
+    assert batch.case(0).steps_done == 3
+    assert batch.cells == sum(cs["xa"].n * cs["ya"].n for cs in cases)
+
+
+def test_sweep_64_cases_sampled_parity():
+    """The 64-case sweep (cavity and channel mixes, 33..513 cells per axis, half
+    stretched, Re log-uniform in [10, 2000], FP32): every case stays finite and
+    conserves nothing it should not lose; four sampled cases match the oracle."""
+    from conftest import oracle_threads
+    specs = I.batched_cases(64, seed=2024)
+    probs = [I.batched_problem(cs) for cs in specs]
+    cases = [dict(xa=p["xa"], ya=p["ya"], nu=p["nu"], cfl=0.5, blend=0.1, wall_u=p["wall_u"],
+                  has_force=p["force"] is not None) for p in probs]
+    batch = FDLBMBatch(cases, precision="fp32", graph_steps=10, autotune=True)
+    for c, p in enumerate(probs):
+        v = batch.case(c)
+        if p["force"] is not None:
+            v.set_force(p["force"])
+        one = np.ones((p["ya"].n, p["xa"].n))
+        v.init_fields(one, 0 * one, 0 * one)
+    steps = 20
+    batch.step(steps)
+    batch.sync()
+    small = [c for c, cs in enumerate(specs) if cs.n <= 200]
+    rng = np.random.default_rng(7)
+    for c in rng.choice(small, size=4, replace=False):
+        p = probs[c]
+        o = O.Oracle(p["xa"], p["ya"], nu=p["nu"], dt=batch.case(c).dt, beta=0.1,
+                     force=p["force"], wall_u=p["wall_u"], nthreads=oracle_threads())
+        one = np.ones((p["ya"].n, p["xa"].n))
+        o.init_fields(one, 0 * one, 0 * one)
+        o.step(steps)
+        err = rel(batch.case(c).get_state(), o.f)
+        assert err <= 2e-6, (c, specs[c], err)
+    for c in range(len(specs)):
+        m, _ = batch.case(c).reduce()       # raises on NaN/Inf
+        assert math.isfinite(m)
+    print(batch.describe)
