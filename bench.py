@@ -55,6 +55,7 @@ def parse():
                    help="FP32 fused kernel variant for the headline timing")
     p.add_argument("--no-variants", action="store_true", help="skip timing the other variant")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-case batched sweep")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurements")
     return p.parse_args()
 
 
@@ -244,6 +245,97 @@ def run_batched(stream_dev, ncases=64, seed=2024, steps=200, graph_steps=50):
     return out
 
 
+# ----------------------------------------------------------------------- reverse mode
+def run_adjoint(dev, n=256, nsteps=2000, iters=6, seed=11):
+    """Adjoint cost against the forward step (256^2 and 4096^2, FP32), and the
+    inverse problem: recover a hidden smooth body force on a 256^2 periodic grid
+    from the final-velocity misfit of a 2000-step rollout (initial vorticity with
+    a k^-3 spectrum up to k = 8), by gradient descent with the adjoint."""
+    import numpy as np
+    import torch
+    import inputs as I
+    from paper_1911_12913_gb300.adjoint import rollout_velocity
+    from paper_1911_12913_gb300.solver import FDLBM
+
+    def cost_ratio(m, k=200):
+        ax = I.periodic_axis(m, 0.0, 2 * math.pi)
+        s = FDLBM(ax, ax, nu=0.01, cfl=CFL, blend=BLEND, precision="fp32", has_force=True,
+                  adjoint=True, device=dev)
+        v = I.spectral_vorticity_velocity(m, seed, kmax=8, umax=0.01)
+        one = np.ones((m, m))
+        s.init_fields(one, v["ux"], v["uy"], [v["dudx"], v["dudy"], v["dvdx"], v["dvdy"]])
+        g = s.save_state(s.new_buffer())
+        lam, lam2 = s.new_buffer(), s.new_buffer()
+        dF = torch.zeros((2, m, m), dtype=torch.float64, device=s.device)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        s.step(5)
+        s.adjoint_step(g, lam, lam2, dF)
+        torch.cuda.synchronize()
+        ev[0].record(s.stream)
+        s.step(k)
+        ev[1].record(s.stream)
+        for _ in range(k):
+            s.adjoint_step(g, lam, lam2, dF)
+            lam, lam2 = lam2, lam
+        ev[2].record(s.stream)
+        torch.cuda.synchronize()
+        fwd = ev[0].elapsed_time(ev[1]) / k
+        adj = ev[1].elapsed_time(ev[2]) / k
+        return {"n": m, "forward_ms": fwd, "adjoint_ms": adj, "ratio": adj / fwd,
+                "forward_kernel": s.describe, "adjoint_kernels_per_step": 3}
+
+    ratios = [cost_ratio(256), cost_ratio(4096)]
+    torch.cuda.empty_cache()
+
+    # inverse problem
+    ax = I.periodic_axis(n, 0.0, 2 * math.pi)
+    s = FDLBM(ax, ax, nu=0.01, cfl=CFL, blend=BLEND, precision="fp32", has_force=True,
+              adjoint=True, device=dev)
+    v = I.spectral_vorticity_velocity(n, seed, kmax=8, umax=0.01)
+    one = np.ones((n, n))
+    s.init_fields(one, v["ux"], v["uy"], [v["dudx"], v["dudy"], v["dvdx"], v["dvdy"]])
+    f0 = s.save_state(s.new_buffer())
+    h = I.spectral_vorticity_velocity(n, seed + 1, kmax=8, umax=1e-5)
+    hidden = torch.tensor(np.stack([h["ux"], h["uy"]]), dtype=torch.float64, device=s.device)
+    with torch.no_grad():
+        target = rollout_velocity(s, hidden, f0, nsteps).clone()
+    F = torch.zeros_like(hidden)
+    losses, t_grad = [], []
+    for it in range(iters):
+        Fv = F.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u = rollout_velocity(s, Fv, f0, nsteps)
+        J = 0.5 * ((u - target) ** 2).sum()
+        J.backward()
+        torch.cuda.synchronize()
+        t_grad.append(time.perf_counter() - t0)
+        g = Fv.grad.detach()
+        losses.append(float(J.detach()))
+        # step along -g with the Gauss-Newton length 2 J / |g|^2, halved until J falls
+        alpha = 2.0 * losses[-1] / float((g * g).sum())
+        for _ in range(8):
+            trial = F - alpha * g
+            with torch.no_grad():
+                ut = rollout_velocity(s, trial, f0, nsteps)
+            if float(0.5 * ((ut - target) ** 2).sum()) < losses[-1]:
+                break
+            alpha *= 0.5
+        F = trial
+    with torch.no_grad():
+        uf = rollout_velocity(s, F, f0, nsteps)
+    final = float(0.5 * ((uf - target) ** 2).sum())
+    err = float(torch.linalg.norm(F - hidden) / torch.linalg.norm(hidden))
+    return {"cost": ratios,
+            "inverse": {"grid": f"{n}x{n} periodic FP32", "steps": nsteps,
+                        "checkpoints": int(math.ceil(math.sqrt(nsteps))),
+                        "loss": losses + [final], "force_rel_error": err,
+                        "gradient_s": statistics.median(t_grad),
+                        "setup": "initial vorticity E(k)~k^-3 up to k=8, max|u|=0.01; hidden force same "
+                                 "spectral form, max 1e-5; nu=0.01, CFL 0.5; gradient descent with the "
+                                 "hand-written adjoint and sqrt(N) checkpointing"}}
+
+
 # ----------------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -369,6 +461,12 @@ def run_ours(args):
         batched = run_batched(stream_dev=dev)
         torch.cuda.empty_cache()
 
+    # ---------------- reverse mode: adjoint cost and the 256^2 inverse problem
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(dev)
+        torch.cuda.empty_cache()
+
     # ---------------- end to end through the C ABI with pinned host buffers
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in f.items()}
     out_host = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(3)]
@@ -415,7 +513,7 @@ def run_ours(args):
                "dtype": "f32", "data": "synthetic",
                "config": config(n, "fp32", args.steps), "clocks": clk.summary(),
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-               "cpu_baseline": cpu, "fp64": fp64, "fp32_variants": variants, "batched": batched,
+               "cpu_baseline": cpu, "fp64": fp64, "fp32_variants": variants, "batched": batched, "adjoint": adjoint,
                "mass_drift_rel": mass_drift,
                "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(out), flush=True)

@@ -100,6 +100,7 @@ typedef struct {
     int rows_per_cta;         /* fused kernel tile height; 0 = automatic */
     int variant;              /* FDLBM_VARIANT_*; PACKED where it does not apply -> EUNSUPPORTED */
     int scheme;               /* FDLBM_SCHEME_T2S2_1 (default) or FDLBM_SCHEME_T2S2_2 */
+    int adjoint;              /* 1: reserve scratch for fdlbm_adjoint_step (periodic grids) */
     void *stream;             /* cudaStream_t used for all work; NULL = default stream */
     void *workspace;          /* caller-owned device memory of fdlbm_workspace_bytes() bytes,
                                  256-byte aligned; NULL = the library allocates its own */
@@ -180,6 +181,36 @@ const char *fdlbm_last_error(fdlbm_t h); /* never NULL */
  * "fused-f32x2 rows=121" (never NULL; valid until the handle is destroyed). */
 const char *fdlbm_describe(fdlbm_t h);
 const char *fdlbm_status_string(fdlbm_status s);
+
+/* ---------------------------------------------------------------------------
+ * Reverse mode.  The paper has no adjoint; this is the discrete adjoint of the
+ * step above (Sec. 2D Steps 1-3 on a periodic grid, scheme T2S2_1), written by
+ * hand, with the body-acceleration field of Eq. 3.12 as the parameter.  States
+ * and cotangents live in device buffers of fdlbm_state_bytes() bytes in the
+ * handle's storage layout (precision of the handle, [9][ny][pitch] deviations
+ * from w_i rho0; cotangents use the same layout).
+ * ------------------------------------------------------------------------- */
+size_t fdlbm_state_bytes(fdlbm_t h);
+/* Row pitch (elements) and element size (4 or 8 bytes) of the storage layout:
+ * value (i, y, x) of a state or cotangent buffer sits at element
+ * (i * ny + y) * pitch + x; elements with x >= nx are padding. */
+fdlbm_status fdlbm_state_layout(fdlbm_t h, int *pitch, int *elem_bytes);
+/* Device copy between the handle's current state and `buf` (storage layout):
+ * to_handle = 1 loads buf into the handle, 0 stores the handle's state into buf. */
+fdlbm_status fdlbm_copy_state(fdlbm_t h, void *buf, int to_handle);
+/* One adjoint step: given the state g^n (state_n) and the cotangent lam_next of
+ * g^{n+1} = step(g^n), write the cotangent lam_prev of g^n and, if dforce is
+ * not NULL, add the cotangent of the force field to dforce (device, FP64,
+ * [2][ny][nx]; a handle without a force field differentiates at zero force).
+ * Needs opts.adjoint, both axes periodic and scheme T2S2_1 (else EUNSUPPORTED).
+ * lam_next and lam_prev may not alias.  Asynchronous on the stream. */
+fdlbm_status fdlbm_adjoint_step(fdlbm_t h, const void *state_n, const void *lam_next,
+                                void *lam_prev, double *dforce);
+/* Cotangent of a state from a cotangent du ([2][ny][nx] FP64 device) of its
+ * velocity (Eq. 3.3): writes lam (storage layout) and adds du * dt/2 to dforce
+ * (if not NULL). */
+fdlbm_status fdlbm_moments_vjp(fdlbm_t h, const void *state, const double *du, void *lam,
+                               double *dforce);
 
 /* ---------------------------------------------------------------------------
  * Batched mode: many independent cases (uneven sizes, walls, forces, Reynolds

@@ -32,6 +32,7 @@ import numpy as np
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "fdlbm_oracle.c"
 _LIB = _HERE / "_build" / "liboracle.so"
+_LIB_C = _HERE / "_build" / "liboracle_complex.so"
 CS2 = 1.0 / 3.0
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -45,25 +46,43 @@ class _Cfg(ctypes.Structure):
         ("tau", ctypes.c_double), ("dt", ctypes.c_double),
         ("A", ctypes.c_double), ("beta", ctypes.c_double),
         ("beta_is_central", ctypes.c_int), ("scheme", ctypes.c_int),
-        ("force", _dp),
+        ("force", ctypes.c_void_p),
         ("wall_u", (ctypes.c_double * 2) * 4),
         ("nthreads", ctypes.c_int),
     ]
 
 
 def build(force: bool = False) -> Path:
-    """Compile the oracle with gcc (FP64, no fast-math, no FMA contraction)."""
+    """Compile the oracle with gcc (FP64, no fast-math, no FMA contraction), once
+    with real values and once with complex values (complex-step derivatives)."""
     _LIB.parent.mkdir(exist_ok=True)
-    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
-        tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
-        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               "-std=c11", str(_SRC), "-o", str(tmp), "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
+    for lib_path, extra in ((_LIB, []), (_LIB_C, ["-DORACLE_COMPLEX"])):
+        if force or not lib_path.exists() or lib_path.stat().st_mtime < _SRC.stat().st_mtime:
+            tmp = lib_path.with_suffix(f".{os.getpid()}.tmp")
+            cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                   "-std=c11", *extra, str(_SRC), "-o", str(tmp), "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, lib_path)
     return _LIB
 
 
 _lib = None
+_lib_c = None
+
+
+def lib_complex():
+    """The complex-valued build (pointer arguments only)."""
+    global _lib_c
+    if _lib_c is None:
+        build()
+        L = ctypes.CDLL(str(_LIB_C))
+        P = ctypes.POINTER(_Cfg)
+        vp = ctypes.c_void_p
+        L.oracle_step.argtypes = [P, vp, ctypes.c_int]
+        L.oracle_step.restype = ctypes.c_int
+        L.oracle_moments.argtypes = [P, vp, vp, vp, vp]
+        _lib_c = L
+    return _lib_c
 
 
 def lib():
@@ -163,7 +182,7 @@ class Oracle:
         c.tau, c.dt, c.A, c.beta = self.tau, dt, A, beta
         c.beta_is_central = int(beta_is_central)
         c.scheme = scheme
-        c.force = _ptr(self.force) if self.force is not None else ctypes.cast(None, _dp)
+        c.force = self.force.ctypes.data if self.force is not None else None
         wu = wall_u if wall_u is not None else [(0.0, 0.0)] * 4
         for s in range(4):
             c.wall_u[s][0], c.wall_u[s][1] = float(wu[s][0]), float(wu[s][1])
@@ -223,3 +242,47 @@ class Oracle:
         """Jacobian-weighted mass sum_{x,y} rho / (m_x m_y) (exact invariant on periodic grids)."""
         r, _, _ = self.moments()
         return float(np.sum(r / np.outer(self.my, self.mx)))
+
+
+# ------------------------------------------------------------------ complex step
+def step_complex(xa, ya, *, nu: float, dt: float, beta: float, f, force=None, A: float = 0.5,
+                 nsteps: int = 1, wall_u=None):
+    """Advance a complex-valued state (and complex force field, if given) with
+    the complex build of the oracle: the same arithmetic as ``Oracle.step``."""
+    o = Oracle(xa, ya, nu=nu, dt=dt, beta=beta, A=A, wall_u=wall_u)
+    fc = np.ascontiguousarray(f, dtype=np.complex128).copy()
+    keep = None
+    if force is not None:
+        keep = np.ascontiguousarray(force, dtype=np.complex128)
+        o._cfg.force = keep.ctypes.data
+    rc = lib_complex().oracle_step(o.cfg, fc.ctypes.data, nsteps)
+    if rc != 0:
+        raise MemoryError("oracle_step (complex) failed")
+    del keep
+    return fc
+
+
+def step_vjp(xa, ya, *, nu: float, dt: float, beta: float, f0, lam, force=None, A: float = 0.5,
+             eps: float = 1e-20):
+    """Reference reverse mode of one step on a tiny periodic grid, by brute
+    force: every column of the step's Jacobian (with respect to the state and to
+    the force field) comes from one complex-step evaluation,
+    J e_k = Im(step(x + i eps e_k)) / eps, exact to rounding.  Returns
+    (J_f^T lam, J_F^T lam), shaped like f0 and like the force field."""
+    f0 = np.asarray(f0, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    F = np.zeros((2,) + f0.shape[1:]) if force is None else np.asarray(force, dtype=np.float64)
+    kw = dict(nu=nu, dt=dt, beta=beta, A=A)
+    out_f = np.zeros(f0.size)
+    for k in range(f0.size):
+        x = f0.astype(np.complex128).ravel()
+        x[k] += 1j * eps
+        y = step_complex(xa, ya, f=x.reshape(f0.shape), force=F, **kw)
+        out_f[k] = float(np.sum(y.imag / eps * lam))
+    out_F = np.zeros(F.size)
+    for k in range(F.size):
+        Fc = F.astype(np.complex128).ravel()
+        Fc[k] += 1j * eps
+        y = step_complex(xa, ya, f=f0, force=Fc.reshape(F.shape), **kw)
+        out_F[k] = float(np.sum(y.imag / eps * lam))
+    return out_f.reshape(f0.shape), out_F.reshape(F.shape)

@@ -35,6 +35,19 @@
 #include <omp.h>
 #endif
 
+/* Value type of distributions and fields.  The default build uses real_t; the
+ * ORACLE_COMPLEX build runs the identical arithmetic on complex numbers, so
+ * that a complex-step perturbation (f + i eps v) yields the exact directional
+ * derivative Im(step(f + i eps v)) / eps of the step (used by the tests to
+ * assemble the step's Jacobian on tiny grids).  Grid metrics, time parameters
+ * and wall velocities are real in both builds. */
+#ifdef ORACLE_COMPLEX
+#include <complex.h>
+typedef double complex real_t;
+#else
+typedef double real_t;
+#endif
+
 /* D2Q9 lattice of Sec. 3 with xi = 1: velocity columns and weights, cs^2 = 1/3. */
 static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -49,7 +62,7 @@ typedef struct {
     double tau, dt, A, beta;      /* relaxation time, time step, t* = tn + A dt, upwind weight */
     int beta_is_central;          /* 1: literal Eq. 2.36 (beta weights the central part) */
     int scheme;                   /* 1: T2S2-FDLBM1 (Eq. 2.23), 2: T2S2-FDLBM2 (Eq. 5.23) */
-    const double *force;          /* [2][ny][nx] body acceleration, or NULL */
+    const real_t *force;          /* [2][ny][nx] body acceleration, or NULL */
     double wall_u[4][2];          /* velocity of the W, E, S, N walls */
     int nthreads;
 } oracle_cfg;
@@ -60,25 +73,25 @@ typedef struct {
 static int nthreads_of(const oracle_cfg *c) { return c->nthreads > 0 ? c->nthreads : 1; }
 
 /* Eq. 3.2: second-order equilibrium. */
-void oracle_feq(double rho, double ux, double uy, double *feq)
+void oracle_feq(real_t rho, real_t ux, real_t uy, real_t *feq)
 {
-    double uu = ux * ux + uy * uy;
+    real_t uu = ux * ux + uy * uy;
     for (int i = 0; i < 9; ++i) {
-        double eu = EX[i] * ux + EY[i] * uy;
+        real_t eu = EX[i] * ux + EY[i] * uy;
         /* uu:(xi xi - cs^2 I) = (xi.u)^2 - cs^2 u.u */
         feq[i] = WQ[i] * rho * (1.0 + eu / CS2 + (eu * eu - CS2 * uu) / (2.0 * CS2 * CS2));
     }
 }
 
 /* Eq. 3.12: forcing term F_i = Fbar.(xi_i - u) f_i^eq / RT with RT = cs^2. */
-void oracle_force_term(const double *feq, double ux, double uy, double Fx, double Fy,
-                       double *F)
+void oracle_force_term(const real_t *feq, real_t ux, real_t uy, real_t Fx, real_t Fy,
+                       real_t *F)
 {
     for (int i = 0; i < 9; ++i)
         F[i] = ((EX[i] - ux) * Fx + (EY[i] - uy) * Fy) * feq[i] / CS2;
 }
 
-static void force_at(const oracle_cfg *c, size_t n, double *Fx, double *Fy)
+static void force_at(const oracle_cfg *c, size_t n, real_t *Fx, real_t *Fy)
 {
     size_t N = (size_t)c->nx * c->ny;
     *Fx = c->force ? c->force[n] : 0.0;
@@ -88,18 +101,18 @@ static void force_at(const oracle_cfg *c, size_t n, double *Fx, double *Fy)
 /* Eq. 3.3 applied to a distribution whose first moment lacks `shift * rho * F`:
  * rho = sum f_i, rho u = sum xi_i f_i + shift rho F.  shift = dt/2 for f~,
  * h/2 for fbar (Eq. 2.31), 0 for the physical f. */
-static void moments_node(const oracle_cfg *c, const double *f, size_t n, double shift,
-                         double *rho, double *ux, double *uy)
+static void moments_node(const oracle_cfg *c, const real_t *f, size_t n, double shift,
+                         real_t *rho, real_t *ux, real_t *uy)
 {
     size_t N = (size_t)c->nx * c->ny;
-    double r = 0.0, jx = 0.0, jy = 0.0;
+    real_t r = 0.0, jx = 0.0, jy = 0.0;
     for (int i = 0; i < 9; ++i) {
-        double v = f[i * N + n];
+        real_t v = f[i * N + n];
         r += v;
         jx += EX[i] * v;
         jy += EY[i] * v;
     }
-    double Fx, Fy;
+    real_t Fx, Fy;
     force_at(c, n, &Fx, &Fy);
     jx += shift * r * Fx;
     jy += shift * r * Fy;
@@ -109,7 +122,7 @@ static void moments_node(const oracle_cfg *c, const double *f, size_t n, double 
 }
 
 /* Eq. 3.3: density and velocity from f~. */
-void oracle_moments(const oracle_cfg *c, const double *f, double *rho, double *ux, double *uy)
+void oracle_moments(const oracle_cfg *c, const real_t *f, real_t *rho, real_t *ux, real_t *uy)
 {
     size_t N = (size_t)c->nx * c->ny;
     for (size_t n = 0; n < N; ++n)
@@ -119,18 +132,18 @@ void oracle_moments(const oracle_cfg *c, const double *f, double *rho, double *u
 /* Eq. 3.5 (coefficient read as rho0 w_i (2 tau + dt) / (2 cs^2), see the
  * module header of the Python wrapper) or Eq. 3.2 alone when grad is NULL.
  * grad = [dudx, dudy, dvdx, dvdy], each [ny][nx]. */
-void oracle_init(const oracle_cfg *c, const double *rho, const double *ux, const double *uy,
-                 const double *grad, double rho0, double *f)
+void oracle_init(const oracle_cfg *c, const real_t *rho, const real_t *ux, const real_t *uy,
+                 const real_t *grad, double rho0, real_t *f)
 {
     size_t N = (size_t)c->nx * c->ny;
     for (size_t n = 0; n < N; ++n) {
-        double feq[9];
+        real_t feq[9];
         oracle_feq(rho[n], ux[n], uy[n], feq);
         for (int i = 0; i < 9; ++i) {
-            double v = feq[i];
+            real_t v = feq[i];
             if (grad) {
                 double xx = EX[i] * EX[i], xy = EX[i] * EY[i], yy = EY[i] * EY[i];
-                double ddot = xx * grad[n] + xy * (grad[N + n] + grad[2 * N + n]) +
+                real_t ddot = xx * grad[n] + xy * (grad[N + n] + grad[2 * N + n]) +
                               yy * grad[3 * N + n];
                 v -= rho0 * WQ[i] * (2.0 * c->tau + c->dt) / (2.0 * CS2) * ddot;
             }
@@ -150,7 +163,7 @@ static int wrap(int k, int n)
     return k;
 }
 
-static double sample(const oracle_cfg *c, const double *fld, int x, int y)
+static real_t sample(const oracle_cfg *c, const real_t *fld, int x, int y)
 {
     if (c->periodic_x) x = wrap(x, c->nx);
     if (c->periodic_y) y = wrap(y, c->ny);
@@ -158,14 +171,14 @@ static double sample(const oracle_cfg *c, const double *fld, int x, int y)
 }
 
 /* Central difference, Eq. 2.37 (index space). */
-static double d_central(const oracle_cfg *c, const double *f, int x, int y, int ax)
+static real_t d_central(const oracle_cfg *c, const real_t *f, int x, int y, int ax)
 {
     int dx = ax == 0, dy = ax == 1;
     return (sample(c, f, x + dx, y + dy) - sample(c, f, x - dx, y - dy)) / 2.0;
 }
 
 /* Second-order upwind difference, Eq. 2.38 (index space), sign s of xi_alpha. */
-static double d_upwind(const oracle_cfg *c, const double *f, int x, int y, int ax, int s)
+static real_t d_upwind(const oracle_cfg *c, const real_t *f, int x, int y, int ax, int s)
 {
     int dx = ax == 0, dy = ax == 1;
     if (s >= 0)
@@ -176,24 +189,24 @@ static double d_upwind(const oracle_cfg *c, const double *f, int x, int y, int a
 }
 
 /* Mixed difference, Eq. 2.36, with the metric: d f/d x_alpha at node (x, y). */
-static double d_mixed(const oracle_cfg *c, const double *f, int x, int y, int ax, int s)
+static real_t d_mixed(const oracle_cfg *c, const real_t *f, int x, int y, int ax, int s)
 {
     double m = ax == 0 ? c->mx[x] : c->my[y];
     int k = ax == 0 ? x : y, n = ax == 0 ? c->nx : c->ny;
     int per = ax == 0 ? c->periodic_x : c->periodic_y;
-    double dc = d_central(c, f, x, y, ax);
+    real_t dc = d_central(c, f, x, y, ax);
     /* upwind stencil leaves a walled domain: central difference alone */
     int upwind_ok = per || (s >= 0 ? k - 2 >= 0 : k + 2 <= n - 1);
     if (!upwind_ok) return m * dc;
-    double du = d_upwind(c, f, x, y, ax, s);
+    real_t du = d_upwind(c, f, x, y, ax, s);
     double wu = c->beta_is_central ? 1.0 - c->beta : c->beta;
     return m * ((1.0 - wu) * dc + wu * du);
 }
 
 /* Eq. 2.27: L(f_i) = -xi_i . grad f_i, evaluated at one node for population i. */
-static double advection(const oracle_cfg *c, const double *fi, int x, int y, int i)
+static real_t advection(const oracle_cfg *c, const real_t *fi, int x, int y, int i)
 {
-    double L = 0.0;
+    real_t L = 0.0;
     if (EX[i]) L -= EX[i] * d_mixed(c, fi, x, y, 0, EX[i]);
     if (EY[i]) L -= EY[i] * d_mixed(c, fi, x, y, 1, EY[i]);
     return L;
@@ -225,7 +238,7 @@ static void wall_partner(const oracle_cfg *c, int x, int y, int *px, int *py, do
 
 /* Eq. 3.10: non-equilibrium extrapolation onto every wall node of f.
  * `shift` selects the first-moment convention of f (see moments_node). */
-static void apply_nee(const oracle_cfg *c, double *f, double shift)
+static void apply_nee(const oracle_cfg *c, real_t *f, double shift)
 {
     size_t N = (size_t)c->nx * c->ny;
     for (int y = 0; y < c->ny; ++y)
@@ -235,7 +248,7 @@ static void apply_nee(const oracle_cfg *c, double *f, double shift)
             double uw[2];
             wall_partner(c, x, y, &jx, &jy, uw);
             size_t nb = IDX(c, x, y), nj = IDX(c, jx, jy);
-            double rj, uxj, uyj, feqj[9], feqb[9];
+            real_t rj, uxj, uyj, feqj[9], feqb[9];
             moments_node(c, f, nj, shift, &rj, &uxj, &uyj);
             oracle_feq(rj, uxj, uyj, feqj);
             oracle_feq(rj, uw[0], uw[1], feqb);
@@ -245,19 +258,19 @@ static void apply_nee(const oracle_cfg *c, double *f, double shift)
 }
 
 typedef struct {
-    double *rho, *ux, *uy, *feq, *F, *fphys, *fbar_plus, *fbar_star, *fstar, *ftil_plus, *L;
+    real_t *rho, *ux, *uy, *feq, *F, *fphys, *fbar_plus, *fbar_star, *fstar, *ftil_plus, *L;
 } work_t;
 
 static int work_alloc(const oracle_cfg *c, work_t *w)
 {
     size_t N = (size_t)c->nx * c->ny;
     memset(w, 0, sizeof(*w));
-    w->rho = malloc(N * sizeof(double));
-    w->ux = malloc(N * sizeof(double));
-    w->uy = malloc(N * sizeof(double));
-    double **big[] = {&w->feq, &w->F, &w->fphys, &w->fbar_plus, &w->fbar_star,
+    w->rho = malloc(N * sizeof(real_t));
+    w->ux = malloc(N * sizeof(real_t));
+    w->uy = malloc(N * sizeof(real_t));
+    real_t **big[] = {&w->feq, &w->F, &w->fphys, &w->fbar_plus, &w->fbar_star,
                       &w->fstar, &w->ftil_plus, &w->L};
-    for (int k = 0; k < 8; ++k) *big[k] = malloc(9 * N * sizeof(double));
+    for (int k = 0; k < 8; ++k) *big[k] = malloc(9 * N * sizeof(real_t));
     int ok = w->rho && w->ux && w->uy;
     for (int k = 0; k < 8; ++k) ok = ok && *big[k];
     return ok ? 0 : -1;
@@ -271,12 +284,12 @@ static void work_free(work_t *w)
 
 /* Node-local pass: rho, u (Eq. 3.3), f^eq (Eq. 3.2), F (Eq. 3.12) of a
  * distribution g whose first moment lacks `shift rho F`. */
-static void macro_pass(const oracle_cfg *c, const double *g, double shift, work_t *w)
+static void macro_pass(const oracle_cfg *c, const real_t *g, double shift, work_t *w)
 {
     size_t N = (size_t)c->nx * c->ny;
 #pragma omp parallel for num_threads(nthreads_of(c)) schedule(static)
     for (long long n = 0; n < (long long)N; ++n) {
-        double fe[9], Fi[9], Fx, Fy;
+        real_t fe[9], Fi[9], Fx, Fy;
         moments_node(c, g, (size_t)n, shift, &w->rho[n], &w->ux[n], &w->uy[n]);
         oracle_feq(w->rho[n], w->ux[n], w->uy[n], fe);
         force_at(c, (size_t)n, &Fx, &Fy);
@@ -289,7 +302,7 @@ static void macro_pass(const oracle_cfg *c, const double *g, double shift, work_
 }
 
 /* Eq. 2.20: post-collision f~+ from f~, f^eq, F. */
-static void post_collision_pass(const oracle_cfg *c, const double *f, work_t *w)
+static void post_collision_pass(const oracle_cfg *c, const real_t *f, work_t *w)
 {
     size_t N = (size_t)c->nx * c->ny;
     double tau = c->tau, dt = c->dt;
@@ -301,7 +314,7 @@ static void post_collision_pass(const oracle_cfg *c, const double *f, work_t *w)
 
 /* Inverse of Eq. 2.31 for the step s (Eq. 2.32): physical f from the
  * half-variable fb = f - (s/2) Omega-bar. */
-static void physical_pass(const oracle_cfg *c, const double *fb, double s, work_t *w)
+static void physical_pass(const oracle_cfg *c, const real_t *fb, double s, work_t *w)
 {
     size_t N = (size_t)c->nx * c->ny;
     double tau = c->tau;
@@ -312,7 +325,7 @@ static void physical_pass(const oracle_cfg *c, const double *fb, double s, work_
 
 /* out = f + (h/2) Omega-bar(f) = (1 - h/2tau) f + (h/2tau) f^eq + (h/2) F
  * (Eq. 2.34, left-hand definition) for the physical f in w->fphys. */
-static void plus_half_pass(const oracle_cfg *c, double h, work_t *w, double *out)
+static void plus_half_pass(const oracle_cfg *c, double h, work_t *w, real_t *out)
 {
     size_t N = (size_t)c->nx * c->ny;
     double tau = c->tau;
@@ -323,7 +336,7 @@ static void plus_half_pass(const oracle_cfg *c, double h, work_t *w, double *out
 
 /* Characteristic estimate, Eqs. 2.33 and 2.35: out = in - h xi_i . grad in
  * at interior nodes (wall nodes are filled later). */
-static void characteristic_pass(const oracle_cfg *c, const double *in, double h, double *out)
+static void characteristic_pass(const oracle_cfg *c, const real_t *in, double h, real_t *out)
 {
     size_t N = (size_t)c->nx * c->ny;
     for (int i = 0; i < 9; ++i) {
@@ -339,7 +352,7 @@ static void characteristic_pass(const oracle_cfg *c, const double *in, double h,
 }
 
 /* Eq. 2.27 with Eq. 2.36 at interior nodes. */
-static void advection_pass(const oracle_cfg *c, const double *fin, double *L)
+static void advection_pass(const oracle_cfg *c, const real_t *fin, real_t *L)
 {
     size_t N = (size_t)c->nx * c->ny;
     for (int i = 0; i < 9; ++i) {
@@ -353,7 +366,7 @@ static void advection_pass(const oracle_cfg *c, const double *fin, double *L)
 }
 
 /* One T2S2-FDLBM1 step (Sec. 2D Steps 1-3; A = 0 gives T1S2, Remark I). */
-static void step_scheme1(const oracle_cfg *c, double *f, work_t *w)
+static void step_scheme1(const oracle_cfg *c, real_t *f, work_t *w)
 {
     size_t N = (size_t)c->nx * c->ny;
     double dt = c->dt, tau = c->tau, h = c->A * dt;
@@ -368,7 +381,7 @@ static void step_scheme1(const oracle_cfg *c, double *f, work_t *w)
     /* Step 1c: moments of fbar*, then f* (Eq. 2.52 with the force term of Eq. 2.32) */
     macro_pass(c, w->fbar_star, 0.5 * h, w);
     physical_pass(c, w->fbar_star, h, w);
-    memcpy(w->fstar, w->fphys, 9 * N * sizeof(double));
+    memcpy(w->fstar, w->fphys, 9 * N * sizeof(real_t));
     if (!c->periodic_x || !c->periodic_y) apply_nee(c, w->fstar, 0.0);
     /* Step 1d: L(f*) (Eqs. 2.27, 2.36) */
     advection_pass(c, w->fstar, w->L);
@@ -379,14 +392,14 @@ static void step_scheme1(const oracle_cfg *c, double *f, work_t *w)
 }
 
 /* One T2S2-FDLBM2 step (Sec. 2D, second sequence; Eq. 5.23, h = dt). */
-static void step_scheme2(const oracle_cfg *c, double *f, work_t *w)
+static void step_scheme2(const oracle_cfg *c, real_t *f, work_t *w)
 {
     size_t N = (size_t)c->nx * c->ny;
     double dt = c->dt;
     /* Step 1: f~ -> f^n (Eq. 2.52 with h = dt) -> L(f^n) */
     macro_pass(c, f, 0.5 * dt, w);
     physical_pass(c, f, dt, w);
-    memcpy(w->fstar, w->fphys, 9 * N * sizeof(double));
+    memcpy(w->fstar, w->fphys, 9 * N * sizeof(real_t));
     if (!c->periodic_x || !c->periodic_y) apply_nee(c, w->fstar, 0.0);
     advection_pass(c, w->fstar, w->L);
     /* Step 2: f~ -> f~+ (Eq. 2.20) -> fbar(t_{n+1}) (Eqs. 2.33, 2.35 with h = dt,
@@ -405,7 +418,7 @@ static void step_scheme2(const oracle_cfg *c, double *f, work_t *w)
 }
 
 /* Advance f~ (layout [9][ny][nx]) by nsteps.  Returns 0, or -1 on allocation failure. */
-int oracle_step(const oracle_cfg *c, double *f, int nsteps)
+int oracle_step(const oracle_cfg *c, real_t *f, int nsteps)
 {
     work_t w;
     if (work_alloc(c, &w)) { work_free(&w); return -1; }
@@ -420,21 +433,21 @@ int oracle_step(const oracle_cfg *c, double *f, int nsteps)
 /* T1S2-FDLBM of Guo et al. written directly from Eqs. 2.18-2.20, independent of
  * step_scheme1: f~^{n+1} = f~+ + dt L(f^n), with f^n recovered from f~ by
  * inverting Eq. 2.19. */
-int oracle_step_t1s2(const oracle_cfg *c, double *f, int nsteps)
+int oracle_step_t1s2(const oracle_cfg *c, real_t *f, int nsteps)
 {
     size_t N = (size_t)c->nx * c->ny;
     double dt = c->dt, tau = c->tau;
-    double *fn = malloc(9 * N * sizeof(double));
-    double *fp = malloc(9 * N * sizeof(double));
-    double *rho = malloc(N * sizeof(double)), *ux = malloc(N * sizeof(double)),
-           *uy = malloc(N * sizeof(double));
+    real_t *fn = malloc(9 * N * sizeof(real_t));
+    real_t *fp = malloc(9 * N * sizeof(real_t));
+    real_t *rho = malloc(N * sizeof(real_t)), *ux = malloc(N * sizeof(real_t)),
+           *uy = malloc(N * sizeof(real_t));
     if (!fn || !fp || !rho || !ux || !uy) {
         free(fn); free(fp); free(rho); free(ux); free(uy);
         return -1;
     }
     for (int s = 0; s < nsteps; ++s) {
         for (size_t n = 0; n < N; ++n) {
-            double fe[9], Fi[9], Fx, Fy;
+            real_t fe[9], Fi[9], Fx, Fy;
             moments_node(c, f, n, 0.5 * dt, &rho[n], &ux[n], &uy[n]);
             oracle_feq(rho[n], ux[n], uy[n], fe);
             force_at(c, n, &Fx, &Fy);
@@ -462,7 +475,7 @@ int oracle_step_t1s2(const oracle_cfg *c, double *f, int nsteps)
 
 /* Stand-alone difference operators for the tests of Eqs. 2.36-2.38:
  * out[y][x] = d fld / d x_alpha (with metric) at interior nodes, for sign s. */
-void oracle_derivative(const oracle_cfg *c, const double *fld, int axis, int s, double *out)
+void oracle_derivative(const oracle_cfg *c, const real_t *fld, int axis, int s, real_t *out)
 {
     for (int y = 0; y < c->ny; ++y)
         for (int x = 0; x < c->nx; ++x)
@@ -471,14 +484,14 @@ void oracle_derivative(const oracle_cfg *c, const double *fld, int axis, int s, 
 
 /* The intermediate quantities of one T2S2 step for inspection by the tests:
  * fbar^{+,h}, fbar*, f*, f~+ and L(f*) (each [9][ny][nx]). */
-int oracle_stages(const oracle_cfg *c, const double *f, double *fbar_plus, double *fbar_star,
-                  double *fstar, double *ftil_plus, double *L)
+int oracle_stages(const oracle_cfg *c, const real_t *f, real_t *fbar_plus, real_t *fbar_star,
+                  real_t *fstar, real_t *ftil_plus, real_t *L)
 {
     size_t N = (size_t)c->nx * c->ny;
     work_t w;
-    double *tmp = malloc(9 * N * sizeof(double));
+    real_t *tmp = malloc(9 * N * sizeof(real_t));
     if (!tmp || work_alloc(c, &w)) { free(tmp); work_free(&w); return -1; }
-    memcpy(tmp, f, 9 * N * sizeof(double));
+    memcpy(tmp, f, 9 * N * sizeof(real_t));
     double h = c->A * c->dt;
     macro_pass(c, tmp, 0.5 * c->dt, &w);
     physical_pass(c, tmp, c->dt, &w);
@@ -487,14 +500,14 @@ int oracle_stages(const oracle_cfg *c, const double *f, double *fbar_plus, doubl
     characteristic_pass(c, w.fbar_plus, h, w.fbar_star);
     macro_pass(c, w.fbar_star, 0.5 * h, &w);
     physical_pass(c, w.fbar_star, h, &w);
-    memcpy(w.fstar, w.fphys, 9 * N * sizeof(double));
+    memcpy(w.fstar, w.fphys, 9 * N * sizeof(real_t));
     if (!c->periodic_x || !c->periodic_y) apply_nee(c, w.fstar, 0.0);
     advection_pass(c, w.fstar, w.L);
-    memcpy(fbar_plus, w.fbar_plus, 9 * N * sizeof(double));
-    memcpy(fbar_star, w.fbar_star, 9 * N * sizeof(double));
-    memcpy(fstar, w.fstar, 9 * N * sizeof(double));
-    memcpy(ftil_plus, w.ftil_plus, 9 * N * sizeof(double));
-    memcpy(L, w.L, 9 * N * sizeof(double));
+    memcpy(fbar_plus, w.fbar_plus, 9 * N * sizeof(real_t));
+    memcpy(fbar_star, w.fbar_star, 9 * N * sizeof(real_t));
+    memcpy(fstar, w.fstar, 9 * N * sizeof(real_t));
+    memcpy(ftil_plus, w.ftil_plus, 9 * N * sizeof(real_t));
+    memcpy(L, w.L, 9 * N * sizeof(real_t));
     free(tmp);
     work_free(&w);
     return 0;

@@ -41,7 +41,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("A", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("precision", ctypes.c_int), ("has_force", ctypes.c_int),
                 ("path", ctypes.c_int), ("rows_per_cta", ctypes.c_int), ("variant", ctypes.c_int),
-                ("scheme", ctypes.c_int),
+                ("scheme", ctypes.c_int), ("adjoint", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -75,6 +75,13 @@ SIGNATURES = [
     ("fdlbm_last_error", ctypes.c_char_p, [_H]),
     ("fdlbm_describe", ctypes.c_char_p, [_H]),
     ("fdlbm_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("fdlbm_state_bytes", ctypes.c_size_t, [_H]),
+    ("fdlbm_copy_state", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
+    ("fdlbm_state_layout", ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("fdlbm_adjoint_step", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    ("fdlbm_moments_vjp", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
     ("fdlbm_batch_workspace_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(Grid),
                                                       ctypes.POINTER(Opts)]),
     ("fdlbm_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Grid), ctypes.POINTER(Metrics),

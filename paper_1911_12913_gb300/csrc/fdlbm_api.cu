@@ -145,7 +145,7 @@ StepArgs<R> step_args(fdlbm_ctx *h)
     a.stc = make_stencil<R>(0.0);
     a.rows = h->rows;
     a.err = reinterpret_cast<int *>(h->ws + h->lay.err);
-    if (h->path == FDLBM_PATH_STAGED) {
+    if (h->path == FDLBM_PATH_STAGED || h->adjoint) {
         a.P = reinterpret_cast<R *>(h->ws + h->lay.P);
         a.Q = reinterpret_cast<R *>(h->ws + h->lay.Q);
         a.S = reinterpret_cast<R *>(h->ws + h->lay.S);
@@ -307,8 +307,9 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
         h->rows = o.rows_per_cta > 0 ? std::min(o.rows_per_cta, g->ny)
                                      : choose_rows(g->nx, g->ny, o.precision, variant);
     h->stream = static_cast<cudaStream_t>(o.stream);
+    h->adjoint = o.adjoint != 0;
     h->lay = make_layout(h->nx, h->ny, h->pitch, h->precision, h->has_force,
-                         path == FDLBM_PATH_STAGED);
+                         path == FDLBM_PATH_STAGED || h->adjoint);
     cudaGetDevice(&h->device);
     *out = h;
     return FDLBM_OK;
@@ -385,7 +386,7 @@ size_t fdlbm_workspace_bytes(const fdlbm_grid *g, const fdlbm_opts *opts)
     const int path = choose_path(g, &o);
     if (path < 0) return 0;
     return make_layout(g->nx, g->ny, pitch_of(g->nx), o.precision, o.has_force,
-                       path == FDLBM_PATH_STAGED)
+                       path == FDLBM_PATH_STAGED || o.adjoint)
         .total;
 }
 
@@ -633,6 +634,75 @@ int fdlbm_kernels_per_step(fdlbm_t h)
     const bool walls = h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL;
     if (h->scheme == FDLBM_SCHEME_T2S2_2) return walls ? 6 : 3;
     return walls ? 5 : 3;
+}
+
+size_t fdlbm_state_bytes(fdlbm_t h)
+{
+    return h ? 9 * h->plane * real_size(h->precision) : 0;
+}
+
+fdlbm_status fdlbm_state_layout(fdlbm_t h, int *pitch, int *elem_bytes)
+{
+    if (!h || !pitch || !elem_bytes) return FDLBM_EINVAL;
+    *pitch = h->pitch;
+    *elem_bytes = (int)real_size(h->precision);
+    return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_copy_state(fdlbm_t h, void *buf, int to_handle)
+{
+    if (!h || !buf) return FDLBM_EINVAL;
+    char *st = h->ws + h->lay.state[h->cur];
+    const size_t n = fdlbm_state_bytes(h);
+    cudaError_t e = to_handle ? cudaMemcpyAsync(st, buf, n, cudaMemcpyDeviceToDevice, h->stream)
+                              : cudaMemcpyAsync(buf, st, n, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy_state");
+    if (to_handle) h->have_uprev = false;
+    return FDLBM_OK;
+}
+
+fdlbm_status fdlbm_adjoint_step(fdlbm_t h, const void *state_n, const void *lam_next,
+                                void *lam_prev, double *dforce)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (!state_n || !lam_next || !lam_prev || lam_next == lam_prev)
+        return fail(h, FDLBM_EINVAL, "adjoint_step: NULL or aliased buffers");
+    if (!h->adjoint || h->bc_x != FDLBM_PERIODIC || h->bc_y != FDLBM_PERIODIC ||
+        h->scheme != FDLBM_SCHEME_T2S2_1)
+        return fail(h, FDLBM_EUNSUPPORTED,
+                    "adjoint_step: needs opts.adjoint, a periodic grid and scheme T2S2_1");
+    cudaError_t e;
+    double *fB = reinterpret_cast<double *>(h->ws + h->lay.S);
+    if (h->precision == FDLBM_FP32_DEV) {
+        StepArgs<float> a = step_args<float>(h);
+        a.gin = static_cast<const float *>(state_n);
+        e = launch_adjoint<float>(a, static_cast<const float *>(lam_next), static_cast<float *>(lam_prev),
+                                  a.P, a.Q, fB, dforce, h->stream);
+    } else {
+        StepArgs<double> a = step_args<double>(h);
+        a.gin = static_cast<const double *>(state_n);
+        e = launch_adjoint<double>(a, static_cast<const double *>(lam_next),
+                                   static_cast<double *>(lam_prev), a.P, a.Q, fB, dforce, h->stream);
+    }
+    return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "adjoint_step");
+}
+
+fdlbm_status fdlbm_moments_vjp(fdlbm_t h, const void *state, const double *du, void *lam,
+                               double *dforce)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (!state || !du || !lam) return fail(h, FDLBM_EINVAL, "moments_vjp: NULL buffer");
+    cudaError_t e;
+    if (h->precision == FDLBM_FP32_DEV) {
+        StepArgs<float> a = step_args<float>(h);
+        a.gin = static_cast<const float *>(state);
+        e = launch_moments_vjp<float>(a, du, static_cast<float *>(lam), dforce, h->stream);
+    } else {
+        StepArgs<double> a = step_args<double>(h);
+        a.gin = static_cast<const double *>(state);
+        e = launch_moments_vjp<double>(a, du, static_cast<double *>(lam), dforce, h->stream);
+    }
+    return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "moments_vjp");
 }
 
 const char *fdlbm_last_error(fdlbm_t h) { return h ? h->err.c_str() : "NULL handle"; }

@@ -64,6 +64,7 @@ struct fdlbm_ctx {
     int path = FDLBM_PATH_FUSED;
     int variant = FDLBM_VARIANT_SCALAR;  // fused kernel actually used
     bool in_batch = false;               // owned by a batch: stepped by fdlbm_batch_step
+    bool adjoint = false;                // scratch for the adjoint step reserved
     int rows = 64;
     cudaStream_t stream = nullptr;
     char *ws = nullptr;
@@ -119,6 +120,13 @@ cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s);
 // step_batched.cu
 template <class R>
 cudaError_t launch_batched(const BatchTables &t, int parity, dim3 blk, cudaStream_t s);
+// adjoint.cu
+template <class R>
+cudaError_t launch_adjoint(const StepArgs<R> &a, const R *lam_next, R *lam_prev, R *P, R *lgs,
+                           double *fB, double *dforce, cudaStream_t s);
+template <class R>
+cudaError_t launch_moments_vjp(const StepArgs<R> &a, const double *du, R *lam, double *dforce,
+                               cudaStream_t s);
 // fields.cu
 cudaError_t launch_init_fields(fdlbm_ctx *h, const double *rho, const double *ux,
                                const double *uy, const double *grad, int row0, int nrows,

@@ -33,7 +33,7 @@ class FDLBM:
     def __init__(self, xa, ya, *, nu: float, cfl: float, blend: float, A: float = 0.5,
                  precision: str = "fp64", rho0: float = 1.0, has_force: bool = False,
                  wall_u=None, path: str = "auto", rows_per_cta: int = 0, variant: str = "auto",
-                 scheme: int = 1, stream=None, device=None):
+                 scheme: int = 1, adjoint: bool = False, stream=None, device=None):
         self._L = L = B.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.nx, self.ny = xa.n, ya.n
@@ -50,6 +50,7 @@ class FDLBM:
         o.path = {"auto": B.PATH_AUTO, "fused": B.PATH_FUSED, "staged": B.PATH_STAGED}[path]
         o.rows_per_cta = rows_per_cta
         o.scheme = {1: B.SCHEME_T2S2_1, 2: B.SCHEME_T2S2_2}[scheme]
+        o.adjoint = int(adjoint)
         o.variant = {"auto": B.VARIANT_AUTO, "scalar": B.VARIANT_SCALAR,
                      "packed": B.VARIANT_PACKED, "tma": B.VARIANT_TMA,
                      "async": B.VARIANT_ASYNC}[variant]
@@ -200,6 +201,40 @@ class FDLBM:
 
     def sync(self):
         _check(self._L, self._h, self._L.fdlbm_sync(self._h), "sync")
+
+    # ----------------------------------------------------------- reverse mode
+    def layout(self):
+        """(pitch, dtype) of the storage layout of states and cotangents."""
+        p, e = ctypes.c_int(), ctypes.c_int()
+        _check(self._L, self._h, self._L.fdlbm_state_layout(self._h, ctypes.byref(p), ctypes.byref(e)),
+               "state_layout")
+        return p.value, (torch.float32 if e.value == 4 else torch.float64)
+
+    def new_buffer(self):
+        """A zeroed device buffer in the storage layout, shaped [9, ny, pitch]."""
+        pitch, dt = self.layout()
+        return torch.zeros((9, self.ny, pitch), dtype=dt, device=self.device)
+
+    def save_state(self, buf):
+        _check(self._L, self._h, self._L.fdlbm_copy_state(self._h, buf.data_ptr(), 0), "copy_state")
+        return buf
+
+    def load_state(self, buf):
+        _check(self._L, self._h, self._L.fdlbm_copy_state(self._h, buf.data_ptr(), 1), "copy_state")
+        return self
+
+    def adjoint_step(self, state_n, lam_next, lam_prev, dforce=None):
+        rc = self._L.fdlbm_adjoint_step(self._h, state_n.data_ptr(), lam_next.data_ptr(),
+                                        lam_prev.data_ptr(),
+                                        dforce.data_ptr() if dforce is not None else None)
+        _check(self._L, self._h, rc, "adjoint_step")
+
+    def moments_vjp(self, state, du, lam, dforce=None):
+        du = du.detach().to(torch.float64).contiguous()
+        rc = self._L.fdlbm_moments_vjp(self._h, state.data_ptr(), du.data_ptr(), lam.data_ptr(),
+                                       dforce.data_ptr() if dforce is not None else None)
+        _check(self._L, self._h, rc, "moments_vjp")
+        return du
 
 
 class FDLBMBatch:

@@ -1,0 +1,166 @@
+"""Reverse mode: the hand-written adjoint step and the checkpointed rollout
+gradient, against (a) the transposed Jacobian of the oracle's step assembled
+column by column from exact complex-step derivatives, (b) finite differences
+of the GPU forward step, (c) central finite differences of the full rollout."""
+import math
+
+import numpy as np
+import pytest
+
+import inputs as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1911_12913_gb300.adjoint import rollout_velocity  # noqa: E402
+from paper_1911_12913_gb300.solver import FDLBM  # noqa: E402
+
+NU, CFL, BETA = 0.02, 0.4, 0.2
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _problem(nx, ny, seed, precision="fp64", metrics=True):
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 0.9)
+    if metrics:
+        xa.metric = I.random_metric(nx, seed + 1, base=nx, spread=0.3)
+        ya.metric = I.random_metric(ny, seed + 2, base=ny / 0.9, spread=0.3)
+    s = FDLBM(xa, ya, nu=NU, cfl=CFL, blend=BETA, has_force=True, adjoint=True,
+              precision=precision)
+    o = O.Oracle(xa, ya, nu=NU, dt=s.dt, beta=BETA)
+    r = I.random_fields(nx, ny, seed)
+    o.init_fields(r["rho"], r["ux"], r["uy"], grad=[r["dudx"], r["dudy"], r["dvdx"], r["dvdy"]])
+    rng = np.random.default_rng(seed + 3)
+    force = 2e-3 * rng.uniform(-1, 1, size=(2, ny, nx))
+    return xa, ya, s, o.f.copy(), force, rng
+
+
+def _to_buffer(s, arr):
+    buf = s.new_buffer()
+    buf[:, :, : s.nx] = torch.as_tensor(arr, dtype=buf.dtype, device=buf.device)
+    return buf
+
+
+@pytest.mark.parametrize("nx,ny", [(6, 5), (9, 7)])
+def test_adjoint_step_equals_oracle_transposed_jacobian(nx, ny):
+    xa, ya, s, f0, force, rng = _problem(nx, ny, seed=10 * nx + ny)
+    lam = rng.normal(size=f0.shape)
+    s.set_state(f0)
+    s.set_force(force)
+    state = s.save_state(s.new_buffer())
+    out = s.new_buffer()
+    dF = torch.zeros((2, ny, nx), dtype=torch.float64, device=s.device)
+    s.adjoint_step(state, _to_buffer(s, lam), out, dF)
+    s.sync()
+    ref_f, ref_F = O.step_vjp(xa, ya, nu=NU, dt=s.dt, beta=BETA, f0=f0, lam=lam, force=force)
+    got_f = out[:, :, :nx].cpu().numpy()
+    assert rel(got_f, ref_f) <= 1e-12
+    assert rel(dF.cpu().numpy(), ref_F) <= 1e-12
+
+
+def test_adjoint_dot_product_against_forward_differences():
+    """<J v, w> from central differences of the GPU forward step equals
+    <v, J^T w> from the adjoint step (16 x 16, FP64)."""
+    nx = ny = 16
+    xa, ya, s, f0, force, rng = _problem(nx, ny, seed=5)
+    s.set_state(f0)
+    s.set_force(force)
+    g = s.save_state(s.new_buffer())
+    v = _to_buffer(s, rng.normal(size=f0.shape))
+    w = _to_buffer(s, rng.normal(size=f0.shape))
+    eps = 1e-6
+
+    def step_of(buf):
+        s.load_state(buf)
+        s.step(1)
+        return s.save_state(s.new_buffer())
+
+    jv = (step_of(g + eps * v) - step_of(g - eps * v)) / (2 * eps)
+    jtw = s.new_buffer()
+    s.adjoint_step(g, w, jtw, None)
+    s.sync()
+    lhs = float((jv[:, :, :nx] * w[:, :, :nx]).sum())
+    rhs = float((v[:, :, :nx] * jtw[:, :, :nx]).sum())
+    assert abs(lhs - rhs) <= 1e-8 * abs(rhs)
+
+
+def _loss_and_grad(s, f0buf, force, target, nsteps):
+    F = torch.tensor(force, dtype=torch.float64, device=s.device, requires_grad=True)
+    u = rollout_velocity(s, F, f0buf, nsteps)
+    loss = 0.5 * ((u - target) ** 2).sum()
+    loss.backward()
+    return float(loss.detach()), F.grad.detach().cpu().numpy()
+
+
+def _loss(s, f0buf, force, target, nsteps):
+    F = torch.tensor(force, dtype=torch.float64, device=s.device)
+    with torch.no_grad():
+        u = rollout_velocity(s, F, f0buf, nsteps)
+    return float(0.5 * ((u - target) ** 2).sum())
+
+
+def test_rollout_gradient_matches_central_differences():
+    """dJ/dF of J = 1/2 |u_N(F) - u*|^2 over a 30-step rollout (checkpoints every
+    6 steps) against central differences along random directions (16 x 16, FP64)."""
+    nx = ny = 16
+    nsteps = 30
+    xa, ya, s, f0, force, rng = _problem(nx, ny, seed=8)
+    s.set_state(f0)
+    f0buf = s.save_state(s.new_buffer())
+    target = torch.zeros((2, ny, nx), dtype=torch.float64, device=s.device)
+    hidden = force + 1e-3 * rng.uniform(-1, 1, size=force.shape)
+    with torch.no_grad():
+        target = rollout_velocity(s, torch.tensor(hidden, device=s.device), f0buf, nsteps).clone()
+    J, grad = _loss_and_grad(s, f0buf, force, target, nsteps)
+    assert J > 0
+    def central(V, eps):
+        return (_loss(s, f0buf, force + eps * V, target, nsteps) -
+                _loss(s, f0buf, force - eps * V, target, nsteps)) / (2 * eps)
+
+    for k in range(3):
+        V = rng.normal(size=force.shape)
+        # Richardson-extrapolated central difference: truncation O(eps^4)
+        eps = 2e-4
+        fd = (4.0 * central(V, eps / 2) - central(V, eps)) / 3.0
+        ad = float(np.sum(grad * V))
+        assert abs(fd - ad) <= 1e-6 * abs(fd), (k, fd, ad)
+
+
+def test_fp32_adjoint_close_to_fp64():
+    nx, ny = 40, 33
+    res = {}
+    for prec in ("fp64", "fp32"):
+        xa, ya, s, f0, force, rng = _problem(nx, ny, seed=21, precision=prec)
+        lam = np.random.default_rng(99).normal(size=f0.shape)
+        s.set_state(f0)
+        s.set_force(force)
+        state = s.save_state(s.new_buffer())
+        out = s.new_buffer()
+        dF = torch.zeros((2, ny, nx), dtype=torch.float64, device=s.device)
+        s.adjoint_step(state, _to_buffer(s, lam), out, dF)
+        s.sync()
+        res[prec] = (out[:, :, :nx].double().cpu().numpy(), dF.cpu().numpy())
+    e_lam = rel(res["fp32"][0], res["fp64"][0])
+    e_F = rel(res["fp32"][1], res["fp64"][1])
+    print(f"FP32 adjoint vs FP64: rel lam {e_lam:.2e}, rel dF {e_F:.2e}")
+    assert e_lam <= 1e-5 and e_F <= 1e-4
+
+
+def test_adjoint_rejects_walls_and_missing_scratch():
+    xa = I.periodic_axis(16, 0.0, 1.0)
+    s = FDLBM(xa, xa, nu=NU, cfl=CFL, blend=BETA)        # no adjoint scratch
+    b = s.new_buffer()
+    with pytest.raises(Exception, match="EUNSUPPORTED"):
+        s.adjoint_step(b, b.clone(), s.new_buffer())
+    wa = I.wall_axis(15, 0.0, 1.0)
+    w = FDLBM(xa, wa, nu=NU, cfl=CFL, blend=BETA, adjoint=True)
+    bw = w.new_buffer()
+    with pytest.raises(Exception, match="EUNSUPPORTED"):
+        w.adjoint_step(bw, bw.clone(), w.new_buffer())

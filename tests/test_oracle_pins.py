@@ -491,3 +491,31 @@ def test_poiseuille_converges_under_refinement():
         assert np.abs(uy).max() < 1e-12
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert errs[-1] < 0.015 and min(orders) > 1.2, (errs, orders)
+
+
+# ----------------------------------------------------------------- complex-step build
+def test_complex_build_is_the_same_arithmetic():
+    """The complex-valued build of the oracle (used for exact complex-step
+    Jacobians) returns the real oracle's step bit for bit in its real part, and
+    its complex-step directional derivative matches central differences."""
+    xa = I.periodic_axis(6, 0.0, 1.0)
+    ya = I.periodic_axis(5, 0.0, 0.9)
+    xa.metric = I.random_metric(6, 2, base=6)
+    r = I.random_fields(6, 5, 3)
+    rng = np.random.default_rng(1)
+    F = 1e-3 * rng.normal(size=(2, 5, 6))
+    o = O.Oracle(xa, ya, nu=0.02, dt=0.05, beta=0.2, force=F)
+    o.init_fields(r["rho"], r["ux"], r["uy"], grad=[r["dudx"], r["dudy"], r["dvdx"], r["dvdy"]])
+    f0 = o.f.copy()
+    v = rng.normal(size=f0.shape)
+    y = O.step_complex(xa, ya, nu=0.02, dt=0.05, beta=0.2, f=f0 + 1e-20j * v, force=F)
+
+    def real_step(f):
+        q = O.Oracle(xa, ya, nu=0.02, dt=0.05, beta=0.2, force=F)
+        q.f = f.copy()
+        return q.step(1).f
+
+    assert np.array_equal(y.real, real_step(f0))
+    eps = 1e-6
+    fd = (real_step(f0 + eps * v) - real_step(f0 - eps * v)) / (2 * eps)
+    assert np.linalg.norm(y.imag / 1e-20 - fd) <= 1e-9 * np.linalg.norm(fd)
