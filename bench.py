@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-variants", action="store_true", help="skip timing the other variant")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-case batched sweep")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurements")
+    p.add_argument("--no-cavity", action="store_true", help="skip the 257^2 cavity march")
     return p.parse_args()
 
 
@@ -243,6 +244,50 @@ def run_batched(stream_dev, ncases=64, seed=2024, steps=200, graph_steps=50):
                        f"Re log-uniform [10, 2000], CFL {CFL}, blend {BLEND}, FP32"}
     b.close()
     return out
+
+
+# ----------------------------------------------------------------------- lid-driven cavity
+def run_cavity(dev, n_cells=256, c=1.5, U=0.1, Re=1000.0, cfl=0.9, eta=0.1, tol=1e-8):
+    """Sec. 3C cavity on the (n_cells + 1)^2 tanh grid: FP64 march to E(u) < tol
+    (checked every 100 steps, CUDA-graph replay of 100 steps), then the same
+    number of steps with FP32-deviation storage.  Wall-clock timing of the whole
+    march, residual checks included."""
+    import numpy as np
+    import torch
+    import inputs as I
+    from paper_1911_12913_gb300.analysis import march_to_steady, stream_function, vortex_centre
+    from paper_1911_12913_gb300.solver import FDLBM
+
+    ax = I.tanh_axis(n_cells, c)
+    lid = [(0, 0), (0, 0), (0, 0), (U, 0.0)]
+    res = {}
+    u = {}
+    steps_cap = 1_000_000
+    for prec in ("fp64", "fp32"):
+        s = FDLBM(ax, ax, nu=U / Re, cfl=cfl, blend=eta, precision=prec, wall_u=lid,
+                  graph_steps=100, device=dev)
+        one = np.ones((ax.n, ax.n))
+        s.init_fields(one, 0 * one, 0 * one)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, r, _ = march_to_steady(s, tol, max_steps=steps_cap)
+        el = time.perf_counter() - t0
+        _, ux, uy = s.moments()
+        psi = stream_function(ax.coords, ux)
+        xc, yc, _ = vortex_centre(ax.coords, ax.coords, psi, (0.3, 0.7, 0.3, 0.8), -1)
+        u[prec] = (ux, uy)
+        res[prec] = {"steps": steps, "E_u": r, "converged": bool(r < tol), "t": steps * s.dt,
+                     "wall_s": el, "MLUPS": ax.n * ax.n * steps / el / 1e6,
+                     "primary_vortex": [round(xc, 4), round(yc, 4)], "kernel": s.describe,
+                     "launches_per_step": s.kernels_per_step}
+        steps_cap = steps   # FP32 runs as many steps as FP64 needed
+        del s
+    du = [np.linalg.norm(u["fp32"][k] - u["fp64"][k]) / np.linalg.norm(u["fp64"][k]) for k in (0, 1)]
+    res["fp32"]["rel_L2_u_vs_fp64"] = float(np.hypot(*du))
+    res["workload"] = (f"lid-driven cavity {ax.n}x{ax.n} tanh c={c}, lid U={U}, Re={Re:g}, CFL {cfl}, "
+                       f"eta {eta}, walls Eq. 3.10, march to E(u) < {tol:g}")
+    res["paper_primary_vortex"] = [0.5330, 0.5670]
+    return res
 
 
 # ----------------------------------------------------------------------- reverse mode
@@ -467,6 +512,12 @@ def run_ours(args):
         adjoint = run_adjoint(dev)
         torch.cuda.empty_cache()
 
+    # ---------------- 257^2 lid-driven cavity at Re = 1000 to steady state
+    cavity = None
+    if not args.no_cavity and rank == 0:
+        cavity = run_cavity(dev)
+        torch.cuda.empty_cache()
+
     # ---------------- end to end through the C ABI with pinned host buffers
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in f.items()}
     out_host = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(3)]
@@ -514,6 +565,7 @@ def run_ours(args):
                "config": config(n, "fp32", args.steps), "clocks": clk.summary(),
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                "cpu_baseline": cpu, "fp64": fp64, "fp32_variants": variants, "batched": batched, "adjoint": adjoint,
+               "cavity": cavity,
                "mass_drift_rel": mass_drift,
                "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(out), flush=True)

@@ -101,6 +101,8 @@ typedef struct {
     int variant;              /* FDLBM_VARIANT_*; PACKED where it does not apply -> EUNSUPPORTED */
     int scheme;               /* FDLBM_SCHEME_T2S2_1 (default) or FDLBM_SCHEME_T2S2_2 */
     int adjoint;              /* 1: reserve scratch for fdlbm_adjoint_step (periodic grids) */
+    int graph_steps;          /* > 0: fdlbm_step replays a CUDA graph of this many steps (rounded
+                                 up to even), captured on first use; 0 = direct launches */
     void *stream;             /* cudaStream_t used for all work; NULL = default stream */
     void *workspace;          /* caller-owned device memory of fdlbm_workspace_bytes() bytes,
                                  256-byte aligned; NULL = the library allocates its own */

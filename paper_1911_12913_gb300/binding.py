@@ -42,6 +42,7 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("has_force", ctypes.c_int),
                 ("path", ctypes.c_int), ("rows_per_cta", ctypes.c_int), ("variant", ctypes.c_int),
                 ("scheme", ctypes.c_int), ("adjoint", ctypes.c_int),
+                ("graph_steps", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 

@@ -153,6 +153,73 @@ StepArgs<R> step_args(fdlbm_ctx *h)
     return a;
 }
 
+// One step of whichever kernel the handle uses, reading state[cur], on stream s.
+cudaError_t launch_step(fdlbm_ctx *h, cudaStream_t s)
+{
+    if (h->precision == FDLBM_FP32_DEV) {
+        auto a = step_args<float>(h);
+        if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
+        if (h->variant == FDLBM_VARIANT_PACKED) return launch_fused_x2(a, a.err, s);
+        if (h->variant == FDLBM_VARIANT_TMA) return launch_fused_tma(a, s);
+        if (h->variant == FDLBM_VARIANT_ASYNC) return launch_fused_async(a, s);
+        return launch_fused(a, s);
+    }
+    auto a = step_args<double>(h);
+    if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
+    if (h->variant == FDLBM_VARIANT_TMA) return launch_fused_tma(a, s);
+    if (h->variant == FDLBM_VARIANT_ASYNC) return launch_fused_async(a, s);
+    return launch_fused(a, s);
+}
+
+fdlbm_status step_direct(fdlbm_ctx *h, int n)
+{
+    for (int k = 0; k < n; ++k) {
+        cudaError_t e = launch_step(h, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step");
+        h->cur = 1 - h->cur;
+        ++h->steps;
+    }
+    return FDLBM_OK;
+}
+
+void drop_step_graph(fdlbm_ctx *h)
+{
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+}
+
+// Record graph_steps steps starting from state[0] on a private stream (capture
+// is not allowed on the legacy default stream); the graph is then replayed on
+// the handle's stream.  Every kernel argument is fixed for the handle's life
+// (buffers live in the workspace), so one capture serves every replay.
+fdlbm_status capture_step_graph(fdlbm_ctx *h)
+{
+    drop_step_graph(h);
+    cudaStream_t cs = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(h, e, "step graph stream");
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    cudaError_t el = cudaSuccess;
+    const int cur0 = h->cur;
+    if (e == cudaSuccess) {
+        for (int k = 0; k < h->graph_steps && el == cudaSuccess; ++k) {
+            h->cur = k & 1;
+            el = launch_step(h, cs);
+        }
+        h->cur = cur0;
+        e = cudaStreamEndCapture(cs, &h->graph);
+    }
+    if (e == cudaSuccess && el == cudaSuccess) e = cudaGraphInstantiate(&h->gexec, h->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess || el != cudaSuccess) {
+        drop_step_graph(h);
+        return cuda_fail(h, e != cudaSuccess ? e : el, "step graph capture");
+    }
+    return FDLBM_OK;
+}
+
 // Copy `nfields` host or device fields ([ny][nx] FP64 each) through the staging
 // area in row chunks and hand each chunk to `kernel(ptr, row0, nrows, fstride)`.
 template <class K>
@@ -253,7 +320,7 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
 {
     if (!grid_ok(g) || !(nu > 0) || !(cfl > 0) || !(blend >= 0 && blend <= 1) ||
         !(o.A >= 0 && o.A <= 1) || !(o.rho0 > 0) ||
-        (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0 ||
+        (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0 || o.graph_steps < 0 ||
         o.variant < FDLBM_VARIANT_AUTO || o.variant > FDLBM_VARIANT_ASYNC ||
         (o.scheme != FDLBM_SCHEME_T2S2_1 && o.scheme != FDLBM_SCHEME_T2S2_2))
         return FDLBM_EINVAL;
@@ -308,6 +375,7 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
                                      : choose_rows(g->nx, g->ny, o.precision, variant);
     h->stream = static_cast<cudaStream_t>(o.stream);
     h->adjoint = o.adjoint != 0;
+    h->graph_steps = o.graph_steps > 0 ? o.graph_steps + (o.graph_steps & 1) : 0;
     h->lay = make_layout(h->nx, h->ny, h->pitch, h->precision, h->has_force,
                          path == FDLBM_PATH_STAGED || h->adjoint);
     cudaGetDevice(&h->device);
@@ -435,6 +503,7 @@ void fdlbm_destroy(fdlbm_t h)
         cudaStreamSynchronize(h->stream);
         cudaFree(h->ws);
     }
+    drop_step_graph(h);
     delete h;
 }
 
@@ -524,36 +593,24 @@ fdlbm_status fdlbm_step(fdlbm_t h, int n)
     if (n < 0) return fail(h, FDLBM_EINVAL, "step: n < 0");
     if (h->in_batch)
         return fail(h, FDLBM_EUNSUPPORTED, "step: a batch case advances with fdlbm_batch_step");
-    for (int k = 0; k < n; ++k) {
-        cudaError_t e;
-        if (h->precision == FDLBM_FP32_DEV) {
-            auto a = step_args<float>(h);
-            if (h->path == FDLBM_PATH_STAGED)
-                e = launch_staged(a, h->stream);
-            else if (h->variant == FDLBM_VARIANT_PACKED)
-                e = launch_fused_x2(a, a.err, h->stream);
-            else if (h->variant == FDLBM_VARIANT_TMA)
-                e = launch_fused_tma(a, h->stream);
-            else if (h->variant == FDLBM_VARIANT_ASYNC)
-                e = launch_fused_async(a, h->stream);
-            else
-                e = launch_fused(a, h->stream);
-        } else {
-            auto a = step_args<double>(h);
-            if (h->path == FDLBM_PATH_STAGED)
-                e = launch_staged(a, h->stream);
-            else if (h->variant == FDLBM_VARIANT_TMA)
-                e = launch_fused_tma(a, h->stream);
-            else if (h->variant == FDLBM_VARIANT_ASYNC)
-                e = launch_fused_async(a, h->stream);
-            else
-                e = launch_fused(a, h->stream);
+    const int G = h->graph_steps;
+    if (G > 0 && n >= G + h->cur) {
+        if (h->cur) {  // the graph starts from state[0]
+            fdlbm_status st = step_direct(h, 1);
+            if (st != FDLBM_OK) return st;
+            --n;
         }
-        if (e != cudaSuccess) return cuda_fail(h, e, "step");
-        h->cur = 1 - h->cur;
-        ++h->steps;
+        if (!h->gexec) {
+            fdlbm_status st = capture_step_graph(h);
+            if (st != FDLBM_OK) return st;
+        }
+        for (; n >= G; n -= G) {
+            cudaError_t e = cudaGraphLaunch(h->gexec, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "step (graph launch)");
+            h->steps += G;
+        }
     }
-    return FDLBM_OK;
+    return step_direct(h, n);
 }
 
 fdlbm_status fdlbm_moments(fdlbm_t h, double *rho, double *ux, double *uy, int where)
@@ -721,6 +778,7 @@ const char *fdlbm_describe(fdlbm_t h)
                        : h->variant == FDLBM_VARIANT_ASYNC  ? "fused-async"
                                                             : "fused";
     h->desc = std::string(kern) + " " + prec + " rows=" + std::to_string(h->rows);
+    if (h->graph_steps) h->desc += " graph_steps=" + std::to_string(h->graph_steps);
     return h->desc.c_str();
 }
 

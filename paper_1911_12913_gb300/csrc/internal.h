@@ -65,6 +65,9 @@ struct fdlbm_ctx {
     int variant = FDLBM_VARIANT_SCALAR;  // fused kernel actually used
     bool in_batch = false;               // owned by a batch: stepped by fdlbm_batch_step
     bool adjoint = false;                // scratch for the adjoint step reserved
+    int graph_steps = 0;                 // steps per replayed CUDA graph (even), 0 = none
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
     int rows = 64;
     cudaStream_t stream = nullptr;
     char *ws = nullptr;

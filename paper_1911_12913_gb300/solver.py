@@ -28,12 +28,15 @@ class FDLBM:
     ``length`` (see ``inputs.Axis``).  ``blend``: upwind weight of the mixed
     difference.  ``precision``: ``"fp64"`` or ``"fp32"`` (FP32 deviation storage).
     ``scheme``: 1 = T2S2-FDLBM1 (Eq. 2.23, A = 0 gives T1S2), 2 = T2S2-FDLBM2 (Eq. 5.23).
+    ``graph_steps``: > 0 replays a CUDA graph of that many steps inside ``step``
+    (small grids, where launch latency dominates).
     """
 
     def __init__(self, xa, ya, *, nu: float, cfl: float, blend: float, A: float = 0.5,
                  precision: str = "fp64", rho0: float = 1.0, has_force: bool = False,
                  wall_u=None, path: str = "auto", rows_per_cta: int = 0, variant: str = "auto",
-                 scheme: int = 1, adjoint: bool = False, stream=None, device=None):
+                 scheme: int = 1, adjoint: bool = False, graph_steps: int = 0, stream=None,
+                 device=None):
         self._L = L = B.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.nx, self.ny = xa.n, ya.n
@@ -51,6 +54,7 @@ class FDLBM:
         o.rows_per_cta = rows_per_cta
         o.scheme = {1: B.SCHEME_T2S2_1, 2: B.SCHEME_T2S2_2}[scheme]
         o.adjoint = int(adjoint)
+        o.graph_steps = graph_steps
         o.variant = {"auto": B.VARIANT_AUTO, "scalar": B.VARIANT_SCALAR,
                      "packed": B.VARIANT_PACKED, "tma": B.VARIANT_TMA,
                      "async": B.VARIANT_ASYNC}[variant]
