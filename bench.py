@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--n", type=int, default=N_GRID)
     p.add_argument("--fp64-steps", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--variant", default="auto", choices=["auto", "scalar", "packed", "tma", "async"],
+    p.add_argument("--variant", default="auto", choices=["auto", "scalar", "packed", "tma", "async", "warp"],
                    help="FP32 fused kernel variant for the headline timing")
     p.add_argument("--no-variants", action="store_true", help="skip timing the other variant")
     p.add_argument("--no-batched", action="store_true", help="skip the 64-case batched sweep")
@@ -455,7 +455,7 @@ def run_ours(args):
     # ---------------- both FP32 fused variants, same workload, shorter runs
     variants = {}
     if not args.no_variants:
-        for var in ("scalar", "async", "tma", "packed"):
+        for var in ("scalar", "async", "tma", "packed", "warp"):
             try:
                 sv = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream,
                            variant=var)

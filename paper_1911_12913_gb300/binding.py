@@ -19,7 +19,7 @@ FP64, FP32_DEV = 0, 1
 PATH_AUTO, PATH_FUSED, PATH_STAGED = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 SCHEME_T2S2_1, SCHEME_T2S2_2 = 0, 1
-VARIANT_AUTO, VARIANT_SCALAR, VARIANT_PACKED, VARIANT_TMA, VARIANT_ASYNC = 0, 1, 2, 3, 4
+VARIANT_AUTO, VARIANT_SCALAR, VARIANT_PACKED, VARIANT_TMA, VARIANT_ASYNC, VARIANT_WARP = 0, 1, 2, 3, 4, 5
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EUNSUPPORTED",
           -6: "ETOOBIG"}
 

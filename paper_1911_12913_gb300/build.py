@@ -20,6 +20,9 @@ BUILD = PKG / "_build"
 LIB = PKG / "_lib" / "libfdlbm.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}", f"-I{CSRC}"]
+# Extra nvcc flags (tuning macros such as -DFDLBM_WARP_MIN_BLOCKS=12); a change
+# here needs build(force=True).
+EXTRA = os.environ.get("FDLBM_NVCC_EXTRA", "").split()
 
 
 def _nvcc() -> str:
@@ -48,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         obj = BUILD / (src.stem + ".o")
         if not force and obj.exists() and obj.stat().st_mtime >= max(src.stat().st_mtime, hdr):
             return obj, False
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", str(src), "-o", str(obj)]
+        cmd = [nvcc, *ARCH, *FLAGS, *EXTRA, "-c", str(src), "-o", str(obj)]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

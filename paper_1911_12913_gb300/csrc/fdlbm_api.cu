@@ -97,6 +97,8 @@ int choose_rows(int nx, int ny, int precision, int variant)
     int per_sm;
     if (variant == FDLBM_VARIANT_PACKED)
         per_sm = fused_x2_blocks_per_sm();
+    else if (variant == FDLBM_VARIANT_WARP)
+        per_sm = fused_warp_blocks_per_sm();
     else if (variant == FDLBM_VARIANT_TMA)
         per_sm = f32 ? fused_tma_blocks_per_sm<float>() : fused_tma_blocks_per_sm<double>();
     else if (variant == FDLBM_VARIANT_ASYNC)
@@ -105,7 +107,9 @@ int choose_rows(int nx, int ny, int precision, int variant)
         per_sm = f32 ? fused_blocks_per_sm<float>() : fused_blocks_per_sm<double>();
     if (per_sm <= 0) per_sm = 1;
     const long long slots = (long long)per_sm * sms;
-    const int W = variant == FDLBM_VARIANT_PACKED ? fused_x2_tile_width() : fused_tile_width();
+    const int W = variant == FDLBM_VARIANT_PACKED ? fused_x2_tile_width()
+                  : variant == FDLBM_VARIANT_WARP ? fused_warp_tile_width()
+                                                  : fused_tile_width();
     const long long strips = (nx + W - 1) / W;
     int best = std::min(ny, 64);
     double best_cost = 1e300;
@@ -160,6 +164,7 @@ cudaError_t launch_step(fdlbm_ctx *h, cudaStream_t s)
         auto a = step_args<float>(h);
         if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
         if (h->variant == FDLBM_VARIANT_PACKED) return launch_fused_x2(a, a.err, s);
+        if (h->variant == FDLBM_VARIANT_WARP) return launch_fused_warp(a, h->tmap[h->cur], s);
         if (h->variant == FDLBM_VARIANT_TMA) return launch_fused_tma(a, s);
         if (h->variant == FDLBM_VARIANT_ASYNC) return launch_fused_async(a, s);
         return launch_fused(a, s);
@@ -321,7 +326,7 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     if (!grid_ok(g) || !(nu > 0) || !(cfl > 0) || !(blend >= 0 && blend <= 1) ||
         !(o.A >= 0 && o.A <= 1) || !(o.rho0 > 0) ||
         (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0 || o.graph_steps < 0 ||
-        o.variant < FDLBM_VARIANT_AUTO || o.variant > FDLBM_VARIANT_ASYNC ||
+        o.variant < FDLBM_VARIANT_AUTO || o.variant > FDLBM_VARIANT_WARP ||
         (o.scheme != FDLBM_SCHEME_T2S2_1 && o.scheme != FDLBM_SCHEME_T2S2_2))
         return FDLBM_EINVAL;
     const int path = force_staged ? FDLBM_PATH_STAGED : choose_path(g, &o);
@@ -331,7 +336,9 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     const bool packed_ok = fused && f32 && !o.has_force && fused_x2_ok(g->nx, g->ny);
     const bool tma_ok = fused && (f32 ? fused_tma_ok<float>(g->nx, g->ny)
                                       : fused_tma_ok<double>(g->nx, g->ny));
+    const bool warp_ok = fused && f32 && !o.has_force && fused_warp_ok(g->nx, g->ny);
     if ((o.variant == FDLBM_VARIANT_PACKED && !packed_ok) ||
+        (o.variant == FDLBM_VARIANT_WARP && !warp_ok) ||
         (o.variant == FDLBM_VARIANT_TMA && !tma_ok) ||
         (o.variant == FDLBM_VARIANT_ASYNC && !fused))
         return FDLBM_EUNSUPPORTED;
@@ -488,6 +495,13 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
         h->ws_bytes = h->lay.total;
     }
     st = handle_upload(h, mx, my);
+    if (st == FDLBM_OK && h->variant == FDLBM_VARIANT_WARP) {
+        // tensor maps of both ping-pong buffers for the warp-tile kernel
+        for (int b = 0; b < 2 && st == FDLBM_OK; ++b)
+            if (fused_warp_encode(h->tmap[b], reinterpret_cast<const float *>(h->ws + h->lay.state[b]),
+                                  h->nx, h->ny, h->pitch, h->plane) != cudaSuccess)
+                st = FDLBM_EUNSUPPORTED;
+    }
     if (st != FDLBM_OK) {
         fdlbm_destroy(h);
         return st;
@@ -774,6 +788,7 @@ const char *fdlbm_describe(fdlbm_t h)
     }
     const char *kern = h->path == FDLBM_PATH_STAGED        ? "staged"
                        : h->variant == FDLBM_VARIANT_PACKED ? "fused-f32x2"
+                       : h->variant == FDLBM_VARIANT_WARP   ? "fused-warp"
                        : h->variant == FDLBM_VARIANT_TMA    ? "fused-tma"
                        : h->variant == FDLBM_VARIANT_ASYNC  ? "fused-async"
                                                             : "fused";

@@ -66,6 +66,7 @@ struct fdlbm_ctx {
     bool in_batch = false;               // owned by a batch: stepped by fdlbm_batch_step
     bool adjoint = false;                // scratch for the adjoint step reserved
     int graph_steps = 0;                 // steps per replayed CUDA graph (even), 0 = none
+    unsigned char tmap[2][128] = {};     // tensor maps of state[0], state[1] (warp-tile kernel)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int rows = 64;
@@ -117,6 +118,14 @@ bool fused_x2_ok(int nx, int ny);
 cudaError_t launch_fused_x2(const StepArgs<float> &a, int *err, cudaStream_t s);
 int fused_x2_tile_width();
 int fused_x2_blocks_per_sm();
+// step_fused_warp.cu (FP32, one independent warp per tile, packed f32x2)
+bool fused_warp_ok(int nx, int ny);
+size_t fused_warp_map_bytes();
+cudaError_t fused_warp_encode(void *map, const float *state, int nx, int ny, int pitch,
+                              size_t plane);
+cudaError_t launch_fused_warp(const StepArgs<float> &a, const void *map_in, cudaStream_t s);
+int fused_warp_tile_width();
+int fused_warp_blocks_per_sm();
 // step_staged.cu
 template <class R>
 cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s);

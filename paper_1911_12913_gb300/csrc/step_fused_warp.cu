@@ -1,0 +1,385 @@
+// Fused FP32-deviation T2S2-FDLBM step for periodic grids: one warp per tile,
+// two adjacent columns per lane in packed FP32x2 arithmetic, no block-level
+// barrier anywhere.
+//
+// The scheme is the one of step_fused.cu (stages A, B, C of Sec. 2D per row of
+// a bottom-to-top sweep, lags of 2 + 2 rows), laid out so that a warp needs
+// nothing from any other warp:
+//   - a warp owns a window of 64 columns (lane l: columns 2l and 2l+1 as the
+//     .x and .y halves of a float2), of which the middle 56 are its output;
+//     the 4 columns on either side are the x-halo of the two difference stages;
+//   - every difference in y (Eqs. 2.36-2.38) reads the lane's own register
+//     window of the last five rows;
+//   - every difference in x reads the neighbouring lanes' centre values by
+//     warp shuffle: for the pair (2l, 2l+1) the taps 2l-2 .. 2l+3 are the
+//     lane's own pair and the halves of lanes l-1 and l+1;
+//   - a row of f~ (all nine populations of the window) arrives in a per-warp
+//     shared-memory ring by one tiled tensor copy (TMA, 3-D box 64 x 1 x 9)
+//     issued three rows ahead of use; a window that crosses the periodic seam
+//     gets its wrapped columns by a second copy into a side ring;
+//   - f~+ waits four rows in a per-lane shared-memory ring.
+// Lanes 0 and 31 have one neighbour only, so their stage-B values are wrong;
+// the stage-C output of lanes 2..29 reads f* of lanes 1..30 only.
+//
+// Every row runs all three stages with no branch in between: before stage B
+// (C) has valid input, in the first 4 (8) rows of a segment, it computes on
+// the zero-initialised windows and its results are discarded (stage-C stores
+// start at row 8; the stage-B rows it then reads were all written from row 4).
+//
+// The x-differences use weights pre-multiplied by the column's metric and the
+// half step (stage B) or step (stage C), with the centre taps of the x and y
+// differences merged into one coefficient.
+//
+// Every wait on an mbarrier is bounded: on timeout the warp records an error
+// flag, keeps its control flow, waits (bounded) for its copies in flight
+// before it exits, and the host reports the flag.
+//
+// Requirements (checked by the host): nx % 4 == 0 and nx >= 64, so that every
+// copy starts on a 16-byte boundary, a window crosses the seam at most once,
+// and the two columns of a lane never straddle it.
+#include <cstddef>
+#include <cstdint>
+#include <cstring>
+#include <type_traits>
+
+#include <cuda.h>
+
+#include "internal.h"
+#include "packed.cuh"
+#include "tma.cuh"
+
+namespace fdlbm {
+namespace {
+
+using namespace packed;
+
+constexpr int kLanes = 32;
+constexpr int kCols = 2 * kLanes;          // window columns per warp
+constexpr int kHalo = 4;
+constexpr int kW = kCols - 2 * kHalo;      // output columns per warp
+constexpr int kStages = 3;                 // rows of f~ buffered / in flight
+constexpr int kQRing = 5;                  // f~+ rows r-4 .. r
+constexpr unsigned kFull = 0xffffffffu;
+// Resident warps per SM the register allocation is sized for: 8 (two per
+// scheduler) leaves ptxas up to 255 registers; 12 caps it at 168.
+#ifndef FDLBM_WARP_MIN_BLOCKS
+#define FDLBM_WARP_MIN_BLOCKS 8
+#endif
+constexpr uint32_t kRowBytes = 9u * kCols * sizeof(float);
+
+struct WarpSmem {
+    float ring[kStages][9][kCols];  // f~ rows of the window, [pop][window column]
+    float wrap[kStages][9][kCols];  // the same rows at the other side of the seam
+    f2 Q[kQRing][9][kLanes];        // f~+ of the lane's two columns
+    uint64_t bar[kStages];
+};
+static_assert(offsetof(WarpSmem, wrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
+
+struct ArgsW {
+    CUtensorMap tin;  // the input state: dims (nx, ny, 9), box (64, 1, 9)
+    float *gout;
+    const float *mx, *my;
+    int nx, ny, pitch;
+    size_t plane;
+    int rows;
+    float rho0, h, dt, b_bar, b_til, b_star;
+    float w[4];  // wm1, w0, w1, w2
+    int *err;
+};
+
+// The taps other than the centre of sign(c) * D_m f in x for the lane's pair
+// (Eq. 2.36 with Eqs. 2.37-2.38), weighted by c[0..2] = weights of the taps
+// at offsets +1, -1, -2 (sgn > 0) or -1, +1, +2 (sgn < 0), added to acc.  The
+// neighbours' halves come by shuffle from lanes l - 1 and l + 1.
+__device__ __forceinline__ f2 xtaps(const f2 c[3], int sgn, f2 v0, f2 acc)
+{
+    if (sgn > 0) {
+        const float Llo = __shfl_up_sync(kFull, v0.x, 1);
+        const float Lhi = __shfl_up_sync(kFull, v0.y, 1);
+        const float Rlo = __shfl_down_sync(kFull, v0.x, 1);
+        acc = fma2(c[0], make_float2(v0.y, Rlo), acc);
+        acc = fma2(c[1], make_float2(Lhi, v0.x), acc);
+        return fma2(c[2], make_float2(Llo, Lhi), acc);
+    }
+    const float Lhi = __shfl_up_sync(kFull, v0.y, 1);
+    const float Rlo = __shfl_down_sync(kFull, v0.x, 1);
+    const float Rhi = __shfl_down_sync(kFull, v0.y, 1);
+    acc = fma2(c[0], make_float2(Lhi, v0.x), acc);
+    acc = fma2(c[1], make_float2(v0.y, Rlo), acc);
+    return fma2(c[2], make_float2(Rlo, Rhi), acc);
+}
+
+// The same in y from the lane's own window (rows k-2 .. k+2 as vm2 .. vp2).
+__device__ __forceinline__ f2 ytaps(const f2 c[3], int sgn, f2 vm2, f2 vm1, f2 vp1, f2 vp2, f2 acc)
+{
+    if (sgn > 0) return fma2(c[2], vm2, fma2(c[1], vm1, fma2(c[0], vp1, acc)));
+    return fma2(c[2], vp2, fma2(c[1], vp1, fma2(c[0], vm1, acc)));
+}
+
+__global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
+    k_step_fused_warp(const __grid_constant__ ArgsW a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    WarpSmem &sm = *reinterpret_cast<WarpSmem *>(smem_raw);
+
+    const int l = threadIdx.x;
+    const int x0 = blockIdx.x * kW;        // first output column
+    const int y0 = blockIdx.y * a.rows;
+    if (y0 >= a.ny) return;                // uniform over the warp
+    const int y1 = min(y0 + a.rows, a.ny);
+    const int iters = (y1 - y0) + 2 * kHalo;
+    const int xs = x0 - kHalo;             // window start before wrapping
+    const int xc = xs + 2 * l;             // the lane's first column
+    const int gx = wrap_index(xc, a.nx);   // even, and gx + 1 < nx
+    const bool store = (l >= 2) && (l < kLanes - 2) && (xc < a.nx);
+
+    // ---- where the lane's pair lands: the main ring, or the side ring filled
+    // from x = nx - 4 (first window) or x = 0 (last window)
+    const bool wrap_lo = xs < 0, wrap_hi = xs + kCols > a.nx;
+    const int wrap_x = wrap_lo ? a.nx - kHalo : 0;
+    uint32_t rd = (uint32_t)offsetof(WarpSmem, ring) + 8u * (uint32_t)l;
+    if (xc < 0) rd = (uint32_t)offsetof(WarpSmem, wrap) + 4u * (uint32_t)(xc + kHalo);
+    if (xc >= a.nx) rd = (uint32_t)offsetof(WarpSmem, wrap) + 4u * (uint32_t)(xc - a.nx);
+    const unsigned char *rd_base = smem_raw + rd;
+
+    // ---- constants: the x weights carry -h m_x (stage B) and -dt m_x (stage C)
+    const f2 rho0 = bc(a.rho0);
+    const f2 mx2 = make_float2(__ldg(a.mx + gx), __ldg(a.mx + gx + 1));
+    const f2 nhx = mul2(bc(-a.h), mx2), ndx = mul2(bc(-a.dt), mx2);
+    const f2 axB[3] = {mul2(nhx, bc(a.w[0])), mul2(nhx, bc(a.w[2])), mul2(nhx, bc(a.w[3]))};
+    const f2 axC[3] = {mul2(ndx, bc(a.w[0])), mul2(ndx, bc(a.w[2])), mul2(ndx, bc(a.w[3]))};
+    const f2 cxB = mul2(nhx, bc(a.w[1])), cxC = mul2(ndx, bc(a.w[1]));
+    const f2 bbar = bc(a.b_bar), btil = bc(a.b_til), bstar = bc(a.b_star);
+
+    const uint32_t bar0 = smem_addr(&sm.bar[0]);
+    const uint32_t ring0 = smem_addr(&sm.ring[0][0][0]), wrap0 = smem_addr(&sm.wrap[0][0][0]);
+    const uint32_t tx = (wrap_lo || wrap_hi) ? 2u * kRowBytes : kRowBytes;
+    int ld_row = wrap_index(y0 - kHalo, a.ny);  // next row to request
+    auto issue = [&](int slot) {
+        if (l == 0) {
+            fence_proxy_async();
+            const uint32_t bar = bar0 + 8u * (uint32_t)slot;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx)
+                         : "memory");
+            tensor_copy_3d(ring0 + (uint32_t)slot * kRowBytes, &a.tin, xs, ld_row, 0, bar);
+            if (wrap_lo || wrap_hi)
+                tensor_copy_3d(wrap0 + (uint32_t)slot * kRowBytes, &a.tin, wrap_x, ld_row, 0, bar);
+        }
+        ld_row = ld_row + 1 == a.ny ? 0 : ld_row + 1;
+    };
+
+    if (l == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&sm.bar[s], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    for (int s = 0; s < kStages && s < iters; ++s) issue(s);
+
+    f2 Pw[9][5];  // fbar^{+,h} of the lane's columns, slot = iteration mod 5
+    f2 Sw[9][5];  // f*
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) Pw[i][j] = Sw[i][j] = bc(0.f);
+    // rows of stage B (y0 - 6 + k) and C (y0 - 8 + k) at iteration k
+    int rs = wrap_index(y0 - 6, a.ny), rq = wrap_index(y0 - 8, a.ny);
+    float myB = __ldg(a.my + rs), myC = __ldg(a.my + rq);
+    int slot = 0;          // iteration mod 3
+    uint32_t parity = 0;   // mbarrier phase parity of the current slot
+    bool timed_out = false;
+
+    auto row = [&](auto PHc, int k) {
+        constexpr int PH = decltype(PHc)::value;
+        constexpr int p0 = PH, p1 = (PH + 4) % 5, p2 = (PH + 3) % 5, p3 = (PH + 2) % 5,
+                      p4 = (PH + 1) % 5;
+        // ------------------------------------------------------------ A (row r)
+        if (!mbar_wait_bounded(&sm.bar[slot], parity)) timed_out = true;
+        {
+            const unsigned char *src = rd_base + slot * kRowBytes;
+            f2 g[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                g[i] = *reinterpret_cast<const f2 *>(src + i * kCols * sizeof(float));
+            const Macro m = moments2(g, rho0);
+            f2 geq[9];
+            equilibrium2(m, geq);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const f2 neq = sub2(geq[i], g[i]);
+                Pw[i][p0] = fma2(bbar, neq, g[i]);
+                sm.Q[PH][i][l] = fma2(btil, neq, g[i]);
+            }
+        }
+        // every lane has read the slot: refill it three rows ahead
+        __syncwarp();
+        if (k + kStages < iters) issue(slot);
+        // ------------------------------------------------------------ B (row r-2)
+        {
+            const float nhy = -a.h * myB;
+            rs = rs + 1 == a.ny ? 0 : rs + 1;
+            myB = __ldg(a.my + rs);
+            const f2 ay[3] = {bc(nhy * a.w[0]), bc(nhy * a.w[2]), bc(nhy * a.w[3])};
+            // centre coefficients: 1 + the centre weights of the differences taken
+            const f2 c_y = bc(1.f + nhy * a.w[1]);
+            const f2 c_x = add2(bc(1.f), cxB), c_d = add2(c_y, cxB);
+            f2 gs[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const f2 v0 = Pw[i][p2];
+                f2 acc;
+                if (cx(i) != 0 && cy(i) != 0) acc = mul2(c_d, v0);
+                else if (cx(i) != 0) acc = mul2(c_x, v0);
+                else if (cy(i) != 0) acc = mul2(c_y, v0);
+                else acc = v0;
+                if (cx(i) != 0) acc = xtaps(axB, cx(i), v0, acc);
+                if (cy(i) != 0) acc = ytaps(ay, cy(i), Pw[i][p4], Pw[i][p3], Pw[i][p1], Pw[i][p0], acc);
+                gs[i] = acc;
+            }
+            const Macro m = moments2(gs, rho0);
+            f2 geq[9];
+            equilibrium2(m, geq);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Sw[i][p0] = fma2(bstar, sub2(geq[i], gs[i]), gs[i]);
+        }
+        // ------------------------------------------------------------ C (row r-4)
+        // f* rows r-6 .. r-2 sit in slots p4, p3, p2, p1, p0 of Sw.
+        {
+            const float ndy = -a.dt * myC;
+            const int qg = rq;
+            rq = rq + 1 == a.ny ? 0 : rq + 1;
+            myC = __ldg(a.my + rq);
+            const f2 by[3] = {bc(ndy * a.w[0]), bc(ndy * a.w[2]), bc(ndy * a.w[3])};
+            const f2 c_y = bc(ndy * a.w[1]);
+            const f2 c_d = add2(c_y, cxC);
+            float *dst = a.gout + (size_t)qg * a.pitch + xc;
+            const bool st = store && k >= 8;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const f2 v0 = Sw[i][p2];
+                f2 acc = sm.Q[p4][i][l];
+                if (cx(i) != 0 && cy(i) != 0) acc = fma2(c_d, v0, acc);
+                else if (cx(i) != 0) acc = fma2(cxC, v0, acc);
+                else if (cy(i) != 0) acc = fma2(c_y, v0, acc);
+                if (cx(i) != 0) acc = xtaps(axC, cx(i), v0, acc);
+                if (cy(i) != 0) acc = ytaps(by, cy(i), Sw[i][p4], Sw[i][p3], Sw[i][p1], Sw[i][p0], acc);
+                if (st) *reinterpret_cast<f2 *>(dst + i * a.plane) = acc;
+            }
+        }
+        if (++slot == kStages) {
+            slot = 0;
+            parity ^= 1u;
+        }
+    };
+
+    for (int k = 0; k < iters; k += 5) {
+        row(std::integral_constant<int, 0>{}, k);
+        if (k + 1 < iters) row(std::integral_constant<int, 1>{}, k + 1);
+        if (k + 2 < iters) row(std::integral_constant<int, 2>{}, k + 2);
+        if (k + 3 < iters) row(std::integral_constant<int, 3>{}, k + 3);
+        if (k + 4 < iters) row(std::integral_constant<int, 4>{}, k + 4);
+    }
+    if (timed_out) {
+        // the last copy into slot s was issued at iteration s + 3 n < iters, in
+        // phase n; wait (bounded) for it before the shared memory is released
+        for (int s = 0; s < kStages && s < iters; ++s) {
+            const int n = (iters - 1 - s) / kStages;
+            (void)mbar_wait_bounded(&sm.bar[s], (uint32_t)(n & 1));
+        }
+        if (l == 0) atomicOr(a.err, 1);
+    }
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+}  // namespace
+
+bool fused_warp_ok(int nx, int ny) { return nx % 4 == 0 && nx >= kCols && ny >= 4; }
+
+size_t fused_warp_map_bytes() { return sizeof(CUtensorMap); }
+
+// Tensor map of one FP32 state buffer [9][ny][pitch]: dims (nx, ny, 9), byte
+// strides (4 pitch, 4 plane), box (64, 1, 9).  Columns outside [0, nx) read
+// as zero (the kernel takes them from the wrapped copy).
+cudaError_t fused_warp_encode(void *map, const float *state, int nx, int ny, int pitch,
+                              size_t plane)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    CUtensorMap m;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(float), (cuuint64_t)plane * sizeof(float)};
+    const cuuint32_t box[3] = {kCols, 1, 9};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                          const_cast<float *>(state), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    std::memcpy(map, &m, sizeof m);
+    return cudaSuccess;
+}
+
+cudaError_t launch_fused_warp(const StepArgs<float> &s, const void *map_in, cudaStream_t stream)
+{
+    ArgsW a;
+    std::memcpy(&a.tin, map_in, sizeof(CUtensorMap));
+    a.gout = s.gout;
+    a.mx = s.mx;
+    a.my = s.my;
+    a.nx = s.nx;
+    a.ny = s.ny;
+    a.pitch = s.pitch;
+    a.plane = s.plane;
+    a.rows = s.rows;
+    a.rho0 = s.c.rho0;
+    a.h = s.c.h;
+    a.dt = s.c.dt;
+    a.b_bar = s.c.b_bar;
+    a.b_til = s.c.b_til;
+    a.b_star = s.c.b_star;
+    a.w[0] = s.st.wm1;
+    a.w[1] = s.st.w0;
+    a.w[2] = s.st.w1;
+    a.w[3] = s.st.w2;
+    a.err = s.err;
+    constexpr size_t smem = sizeof(WarpSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_step_fused_warp,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((s.nx + kW - 1) / kW, (s.ny + s.rows - 1) / s.rows);
+    k_step_fused_warp<<<grid, kLanes, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+int fused_warp_tile_width() { return kW; }
+
+int fused_warp_blocks_per_sm()
+{
+    int n = 0;
+    constexpr size_t smem = sizeof(WarpSmem);
+    cudaFuncSetAttribute(k_step_fused_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_fused_warp, kLanes, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+}  // namespace fdlbm

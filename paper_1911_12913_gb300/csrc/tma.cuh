@@ -78,6 +78,21 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_
         : "memory");
 }
 
+// Tiled 3-D tensor copy (cp.async.bulk.tensor) of the box at coordinates
+// (c0, c1, c2) of the tensor map `tmap` (a __grid_constant__ kernel parameter)
+// into shared memory at `dst` (128-byte aligned); completion counts against
+// the mbarrier at `bar`.  c0 times the element size must be a multiple of 16
+// bytes; parts of the box outside the tensor are filled with zeros.
+__device__ __forceinline__ void tensor_copy_3d(uint32_t dst, const void *tmap, int c0, int c1,
+                                               int c2, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
 // Pieces of a periodic row segment: columns xs .. xs+n-1 (may start below 0 or
 // run past nx, n <= nx) split where they wrap.  Piece k (0 or 1) goes to
 // segment column c, comes from global column g and has `len` columns; returns

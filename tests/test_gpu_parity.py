@@ -106,7 +106,7 @@ def test_random_state_force_stretched_fp64(path, rows, nx, ny):
     assert rel(s.get_state(), o.f) <= FP64_TOL
 
 
-@pytest.mark.parametrize("variant", ["packed", "tma", "scalar", "async"])
+@pytest.mark.parametrize("variant", ["packed", "tma", "scalar", "async", "warp"])
 @pytest.mark.parametrize("nx,ny,rows", [(500, 37, 0), (256, 21, 7), (964, 40, 0), (4096, 9, 0),
                                         (260, 12, 1)])
 def test_fp32_fused_variants(variant, nx, ny, rows):
@@ -121,7 +121,8 @@ def test_fp32_fused_variants(variant, nx, ny, rows):
               variant=variant)
     o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2)
     assert s.describe.split()[0] == {"packed": "fused-f32x2", "tma": "fused-tma",
-                                     "scalar": "fused", "async": "fused-async"}[variant], s.describe
+                                     "scalar": "fused", "async": "fused-async",
+                                     "warp": "fused-warp"}[variant], s.describe
     _init_both(s, o, I.random_fields(nx, ny, 23))
     s.step(25)
     o.step(25)
@@ -171,12 +172,46 @@ def test_async_variant_odd_sizes_with_force(precision, tol, nx, ny, rows):
     assert rel(s.get_state(), o.f) <= tol
 
 
+@pytest.mark.parametrize("nx,ny,rows", [(64, 9, 0), (68, 13, 2), (120, 21, 0), (112, 7, 3),
+                                        (124, 40, 5)])
+def test_fp32_warp_variant_small_windows(nx, ny, rows):
+    """Warp-tile kernel where every 64-column window wraps (nx = 64, 68), where
+    the last tile is mostly outside the domain (120 = 2 x 56 + 8), and with
+    row segments of 2..5 rows: 25 steps against the FP64 oracle."""
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 0.7)
+    xa.metric = I.random_metric(nx, 71, base=nx, spread=0.3)
+    ya.metric = I.random_metric(ny, 72, base=ny / 0.7, spread=0.3)
+    s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, precision="fp32", rows_per_cta=rows,
+              variant="warp")
+    assert s.describe.startswith("fused-warp fp32dev"), s.describe
+    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2)
+    _init_both(s, o, I.random_fields(nx, ny, 37))
+    s.step(25)
+    o.step(25)
+    s.sync()
+    err = rel(s.get_state(), o.f)
+    print(f"{s.describe} {nx}x{ny}: rel L2(f~) = {err:.3e}")
+    assert err <= 1e-6
+
+
 def test_variant_not_applicable_is_rejected():
     xa = I.periodic_axis(130, 0.0, 1.0)   # 130 % 4 != 0: no 16-byte FP32 row pieces
     with pytest.raises(Exception, match="EUNSUPPORTED"):
         FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="tma")
     with pytest.raises(Exception, match="EUNSUPPORTED"):
         FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="packed")
+    with pytest.raises(Exception, match="EUNSUPPORTED"):
+        FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="warp")
+    xs = I.periodic_axis(60, 0.0, 1.0)    # narrower than one 64-column window
+    with pytest.raises(Exception, match="EUNSUPPORTED"):
+        FDLBM(xs, xs, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="warp")
+    x4 = I.periodic_axis(128, 0.0, 1.0)
+    with pytest.raises(Exception, match="EUNSUPPORTED"):
+        FDLBM(x4, x4, nu=0.01, cfl=0.5, blend=0.1, precision="fp64", variant="warp")
+    with pytest.raises(Exception, match="EUNSUPPORTED"):
+        FDLBM(x4, x4, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="warp",
+              has_force=True)
 
 
 def test_scalar_fp32_fused_with_force():
