@@ -135,15 +135,32 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------- helpers
-def kernel_traffic(precision):
-    """Per-launch DRAM bytes of the fused kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged."""
-    f = ROOT / "profiles" / f"fused_{precision}_traffic.json"
+# committed ncu DRAM-traffic record and the sources it was taken from, per kernel
+TRAFFIC = {
+    "fused-warp": ("warp_fp32_traffic.json",
+                   ["step_fused_warp.cu", "packed.cuh", "tma.cuh", "lattice.cuh", "internal.h"]),
+    "fused": ("fused_fp32_traffic.json", ["step_fused.cu"]),
+}
+
+
+def sources_sha256(names):
+    h = hashlib.sha256()
+    for nm in names:
+        h.update((ROOT / "paper_1911_12913_gb300" / "csrc" / nm).read_bytes())
+    return h.hexdigest()
+
+
+def kernel_traffic(kernel_desc):
+    """Per-launch DRAM bytes of the timed kernel from the committed ncu record,
+    valid only while the kernel's sources are unchanged."""
+    rec = TRAFFIC.get(kernel_desc.split()[0])
+    if rec is None:
+        return None
+    f = ROOT / "profiles" / rec[0]
     if not f.exists():
         return None
     d = json.loads(f.read_text())
-    src = (ROOT / "paper_1911_12913_gb300" / "csrc" / "step_fused.cu").read_bytes()
-    if d.get("kernel_sha256") != hashlib.sha256(src).hexdigest():
+    if d.get("kernel_sha256") != sources_sha256(rec[1]):
         return None
     return d.get("dram_bytes_per_launch_full")
 
@@ -446,7 +463,7 @@ def run_ours(args):
     hbm = hbm or 6800.0
     achieved = BYTES_PER_CELL["fp32"] * N / per_launch_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": kernel_traffic("fp32"),
+                "frac": achieved / hbm, "traffic": kernel_traffic(kernel_desc),
                 "peak_source": peak_note + " (MEASURED_PEAKS.json hbm_gbs, burst copy)",
                 "bytes_per_cell": BYTES_PER_CELL["fp32"], "kernel": kernel_desc}
     del s

@@ -61,10 +61,11 @@ enum { FDLBM_MEM_HOST = 0, FDLBM_MEM_DEVICE = 1 };
  *  WARP    FP32 only, one independent warp per 56-column tile, two adjacent
  *          columns per lane in packed f32x2 arithmetic, x-neighbours by warp
  *          shuffle, rows by bulk copies into a per-warp ring; no block-level
- *          barrier (no force field, nx % 4 == 0, nx >= 64).
- * AUTO picks SCALAR (the fastest measured on GB300 for the periodic 4096^2
- * throughput case).  Asking for a variant that does not apply returns
- * FDLBM_EUNSUPPORTED. */
+ *          barrier (no force field, nx % 4 == 0, nx >= 64, fewer than 2^32
+ *          values in the state).
+ * AUTO picks WARP where it applies (the fastest measured on GB300 for the
+ * periodic 4096^2 throughput case) and SCALAR otherwise.  Asking for a
+ * variant that does not apply returns FDLBM_EUNSUPPORTED. */
 enum { FDLBM_VARIANT_AUTO = 0, FDLBM_VARIANT_SCALAR = 1, FDLBM_VARIANT_PACKED = 2,
        FDLBM_VARIANT_TMA = 3, FDLBM_VARIANT_ASYNC = 4, FDLBM_VARIANT_WARP = 5 };
 enum { FDLBM_WALL_W = 0, FDLBM_WALL_E = 1, FDLBM_WALL_S = 2, FDLBM_WALL_N = 3 };

@@ -343,7 +343,7 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
         (o.variant == FDLBM_VARIANT_ASYNC && !fused))
         return FDLBM_EUNSUPPORTED;
     int variant = o.variant;
-    if (variant == FDLBM_VARIANT_AUTO) variant = FDLBM_VARIANT_SCALAR;
+    if (variant == FDLBM_VARIANT_AUTO) variant = warp_ok ? FDLBM_VARIANT_WARP : FDLBM_VARIANT_SCALAR;
     mx.assign(g->nx, 0.0);
     my.assign(g->ny, 0.0);
     for (int i = 0; i < g->nx; ++i)

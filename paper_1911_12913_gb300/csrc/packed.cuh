@@ -18,6 +18,8 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
+
+
 // 1/x from the hardware approximation (about one ulp for normal x), enough
 // for FP32 storage; the density is O(1).
 __device__ __forceinline__ float rcp_approx(float x)

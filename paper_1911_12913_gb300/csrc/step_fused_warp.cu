@@ -15,8 +15,9 @@
 //     lane's own pair and the halves of lanes l-1 and l+1;
 //   - a row of f~ (all nine populations of the window) arrives in a per-warp
 //     shared-memory ring by one tiled tensor copy (TMA, 3-D box 64 x 1 x 9)
-//     issued three rows ahead of use; a window that crosses the periodic seam
-//     gets its wrapped columns by a second copy into a side ring;
+//     issued at the end of the row that freed its slot, for the row three
+//     ahead; a window that crosses the periodic seam gets its wrapped columns
+//     by a second copy into a side ring;
 //   - f~+ waits four rows in a per-lane shared-memory ring.
 // Lanes 0 and 31 have one neighbour only, so their stage-B values are wrong;
 // the stage-C output of lanes 2..29 reads f* of lanes 1..30 only.
@@ -36,7 +37,8 @@
 //
 // Requirements (checked by the host): nx % 4 == 0 and nx >= 64, so that every
 // copy starts on a 16-byte boundary, a window crosses the seam at most once,
-// and the two columns of a lane never straddle it.
+// and the two columns of a lane never straddle it; the state holds fewer than
+// 2^32 values, so that element offsets fit 32 bits.
 #include <cstddef>
 #include <cstdint>
 #include <cstring>
@@ -210,9 +212,6 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 sm.Q[PH][i][l] = fma2(btil, neq, g[i]);
             }
         }
-        // every lane has read the slot: refill it three rows ahead
-        __syncwarp();
-        if (k + kStages < iters) issue(slot);
         // ------------------------------------------------------------ B (row r-2)
         {
             const float nhy = -a.h * myB;
@@ -251,7 +250,10 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
             const f2 by[3] = {bc(ndy * a.w[0]), bc(ndy * a.w[2]), bc(ndy * a.w[3])};
             const f2 c_y = bc(ndy * a.w[1]);
             const f2 c_d = add2(c_y, cxC);
-            float *dst = a.gout + (size_t)qg * a.pitch + xc;
+            // element offsets fit 32 bits (9 planes < 2^32 elements, checked on
+            // the host): one wide multiply-add per store address
+            const unsigned roff = (unsigned)qg * (unsigned)a.pitch + (unsigned)xc;
+            const unsigned plane32 = (unsigned)a.plane;
             const bool st = store && k >= 8;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -262,9 +264,14 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 else if (cy(i) != 0) acc = fma2(c_y, v0, acc);
                 if (cx(i) != 0) acc = xtaps(axC, cx(i), v0, acc);
                 if (cy(i) != 0) acc = ytaps(by, cy(i), Sw[i][p4], Sw[i][p3], Sw[i][p1], Sw[i][p0], acc);
-                if (st) *reinterpret_cast<f2 *>(dst + i * a.plane) = acc;
+                if (st) *reinterpret_cast<f2 *>(a.gout + (roff + (unsigned)i * plane32)) = acc;
             }
         }
+        // every lane has read the slot: refill it three rows ahead.  The copy
+        // is issued at the end of the row so that its memory ordering does not
+        // split stages A and B, C into separately scheduled regions.
+        __syncwarp();
+        if (k + kStages < iters) issue(slot);
         if (++slot == kStages) {
             slot = 0;
             parity ^= 1u;
@@ -311,7 +318,11 @@ EncodeTiledFn encode_fn()
 
 }  // namespace
 
-bool fused_warp_ok(int nx, int ny) { return nx % 4 == 0 && nx >= kCols && ny >= 4; }
+bool fused_warp_ok(int nx, int ny)
+{
+    const unsigned long long pitch = (nx + 31ull) / 32ull * 32ull;
+    return nx % 4 == 0 && nx >= kCols && ny >= 4 && 9ull * pitch * (unsigned long long)ny < (1ull << 32);
+}
 
 size_t fused_warp_map_bytes() { return sizeof(CUtensorMap); }
 
