@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the 64-case batched sweep")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurements")
     p.add_argument("--no-cavity", action="store_true", help="skip the 257^2 cavity march")
+    p.add_argument("--adjoint-cost", type=int, default=0, metavar="N",
+                   help="only time adjoint against forward steps on an N^2 grid and print that")
     return p.parse_args()
 
 
@@ -308,6 +310,41 @@ def run_cavity(dev, n_cells=256, c=1.5, U=0.1, Re=1000.0, cfl=0.9, eta=0.1, tol=
 
 
 # ----------------------------------------------------------------------- reverse mode
+def adjoint_cost(dev, m, k=200, seed=11):
+    """Time k adjoint steps against k forward steps on an m^2 periodic FP32 grid
+    with a force field (the configuration of the inverse problem)."""
+    import numpy as np
+    import torch
+    import inputs as I
+    from paper_1911_12913_gb300.solver import FDLBM
+
+    ax = I.periodic_axis(m, 0.0, 2 * math.pi)
+    s = FDLBM(ax, ax, nu=0.01, cfl=CFL, blend=BLEND, precision="fp32", has_force=True,
+              adjoint=True, device=dev)
+    v = I.spectral_vorticity_velocity(m, seed, kmax=8, umax=0.01)
+    one = np.ones((m, m))
+    s.init_fields(one, v["ux"], v["uy"], [v["dudx"], v["dudy"], v["dvdx"], v["dvdy"]])
+    g = s.save_state(s.new_buffer())
+    lam, lam2 = s.new_buffer(), s.new_buffer()
+    dF = torch.zeros((2, m, m), dtype=torch.float64, device=s.device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    s.step(5)
+    s.adjoint_step(g, lam, lam2, dF)
+    torch.cuda.synchronize()
+    ev[0].record(s.stream)
+    s.step(k)
+    ev[1].record(s.stream)
+    for _ in range(k):
+        s.adjoint_step(g, lam, lam2, dF)
+        lam, lam2 = lam2, lam
+    ev[2].record(s.stream)
+    torch.cuda.synchronize()
+    fwd = ev[0].elapsed_time(ev[1]) / k
+    adj = ev[1].elapsed_time(ev[2]) / k
+    return {"n": m, "forward_ms": fwd, "adjoint_ms": adj, "ratio": adj / fwd,
+            "forward_kernel": s.describe, "adjoint_kernels_per_step": 1}
+
+
 def run_adjoint(dev, n=256, nsteps=2000, iters=6, seed=11):
     """Adjoint cost against the forward step (256^2 and 4096^2, FP32), and the
     inverse problem: recover a hidden smooth body force on a 256^2 periodic grid
@@ -319,34 +356,7 @@ def run_adjoint(dev, n=256, nsteps=2000, iters=6, seed=11):
     from paper_1911_12913_gb300.adjoint import rollout_velocity
     from paper_1911_12913_gb300.solver import FDLBM
 
-    def cost_ratio(m, k=200):
-        ax = I.periodic_axis(m, 0.0, 2 * math.pi)
-        s = FDLBM(ax, ax, nu=0.01, cfl=CFL, blend=BLEND, precision="fp32", has_force=True,
-                  adjoint=True, device=dev)
-        v = I.spectral_vorticity_velocity(m, seed, kmax=8, umax=0.01)
-        one = np.ones((m, m))
-        s.init_fields(one, v["ux"], v["uy"], [v["dudx"], v["dudy"], v["dvdx"], v["dvdy"]])
-        g = s.save_state(s.new_buffer())
-        lam, lam2 = s.new_buffer(), s.new_buffer()
-        dF = torch.zeros((2, m, m), dtype=torch.float64, device=s.device)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        s.step(5)
-        s.adjoint_step(g, lam, lam2, dF)
-        torch.cuda.synchronize()
-        ev[0].record(s.stream)
-        s.step(k)
-        ev[1].record(s.stream)
-        for _ in range(k):
-            s.adjoint_step(g, lam, lam2, dF)
-            lam, lam2 = lam2, lam
-        ev[2].record(s.stream)
-        torch.cuda.synchronize()
-        fwd = ev[0].elapsed_time(ev[1]) / k
-        adj = ev[1].elapsed_time(ev[2]) / k
-        return {"n": m, "forward_ms": fwd, "adjoint_ms": adj, "ratio": adj / fwd,
-                "forward_kernel": s.describe, "adjoint_kernels_per_step": 3}
-
-    ratios = [cost_ratio(256), cost_ratio(4096)]
+    ratios = [adjoint_cost(dev, 256), adjoint_cost(dev, 4096)]
     torch.cuda.empty_cache()
 
     # inverse problem
@@ -595,6 +605,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint_cost:
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        print(json.dumps(adjoint_cost(dev, args.adjoint_cost, k=max(1, args.steps))), flush=True)
+        return 0
     return run_ours(args)
 
 

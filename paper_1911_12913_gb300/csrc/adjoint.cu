@@ -19,73 +19,45 @@
 //   (T^T lam)(k) = sum_j w_j m(k + s j) lam(k + s j).
 // Three kernels per step: recompute P; stage B adjoint (needs P and lam' in a
 // +-2 neighbourhood); stage A adjoint (needs lam_gs in a +-2 neighbourhood).
+#include <algorithm>
+#include <type_traits>
+
+#include "adjoint_node.cuh"
 #include "internal.h"
 
 namespace fdlbm {
 namespace {
 
-// Node map of stage A or B: moments (with force shift `sh`), equilibrium and
-// forcing, and the derivatives needed by its vector-Jacobian product.
+// ---------------------------------------------------------------- fused sweep
+// One kernel per adjoint step, laid out like the forward sweep (step_fused.cu):
+// a CTA of NT threads owns NT - 8 output columns and a segment of rows, thread
+// t owns one column, and the sweep runs bottom to top with
+//   A' (row r)    load g, lam', F; P = stage A of the forward step
+//   B' (row r-2)  gs = P - h D(P); lam_S = -dt D^T lam'; node VJP of stage B
+//                 -> lam_gs and the force cotangent of stage B
+//   C' (row r-4)  lam_P = lam_gs - h D^T lam_gs; node VJP of stage A with
+//                 lam_Q = lam' -> lam (stored) and the force cotangent (added
+//                 to dforce in FP64)
+// Differences in y read per-thread register windows of five rows; differences
+// in x read shared-memory rings written by the neighbouring threads.  The
+// transposed x-differences need the metric of the node they gather from, so
+// the rings hold lam' m_x and lam_gs m_x, each multiplied by its writer's own
+// column metric; the transposed y-differences weight the window rows by a
+// window of m_y.  g waits four rows in a per-thread ring for stage C'.
+// One barrier per row, as in the forward sweep (5-slot rings, 5-row unroll):
+// a ring slot is rewritten five rows after it was written, and every reader
+// of it has passed a barrier in between.
+
+constexpr int kAdjNT = 128;
+constexpr int kAdjHalo = 4;
+constexpr int kAdjRing = 5;
+
 template <class R>
-struct NodeMap {
-    R drho, rho, ux, uy, eu[9], t[9], feq[9], s[9];
-
-    __device__ void eval(const R g[9], R rho0, R Fx, R Fy, R sh)
-    {
-        R jx, jy;
-        moments_dev(g, drho, jx, jy);
-        rho = rho0 + drho;
-        jx += sh * rho * Fx;
-        jy += sh * rho * Fy;
-        ux = jx / rho;
-        uy = jy / rho;
-        const R usq = R(1.5) * (ux * ux + uy * uy);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            eu[i] = xi_dot<R>(i, ux, uy);
-            t[i] = eu[i] * (R(3) + R(4.5) * eu[i]) - usq;
-            feq[i] = wq<R>(i) * rho0 + wq<R>(i) * (drho + rho * t[i]);
-            s[i] = (R(cx(i)) - ux) * Fx + (R(cy(i)) - uy) * Fy;
-        }
-    }
-
-    // Given lam_geq and lam_F (per population), add the cotangent of g (lam_g)
-    // and of the force (lFx, lFy).
-    __device__ void vjp(const R lgeq_in[9], const R lF[9], R Fx, R Fy, R sh, R lam_g[9], R &lFx,
-                        R &lFy) const
-    {
-        R lux = R(0), luy = R(0), lrho = R(0), ldrho = R(0), lusq = R(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            // F_i = 3 s_i feq_i
-            const R lgeq = lgeq_in[i] + R(3) * s[i] * lF[i];
-            const R ls = R(3) * feq[i] * lF[i];
-            lux -= Fx * ls;
-            luy -= Fy * ls;
-            lFx += (R(cx(i)) - ux) * ls;
-            lFy += (R(cy(i)) - uy) * ls;
-            // geq_i = w_i (drho + rho t_i), t_i = eu_i (3 + 4.5 eu_i) - usq
-            ldrho += wq<R>(i) * lgeq;
-            lrho += wq<R>(i) * t[i] * lgeq;
-            const R lt = wq<R>(i) * rho * lgeq;
-            const R leu = (R(3) + R(9) * eu[i]) * lt;
-            lusq -= lt;
-            lux += R(cx(i)) * leu;
-            luy += R(cy(i)) * leu;
-        }
-        // usq = 1.5 (ux^2 + uy^2)
-        lux += R(3) * ux * lusq;
-        luy += R(3) * uy * lusq;
-        // u = j'/rho, j' = j + sh rho F
-        const R ljx = lux / rho, ljy = luy / rho;
-        lrho -= (ux * lux + uy * luy) / rho;
-        lrho += sh * (Fx * ljx + Fy * ljy);
-        lFx += sh * rho * ljx;
-        lFy += sh * rho * ljy;
-        ldrho += lrho;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) lam_g[i] += ldrho + R(cx(i)) * ljx + R(cy(i)) * ljy;
-    }
+struct AdjSmem {
+    R P[kAdjRing][6][kAdjNT];   // fbar^{+,h} of the x-moving populations
+    R L[kAdjRing][6][kAdjNT];   // lam' m_x of the x-moving populations
+    R LG[kAdjRing][6][kAdjNT];  // lam_gs m_x of the x-moving populations
+    R G[kAdjRing][9][kAdjNT];   // g (own column only)
 };
 
 template <class R>
@@ -93,158 +65,268 @@ struct AdjArgs {
     StepArgs<R> a;       // grid, metrics, coefficients (gin = state g^n)
     const R *lam_next;   // cotangent of g^{n+1}
     R *lam_prev;         // cotangent of g^n (output)
-    R *P;                // recomputed fbar^{+,h}
-    R *lgs;              // cotangent of gs
-    double *fB;          // [2][N] force cotangent of stage B (scratch)
     double *dforce;      // [2][ny][nx] accumulated force cotangent, or nullptr
+    int rows;            // tile height of the sweep
 };
+
+template <class R, bool FORCE>
+__global__ void __launch_bounds__(kAdjNT, sizeof(R) == 4 ? 2 : 1) k_adj_fused(const AdjArgs<R> p)
+{
+    constexpr int NT = kAdjNT, W = NT - 2 * kAdjHalo;
+    const StepArgs<R> &a = p.a;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AdjSmem<R> &sm = *reinterpret_cast<AdjSmem<R> *>(smem_raw);
+
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * W;
+    const int xc = x0 - kAdjHalo + t;
+    const int y0 = blockIdx.y * p.rows;
+    if (y0 >= a.ny) return;  // uniform over the block
+    const int y1 = min(y0 + p.rows, a.ny);
+    const int gx = wrap_index(xc, a.nx);
+    const bool act1 = (t >= 2) && (t < NT - 2);
+    const bool act2 = (t >= kAdjHalo) && (t < NT - kAdjHalo) && (xc < a.nx);
+    const Coeffs<R> c = a.c;
+    const Stencil<R> st = a.st;
+    const R mxc = a.mx[gx];
+    const R hx = c.h * mxc;
+    const R wgt[4] = {st.wm1, st.w0, st.w1, st.w2};
+    const size_t N = (size_t)a.nx * a.ny;
+
+    R Pw[9][kAdjRing];   // P of this column, slot = iteration mod 5
+    R Lw[9][kAdjRing];   // lam'
+    R Gw[9][kAdjRing];   // lam_gs
+    R Mw[kAdjRing];      // m_y of the rows in the windows above
+    R Mg[kAdjRing];      // m_y of the rows of Gw
+    R fBx[kAdjRing], fBy[kAdjRing];  // force cotangent of stage B, per row
+    R gcur[9], lcur[9], gnxt[9], lnxt[9];
+    int rl = wrap_index(y0 - kAdjHalo, a.ny);   // row of gcur / lcur
+    int rs = wrap_index(y0 - 6, a.ny);          // stage B' row at iteration k: y0 - 6 + k
+    int rq = wrap_index(y0 - 8, a.ny);          // stage C' row: y0 - 8 + k
+    auto load = [&](R *g, R *l, int row) {
+        const size_t off = (size_t)row * a.pitch + gx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            g[i] = __ldg(a.gin + i * a.plane + off);
+            l[i] = __ldg(p.lam_next + i * a.plane + off);
+        }
+    };
+    load(gcur, lcur, rl);
+    const int iters = (y1 - y0) + 2 * kAdjHalo;
+
+    auto row = [&](auto PHc, int k) {
+        constexpr int PH = decltype(PHc)::value;
+        constexpr int p0 = PH, p1 = (PH + 4) % 5, p2 = (PH + 3) % 5, p3 = (PH + 2) % 5,
+                      p4 = (PH + 1) % 5;
+        const int rA = rl;
+        if (k + 1 < iters) {
+            rl = rl + 1 == a.ny ? 0 : rl + 1;
+            load(gnxt, lnxt, rl);
+        }
+        // rows of stages B' and C', and their global inputs, loaded before the
+        // barrier so that the loads overlap stage A'
+        const int rB = rs, rC = rq;
+        rs = rs + 1 == a.ny ? 0 : rs + 1;
+        rq = rq + 1 == a.ny ? 0 : rq + 1;
+        R FBx = R(0), FBy = R(0), FCx = R(0), FCy = R(0);
+        if (FORCE) {
+            const size_t fb = (size_t)rB * a.pitch + gx, fc = (size_t)rC * a.pitch + gx;
+            FBx = __ldg(a.force + fb);
+            FBy = __ldg(a.force + a.plane + fb);
+            FCx = __ldg(a.force + fc);
+            FCy = __ldg(a.force + a.plane + fc);
+        }
+        const bool doC = k >= 8 && act2;
+        const size_t nC = (size_t)rC * a.nx + xc;
+        double dFx = 0.0, dFy = 0.0;
+        if (p.dforce && doC) {
+            dFx = p.dforce[nC];
+            dFy = p.dforce[N + nC];
+        }
+        // ------------------------------------------------------------ A' (row r)
+        {
+            R Fx = R(0), Fy = R(0);
+            if (FORCE) {
+                const size_t fo = (size_t)rA * a.pitch + gx;
+                Fx = __ldg(a.force + fo);
+                Fy = __ldg(a.force + a.plane + fo);
+            }
+            R drho, jx, jy;
+            moments_dev(gcur, drho, jx, jy);
+            const R rho = c.rho0 + drho;
+            jx += c.half_dt * rho * Fx;
+            jy += c.half_dt * rho * Fy;
+            const R inv = node_recip(rho);
+            const R ux = jx * inv, uy = jy * inv;
+            R geq[9], F[9];
+            equilibrium_dev(drho, rho, ux, uy, geq);
+            if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                R P = gcur[i] + c.b_bar * (geq[i] - gcur[i]);
+                if (FORCE) P += c.c_bar * F[i];
+                Pw[i][p0] = P;
+                Lw[i][p0] = lcur[i];
+                sm.G[p0][i][t] = gcur[i];
+                if (xslot(i) >= 0) {
+                    sm.P[p0][xslot(i)][t] = P;
+                    sm.L[p0][xslot(i)][t] = lcur[i] * mxc;
+                }
+            }
+            Mw[p0] = a.my[rA];
+        }
+        __syncthreads();
+        // ------------------------------------------------------------ B' (row r-2)
+        // rows r-4 .. r sit in slots p4, p3, p2, p1, p0 of Pw, Lw and Mw
+        if (k >= 4 && act1) {
+            const R hy = c.h * Mw[p2];
+            // transposed y weights: sign +: rows r-3, r-2, r-1, r (j = -1..2 at
+            // rows rB + j); sign -: rows r-1, r-2, r-3, r-4 (rows rB - j)
+            const R yp[4] = {wgt[0] * Mw[p3], wgt[1] * Mw[p2], wgt[2] * Mw[p1], wgt[3] * Mw[p0]};
+            const R ym[4] = {wgt[0] * Mw[p1], wgt[1] * Mw[p2], wgt[2] * Mw[p3], wgt[3] * Mw[p4]};
+            R gs[9], lS[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const R v0 = Pw[i][p2];
+                R acc = v0, lt = R(0);
+                if (cx(i) != 0) {
+                    const R *rw = sm.P[p2][xslot(i)];
+                    acc -= hx * apply_stencil(st, cx(i), rw[t - 2], rw[t - 1], v0, rw[t + 1], rw[t + 2]);
+                    const R *lw = sm.L[p2][xslot(i)];
+                    const int s = cx(i);
+                    // sum_j w_j (lam' m_x)(x + s j), j = -1 .. 2
+                    lt += wgt[0] * lw[t - s] + wgt[1] * lw[t] + wgt[2] * lw[t + s] + wgt[3] * lw[t + 2 * s];
+                }
+                if (cy(i) != 0) {
+                    acc -= hy * apply_stencil(st, cy(i), Pw[i][p4], Pw[i][p3], v0, Pw[i][p1], Pw[i][p0]);
+                    if (cy(i) > 0)
+                        lt += yp[0] * Lw[i][p3] + yp[1] * Lw[i][p2] + yp[2] * Lw[i][p1] + yp[3] * Lw[i][p0];
+                    else
+                        lt += ym[0] * Lw[i][p1] + ym[1] * Lw[i][p2] + ym[2] * Lw[i][p3] + ym[3] * Lw[i][p4];
+                }
+                gs[i] = acc;
+                lS[i] = -c.dt * lt;
+            }
+            const R Fx = FBx, Fy = FBy;
+            NodeMap<R> m;
+            m.eval(gs, c.rho0, Fx, Fy, c.half_h);
+            R lgeq[9], lF[9], lg[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                lgeq[i] = c.b_star * lS[i];
+                lF[i] = c.c_star * lS[i];
+                lg[i] = (R(1) - c.b_star) * lS[i];
+            }
+            R lFx = R(0), lFy = R(0);
+            m.vjp(lgeq, lF, Fx, Fy, c.half_h, lg, lFx, lFy);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                Gw[i][p0] = lg[i];
+                if (xslot(i) >= 0) sm.LG[p0][xslot(i)][t] = lg[i] * mxc;
+            }
+            fBx[p0] = lFx;
+            fBy[p0] = lFy;
+        }
+        Mg[p0] = Mw[p2];
+        // ------------------------------------------------------------ C' (row r-4)
+        // (the lam_gs ring slot read here was written two rows ago, before the
+        // barrier of the previous row; no second barrier is needed)
+        // lam_gs rows r-6 .. r-2 sit in slots p4, p3, p2, p1, p0 of Gw and Mg;
+        // lam' of row r-4 in slot p4 of Lw; g of row r-4 in ring slot p4
+        if (doC) {
+            const R hyg = c.h;
+            const R yp[4] = {wgt[0] * Mg[p3], wgt[1] * Mg[p2], wgt[2] * Mg[p1], wgt[3] * Mg[p0]};
+            const R ym[4] = {wgt[0] * Mg[p1], wgt[1] * Mg[p2], wgt[2] * Mg[p3], wgt[3] * Mg[p4]};
+            R lP[9], lQ[9], g[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                R lt = R(0);
+                if (cx(i) != 0) {
+                    const R *lw = sm.LG[p2][xslot(i)];
+                    const int s = cx(i);
+                    lt += wgt[0] * lw[t - s] + wgt[1] * lw[t] + wgt[2] * lw[t + s] + wgt[3] * lw[t + 2 * s];
+                }
+                if (cy(i) != 0) {
+                    if (cy(i) > 0)
+                        lt += yp[0] * Gw[i][p3] + yp[1] * Gw[i][p2] + yp[2] * Gw[i][p1] + yp[3] * Gw[i][p0];
+                    else
+                        lt += ym[0] * Gw[i][p1] + ym[1] * Gw[i][p2] + ym[2] * Gw[i][p3] + ym[3] * Gw[i][p4];
+                }
+                lP[i] = Gw[i][p2] - hyg * lt;
+                lQ[i] = Lw[i][p4];
+                g[i] = sm.G[p4][i][t];
+            }
+            const R Fx = FCx, Fy = FCy;
+            NodeMap<R> m;
+            m.eval(g, c.rho0, Fx, Fy, c.half_dt);
+            R lgeq[9], lF[9], lg[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                lgeq[i] = c.b_bar * lP[i] + c.b_til * lQ[i];
+                lF[i] = c.c_bar * lP[i] + c.c_til * lQ[i];
+                lg[i] = (R(1) - c.b_bar) * lP[i] + (R(1) - c.b_til) * lQ[i];
+            }
+            R lFx = R(0), lFy = R(0);
+            m.vjp(lgeq, lF, Fx, Fy, c.half_dt, lg, lFx, lFy);
+            const size_t off = (size_t)rC * a.pitch + xc;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) p.lam_prev[i * a.plane + off] = lg[i];
+            if (p.dforce) {
+                p.dforce[nC] = dFx + (double(lFx) + double(fBx[p2]));
+                p.dforce[N + nC] = dFy + (double(lFy) + double(fBy[p2]));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            gcur[i] = gnxt[i];
+            lcur[i] = lnxt[i];
+        }
+    };
+    for (int k = 0; k < iters; k += 5) {
+        row(std::integral_constant<int, 0>{}, k);
+        if (k + 1 < iters) row(std::integral_constant<int, 1>{}, k + 1);
+        if (k + 2 < iters) row(std::integral_constant<int, 2>{}, k + 2);
+        if (k + 3 < iters) row(std::integral_constant<int, 3>{}, k + 3);
+        if (k + 4 < iters) row(std::integral_constant<int, 4>{}, k + 4);
+    }
+}
+
+template <class R>
+int adj_blocks_per_sm(bool force)
+{
+    int n = 0;
+    const size_t smem = sizeof(AdjSmem<R>);
+    auto fn = force ? k_adj_fused<R, true> : k_adj_fused<R, false>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kAdjNT, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+// Tile height minimising (waves) x (rows + 8), as for the forward sweep.
+int adj_rows(int nx, int ny, int per_sm)
+{
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long slots = (long long)per_sm * sms;
+    const long long strips = (nx + (kAdjNT - 2 * kAdjHalo) - 1) / (kAdjNT - 2 * kAdjHalo);
+    int best = std::min(ny, 64);
+    double best_cost = 1e300;
+    for (int rows = 8; rows <= std::min(ny, 512); ++rows) {
+        const long long ctas = strips * ((ny + rows - 1) / rows);
+        const double cost = (double)((ctas + slots - 1) / slots) * (rows + 8);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = rows;
+        }
+    }
+    return std::max(1, std::min(best, ny));
+}
 
 template <class R>
 __device__ __forceinline__ R force_at(const StepArgs<R> &a, int c, size_t o)
 {
     return a.force ? a.force[c * a.plane + o] : R(0);
-}
-
-// D_i f at (x, y) on a periodic grid.
-template <class R>
-__device__ R dop(const StepArgs<R> &a, const R *fld, int i, int x, int y)
-{
-    R out = R(0);
-    if (cx(i) != 0) {
-        const int s = cx(i);
-        const R *row = fld + (size_t)y * a.pitch;
-        auto at = [&](int d) { return row[wrap_index(x + d, a.nx)]; };
-        out += a.mx[x] * apply_stencil(a.st, s, at(-2), at(-1), at(0), at(1), at(2));
-    }
-    if (cy(i) != 0) {
-        const int s = cy(i);
-        auto at = [&](int d) { return fld[(size_t)wrap_index(y + d, a.ny) * a.pitch + x]; };
-        out += a.my[y] * apply_stencil(a.st, s, at(-2), at(-1), at(0), at(1), at(2));
-    }
-    return out;
-}
-
-// D_i^T lam at (x, y): sum_j w_j m(k + s j) lam(k + s j) along each axis, with
-// w_{-1}, w_0, w_1, w_2 the weights of sign(c) * D_m (lattice.cuh).
-template <class R>
-__device__ R dop_t(const StepArgs<R> &a, const R *lam, int i, int x, int y)
-{
-    R out = R(0);
-    const R w[4] = {a.st.wm1, a.st.w0, a.st.w1, a.st.w2};
-    if (cx(i) != 0) {
-        const int s = cx(i);
-        const R *row = lam + (size_t)y * a.pitch;
-#pragma unroll
-        for (int j = -1; j <= 2; ++j) {
-            const int xx = wrap_index(x + s * j, a.nx);
-            out += w[j + 1] * a.mx[xx] * row[xx];
-        }
-    }
-    if (cy(i) != 0) {
-        const int s = cy(i);
-#pragma unroll
-        for (int j = -1; j <= 2; ++j) {
-            const int yy = wrap_index(y + s * j, a.ny);
-            out += w[j + 1] * a.my[yy] * lam[(size_t)yy * a.pitch + x];
-        }
-    }
-    return out;
-}
-
-// Recompute P = fbar^{+,h}(g^n) at every node.
-template <class R>
-__global__ void k_adj_recompute(const AdjArgs<R> p)
-{
-    const StepArgs<R> &a = p.a;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.nx || y >= a.ny) return;
-    const size_t o = (size_t)y * a.pitch + x;
-    R g[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = a.gin[i * a.plane + o];
-    const R Fx = force_at(a, 0, o), Fy = force_at(a, 1, o);
-    NodeMap<R> m;
-    m.eval(g, a.c.rho0, Fx, Fy, a.c.half_dt);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const R geq = m.feq[i] - wq<R>(i) * a.c.rho0;
-        const R F = R(3) * m.s[i] * m.feq[i];
-        p.P[i * a.plane + o] = g[i] + a.c.b_bar * (geq - g[i]) + a.c.c_bar * F;
-    }
-}
-
-// Stage B adjoint at every node: lam_S = -dt D^T lam', gs = P - h D(P),
-// lam_gs = (dS/dgs)^T lam_S, force cotangent of stage B.
-template <class R>
-__global__ void k_adj_stage_b(const AdjArgs<R> p)
-{
-    const StepArgs<R> &a = p.a;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.nx || y >= a.ny) return;
-    const size_t o = (size_t)y * a.pitch + x;
-    R gs[9], lS[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        gs[i] = p.P[i * a.plane + o] - a.c.h * dop(a, p.P + i * a.plane, i, x, y);
-        lS[i] = -a.c.dt * dop_t(a, p.lam_next + i * a.plane, i, x, y);
-    }
-    const R Fx = force_at(a, 0, o), Fy = force_at(a, 1, o);
-    NodeMap<R> m;
-    m.eval(gs, a.c.rho0, Fx, Fy, a.c.half_h);
-    R lgeq[9], lF[9], lg[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        lgeq[i] = a.c.b_star * lS[i];
-        lF[i] = a.c.c_star * lS[i];
-        lg[i] = (R(1) - a.c.b_star) * lS[i];
-    }
-    R lFx = R(0), lFy = R(0);
-    m.vjp(lgeq, lF, Fx, Fy, a.c.half_h, lg, lFx, lFy);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) p.lgs[i * a.plane + o] = lg[i];
-    const size_t n = (size_t)y * a.nx + x, N = (size_t)a.nx * a.ny;
-    p.fB[n] = double(lFx);
-    p.fB[N + n] = double(lFy);
-}
-
-// Stage A adjoint at every node: lam_P = lam_gs - h D^T lam_gs, lam_Q = lam',
-// lam = (dP/dg)^T lam_P + (dQ/dg)^T lam_Q; accumulate the force cotangent.
-template <class R>
-__global__ void k_adj_stage_a(const AdjArgs<R> p)
-{
-    const StepArgs<R> &a = p.a;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.nx || y >= a.ny) return;
-    const size_t o = (size_t)y * a.pitch + x;
-    R g[9], lP[9], lQ[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        g[i] = a.gin[i * a.plane + o];
-        lP[i] = p.lgs[i * a.plane + o] - a.c.h * dop_t(a, p.lgs + i * a.plane, i, x, y);
-        lQ[i] = p.lam_next[i * a.plane + o];
-    }
-    const R Fx = force_at(a, 0, o), Fy = force_at(a, 1, o);
-    NodeMap<R> m;
-    m.eval(g, a.c.rho0, Fx, Fy, a.c.half_dt);
-    R lgeq[9], lF[9], lg[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        lgeq[i] = a.c.b_bar * lP[i] + a.c.b_til * lQ[i];
-        lF[i] = a.c.c_bar * lP[i] + a.c.c_til * lQ[i];
-        lg[i] = (R(1) - a.c.b_bar) * lP[i] + (R(1) - a.c.b_til) * lQ[i];
-    }
-    R lFx = R(0), lFy = R(0);
-    m.vjp(lgeq, lF, Fx, Fy, a.c.half_dt, lg, lFx, lFy);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) p.lam_prev[i * a.plane + o] = lg[i];
-    if (p.dforce) {
-        const size_t n = (size_t)y * a.nx + x, N = (size_t)a.nx * a.ny;
-        p.dforce[n] += double(lFx) + p.fB[n];
-        p.dforce[N + n] += double(lFy) + p.fB[N + n];
-    }
 }
 
 // Cotangent of the state from a cotangent du of the velocity of Eq. 3.3:
@@ -278,14 +360,18 @@ __global__ void k_moments_vjp(const StepArgs<R> a, const double *du, R *lam, dou
 }  // namespace
 
 template <class R>
-cudaError_t launch_adjoint(const StepArgs<R> &a, const R *lam_next, R *lam_prev, R *P, R *lgs,
-                           double *fB, double *dforce, cudaStream_t s)
+cudaError_t launch_adjoint(const StepArgs<R> &a, const R *lam_next, R *lam_prev, R *, R *,
+                           double *, double *dforce, cudaStream_t s)
 {
-    AdjArgs<R> p{a, lam_next, lam_prev, P, lgs, fB, dforce};
-    const dim3 blk(32, 8), grd((a.nx + 31) / 32, (a.ny + 7) / 8);
-    k_adj_recompute<R><<<grd, blk, 0, s>>>(p);
-    k_adj_stage_b<R><<<grd, blk, 0, s>>>(p);
-    k_adj_stage_a<R><<<grd, blk, 0, s>>>(p);
+    const bool force = a.force != nullptr;
+    AdjArgs<R> p{a, lam_next, lam_prev, dforce, adj_rows(a.nx, a.ny, adj_blocks_per_sm<R>(force))};
+    const size_t smem = sizeof(AdjSmem<R>);
+    const dim3 grid((a.nx + kAdjNT - 2 * kAdjHalo - 1) / (kAdjNT - 2 * kAdjHalo),
+                    (a.ny + p.rows - 1) / p.rows);
+    auto fn = force ? k_adj_fused<R, true> : k_adj_fused<R, false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<grid, kAdjNT, smem, s>>>(p);
     return cudaGetLastError();
 }
 

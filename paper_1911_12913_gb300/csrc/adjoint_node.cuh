@@ -1,0 +1,87 @@
+// Node maps of the T2S2-FDLBM step and their vector-Jacobian products, for the
+// discrete adjoint: moments (Eq. 3.3, with the force shift of the stage),
+// equilibrium (Eq. 3.2) and forcing (Eq. 3.12).
+#pragma once
+
+#include "lattice.cuh"
+
+namespace fdlbm {
+
+// Node map of stage A or B: moments (with force shift `sh`), equilibrium and
+// forcing, and the derivatives needed by its vector-Jacobian product.
+// 1/rho: correctly rounded in FP32, a plain division in FP64.
+template <class R>
+__device__ __forceinline__ R node_recip(R v)
+{
+    return R(1) / v;
+}
+template <>
+__device__ __forceinline__ float node_recip<float>(float v)
+{
+    return __frcp_rn(v);
+}
+
+template <class R>
+struct NodeMap {
+    R drho, rho, inv, ux, uy, eu[9], t[9], feq[9], s[9];
+
+    __device__ __forceinline__ void eval(const R g[9], R rho0, R Fx, R Fy, R sh)
+    {
+        R jx, jy;
+        moments_dev(g, drho, jx, jy);
+        rho = rho0 + drho;
+        jx += sh * rho * Fx;
+        jy += sh * rho * Fy;
+        inv = node_recip(rho);
+        ux = jx * inv;
+        uy = jy * inv;
+        const R usq = R(1.5) * (ux * ux + uy * uy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            eu[i] = xi_dot<R>(i, ux, uy);
+            t[i] = eu[i] * (R(3) + R(4.5) * eu[i]) - usq;
+            feq[i] = wq<R>(i) * rho0 + wq<R>(i) * (drho + rho * t[i]);
+            s[i] = (R(cx(i)) - ux) * Fx + (R(cy(i)) - uy) * Fy;
+        }
+    }
+
+    // Given lam_geq and lam_F (per population), add the cotangent of g (lam_g)
+    // and of the force (lFx, lFy).
+    __device__ __forceinline__ void vjp(const R lgeq_in[9], const R lF[9], R Fx, R Fy, R sh, R lam_g[9], R &lFx,
+                        R &lFy) const
+    {
+        R lux = R(0), luy = R(0), lrho = R(0), ldrho = R(0), lusq = R(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            // F_i = 3 s_i feq_i
+            const R lgeq = lgeq_in[i] + R(3) * s[i] * lF[i];
+            const R ls = R(3) * feq[i] * lF[i];
+            lux -= Fx * ls;
+            luy -= Fy * ls;
+            lFx += (R(cx(i)) - ux) * ls;
+            lFy += (R(cy(i)) - uy) * ls;
+            // geq_i = w_i (drho + rho t_i), t_i = eu_i (3 + 4.5 eu_i) - usq
+            ldrho += wq<R>(i) * lgeq;
+            lrho += wq<R>(i) * t[i] * lgeq;
+            const R lt = wq<R>(i) * rho * lgeq;
+            const R leu = (R(3) + R(9) * eu[i]) * lt;
+            lusq -= lt;
+            lux += R(cx(i)) * leu;
+            luy += R(cy(i)) * leu;
+        }
+        // usq = 1.5 (ux^2 + uy^2)
+        lux += R(3) * ux * lusq;
+        luy += R(3) * uy * lusq;
+        // u = j'/rho, j' = j + sh rho F
+        const R ljx = lux * inv, ljy = luy * inv;
+        lrho -= (ux * lux + uy * luy) * inv;
+        lrho += sh * (Fx * ljx + Fy * ljy);
+        lFx += sh * rho * ljx;
+        lFy += sh * rho * ljy;
+        ldrho += lrho;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) lam_g[i] += ldrho + R(cx(i)) * ljx + R(cy(i)) * ljy;
+    }
+};
+
+}  // namespace fdlbm
