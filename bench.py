@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the 64-case batched sweep")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurements")
     p.add_argument("--no-cavity", action="store_true", help="skip the 257^2 cavity march")
+    p.add_argument("--no-sweep", action="store_true", help="skip the 512^2..4096^2 size sweep")
     p.add_argument("--adjoint-cost", type=int, default=0, metavar="N",
                    help="only time adjoint against forward steps on an N^2 grid and print that")
     return p.parse_args()
@@ -262,6 +263,38 @@ def run_batched(stream_dev, ncases=64, seed=2024, steps=200, graph_steps=50):
            "workload": f"{ncases} cases seed {seed}: cavity/channel, 33..513 cells, half stretched, "
                        f"Re log-uniform [10, 2000], CFL {CFL}, blend {BLEND}, FP32"}
     b.close()
+    return out
+
+
+# ----------------------------------------------------------------------- size sweep
+def run_sweep(dev, stream, sizes=(512, 1024, 2048, 4096)):
+    """The throughput sweep of the configs: MLUPS and HBM fraction per size, FP32
+    (automatic kernel) and FP64, on the random-phase Taylor-vortex field."""
+    import torch
+    from paper_1911_12913_gb300.solver import FDLBM
+
+    hbm = peaks().get("hbm_gbs") or 6800.0
+    out = []
+    for n in sizes:
+        ax, f, _ = workload_fields(n)
+        grad = [f["dudx"], f["dudy"], f["dvdx"], f["dvdy"]]
+        for prec, k in (("fp32", 400), ("fp64", 20)):
+            s = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision=prec, stream=stream)
+            s.init_fields(f["rho"], f["ux"], f["uy"], grad)
+            s.step(5)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s.step(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s.sync()
+            t = e0.elapsed_time(e1) / 1e3 / k
+            out.append({"n": n, "precision": prec, "kernel": s.describe, "MLUPS": n * n / t / 1e6,
+                        "GBs": BYTES_PER_CELL[prec] * n * n / t / 1e9,
+                        "hbm_frac": BYTES_PER_CELL[prec] * n * n / t / 1e9 / hbm, "steps": k})
+            del s
+            torch.cuda.empty_cache()
     return out
 
 
@@ -539,6 +572,11 @@ def run_ours(args):
         adjoint = run_adjoint(dev)
         torch.cuda.empty_cache()
 
+    # ---------------- the throughput sweep over sizes
+    sweep = None
+    if not args.no_sweep:
+        sweep = run_sweep(dev, stream)
+
     # ---------------- 257^2 lid-driven cavity at Re = 1000 to steady state
     cavity = None
     if not args.no_cavity and rank == 0:
@@ -592,7 +630,7 @@ def run_ours(args):
                "config": config(n, "fp32", args.steps), "clocks": clk.summary(),
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                "cpu_baseline": cpu, "fp64": fp64, "fp32_variants": variants, "batched": batched, "adjoint": adjoint,
-               "cavity": cavity,
+               "cavity": cavity, "sweep": sweep,
                "mass_drift_rel": mass_drift,
                "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(out), flush=True)
