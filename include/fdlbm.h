@@ -255,6 +255,13 @@ int fdlbm_batch_size(fdlbm_batch_t b);
 long long fdlbm_batch_cells(fdlbm_batch_t b);        /* nodes of all cases */
 /* Advance every case by n steps (asynchronous on the batch stream). */
 fdlbm_status fdlbm_batch_step(fdlbm_batch_t b, int n);
+/* on != 0: later fdlbm_batch_step calls (and graph captures) run one persistent
+ * cooperative launch for all their steps, the stages separated by a grid-wide
+ * barrier with bounded waits (a timeout sets every case's error flag, which
+ * fdlbm_sync / fdlbm_reduce of a case report); on = 0: one launch per stage and
+ * step (the default, faster on GB300 because every stage kernel runs at its own
+ * occupancy).  Synchronises the batch stream and drops a captured graph. */
+fdlbm_status fdlbm_batch_set_persistent(fdlbm_batch_t b, int on);
 fdlbm_status fdlbm_batch_sync(fdlbm_batch_t b);
 void *fdlbm_batch_stream(fdlbm_batch_t b);           /* cudaStream_t of the batch */
 const char *fdlbm_batch_describe(fdlbm_batch_t b);

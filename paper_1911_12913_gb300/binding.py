@@ -93,6 +93,7 @@ SIGNATURES = [
     ("fdlbm_batch_size", ctypes.c_int, [_H]),
     ("fdlbm_batch_cells", ctypes.c_longlong, [_H]),
     ("fdlbm_batch_step", ctypes.c_int, [_H, ctypes.c_int]),
+    ("fdlbm_batch_set_persistent", ctypes.c_int, [_H, ctypes.c_int]),
     ("fdlbm_batch_sync", ctypes.c_int, [_H]),
     ("fdlbm_batch_stream", ctypes.c_void_p, [_H]),
     ("fdlbm_batch_describe", ctypes.c_char_p, [_H]),

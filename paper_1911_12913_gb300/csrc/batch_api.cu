@@ -1,7 +1,9 @@
 // Batched mode of the C ABI (fdlbm_batch_*, declared in include/fdlbm.h):
 // many independent cases in one workspace, advanced together by the batched
-// staged kernels, with a fixed number of steps captured once into a CUDA graph
-// and replayed, and a small autotuner for the block shape of the node kernels.
+// staged kernels (one launch per stage for all cases, step_batched.cu) or, in
+// the persistent mode, by one cooperative launch for any number of steps
+// (step_persist.cu); a fixed number of steps is captured once into a CUDA
+// graph and replayed, and a small autotuner picks the block shape.
 //
 // Each case is an ordinary handle (fdlbm_t) whose memory lies inside the batch
 // workspace, so the per-case calls (init_fields, set_force, get_state,
@@ -32,9 +34,11 @@ struct fdlbm_batch_ctx {
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
     void *d_args = nullptr;    // 2 x ncases argument blocks
-    int *d_ints = nullptr;     // blk_case | blk_start | tiles_x | wall_start
+    int *d_ints = nullptr;     // blk_start | tiles_x | wall_start | grid barrier | blk_case
     size_t d_ints_cap = 0;
     BatchTables tab{};
+    void *bar = nullptr;       // grid barrier of the persistent kernel (in d_ints)
+    bool persistent = false;   // one cooperative launch per call instead of per-stage launches
     dim3 blk{32, 8, 1};
     int graph_steps = 0;
     cudaGraph_t graph = nullptr;
@@ -66,21 +70,23 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk)
 {
     const int n = (int)b->cases.size();
     std::vector<int> blk_start(n), tiles_x(n), wall_start(n), blk_case;
-    int total_wall = 0;
+    int total_wall = 0, total_blocks = 0;
     bool any2 = false;
     for (int c = 0; c < n; ++c) {
         const fdlbm_ctx *h = b->cases[c];
         const int tx = (h->nx + (int)blk.x - 1) / (int)blk.x;
         const int ty = (h->ny + (int)blk.y - 1) / (int)blk.y;
-        blk_start[c] = (int)blk_case.size();
+        blk_start[c] = total_blocks;
         tiles_x[c] = tx;
+        total_blocks += tx * ty;
         blk_case.insert(blk_case.end(), (size_t)tx * ty, c);
         wall_start[c] = total_wall;
         const bool wy = h->bc_y == FDLBM_WALL, wx = h->bc_x == FDLBM_WALL;
         total_wall += (wy ? 2 * h->nx : 0) + (wx ? 2 * (wy ? h->ny - 2 : h->ny) : 0);
         any2 = any2 || h->scheme == FDLBM_SCHEME_T2S2_2;
     }
-    const size_t nints = blk_case.size() + 3 * (size_t)n;
+    const size_t nbar = (persistent_barrier_bytes() + sizeof(int) - 1) / sizeof(int);
+    const size_t nints = 3 * (size_t)n + nbar + blk_case.size();
     if (nints > b->d_ints_cap) {
         if (b->d_ints) cudaFree(b->d_ints);
         b->d_ints = nullptr;
@@ -90,10 +96,11 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk)
     }
     std::vector<int> all;
     all.reserve(nints);
-    all.insert(all.end(), blk_case.begin(), blk_case.end());
     all.insert(all.end(), blk_start.begin(), blk_start.end());
     all.insert(all.end(), tiles_x.begin(), tiles_x.end());
     all.insert(all.end(), wall_start.begin(), wall_start.end());
+    all.resize(3 * (size_t)n + nbar, 0);
+    all.insert(all.end(), blk_case.begin(), blk_case.end());
     if (cudaMemcpy(b->d_ints, all.data(), nints * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
         return bfail(b, FDLBM_ECUDA, "batch: table upload failed");
     // argument blocks for both parities (every case at cur = 0 for even steps)
@@ -115,25 +122,34 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk)
         }
     if (cudaMemcpy(b->d_args, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return bfail(b, FDLBM_ECUDA, "batch: argument upload failed");
-    const int nb = (int)blk_case.size();
     b->tab.args[0] = b->d_args;
     b->tab.args[1] = static_cast<char *>(b->d_args) + n * as;
-    b->tab.blk_case = b->d_ints;
-    b->tab.blk_start = b->d_ints + nb;
-    b->tab.tiles_x = b->d_ints + nb + n;
-    b->tab.wall_start = b->d_ints + nb + 2 * n;
+    b->tab.blk_start = b->d_ints;
+    b->tab.tiles_x = b->d_ints + n;
+    b->tab.wall_start = b->d_ints + 2 * n;
+    b->bar = b->d_ints + 3 * n;
+    b->tab.blk_case = b->d_ints + 3 * n + nbar;
     b->tab.ncases = n;
-    b->tab.total_blocks = nb;
+    b->tab.total_blocks = total_blocks;
     b->tab.total_wall = total_wall;
     b->tab.any_scheme2 = any2;
     b->blk = blk;
     return FDLBM_OK;
 }
 
-cudaError_t launch_one(fdlbm_batch_ctx *b, int parity)
+// n steps starting at ping-pong parity `parity`: one persistent launch, or one
+// launch per stage and step.
+cudaError_t launch_steps(fdlbm_batch_ctx *b, int parity, int n)
 {
-    return b->precision == FDLBM_FP32_DEV ? launch_batched<float>(b->tab, parity, b->blk, b->stream)
-                                          : launch_batched<double>(b->tab, parity, b->blk, b->stream);
+    const bool f32 = b->precision == FDLBM_FP32_DEV;
+    if (b->persistent)
+        return f32 ? launch_persistent<float>(b->tab, b->bar, parity, n, b->blk, b->stream)
+                   : launch_persistent<double>(b->tab, b->bar, parity, n, b->blk, b->stream);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < n && e == cudaSuccess; ++k)
+        e = f32 ? launch_batched<float>(b->tab, (parity + k) & 1, b->blk, b->stream)
+                : launch_batched<double>(b->tab, (parity + k) & 1, b->blk, b->stream);
+    return e;
 }
 
 void advance_bookkeeping(fdlbm_batch_ctx *b, long long n)
@@ -147,11 +163,10 @@ void advance_bookkeeping(fdlbm_batch_ctx *b, long long n)
 
 fdlbm_status step_direct(fdlbm_batch_ctx *b, int n)
 {
-    for (int k = 0; k < n; ++k) {
-        cudaError_t e = launch_one(b, (int)(b->steps & 1));
-        if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, std::string("batch step: ") + cudaGetErrorString(e));
-        advance_bookkeeping(b, 1);
-    }
+    if (n <= 0) return FDLBM_OK;
+    cudaError_t e = launch_steps(b, (int)(b->steps & 1), n);
+    if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, std::string("batch step: ") + cudaGetErrorString(e));
+    advance_bookkeeping(b, n);
     return FDLBM_OK;
 }
 
@@ -167,10 +182,9 @@ void drop_graph(fdlbm_batch_ctx *b)
 fdlbm_status capture(fdlbm_batch_ctx *b)
 {
     drop_graph(b);
-    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
-    cudaError_t el = cudaSuccess;
-    for (int k = 0; k < b->graph_steps && el == cudaSuccess; ++k) el = launch_one(b, k & 1);
+    const cudaError_t el = launch_steps(b, 0, b->graph_steps);
     e = cudaStreamEndCapture(b->stream, &b->graph);
     if (el != cudaSuccess || e != cudaSuccess) {
         drop_graph(b);
@@ -417,6 +431,16 @@ fdlbm_status fdlbm_batch_step(fdlbm_batch_t b, int n)
     return step_direct(b, n);
 }
 
+fdlbm_status fdlbm_batch_set_persistent(fdlbm_batch_t b, int on)
+{
+    if (!b) return FDLBM_EINVAL;
+    fdlbm_status st = fdlbm_batch_sync(b);
+    if (st != FDLBM_OK) return st;
+    drop_graph(b);
+    b->persistent = on != 0;
+    return FDLBM_OK;
+}
+
 fdlbm_status fdlbm_batch_sync(fdlbm_batch_t b)
 {
     if (!b) return FDLBM_EINVAL;
@@ -430,10 +454,12 @@ const char *fdlbm_batch_describe(fdlbm_batch_t b)
 {
     if (!b) return "NULL batch";
     std::ostringstream os;
-    os << "batched-staged " << (b->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64")
-       << " cases=" << b->cases.size() << " block=" << b->blk.x << "x" << b->blk.y
-       << " graph_steps=" << b->graph_steps << " launches_per_step="
-       << (3 + (b->tab.total_wall > 0 ? 2 : 0) + (b->tab.total_wall > 0 && b->tab.any_scheme2 ? 1 : 0));
+    const int per_step =
+        3 + (b->tab.total_wall > 0 ? 2 : 0) + (b->tab.total_wall > 0 && b->tab.any_scheme2 ? 1 : 0);
+    os << (b->persistent ? "batched-persistent " : "batched-staged ")
+       << (b->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64") << " cases=" << b->cases.size()
+       << " block=" << b->blk.x << "x" << b->blk.y << " graph_steps=" << b->graph_steps
+       << (b->persistent ? " grid_barriers_per_step=" : " launches_per_step=") << per_step;
     if (b->tuned) os << " tuned_ms_per_step=" << b->tuned_ms;
     b->desc = os.str();
     return b->desc.c_str();

@@ -33,11 +33,11 @@ struct StepArgs {
     R *P, *Q, *S;
 };
 
-// Device tables of a batch (see step_batched.cu).
+// Device tables of a batch (step_batched.cu, step_persist.cu).
 struct BatchTables {
     const void *args[2];   // StepArgs<R>[ncases] for even / odd steps (ping-pong)
-    const int *blk_case;   // [total_blocks]
-    const int *blk_start;  // [ncases]
+    const int *blk_case;   // [total_blocks] case of each node tile
+    const int *blk_start;  // [ncases] first node tile of each case
     const int *tiles_x;    // [ncases]
     const int *wall_start; // [ncases]
     int ncases, total_blocks, total_wall;
@@ -129,9 +129,16 @@ int fused_warp_blocks_per_sm();
 // step_staged.cu
 template <class R>
 cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s);
-// step_batched.cu
+// step_batched.cu (one launch per stage for all cases of a batch)
 template <class R>
 cudaError_t launch_batched(const BatchTables &t, int parity, dim3 blk, cudaStream_t s);
+// step_persist.cu (one cooperative launch for many steps of all cases)
+template <class R>
+cudaError_t launch_persistent(const BatchTables &t, void *bar, int parity0, int nsteps, dim3 blk,
+                              cudaStream_t s);
+template <class R>
+int persistent_blocks_per_sm(dim3 blk);
+size_t persistent_barrier_bytes();
 // adjoint.cu
 template <class R>
 cudaError_t launch_adjoint(const StepArgs<R> &a, const R *lam_next, R *lam_prev, R *P, R *lgs,

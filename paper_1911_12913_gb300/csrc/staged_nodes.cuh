@@ -1,6 +1,6 @@
 // Per-node stages of the staged T2S2-FDLBM step (any boundary combination),
-// shared by the single-case kernels (step_staged.cu) and the batched kernels
-// (step_batched.cu).
+// shared by the single-case kernels (step_staged.cu), the batched kernels
+// (step_batched.cu) and the persistent batched kernel (step_persist.cu).
 //
 //   prepare_node  all nodes        P = fbar^{+,h} (Eqs. 2.19, 2.34), Q = f~+ (Eq. 2.20)
 //                                  (scheme 2: P = physical f^n, Eq. 2.32 with h = dt)

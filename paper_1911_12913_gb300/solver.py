@@ -249,7 +249,7 @@ class FDLBMBatch:
     read-back; ``batch.step(n)`` advances every case."""
 
     def __init__(self, cases, *, precision: str = "fp32", graph_steps: int = 50,
-                 autotune: bool = True, device=None):
+                 autotune: bool = True, persistent: bool = False, device=None):
         self._L = L = B.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         n = len(cases)
@@ -282,6 +282,10 @@ class FDLBMBatch:
                                   ctypes.byref(h))
         if rc != 0:
             raise B.FdlbmError(rc, "fdlbm_batch_create")
+        if persistent:
+            rc = L.fdlbm_batch_set_persistent(h, 1)
+            if rc != 0:
+                raise B.FdlbmError(rc, "fdlbm_batch_set_persistent")
         self._h = h
         self.stream = torch.cuda.ExternalStream(L.fdlbm_batch_stream(h), device=self.device)
         self._cases = [FDLBM._case_view(L, L.fdlbm_batch_case(h, c), cs["xa"], cs["ya"], self.stream,

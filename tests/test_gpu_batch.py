@@ -79,10 +79,15 @@ def _setup(batch, cases):
     return oracles
 
 
-@pytest.mark.parametrize("precision,tol,autotune", [("fp64", 1e-12, False), ("fp32", 2e-6, True)])
-def test_mixed_batch_matches_oracle(precision, tol, autotune):
+@pytest.mark.parametrize("precision,tol,autotune,persistent",
+                         [("fp64", 1e-12, False, False), ("fp32", 2e-6, True, False),
+                          ("fp64", 1e-12, False, True), ("fp32", 2e-6, False, True)])
+def test_mixed_batch_matches_oracle(precision, tol, autotune, persistent):
+    """Per-stage launches (default) and the persistent cooperative launch."""
     cases = _mixed_cases()
-    batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=autotune)
+    batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=autotune,
+                       persistent=persistent)
+    assert batch.describe.startswith("batched-persistent" if persistent else "batched-staged")
     assert "cases=6" in batch.describe
     oracles = _setup(batch, cases)
     # 11 steps: 4 + 4 by graph replay, 3 launched directly; then 1 more
