@@ -50,7 +50,8 @@ enum { FDLBM_PERIODIC = 0, FDLBM_WALL = 1 };            /* boundary kind of an a
 enum { FDLBM_FP64 = 0, FDLBM_FP32_DEV = 1 };            /* storage / arithmetic precision */
 enum { FDLBM_PATH_AUTO = 0, FDLBM_PATH_FUSED = 1, FDLBM_PATH_STAGED = 2 };
 enum { FDLBM_MEM_HOST = 0, FDLBM_MEM_DEVICE = 1 };
-/* Fused-kernel variant (periodic grids):
+/* Fused-kernel variant (periodic grids; a grid with a walled axis runs the
+ * scalar sweep with Eq. 3.10 inside it, and any other variant is unsupported):
  *  SCALAR  one column per thread, rows loaded through registers (any nx >= 4);
  *  TMA     one column per thread, rows streamed into shared memory by bulk
  *          copies (nx a multiple of 16 bytes worth of values, nx >= 128);
@@ -101,7 +102,9 @@ typedef struct {
     double rho0;              /* reference density; FP32 storage keeps f~_i - w_i rho0 */
     int precision;            /* FDLBM_FP64 or FDLBM_FP32_DEV */
     int has_force;            /* 1: reserve a body-acceleration field (fdlbm_set_force), Eq. 3.12 */
-    int path;                 /* FDLBM_PATH_AUTO: fused kernel for periodic grids, staged otherwise */
+    int path;                 /* FDLBM_PATH_AUTO: the fused kernel for T2S2-FDLBM1 (periodic grids,
+                                 and walled grids in FP32), the staged kernels for walled
+                                 grids in FP64 and for T2S2-FDLBM2 */
     int rows_per_cta;         /* fused kernel tile height; 0 = automatic */
     int variant;              /* FDLBM_VARIANT_*; PACKED where it does not apply -> EUNSUPPORTED */
     int scheme;               /* FDLBM_SCHEME_T2S2_1 (default) or FDLBM_SCHEME_T2S2_2 */

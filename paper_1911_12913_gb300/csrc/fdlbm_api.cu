@@ -72,30 +72,36 @@ bool grid_ok(const fdlbm_grid *g)
 
 int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
 
-bool fused_ok(const fdlbm_grid *g)
-{
-    return g->bc_x == FDLBM_PERIODIC && g->bc_y == FDLBM_PERIODIC && g->nx >= 4 && g->ny >= 4;
-}
+bool fused_ok(const fdlbm_grid *g) { return g->nx >= 4 && g->ny >= 4; }
 
+bool walled(const fdlbm_grid *g) { return g->bc_x == FDLBM_WALL || g->bc_y == FDLBM_WALL; }
+
+// The automatic choice takes the fused sweep for T2S2-FDLBM1, except on walled
+// grids in FP64: there the work is bound by the FP64 units, and the halo rows
+// the sweep recomputes on small walled grids cost more than the staged
+// kernels' extra traffic (257^2 cavity: 198 against 81 us per step on GB300).
 int choose_path(const fdlbm_grid *g, const fdlbm_opts *o)
 {
     const bool can_fuse = fused_ok(g) && o->scheme == FDLBM_SCHEME_T2S2_1;
     if (o->path == FDLBM_PATH_STAGED) return FDLBM_PATH_STAGED;
     if (o->path == FDLBM_PATH_FUSED) return can_fuse ? FDLBM_PATH_FUSED : -1;
+    if (walled(g) && o->precision == FDLBM_FP64) return FDLBM_PATH_STAGED;
     return can_fuse ? FDLBM_PATH_FUSED : FDLBM_PATH_STAGED;
 }
 
 // Rows per CTA of the fused kernel.  Each CTA recomputes 8 halo rows, so tall
 // tiles waste less; the grid should also fill whole waves of resident CTAs.
 // Pick the height that minimises (waves) x (rows + 8), the modelled sweep time.
-int choose_rows(int nx, int ny, int precision, int variant)
+int choose_rows(int nx, int ny, int precision, int variant, bool walls)
 {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool f32 = precision == FDLBM_FP32_DEV;
     int per_sm;
-    if (variant == FDLBM_VARIANT_PACKED)
+    if (walls)
+        per_sm = f32 ? fused_walls_blocks_per_sm<float>() : fused_walls_blocks_per_sm<double>();
+    else if (variant == FDLBM_VARIANT_PACKED)
         per_sm = fused_x2_blocks_per_sm();
     else if (variant == FDLBM_VARIANT_WARP)
         per_sm = fused_warp_blocks_per_sm();
@@ -160,9 +166,11 @@ StepArgs<R> step_args(fdlbm_ctx *h)
 // One step of whichever kernel the handle uses, reading state[cur], on stream s.
 cudaError_t launch_step(fdlbm_ctx *h, cudaStream_t s)
 {
+    const bool walls = h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL;
     if (h->precision == FDLBM_FP32_DEV) {
         auto a = step_args<float>(h);
         if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
+        if (walls) return launch_fused_walls(a, s);
         if (h->variant == FDLBM_VARIANT_PACKED) return launch_fused_x2(a, a.err, s);
         if (h->variant == FDLBM_VARIANT_WARP) return launch_fused_warp(a, h->tmap[h->cur], s);
         if (h->variant == FDLBM_VARIANT_TMA) return launch_fused_tma(a, s);
@@ -171,6 +179,7 @@ cudaError_t launch_step(fdlbm_ctx *h, cudaStream_t s)
     }
     auto a = step_args<double>(h);
     if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
+    if (walls) return launch_fused_walls(a, s);
     if (h->variant == FDLBM_VARIANT_TMA) return launch_fused_tma(a, s);
     if (h->variant == FDLBM_VARIANT_ASYNC) return launch_fused_async(a, s);
     return launch_fused(a, s);
@@ -333,14 +342,15 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     if (path < 0) return FDLBM_EUNSUPPORTED;
     const bool fused = path == FDLBM_PATH_FUSED;
     const bool f32 = o.precision == FDLBM_FP32_DEV;
-    const bool packed_ok = fused && f32 && !o.has_force && fused_x2_ok(g->nx, g->ny);
-    const bool tma_ok = fused && (f32 ? fused_tma_ok<float>(g->nx, g->ny)
-                                      : fused_tma_ok<double>(g->nx, g->ny));
-    const bool warp_ok = fused && f32 && !o.has_force && fused_warp_ok(g->nx, g->ny);
+    const bool packed_ok = fused && !walled(g) && f32 && !o.has_force && fused_x2_ok(g->nx, g->ny);
+    const bool tma_ok = fused && !walled(g) && (f32 ? fused_tma_ok<float>(g->nx, g->ny)
+                                                    : fused_tma_ok<double>(g->nx, g->ny));
+    const bool periodic = !walled(g);
+    const bool warp_ok = fused && periodic && f32 && !o.has_force && fused_warp_ok(g->nx, g->ny);
     if ((o.variant == FDLBM_VARIANT_PACKED && !packed_ok) ||
         (o.variant == FDLBM_VARIANT_WARP && !warp_ok) ||
         (o.variant == FDLBM_VARIANT_TMA && !tma_ok) ||
-        (o.variant == FDLBM_VARIANT_ASYNC && !fused))
+        (o.variant == FDLBM_VARIANT_ASYNC && (!fused || walled(g))))
         return FDLBM_EUNSUPPORTED;
     int variant = o.variant;
     if (variant == FDLBM_VARIANT_AUTO) variant = warp_ok ? FDLBM_VARIANT_WARP : FDLBM_VARIANT_SCALAR;
@@ -379,7 +389,7 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     h->variant = variant;
     if (path == FDLBM_PATH_FUSED)
         h->rows = o.rows_per_cta > 0 ? std::min(o.rows_per_cta, g->ny)
-                                     : choose_rows(g->nx, g->ny, o.precision, variant);
+                                     : choose_rows(g->nx, g->ny, o.precision, variant, walled(g));
     h->stream = static_cast<cudaStream_t>(o.stream);
     h->adjoint = o.adjoint != 0;
     h->graph_steps = o.graph_steps > 0 ? o.graph_steps + (o.graph_steps & 1) : 0;
@@ -786,7 +796,9 @@ const char *fdlbm_describe(fdlbm_t h)
         h->desc = std::string("staged-scheme2 ") + prec;
         return h->desc.c_str();
     }
+    const bool walls = h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL;
     const char *kern = h->path == FDLBM_PATH_STAGED        ? "staged"
+                       : walls                              ? "fused-walls"
                        : h->variant == FDLBM_VARIANT_PACKED ? "fused-f32x2"
                        : h->variant == FDLBM_VARIANT_WARP   ? "fused-warp"
                        : h->variant == FDLBM_VARIANT_TMA    ? "fused-tma"

@@ -126,6 +126,11 @@ cudaError_t fused_warp_encode(void *map, const float *state, int nx, int ny, int
 cudaError_t launch_fused_warp(const StepArgs<float> &a, const void *map_in, cudaStream_t s);
 int fused_warp_tile_width();
 int fused_warp_blocks_per_sm();
+// step_fused_walls.cu (scalar sweep with walled axes and Eq. 3.10 inside)
+template <class R>
+cudaError_t launch_fused_walls(const StepArgs<R> &a, cudaStream_t s);
+template <class R>
+int fused_walls_blocks_per_sm();
 // step_staged.cu
 template <class R>
 cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s);

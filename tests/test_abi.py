@@ -105,10 +105,13 @@ def test_workspace_and_validation_without_gpu(B):
     assert n64 > n32 >= 2 * 9 * 64 * 64 * 4
     o.path = B.PATH_STAGED
     assert L.fdlbm_workspace_bytes(ctypes.byref(grid), ctypes.byref(o)) > n32
-    # walled grids cannot take the fused path
+    # walled grids take the fused path (Eq. 3.10 inside the sweep); T2S2-FDLBM2
+    # does not
     wa = I.wall_axis(20, 0.0, 1.0)
     wgrid, keep2 = B.make_grid(xa, wa)
     o.path = B.PATH_FUSED
+    assert L.fdlbm_workspace_bytes(ctypes.byref(wgrid), ctypes.byref(o)) > 0
+    o.scheme = B.SCHEME_T2S2_2
     assert L.fdlbm_workspace_bytes(ctypes.byref(wgrid), ctypes.byref(o)) == 0
     h = ctypes.c_void_p()
     assert L.fdlbm_create(ctypes.byref(wgrid), None, 0.01, 0.5, 0.1, ctypes.byref(o),

@@ -220,6 +220,49 @@ def test_fp32_warp_variant_small_windows(nx, ny, rows):
     assert err <= 1e-6
 
 
+# ------------------------------------------------------------------ walls in the fused sweep
+_WALL_CASES = [
+    # (bc_x, bc_y, nx, ny, rows): cavity-like, channel-like, walled x only;
+    # several strips (nx > 120), short segments, tiny grids
+    ("wall", "wall", 17, 17, 0), ("wall", "wall", 40, 33, 3), ("wall", "wall", 257, 21, 1),
+    ("wall", "wall", 130, 9, 2), ("periodic", "wall", 96, 24, 5), ("periodic", "wall", 250, 13, 0),
+    ("wall", "periodic", 33, 40, 4), ("wall", "periodic", 125, 11, 0), ("wall", "wall", 5, 6, 1),
+]
+
+
+def _axis(kind, n, seed, length):
+    if kind == "periodic":
+        ax = I.periodic_axis(n, 0.0, length)
+        ax.metric = I.random_metric(n, seed, base=n / length, spread=0.3)
+        return ax
+    return I.tanh_axis(n - 1, 1.5) if length == 1.0 else I.wall_axis(n - 1, 0.0, length)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 1e-6)])
+@pytest.mark.parametrize("bcx,bcy,nx,ny,rows", _WALL_CASES)
+def test_fused_walls_match_oracle(precision, tol, bcx, bcy, nx, ny, rows):
+    """The fused sweep with Eq. 3.10 inside it, on walled grids (tanh-stretched
+    or uniform), with moving walls on every side, a random force field and a
+    random state: 12 steps against the oracle."""
+    xa = _axis(bcx, nx, 81, 1.0)
+    ya = _axis(bcy, ny, 82, 0.8)
+    rng = np.random.default_rng(nx * 1000 + ny)
+    force = 1e-3 * rng.uniform(-1, 1, size=(2, ny, nx))
+    wall_u = [tuple(0.05 * rng.uniform(-1, 1, size=2)) for _ in range(4)]
+    s, o = _pair(xa, ya, nu=0.02, cfl=0.4, beta=0.2, precision=precision, force=force,
+                 wall_u=wall_u, rows=rows, path="fused")
+    assert s.describe.startswith("fused-walls"), s.describe
+    assert s.kernels_per_step == 1
+    _init_both(s, o, I.random_fields(nx, ny, 90 + nx))
+    for n in (1, 11):
+        s.step(n)
+        o.step(n)
+    s.sync()
+    err = rel(s.get_state(), o.f)
+    print(f"{s.describe} {bcx}/{bcy} {nx}x{ny}: rel L2(f~) = {err:.3e}")
+    assert err <= tol
+
+
 def test_variant_not_applicable_is_rejected():
     xa = I.periodic_axis(130, 0.0, 1.0)   # 130 % 4 != 0: no 16-byte FP32 row pieces
     with pytest.raises(Exception, match="EUNSUPPORTED"):
@@ -305,7 +348,8 @@ def test_t1s2_special_case_fp64():
 
 
 # ------------------------------------------------------------------ walls (Eq. 3.10)
-def test_poiseuille_stretched_walls_fp64():
+@pytest.mark.parametrize("path", ["fused", "staged"])
+def test_poiseuille_stretched_walls_fp64(path):
     """Channel: periodic x, tanh-stretched walled y (Eq. 3.9, 10 x 20 cells), body force."""
     F = 0.01
     nu = math.sqrt(F / 80.0)
@@ -313,8 +357,8 @@ def test_poiseuille_stretched_walls_fp64():
     ya = I.tanh_axis(20, 1.5)
     force = np.zeros((2, ya.n, xa.n))
     force[0] = F
-    s, o = _pair(xa, ya, nu=nu, cfl=0.9, beta=0.1, force=force)
-    assert s.path == "staged"
+    s, o = _pair(xa, ya, nu=nu, cfl=0.9, beta=0.1, force=force, path=path)
+    assert s.path == path
     one = np.ones((ya.n, xa.n))
     s.init_fields(one, 0 * one, 0 * one)
     o.init_fields(one, 0 * one, 0 * one)
@@ -323,13 +367,16 @@ def test_poiseuille_stretched_walls_fp64():
     assert rel(s.get_state(), o.f) <= FP64_TOL
 
 
+@pytest.mark.parametrize("path", ["fused", "staged"])
 @pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 2e-6)])
-def test_cavity_stretched_walls(precision, tol):
+def test_cavity_stretched_walls(precision, tol, path):
     """Lid-driven cavity on a tanh grid (walls on all sides, lid U = 0.1)."""
     n = 24
     ax = I.tanh_axis(n, 1.5)
     wall_u = [(0, 0), (0, 0), (0, 0), (0.1, 0.0)]
-    s, o = _pair(ax, ax, nu=0.1 / 100.0, cfl=0.9, beta=0.1, wall_u=wall_u, precision=precision)
+    s, o = _pair(ax, ax, nu=0.1 / 100.0, cfl=0.9, beta=0.1, wall_u=wall_u, precision=precision,
+                 path=path)
+    assert s.path == path
     one = np.ones((ax.n, ax.n))
     s.init_fields(one, 0 * one, 0 * one)
     o.init_fields(one, 0 * one, 0 * one)
