@@ -256,21 +256,24 @@ def run_batched(stream_dev, ncases=64, seed=2024, steps=200, graph_steps=50):
     b.sync()
     t = e0.elapsed_time(e1) / 1e3
     kernel = b.describe
-    # the same steps as one persistent cooperative launch per graph replay
-    b._L.fdlbm_batch_set_persistent(b._h, 1)
-    b.step(2 * graph_steps)
-    b.sync()
-    e0.record(b.stream)
-    b.step(steps)
-    e1.record(b.stream)
-    b.sync()
-    t_persist = e0.elapsed_time(e1) / 1e3
+    # the same steps in the other two modes (per-stage staged launches, and
+    # one persistent cooperative launch per graph replay)
+    other = {}
+    for name, mode in (("staged", 1), ("persistent", 2)):
+        b._L.fdlbm_batch_set_mode(b._h, mode)
+        b.step(2 * graph_steps)
+        b.sync()
+        e0.record(b.stream)
+        b.step(steps)
+        e1.record(b.stream)
+        b.sync()
+        other[name] = b.cells * steps / (e0.elapsed_time(e1) / 1e3) / 1e6
     finite = all(np.isfinite(b.case(c).reduce()[0]) for c in range(len(probs)))
     out = {"cases": len(probs), "cells": b.cells, "steps": steps,
            "MLUPS": b.cells * steps / t / 1e6, "ms_per_step": t / steps * 1e3,
-           "bytes_per_cell": 288, "hbm_frac": 288 * b.cells * steps / t / 1e9 / (peaks().get("hbm_gbs") or 6800.0),
+           "bytes_per_cell": 72, "hbm_frac": 72 * b.cells * steps / t / 1e9 / (peaks().get("hbm_gbs") or 6800.0),
            "kernel": kernel, "all_finite": bool(finite),
-           "persistent_MLUPS": b.cells * steps / t_persist / 1e6,
+           "staged_MLUPS": other["staged"], "persistent_MLUPS": other["persistent"],
            "workload": f"{ncases} cases seed {seed}: cavity/channel, 33..513 cells, half stretched, "
                        f"Re log-uniform [10, 2000], CFL {CFL}, blend {BLEND}, FP32"}
     b.close()

@@ -244,9 +244,10 @@ size_t fdlbm_batch_workspace_bytes(int ncases, const fdlbm_grid *grids, const fd
  * opts[0].stream, or a private non-blocking stream when NULL (graph capture
  * needs a non-legacy stream).  graph_steps > 0: fdlbm_batch_step replays a CUDA
  * graph of that many steps (rounded up to even) captured on first use, and
- * launches any remainder directly.  autotune != 0: time a few block shapes of
- * the node kernels on this batch and keep the fastest (cached per batch
- * signature for the process); the states are reset to rest afterwards.
+ * launches any remainder directly.  autotune != 0: time a few tile shapes
+ * (block shapes of the staged node kernels, or tile heights of the fused sweep)
+ * on this batch and keep the fastest (cached per batch signature for the
+ * process); the states are reset to rest afterwards.
  * workspace: caller device memory of fdlbm_batch_workspace_bytes() bytes,
  * 256-byte aligned, or NULL (the library allocates). */
 fdlbm_status fdlbm_batch_create(int ncases, const fdlbm_grid *grids, const fdlbm_metrics *metrics,
@@ -258,13 +259,22 @@ int fdlbm_batch_size(fdlbm_batch_t b);
 long long fdlbm_batch_cells(fdlbm_batch_t b);        /* nodes of all cases */
 /* Advance every case by n steps (asynchronous on the batch stream). */
 fdlbm_status fdlbm_batch_step(fdlbm_batch_t b, int n);
-/* on != 0: later fdlbm_batch_step calls (and graph captures) run one persistent
- * cooperative launch for all their steps, the stages separated by a grid-wide
- * barrier with bounded waits (a timeout sets every case's error flag, which
- * fdlbm_sync / fdlbm_reduce of a case report); on = 0: one launch per stage and
- * step (the default, faster on GB300 because every stage kernel runs at its own
- * occupancy).  Synchronises the batch stream and drops a captured graph. */
-fdlbm_status fdlbm_batch_set_persistent(fdlbm_batch_t b, int on);
+/* How fdlbm_batch_step advances the cases:
+ *  FUSED       one launch per step of the fused sweep with Eq. 3.10 inside it,
+ *              over tiles of every case (FP32 and T2S2-FDLBM1 only; the default
+ *              where it applies);
+ *  STAGED      one launch per stage and step of the staged kernels (the default
+ *              otherwise);
+ *  PERSISTENT  the staged stages in one cooperative launch for all the steps of
+ *              a call (or of a graph replay), separated by a grid-wide barrier
+ *              with bounded waits (a timeout sets every case's error flag, which
+ *              fdlbm_sync / fdlbm_reduce of a case report).
+ * fdlbm_batch_set_mode synchronises the batch stream, drops a captured graph and
+ * rebuilds the tables with the mode's default tile shape (no autotuning);
+ * EUNSUPPORTED if FUSED does not apply. */
+enum { FDLBM_BATCH_FUSED = 0, FDLBM_BATCH_STAGED = 1, FDLBM_BATCH_PERSISTENT = 2 };
+fdlbm_status fdlbm_batch_set_mode(fdlbm_batch_t b, int mode);
+int fdlbm_batch_mode(fdlbm_batch_t b);               /* -1 for NULL */
 fdlbm_status fdlbm_batch_sync(fdlbm_batch_t b);
 void *fdlbm_batch_stream(fdlbm_batch_t b);           /* cudaStream_t of the batch */
 const char *fdlbm_batch_describe(fdlbm_batch_t b);

@@ -19,6 +19,7 @@ FP64, FP32_DEV = 0, 1
 PATH_AUTO, PATH_FUSED, PATH_STAGED = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 SCHEME_T2S2_1, SCHEME_T2S2_2 = 0, 1
+BATCH_FUSED, BATCH_STAGED, BATCH_PERSISTENT = 0, 1, 2
 VARIANT_AUTO, VARIANT_SCALAR, VARIANT_PACKED, VARIANT_TMA, VARIANT_ASYNC, VARIANT_WARP = 0, 1, 2, 3, 4, 5
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EUNSUPPORTED",
           -6: "ETOOBIG"}
@@ -93,7 +94,8 @@ SIGNATURES = [
     ("fdlbm_batch_size", ctypes.c_int, [_H]),
     ("fdlbm_batch_cells", ctypes.c_longlong, [_H]),
     ("fdlbm_batch_step", ctypes.c_int, [_H, ctypes.c_int]),
-    ("fdlbm_batch_set_persistent", ctypes.c_int, [_H, ctypes.c_int]),
+    ("fdlbm_batch_set_mode", ctypes.c_int, [_H, ctypes.c_int]),
+    ("fdlbm_batch_mode", ctypes.c_int, [_H]),
     ("fdlbm_batch_sync", ctypes.c_int, [_H]),
     ("fdlbm_batch_stream", ctypes.c_void_p, [_H]),
     ("fdlbm_batch_describe", ctypes.c_char_p, [_H]),

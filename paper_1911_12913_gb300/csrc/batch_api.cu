@@ -38,7 +38,8 @@ struct fdlbm_batch_ctx {
     size_t d_ints_cap = 0;
     BatchTables tab{};
     void *bar = nullptr;       // grid barrier of the persistent kernel (in d_ints)
-    bool persistent = false;   // one cooperative launch per call instead of per-stage launches
+    int mode = FDLBM_BATCH_STAGED;  // FDLBM_BATCH_FUSED / _STAGED / _PERSISTENT
+    int fused_rows = 0;             // tile height of the fused sweep (0: staged tables)
     dim3 blk{32, 8, 1};
     int graph_steps = 0;
     cudaGraph_t graph = nullptr;
@@ -65,17 +66,28 @@ fdlbm_status bfail(fdlbm_batch_ctx *b, fdlbm_status s, const std::string &what)
     return s;
 }
 
-// Host-side tables for block shape `blk`, uploaded to the device.
-fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk)
+// Host-side tables, uploaded to the device: for the staged kernels, node tiles
+// of block shape `blk`; for the fused sweep (fused_rows > 0), tiles of one
+// strip of the sweep's width by min(fused_rows, ny) rows (each case's tile
+// height goes into its argument block).
+fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
 {
     const int n = (int)b->cases.size();
     std::vector<int> blk_start(n), tiles_x(n), wall_start(n), blk_case;
     int total_wall = 0, total_blocks = 0;
     bool any2 = false;
     for (int c = 0; c < n; ++c) {
-        const fdlbm_ctx *h = b->cases[c];
-        const int tx = (h->nx + (int)blk.x - 1) / (int)blk.x;
-        const int ty = (h->ny + (int)blk.y - 1) / (int)blk.y;
+        fdlbm_ctx *h = b->cases[c];
+        int tx, ty;
+        if (fused_rows > 0) {
+            h->rows = std::min(fused_rows, h->ny);
+            tx = (h->nx + fused_tile_width_walls() - 1) / fused_tile_width_walls();
+            ty = (h->ny + h->rows - 1) / h->rows;
+        } else {
+            h->rows = 1;
+            tx = (h->nx + (int)blk.x - 1) / (int)blk.x;
+            ty = (h->ny + (int)blk.y - 1) / (int)blk.y;
+        }
         blk_start[c] = total_blocks;
         tiles_x[c] = tx;
         total_blocks += tx * ty;
@@ -134,7 +146,43 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk)
     b->tab.total_wall = total_wall;
     b->tab.any_scheme2 = any2;
     b->blk = blk;
+    b->fused_rows = fused_rows;
     return FDLBM_OK;
+}
+
+// Every case T2S2-FDLBM1 in FP32: the fused sweep applies (FP64 walled cases are
+// bound by the FP64 units, where the staged kernels do better).
+bool fused_eligible(const fdlbm_batch_ctx *b)
+{
+    if (b->precision != FDLBM_FP32_DEV) return false;
+    for (const fdlbm_ctx *h : b->cases)
+        if (h->scheme != FDLBM_SCHEME_T2S2_1) return false;
+    return true;
+}
+
+// Tile height of the fused batch: minimise (waves) x (rows + 8) over the tiles
+// of all cases, as for a single grid.
+int fused_rows_model(const fdlbm_batch_ctx *b)
+{
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = std::max(1, fused_walls_blocks_per_sm<float>());
+    const long long slots = (long long)per_sm * sms;
+    const int W = fused_tile_width_walls();
+    int best = 64;
+    double best_cost = 1e300;
+    for (int rows = 8; rows <= 512; ++rows) {
+        long long ctas = 0;
+        for (const fdlbm_ctx *h : b->cases)
+            ctas += (long long)((h->nx + W - 1) / W) * ((h->ny + std::min(rows, h->ny) - 1) / std::min(rows, h->ny));
+        const double cost = (double)((ctas + slots - 1) / slots) * (rows + 8);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = rows;
+        }
+    }
+    return best;
 }
 
 // n steps starting at ping-pong parity `parity`: one persistent launch, or one
@@ -142,7 +190,14 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk)
 cudaError_t launch_steps(fdlbm_batch_ctx *b, int parity, int n)
 {
     const bool f32 = b->precision == FDLBM_FP32_DEV;
-    if (b->persistent)
+    if (b->mode == FDLBM_BATCH_FUSED) {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < n && e == cudaSuccess; ++k)
+            e = f32 ? launch_batched_fused<float>(b->tab, (parity + k) & 1, b->stream)
+                    : launch_batched_fused<double>(b->tab, (parity + k) & 1, b->stream);
+        return e;
+    }
+    if (b->mode == FDLBM_BATCH_PERSISTENT)
         return f32 ? launch_persistent<float>(b->tab, b->bar, parity, n, b->blk, b->stream)
                    : launch_persistent<double>(b->tab, b->bar, parity, n, b->blk, b->stream);
     cudaError_t e = cudaSuccess;
@@ -201,14 +256,18 @@ fdlbm_status capture(fdlbm_batch_ctx *b)
 std::string signature(const fdlbm_batch_ctx *b)
 {
     std::ostringstream os;
-    os << b->precision;
+    os << b->precision << '/' << b->mode;
     for (const fdlbm_ctx *h : b->cases)
         os << ';' << h->nx << 'x' << h->ny << ':' << h->bc_x << h->bc_y << h->has_force << h->scheme;
     return os.str();
 }
 
 std::mutex g_tune_mu;
-std::map<std::string, std::pair<dim3, double>> g_tune_cache;
+struct TuneChoice {
+    dim3 blk;  // staged: node tile shape
+    int rows;  // fused: tile height (0 for staged)
+};
+std::map<std::string, std::pair<TuneChoice, double>> g_tune_cache;
 
 // Reset every case to fluid at rest (after tuning runs on the state).
 fdlbm_status reset_states(fdlbm_batch_ctx *b)
@@ -237,17 +296,26 @@ fdlbm_status autotune(fdlbm_batch_ctx *b)
         if (it != g_tune_cache.end()) {
             b->tuned = true;
             b->tuned_ms = it->second.second;
-            return build_tables(b, it->second.first);
+            return build_tables(b, it->second.first.blk, it->second.first.rows);
         }
     }
-    const dim3 cand[] = {dim3(32, 8), dim3(64, 4), dim3(128, 2), dim3(32, 4), dim3(16, 16), dim3(256, 1)};
+    std::vector<TuneChoice> cand;
+    if (b->mode == FDLBM_BATCH_FUSED) {
+        const int r0 = fused_rows_model(b);
+        for (int r : {r0, std::max(8, r0 / 2), std::max(8, 3 * r0 / 4), std::min(512, 2 * r0)})
+            if (std::none_of(cand.begin(), cand.end(), [&](const TuneChoice &c) { return c.rows == r; }))
+                cand.push_back({dim3(128, 1), r});
+    } else {
+        for (const dim3 &d : {dim3(32, 8), dim3(64, 4), dim3(128, 2), dim3(32, 4), dim3(16, 16), dim3(256, 1)})
+            cand.push_back({d, 0});
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    dim3 best = cand[0];
+    TuneChoice best = cand[0];
     float best_ms = 1e30f;
-    for (const dim3 &c : cand) {
-        fdlbm_status st = build_tables(b, c);
+    for (const TuneChoice &c : cand) {
+        fdlbm_status st = build_tables(b, c.blk, c.rows);
         if (st == FDLBM_OK) st = step_direct(b, 2);
         if (st != FDLBM_OK) break;
         cudaEventRecord(e0, b->stream);
@@ -269,9 +337,16 @@ fdlbm_status autotune(fdlbm_batch_ctx *b)
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = {best, b->tuned_ms};
     }
-    fdlbm_status st = build_tables(b, best);
+    fdlbm_status st = build_tables(b, best.blk, best.rows);
     if (st != FDLBM_OK) return st;
     return reset_states(b);
+}
+
+// Tables of the current mode with its default parameters.
+fdlbm_status default_tables(fdlbm_batch_ctx *b)
+{
+    return b->mode == FDLBM_BATCH_FUSED ? build_tables(b, dim3(128, 1), fused_rows_model(b))
+                                        : build_tables(b, dim3(32, 8));
 }
 
 void release(fdlbm_batch_ctx *b)
@@ -382,7 +457,8 @@ fdlbm_status fdlbm_batch_create(int ncases, const fdlbm_grid *grids, const fdlbm
         return FDLBM_ENOMEM;
     }
     b->graph_steps = graph_steps + (graph_steps & 1);  // even: starts and ends on the same parity
-    fdlbm_status st = autotune_blocks ? autotune(b) : build_tables(b, dim3(32, 8));
+    b->mode = fused_eligible(b) ? FDLBM_BATCH_FUSED : FDLBM_BATCH_STAGED;
+    fdlbm_status st = autotune_blocks ? autotune(b) : default_tables(b);
     if (st != FDLBM_OK) {
         release(b);
         return st;
@@ -431,15 +507,22 @@ fdlbm_status fdlbm_batch_step(fdlbm_batch_t b, int n)
     return step_direct(b, n);
 }
 
-fdlbm_status fdlbm_batch_set_persistent(fdlbm_batch_t b, int on)
+fdlbm_status fdlbm_batch_set_mode(fdlbm_batch_t b, int mode)
 {
     if (!b) return FDLBM_EINVAL;
+    if (mode != FDLBM_BATCH_FUSED && mode != FDLBM_BATCH_STAGED && mode != FDLBM_BATCH_PERSISTENT)
+        return bfail(b, FDLBM_EINVAL, "batch set_mode: unknown mode");
+    if (mode == FDLBM_BATCH_FUSED && !fused_eligible(b))
+        return bfail(b, FDLBM_EUNSUPPORTED, "batch set_mode: the fused sweep needs FP32 and T2S2-FDLBM1");
     fdlbm_status st = fdlbm_batch_sync(b);
     if (st != FDLBM_OK) return st;
     drop_graph(b);
-    b->persistent = on != 0;
-    return FDLBM_OK;
+    b->mode = mode;
+    b->tuned = false;
+    return default_tables(b);
 }
+
+int fdlbm_batch_mode(fdlbm_batch_t b) { return b ? b->mode : -1; }
 
 fdlbm_status fdlbm_batch_sync(fdlbm_batch_t b)
 {
@@ -454,12 +537,18 @@ const char *fdlbm_batch_describe(fdlbm_batch_t b)
 {
     if (!b) return "NULL batch";
     std::ostringstream os;
-    const int per_step =
-        3 + (b->tab.total_wall > 0 ? 2 : 0) + (b->tab.total_wall > 0 && b->tab.any_scheme2 ? 1 : 0);
-    os << (b->persistent ? "batched-persistent " : "batched-staged ")
-       << (b->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64") << " cases=" << b->cases.size()
-       << " block=" << b->blk.x << "x" << b->blk.y << " graph_steps=" << b->graph_steps
-       << (b->persistent ? " grid_barriers_per_step=" : " launches_per_step=") << per_step;
+    const char *prec = b->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64";
+    if (b->mode == FDLBM_BATCH_FUSED) {
+        os << "batched-fused " << prec << " cases=" << b->cases.size() << " rows=" << b->fused_rows
+           << " graph_steps=" << b->graph_steps << " launches_per_step=1";
+    } else {
+        const int per_step =
+            3 + (b->tab.total_wall > 0 ? 2 : 0) + (b->tab.total_wall > 0 && b->tab.any_scheme2 ? 1 : 0);
+        const bool pers = b->mode == FDLBM_BATCH_PERSISTENT;
+        os << (pers ? "batched-persistent " : "batched-staged ") << prec << " cases=" << b->cases.size()
+           << " block=" << b->blk.x << "x" << b->blk.y << " graph_steps=" << b->graph_steps
+           << (pers ? " grid_barriers_per_step=" : " launches_per_step=") << per_step;
+    }
     if (b->tuned) os << " tuned_ms_per_step=" << b->tuned_ms;
     b->desc = os.str();
     return b->desc.c_str();

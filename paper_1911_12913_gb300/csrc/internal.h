@@ -131,6 +131,9 @@ template <class R>
 cudaError_t launch_fused_walls(const StepArgs<R> &a, cudaStream_t s);
 template <class R>
 int fused_walls_blocks_per_sm();
+template <class R>
+cudaError_t launch_batched_fused(const BatchTables &t, int parity, cudaStream_t s);
+int fused_tile_width_walls();
 // step_staged.cu
 template <class R>
 cudaError_t launch_staged(const StepArgs<R> &a, cudaStream_t s);

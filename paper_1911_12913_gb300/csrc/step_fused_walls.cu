@@ -115,7 +115,7 @@ struct SweepW {
     __device__ void force_at(int r, R &Fx, R &Fy) const
     {
         Fx = Fy = R(0);
-        if (FORCE) {
+        if (FORCE && a.force) {
             const size_t fo = (size_t)mem_row(r) * a.pitch + gx;
             Fx = __ldg(a.force + fo);
             Fy = __ldg(a.force + a.plane + fo);
@@ -305,18 +305,12 @@ struct SweepW {
     }
 };
 
+// One tile: output columns x0 .. x0 + W - 1 and rows y0 .. y0 + a.rows - 1.
 template <class R, bool FORCE>
-__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) k_step_fused_walls(const StepArgs<R> a)
+__device__ __forceinline__ void sweep_tile(const StepArgs<R> &a, Smem<R> &sm, int x0, int y0)
 {
-    constexpr int W = NT - 2 * kHalo;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<R> &sm = *reinterpret_cast<Smem<R> *>(smem_raw);
-
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * W;
     const int xc = x0 - kHalo + t;
-    const int y0 = blockIdx.y * a.rows;
-    if (y0 >= a.ny) return;  // uniform over the block
     const int y1 = min(y0 + a.rows, a.ny);
     const bool wx = a.bc_x == FDLBM_WALL, wy = a.bc_y == FDLBM_WALL;
     const bool inside = !wx || (xc >= 0 && xc < a.nx);
@@ -356,6 +350,42 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) k_step_fused_walls
 }
 
 template <class R, bool FORCE>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) k_step_fused_walls(const StepArgs<R> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<R> &sm = *reinterpret_cast<Smem<R> *>(smem_raw);
+    const int y0 = blockIdx.y * a.rows;
+    if (y0 >= a.ny) return;  // uniform over the block
+    sweep_tile<R, FORCE>(a, sm, blockIdx.x * (NT - 2 * kHalo), y0);
+}
+
+// Batched: block b is tile (b - blk_start[c]) of case c = blk_case[b], with
+// strips[c] strips per row of tiles; the case's arguments (its own tile height
+// in .rows) are copied into shared memory first.
+template <class R>
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2)
+    kb_step_fused_walls(const StepArgs<R> *cases, const int *blk_case, const int *blk_start,
+                        const int *strips)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<R> &sm = *reinterpret_cast<Smem<R> *>(smem_raw);
+    __shared__ __align__(16) unsigned char abuf[sizeof(StepArgs<R>)];
+    static_assert(sizeof(StepArgs<R>) % 4 == 0, "argument block is copied as 32-bit words");
+    const int c = blk_case[blockIdx.x];
+    {
+        const int *src = reinterpret_cast<const int *>(cases + c);
+        int *dst = reinterpret_cast<int *>(abuf);
+        for (int k = threadIdx.x; k < (int)(sizeof(StepArgs<R>) / 4); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const StepArgs<R> &a = *reinterpret_cast<const StepArgs<R> *>(abuf);
+    const int lb = blockIdx.x - blk_start[c], ns = strips[c];
+    const int y0 = (lb / ns) * a.rows;
+    if (y0 >= a.ny) return;  // uniform over the block
+    sweep_tile<R, true>(a, sm, (lb % ns) * (NT - 2 * kHalo), y0);
+}
+
+template <class R, bool FORCE>
 cudaError_t launch_t(const StepArgs<R> &a, cudaStream_t s)
 {
     constexpr int W = NT - 2 * kHalo;
@@ -389,6 +419,23 @@ int fused_walls_blocks_per_sm()
     return n;
 }
 
+// One step of every case of a batch (all T2S2-FDLBM1): one launch.
+template <class R>
+cudaError_t launch_batched_fused(const BatchTables &t, int parity, cudaStream_t s)
+{
+    constexpr size_t smem = sizeof(Smem<R>);
+    cudaError_t e = cudaFuncSetAttribute(kb_step_fused_walls<R>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kb_step_fused_walls<R><<<t.total_blocks, NT, smem, s>>>(
+        static_cast<const StepArgs<R> *>(t.args[parity]), t.blk_case, t.blk_start, t.tiles_x);
+    return cudaGetLastError();
+}
+
+int fused_tile_width_walls() { return NT - 2 * kHalo; }
+
+template cudaError_t launch_batched_fused<float>(const BatchTables &, int, cudaStream_t);
+template cudaError_t launch_batched_fused<double>(const BatchTables &, int, cudaStream_t);
 template cudaError_t launch_fused_walls<float>(const StepArgs<float> &, cudaStream_t);
 template cudaError_t launch_fused_walls<double>(const StepArgs<double> &, cudaStream_t);
 template int fused_walls_blocks_per_sm<float>();

@@ -249,7 +249,7 @@ class FDLBMBatch:
     read-back; ``batch.step(n)`` advances every case."""
 
     def __init__(self, cases, *, precision: str = "fp32", graph_steps: int = 50,
-                 autotune: bool = True, persistent: bool = False, device=None):
+                 autotune: bool = True, mode: str = "auto", device=None):
         self._L = L = B.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         n = len(cases)
@@ -282,10 +282,11 @@ class FDLBMBatch:
                                   ctypes.byref(h))
         if rc != 0:
             raise B.FdlbmError(rc, "fdlbm_batch_create")
-        if persistent:
-            rc = L.fdlbm_batch_set_persistent(h, 1)
+        if mode != "auto":
+            rc = L.fdlbm_batch_set_mode(h, {"fused": B.BATCH_FUSED, "staged": B.BATCH_STAGED,
+                                            "persistent": B.BATCH_PERSISTENT}[mode])
             if rc != 0:
-                raise B.FdlbmError(rc, "fdlbm_batch_set_persistent")
+                raise B.FdlbmError(rc, "fdlbm_batch_set_mode")
         self._h = h
         self.stream = torch.cuda.ExternalStream(L.fdlbm_batch_stream(h), device=self.device)
         self._cases = [FDLBM._case_view(L, L.fdlbm_batch_case(h, c), cs["xa"], cs["ya"], self.stream,

@@ -79,16 +79,21 @@ def _setup(batch, cases):
     return oracles
 
 
-@pytest.mark.parametrize("precision,tol,autotune,persistent",
-                         [("fp64", 1e-12, False, False), ("fp32", 2e-6, True, False),
-                          ("fp64", 1e-12, False, True), ("fp32", 2e-6, False, True)])
-def test_mixed_batch_matches_oracle(precision, tol, autotune, persistent):
-    """Per-stage launches (default) and the persistent cooperative launch."""
+@pytest.mark.parametrize("precision,tol,autotune,mode",
+                         [("fp64", 1e-12, False, "auto"), ("fp32", 2e-6, True, "auto"),
+                          ("fp32", 2e-6, True, "fused"), ("fp32", 2e-6, False, "staged"),
+                          ("fp64", 1e-12, False, "persistent"), ("fp32", 2e-6, False, "persistent")])
+def test_mixed_batch_matches_oracle(precision, tol, autotune, mode):
+    """The three batch modes: the fused sweep with walls (FP32, T2S2-FDLBM1 cases
+    only, the default where it applies), per-stage launches of the staged
+    kernels, and the persistent cooperative launch."""
     cases = _mixed_cases()
-    batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=autotune,
-                       persistent=persistent)
-    assert batch.describe.startswith("batched-persistent" if persistent else "batched-staged")
-    assert "cases=6" in batch.describe
+    if mode == "fused":
+        cases = [cs for cs in cases if cs.get("scheme", 1) == 1]
+    batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=autotune, mode=mode)
+    want = {"fused": "batched-fused", "staged": "batched-staged",
+            "persistent": "batched-persistent", "auto": "batched-staged"}[mode]
+    assert batch.describe.startswith(want), batch.describe
     oracles = _setup(batch, cases)
     # 11 steps: 4 + 4 by graph replay, 3 launched directly; then 1 more
     # (odd parity) and 5 more (realignment + graph + direct)
@@ -101,6 +106,16 @@ def test_mixed_batch_matches_oracle(precision, tol, autotune, persistent):
         err = rel(batch.case(c).get_state(), o.f)
         assert err <= tol, (c, err, batch.describe)
     print(batch.describe)
+
+
+def test_batch_fused_mode_needs_fp32_scheme1():
+    cases = _mixed_cases()
+    with pytest.raises(Exception, match="EUNSUPPORTED"):
+        FDLBMBatch(cases, precision="fp32", graph_steps=0, autotune=False, mode="fused")
+    with pytest.raises(Exception, match="EUNSUPPORTED"):
+        FDLBMBatch(cases[:5], precision="fp64", graph_steps=0, autotune=False, mode="fused")
+    b = FDLBMBatch(cases[:5], precision="fp32", graph_steps=0, autotune=False)
+    assert b.describe.startswith("batched-fused"), b.describe
 
 
 def test_batch_case_restrictions():
@@ -127,6 +142,7 @@ def test_sweep_64_cases_sampled_parity():
     cases = [dict(xa=p["xa"], ya=p["ya"], nu=p["nu"], cfl=0.5, blend=0.1, wall_u=p["wall_u"],
                   has_force=p["force"] is not None) for p in probs]
     batch = FDLBMBatch(cases, precision="fp32", graph_steps=10, autotune=True)
+    assert batch.describe.startswith("batched-fused"), batch.describe
     for c, p in enumerate(probs):
         v = batch.case(c)
         if p["force"] is not None:
