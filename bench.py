@@ -456,29 +456,55 @@ def run_adjoint(dev, n=256, nsteps=2000, iters=6, seed=11):
 
 
 # ----------------------------------------------------------------------- our arm
+class Ranks:
+    """The ranks of a run, from RANK / WORLD_SIZE / LOCAL_RANK.  Every rank runs
+    an independent replica of the workload (the step has no data-path
+    collective); the only collectives are the barriers around the timed region
+    and the maximum of the ranks' times."""
+
+    def __init__(self, backend="nccl", device=None):
+        import torch
+        import torch.distributed as dist
+        self.dist = dist
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        if device is None:
+            torch.cuda.set_device(self.local)
+            device = torch.device("cuda", self.local)
+        self.device = device
+        if self.world > 1 and not dist.is_initialized():
+            kw = {"device_id": device} if backend == "nccl" else {}
+            dist.init_process_group(backend, **kw)
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, v):
+        if self.world == 1:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def aggregate(self, units_per_rank, seconds_max):
+        """Whole-job throughput: the units of all ranks over the slowest rank's time."""
+        return self.world * units_per_rank / seconds_max
+
+    def close(self):
+        if self.world > 1 and self.dist.is_initialized():
+            self.dist.destroy_process_group()
+
+
 def run_ours(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", torch.cuda.current_device())
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks("nccl")
+    world, rank, dev = ranks.world, ranks.rank, ranks.device
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     from paper_1911_12913_gb300.solver import FDLBM
 
@@ -512,7 +538,7 @@ def run_ours(args):
     mass_drift = abs(m1 - m0) / abs(m0)
     launches = args.steps * s.kernels_per_step
     per_launch_s = ms / 1e3 / args.steps
-    value = world * N * args.steps / (ms_max / 1e3) / 1e6
+    value = ranks.aggregate(N * args.steps, ms_max / 1e3) / 1e6
 
     pk = peaks()
     hbm = pk.get("hbm_gbs")
@@ -624,7 +650,7 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     barrier()
     e2e_s = max_over_ranks(e2e_s)
-    e2e = {"value": world * N * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+    e2e = {"value": ranks.aggregate(N * args.steps, e2e_s) / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": 7 * N * 8 / args.steps,
            "d2h_bytes_per_step": (3 * N * 8 + 3 * 8) / args.steps,
            "job": "init_fields(host rho,u,grad u) + K steps + reduce + moments(host), per rank"}
@@ -648,8 +674,7 @@ def run_ours(args):
                "mass_drift_rel": mass_drift,
                "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(out), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 

@@ -153,6 +153,42 @@ def test_fp32_adjoint_close_to_fp64():
     assert e_lam <= 1e-5 and e_F <= 1e-4
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_adjoint_256_against_oracle_directional_derivative(precision, tol):
+    """The adjoint step on the inverse problem's grid (256^2 periodic, initial
+    velocity from a k^-3 vorticity spectrum up to k = 8, smooth force field):
+    <J v, w>, with J v the oracle's complex-step directional derivative of one
+    step along a random state and force direction (exact to rounding), equals
+    <v, J^T w> from the GPU adjoint step."""
+    n = 256
+    ax = I.periodic_axis(n, 0.0, 2 * math.pi)
+    s = FDLBM(ax, ax, nu=0.01, cfl=0.5, blend=0.1, precision=precision, has_force=True,
+              adjoint=True)
+    v = I.spectral_vorticity_velocity(n, 11, kmax=8, umax=0.01)
+    o = O.Oracle(ax, ax, nu=0.01, dt=s.dt, beta=0.1)
+    one = np.ones((n, n))
+    o.init_fields(one, v["ux"], v["uy"], [v["dudx"], v["dudy"], v["dvdx"], v["dvdy"]])
+    f0 = o.f.copy()
+    h = I.spectral_vorticity_velocity(n, 12, kmax=8, umax=1e-5)
+    F = np.stack([h["ux"], h["uy"]])
+    rng = np.random.default_rng(256)
+    dv, dF, w = rng.normal(size=f0.shape), rng.normal(size=F.shape), rng.normal(size=f0.shape)
+    eps = 1e-20
+    y = O.step_complex(ax, ax, nu=0.01, dt=s.dt, beta=0.1, f=f0 + 1j * eps * dv,
+                       force=F + 1j * eps * dF)
+    lhs = float(np.sum(y.imag / eps * w))
+    s.set_state(f0)
+    s.set_force(F)
+    state = s.save_state(s.new_buffer())
+    out = s.new_buffer()
+    dFg = torch.zeros((2, n, n), dtype=torch.float64, device=s.device)
+    s.adjoint_step(state, _to_buffer(s, w), out, dFg)
+    s.sync()
+    rhs = float(np.sum(dv * out[:, :, :n].double().cpu().numpy()) + np.sum(dF * dFg.cpu().numpy()))
+    print(f"{precision} 256^2: <Jv, w> = {lhs:.12e}, <v, J^T w> = {rhs:.12e}, rel {abs(lhs - rhs) / abs(lhs):.2e}")
+    assert abs(lhs - rhs) <= tol * abs(lhs)
+
+
 def test_adjoint_rejects_walls_and_missing_scratch():
     xa = I.periodic_axis(16, 0.0, 1.0)
     s = FDLBM(xa, xa, nu=NU, cfl=CFL, blend=BETA)        # no adjoint scratch
