@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurements")
     p.add_argument("--no-cavity", action="store_true", help="skip the 257^2 cavity march")
     p.add_argument("--no-sweep", action="store_true", help="skip the 512^2..4096^2 size sweep")
+    p.add_argument("--rows", type=int, default=0, help="tile height of the fused kernel (0: automatic)")
+    p.add_argument("--cavity-steps", type=int, default=0, metavar="K",
+                   help="only time K steps of the 257^2 cavity (FP32, fused walls) and print that")
     p.add_argument("--adjoint-cost", type=int, default=0, metavar="N",
                    help="only time adjoint against forward steps on an N^2 grid and print that")
     return p.parse_args()
@@ -356,6 +359,30 @@ def run_cavity(dev, n_cells=256, c=1.5, U=0.1, Re=1000.0, cfl=0.9, eta=0.1, tol=
     return res
 
 
+def cavity_steps(k, n_cells=256, c=1.5, U=0.1, Re=1000.0, cfl=0.9, eta=0.1):
+    """K steps of the 257^2 cavity from rest in FP32 (the automatic kernel: the
+    fused sweep with walls), timed with CUDA events."""
+    import numpy as np
+    import torch
+    import inputs as I
+    from paper_1911_12913_gb300.solver import FDLBM
+
+    ax = I.tanh_axis(n_cells, c)
+    s = FDLBM(ax, ax, nu=U / Re, cfl=cfl, blend=eta, precision="fp32",
+              wall_u=[(0, 0), (0, 0), (0, 0), (U, 0.0)])
+    one = np.ones((ax.n, ax.n))
+    s.init_fields(one, 0 * one, 0 * one)
+    s.step(5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s.stream)
+    s.step(k)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / k
+    return {"steps": k, "us_per_step": t * 1e6, "MLUPS": ax.n * ax.n / t / 1e6, "kernel": s.describe}
+
+
 # ----------------------------------------------------------------------- reverse mode
 def adjoint_cost(dev, m, k=200, seed=11):
     """Time k adjoint steps against k forward steps on an m^2 periodic FP32 grid
@@ -516,7 +543,7 @@ def run_ours(args):
 
     # ---------------- device-resident timing (FP32 deviation, the headline)
     s = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream,
-              variant=args.variant)
+              variant=args.variant, rows_per_cta=args.rows)
     kernel_desc = s.describe
     s.init_fields(f["rho"], f["ux"], f["uy"], grad)
     m0, _ = s.reduce()
@@ -682,6 +709,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.cavity_steps:
+        print(json.dumps(cavity_steps(args.cavity_steps)), flush=True)
+        return 0
     if args.adjoint_cost:
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())

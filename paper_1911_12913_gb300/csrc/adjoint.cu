@@ -312,7 +312,7 @@ int adj_rows(int nx, int ny, int per_sm)
     const long long strips = (nx + (kAdjNT - 2 * kAdjHalo) - 1) / (kAdjNT - 2 * kAdjHalo);
     int best = std::min(ny, 64);
     double best_cost = 1e300;
-    for (int rows = 8; rows <= std::min(ny, 512); ++rows) {
+    for (int rows = 1; rows <= std::min(ny, 512); ++rows) {
         const long long ctas = strips * ((ny + rows - 1) / rows);
         const double cost = (double)((ctas + slots - 1) / slots) * (rows + 8);
         if (cost < best_cost - 1e-9) {

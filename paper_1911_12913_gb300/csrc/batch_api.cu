@@ -172,7 +172,7 @@ int fused_rows_model(const fdlbm_batch_ctx *b)
     const int W = fused_tile_width_walls();
     int best = 64;
     double best_cost = 1e300;
-    for (int rows = 8; rows <= 512; ++rows) {
+    for (int rows = 1; rows <= 512; ++rows) {
         long long ctas = 0;
         for (const fdlbm_ctx *h : b->cases)
             ctas += (long long)((h->nx + W - 1) / W) * ((h->ny + std::min(rows, h->ny) - 1) / std::min(rows, h->ny));

@@ -91,7 +91,8 @@ int choose_path(const fdlbm_grid *g, const fdlbm_opts *o)
 
 // Rows per CTA of the fused kernel.  Each CTA recomputes 8 halo rows, so tall
 // tiles waste less; the grid should also fill whole waves of resident CTAs.
-// Pick the height that minimises (waves) x (rows + 8), the modelled sweep time.
+// Pick the height that minimises (waves) x (rows + 8), the modelled sweep time
+// (on small grids that is a short segment: more CTAs, each walking fewer rows).
 int choose_rows(int nx, int ny, int precision, int variant, bool walls)
 {
     int dev = 0, sms = 152;
@@ -119,7 +120,7 @@ int choose_rows(int nx, int ny, int precision, int variant, bool walls)
     const long long strips = (nx + W - 1) / W;
     int best = std::min(ny, 64);
     double best_cost = 1e300;
-    for (int rows = 8; rows <= std::min(ny, 512); ++rows) {
+    for (int rows = 1; rows <= std::min(ny, 512); ++rows) {
         const long long ctas = strips * ((ny + rows - 1) / rows);
         const long long waves = (ctas + slots - 1) / slots;
         const double cost = (double)waves * (rows + 8);
