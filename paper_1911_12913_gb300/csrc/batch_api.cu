@@ -302,7 +302,7 @@ fdlbm_status autotune(fdlbm_batch_ctx *b)
     std::vector<TuneChoice> cand;
     if (b->mode == FDLBM_BATCH_FUSED) {
         const int r0 = fused_rows_model(b);
-        for (int r : {r0, std::max(8, r0 / 2), std::max(8, 3 * r0 / 4), std::min(512, 2 * r0)})
+        for (int r : {r0, std::max(1, r0 / 2), std::max(1, 3 * r0 / 4), std::min(512, 2 * r0)})
             if (std::none_of(cand.begin(), cand.end(), [&](const TuneChoice &c) { return c.rows == r; }))
                 cand.push_back({dim3(128, 1), r});
     } else {
