@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define FDLBM_ABI_VERSION 1
+#define FDLBM_ABI_VERSION 2
 
 typedef struct fdlbm_ctx *fdlbm_t;
 
@@ -50,6 +50,17 @@ enum { FDLBM_PERIODIC = 0, FDLBM_WALL = 1 };            /* boundary kind of an a
 enum { FDLBM_FP64 = 0, FDLBM_FP32_DEV = 1 };            /* storage / arithmetic precision */
 enum { FDLBM_PATH_AUTO = 0, FDLBM_PATH_FUSED = 1, FDLBM_PATH_STAGED = 2 };
 enum { FDLBM_MEM_HOST = 0, FDLBM_MEM_DEVICE = 1 };
+/* Equilibrium of the BGK collision.  STANDARD is Eq. 3.2.  INCOMPRESSIBLE is
+ * the incompressible equilibrium of He and Luo, which Sec. 2 of the paper says
+ * can be combined with both T2S2 schemes without printing it:
+ *   f_i^eq = w_i [rho + rho0 (xi.u / cs^2 + ((xi.u)^2 - cs^2 u.u) / (2 cs^4))],
+ * with the velocity read from rho0 u = sum xi f~ + (dt/2) rho0 F (Eq. 3.3 with
+ * rho0 for rho) and the forcing term of Eq. 3.12 taken with the equilibrium at
+ * rho0.  It runs on the scalar, warp-tile, walls and staged kernels and in
+ * batches; the TMA, ASYNC and PACKED variants and the adjoint step return
+ * FDLBM_EUNSUPPORTED with it.  fdlbm_moments returns the density and this
+ * velocity. */
+enum { FDLBM_EQ_STANDARD = 0, FDLBM_EQ_INCOMPRESSIBLE = 1 };
 /* Fused-kernel variant (periodic grids; a grid with a walled axis runs the
  * scalar sweep with Eq. 3.10 inside it, and any other variant is unsupported):
  *  SCALAR  one column per thread, rows loaded through registers (any nx >= 4);
@@ -111,6 +122,7 @@ typedef struct {
     int adjoint;              /* 1: reserve scratch for fdlbm_adjoint_step (periodic grids) */
     int graph_steps;          /* > 0: fdlbm_step replays a CUDA graph of this many steps (rounded
                                  up to even), captured on first use; 0 = direct launches */
+    int equilibrium;          /* FDLBM_EQ_STANDARD (Eq. 3.2) or FDLBM_EQ_INCOMPRESSIBLE */
     void *stream;             /* cudaStream_t used for all work; NULL = default stream */
     void *workspace;          /* caller-owned device memory of fdlbm_workspace_bytes() bytes,
                                  256-byte aligned; NULL = the library allocates its own */

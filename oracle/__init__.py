@@ -49,6 +49,8 @@ class _Cfg(ctypes.Structure):
         ("force", ctypes.c_void_p),
         ("wall_u", (ctypes.c_double * 2) * 4),
         ("nthreads", ctypes.c_int),
+        ("incomp", ctypes.c_int),
+        ("rho0", ctypes.c_double),
     ]
 
 
@@ -98,6 +100,7 @@ def lib():
         L.oracle_moments.argtypes = [P, _dp, _dp, _dp, _dp]
         L.oracle_init.argtypes = [P, _dp, _dp, _dp, _dp, ctypes.c_double, _dp]
         L.oracle_feq.argtypes = [ctypes.c_double] * 3 + [_dp]
+        L.oracle_feq_incomp.argtypes = [ctypes.c_double] * 4 + [_dp]
         L.oracle_force_term.argtypes = [_dp] + [ctypes.c_double] * 4 + [_dp]
         L.oracle_derivative.argtypes = [P, _dp, ctypes.c_int, ctypes.c_int, _dp]
         L.oracle_stages.argtypes = [P, _dp] + [_dp] * 5
@@ -147,6 +150,15 @@ def feq(rho: float, ux: float, uy: float) -> np.ndarray:
     return out
 
 
+def feq_incomp(rho: float, rho0: float, ux: float, uy: float) -> np.ndarray:
+    """The incompressible equilibrium of He and Luo at one node (the paper cites
+    it in Sec. 2 as usable with both schemes but does not print it):
+    Eq. 3.2 with rho0 in place of rho in the velocity terms."""
+    out = np.zeros(9)
+    lib().oracle_feq_incomp(rho, rho0, ux, uy, _ptr(out))
+    return out
+
+
 def force_term(fe: np.ndarray, ux: float, uy: float, Fx: float, Fy: float) -> np.ndarray:
     """Eq. 3.12 at one node."""
     fe = np.ascontiguousarray(fe, dtype=np.float64)
@@ -160,12 +172,15 @@ class Oracle:
 
     ``A``: the intermediate time fraction (0.5: T2S2-FDLBM1, 0: T1S2-FDLBM).
     ``beta``: upwind weight of the mixed difference.  ``scheme=2`` selects
-    T2S2-FDLBM2 (Eq. 5.23).
+    T2S2-FDLBM2 (Eq. 5.23).  ``incomp=True`` selects the incompressible
+    equilibrium of He and Luo with reference density ``rho0`` (velocity from
+    rho0 u = sum xi f, forcing term at rho0).
     """
 
     def __init__(self, xa, ya, *, nu: float, dt: float, beta: float, A: float = 0.5,
                  scheme: int = 1, force=None, wall_u=None, beta_is_central: bool = False,
-                 nthreads: int = 1, tau: float | None = None):
+                 nthreads: int = 1, tau: float | None = None, incomp: bool = False,
+                 rho0: float = 1.0):
         self.xa, self.ya = xa, ya
         self.nx, self.ny = xa.n, ya.n
         self.mx = np.ascontiguousarray(xa.metric, dtype=np.float64)
@@ -187,6 +202,9 @@ class Oracle:
         for s in range(4):
             c.wall_u[s][0], c.wall_u[s][1] = float(wu[s][0]), float(wu[s][1])
         c.nthreads = nthreads
+        c.incomp = int(incomp)
+        c.rho0 = rho0
+        self.rho0 = rho0
         self._cfg = c
         self.f = np.zeros((9, self.ny, self.nx))
 
@@ -197,8 +215,10 @@ class Oracle:
     def set_threads(self, n: int):
         self._cfg.nthreads = n
 
-    def init_fields(self, rho, ux, uy, grad=None, rho0: float = 1.0):
-        """Eq. 3.2, or Eq. 3.5 when the velocity gradient is given."""
+    def init_fields(self, rho, ux, uy, grad=None, rho0: float | None = None):
+        """Eq. 3.2 (or the incompressible equilibrium), plus the gradient term
+        of Eq. 3.5 when the velocity gradient is given."""
+        rho0 = self.rho0 if rho0 is None else rho0
         a = [np.ascontiguousarray(v, dtype=np.float64) for v in (rho, ux, uy)]
         g = None
         if grad is not None:

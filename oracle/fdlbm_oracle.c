@@ -26,7 +26,14 @@
  *   - walls use the non-equilibrium extrapolation of Eq. 3.10 with the density
  *     of the nearest interior node; the intermediate f* at wall nodes is set the
  *     same way; interior nodes whose upwind stencil would leave the domain use
- *     the central difference alone.
+ *     the central difference alone;
+ *   - `incomp = 1` swaps Eq. 3.2 for the incompressible equilibrium of He and
+ *     Luo, which Sec. 2 says may be used with both schemes but does not print:
+ *     f_i^eq = w_i [rho + rho0 (xi.u / cs^2 + ((xi.u)^2 - cs^2 u.u) / (2 cs^4))],
+ *     whose first moment is rho0 u.  Accordingly the velocity is read from
+ *     rho0 u = sum xi f + shift rho0 F (Eq. 3.3 with rho0 for rho), and the
+ *     forcing term of Eq. 3.12 takes the equilibrium at rho0, so that it adds
+ *     no mass and the momentum rho0 F per unit time.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -65,6 +72,8 @@ typedef struct {
     const real_t *force;          /* [2][ny][nx] body acceleration, or NULL */
     double wall_u[4][2];          /* velocity of the W, E, S, N walls */
     int nthreads;
+    int incomp;                   /* 1: incompressible equilibrium of He and Luo */
+    double rho0;                  /* its reference density */
 } oracle_cfg;
 
 #define IDX(c, x, y) ((size_t)(y) * (size_t)(c)->nx + (size_t)(x))
@@ -81,6 +90,24 @@ void oracle_feq(real_t rho, real_t ux, real_t uy, real_t *feq)
         /* uu:(xi xi - cs^2 I) = (xi.u)^2 - cs^2 u.u */
         feq[i] = WQ[i] * rho * (1.0 + eu / CS2 + (eu * eu - CS2 * uu) / (2.0 * CS2 * CS2));
     }
+}
+
+/* The incompressible equilibrium of He and Luo (cited in Sec. 2, not printed
+ * there): Eq. 3.2 with rho0 in place of rho in every velocity term. */
+void oracle_feq_incomp(real_t rho, double rho0, real_t ux, real_t uy, real_t *feq)
+{
+    real_t uu = ux * ux + uy * uy;
+    for (int i = 0; i < 9; ++i) {
+        real_t eu = EX[i] * ux + EY[i] * uy;
+        feq[i] = WQ[i] * (rho + rho0 * (eu / CS2 + (eu * eu - CS2 * uu) / (2.0 * CS2 * CS2)));
+    }
+}
+
+/* The equilibrium of the configured model at (rho, u). */
+static void feq_model(const oracle_cfg *c, real_t rho, real_t ux, real_t uy, real_t *feq)
+{
+    if (c->incomp) oracle_feq_incomp(rho, c->rho0, ux, uy, feq);
+    else oracle_feq(rho, ux, uy, feq);
 }
 
 /* Eq. 3.12: forcing term F_i = Fbar.(xi_i - u) f_i^eq / RT with RT = cs^2. */
@@ -114,11 +141,29 @@ static void moments_node(const oracle_cfg *c, const real_t *f, size_t n, double 
     }
     real_t Fx, Fy;
     force_at(c, n, &Fx, &Fy);
-    jx += shift * r * Fx;
-    jy += shift * r * Fy;
+    /* the density that carries the momentum: rho (Eq. 3.3), or rho0 */
+    real_t rm = c->incomp ? (real_t)c->rho0 : r;
+    jx += shift * rm * Fx;
+    jy += shift * rm * Fy;
     *rho = r;
-    *ux = jx / r;
-    *uy = jy / r;
+    *ux = jx / rm;
+    *uy = jy / rm;
+}
+
+/* f^eq of the model and the forcing term of Eq. 3.12 at one node.  The
+ * forcing term takes the equilibrium at rho0 under the incompressible model. */
+static void node_feq_force(const oracle_cfg *c, size_t n, real_t rho, real_t ux, real_t uy,
+                           real_t *fe, real_t *Fi)
+{
+    real_t Fx, Fy, fF[9];
+    feq_model(c, rho, ux, uy, fe);
+    force_at(c, n, &Fx, &Fy);
+    if (c->incomp) {
+        oracle_feq(c->rho0, ux, uy, fF);
+        oracle_force_term(fF, ux, uy, Fx, Fy, Fi);
+    } else {
+        oracle_force_term(fe, ux, uy, Fx, Fy, Fi);
+    }
 }
 
 /* Eq. 3.3: density and velocity from f~. */
@@ -138,7 +183,7 @@ void oracle_init(const oracle_cfg *c, const real_t *rho, const real_t *ux, const
     size_t N = (size_t)c->nx * c->ny;
     for (size_t n = 0; n < N; ++n) {
         real_t feq[9];
-        oracle_feq(rho[n], ux[n], uy[n], feq);
+        feq_model(c, rho[n], ux[n], uy[n], feq);
         for (int i = 0; i < 9; ++i) {
             real_t v = feq[i];
             if (grad) {
@@ -250,8 +295,8 @@ static void apply_nee(const oracle_cfg *c, real_t *f, double shift)
             size_t nb = IDX(c, x, y), nj = IDX(c, jx, jy);
             real_t rj, uxj, uyj, feqj[9], feqb[9];
             moments_node(c, f, nj, shift, &rj, &uxj, &uyj);
-            oracle_feq(rj, uxj, uyj, feqj);
-            oracle_feq(rj, uw[0], uw[1], feqb);
+            feq_model(c, rj, uxj, uyj, feqj);
+            feq_model(c, rj, uw[0], uw[1], feqb);
             for (int i = 0; i < 9; ++i)
                 f[i * N + nb] = feqb[i] + (f[i * N + nj] - feqj[i]);
         }
@@ -282,18 +327,16 @@ static void work_free(work_t *w)
     free(w->fbar_plus); free(w->fbar_star); free(w->fstar); free(w->ftil_plus); free(w->L);
 }
 
-/* Node-local pass: rho, u (Eq. 3.3), f^eq (Eq. 3.2), F (Eq. 3.12) of a
+/* Node-local pass: rho, u (Eq. 3.3), f^eq (Eq. 3.2 or He-Luo), F (Eq. 3.12) of a
  * distribution g whose first moment lacks `shift rho F`. */
 static void macro_pass(const oracle_cfg *c, const real_t *g, double shift, work_t *w)
 {
     size_t N = (size_t)c->nx * c->ny;
 #pragma omp parallel for num_threads(nthreads_of(c)) schedule(static)
     for (long long n = 0; n < (long long)N; ++n) {
-        real_t fe[9], Fi[9], Fx, Fy;
+        real_t fe[9], Fi[9];
         moments_node(c, g, (size_t)n, shift, &w->rho[n], &w->ux[n], &w->uy[n]);
-        oracle_feq(w->rho[n], w->ux[n], w->uy[n], fe);
-        force_at(c, (size_t)n, &Fx, &Fy);
-        oracle_force_term(fe, w->ux[n], w->uy[n], Fx, Fy, Fi);
+        node_feq_force(c, (size_t)n, w->rho[n], w->ux[n], w->uy[n], fe, Fi);
         for (int i = 0; i < 9; ++i) {
             w->feq[i * N + n] = fe[i];
             w->F[i * N + n] = Fi[i];
@@ -447,11 +490,9 @@ int oracle_step_t1s2(const oracle_cfg *c, real_t *f, int nsteps)
     }
     for (int s = 0; s < nsteps; ++s) {
         for (size_t n = 0; n < N; ++n) {
-            real_t fe[9], Fi[9], Fx, Fy;
+            real_t fe[9], Fi[9];
             moments_node(c, f, n, 0.5 * dt, &rho[n], &ux[n], &uy[n]);
-            oracle_feq(rho[n], ux[n], uy[n], fe);
-            force_at(c, n, &Fx, &Fy);
-            oracle_force_term(fe, ux[n], uy[n], Fx, Fy, Fi);
+            node_feq_force(c, n, rho[n], ux[n], uy[n], fe, Fi);
             for (int i = 0; i < 9; ++i) {
                 size_t k = i * N + n;
                 /* f~ = f - (dt/2)[-(f - feq)/tau + F]  =>  f = (f~ + dt/(2tau) feq + dt/2 F)/(1 + dt/(2tau)) */

@@ -19,6 +19,7 @@ FP64, FP32_DEV = 0, 1
 PATH_AUTO, PATH_FUSED, PATH_STAGED = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 SCHEME_T2S2_1, SCHEME_T2S2_2 = 0, 1
+EQ_STANDARD, EQ_INCOMPRESSIBLE = 0, 1
 BATCH_FUSED, BATCH_STAGED, BATCH_PERSISTENT = 0, 1, 2
 VARIANT_AUTO, VARIANT_SCALAR, VARIANT_PACKED, VARIANT_TMA, VARIANT_ASYNC, VARIANT_WARP = 0, 1, 2, 3, 4, 5
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EUNSUPPORTED",
@@ -43,7 +44,7 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("has_force", ctypes.c_int),
                 ("path", ctypes.c_int), ("rows_per_cta", ctypes.c_int), ("variant", ctypes.c_int),
                 ("scheme", ctypes.c_int), ("adjoint", ctypes.c_int),
-                ("graph_steps", ctypes.c_int),
+                ("graph_steps", ctypes.c_int), ("equilibrium", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 

@@ -151,6 +151,7 @@ StepArgs<R> step_args(fdlbm_ctx *h)
         for (int k = 0; k < 2; ++k) a.wall_u[s][k] = R(h->wall_u[s][k]);
     // T2S2-FDLBM2 marches its characteristic estimate over h = dt
     a.c = make_coeffs<R>(h->tau, h->dt, h->scheme == FDLBM_SCHEME_T2S2_2 ? 1.0 : h->A, h->rho0);
+    a.c.incomp = h->incomp;
     a.scheme = h->scheme;
     a.st = make_stencil<R>(h->beta);
     a.stc = make_stencil<R>(0.0);
@@ -337,8 +338,14 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
         !(o.A >= 0 && o.A <= 1) || !(o.rho0 > 0) ||
         (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0 || o.graph_steps < 0 ||
         o.variant < FDLBM_VARIANT_AUTO || o.variant > FDLBM_VARIANT_WARP ||
-        (o.scheme != FDLBM_SCHEME_T2S2_1 && o.scheme != FDLBM_SCHEME_T2S2_2))
+        (o.scheme != FDLBM_SCHEME_T2S2_1 && o.scheme != FDLBM_SCHEME_T2S2_2) ||
+        (o.equilibrium != FDLBM_EQ_STANDARD && o.equilibrium != FDLBM_EQ_INCOMPRESSIBLE))
         return FDLBM_EINVAL;
+    // the incompressible equilibrium runs on the default kernels only
+    if (o.equilibrium == FDLBM_EQ_INCOMPRESSIBLE &&
+        (o.adjoint || o.variant == FDLBM_VARIANT_TMA || o.variant == FDLBM_VARIANT_ASYNC ||
+         o.variant == FDLBM_VARIANT_PACKED))
+        return FDLBM_EUNSUPPORTED;
     const int path = force_staged ? FDLBM_PATH_STAGED : choose_path(g, &o);
     if (path < 0) return FDLBM_EUNSUPPORTED;
     const bool fused = path == FDLBM_PATH_FUSED;
@@ -377,6 +384,7 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     std::memcpy(h->wall_u, g->wall_u, sizeof(h->wall_u));
     h->precision = o.precision;
     h->scheme = o.scheme;
+    h->incomp = o.equilibrium == FDLBM_EQ_INCOMPRESSIBLE ? 1 : 0;
     h->nu = nu;
     h->tau = nu * 3.0;  // tau = nu / cs^2
     h->cfl = cfl;
@@ -795,6 +803,7 @@ const char *fdlbm_describe(fdlbm_t h)
     const char *prec = h->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64";
     if (h->scheme == FDLBM_SCHEME_T2S2_2) {
         h->desc = std::string("staged-scheme2 ") + prec;
+        if (h->incomp) h->desc += " incompressible";
         return h->desc.c_str();
     }
     const bool walls = h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL;
@@ -807,6 +816,7 @@ const char *fdlbm_describe(fdlbm_t h)
                                                             : "fused";
     h->desc = std::string(kern) + " " + prec + " rows=" + std::to_string(h->rows);
     if (h->graph_steps) h->desc += " graph_steps=" + std::to_string(h->graph_steps);
+    if (h->incomp) h->desc += " incompressible";
     return h->desc.c_str();
 }
 

@@ -23,7 +23,7 @@ __global__ void k_init(StepArgs<R> a, const double *rho, const double *ux, const
     const size_t l = (size_t)j * a.nx + x;
     const double r = rho[l], u = ux[l], v = uy[l];
     double geq[9];
-    equilibrium_dev<double>(r - rho0, r, u, v, geq);
+    equilibrium_dev<double>(r - rho0, a.c.incomp ? rho0 : r, u, v, geq);
     // Eq. 3.5 with the coefficient rho0 w_i (2 tau + dt) / (2 cs^2)
     const double k = rho0 * (2.0 * tau + dt) * 1.5;
     const size_t o = (size_t)(row0 + j) * a.pitch + x;
@@ -88,12 +88,13 @@ __device__ void node_moments(const StepArgs<R> &a, const R *force, size_t o, dou
     double drho, jx, jy;
     moments_dev<double>(g, drho, jx, jy);
     rho = rho0 + drho;
+    const double rm = a.c.incomp ? rho0 : rho;  // the density of the momentum
     if (force) {
-        jx += half_dt * rho * double(force[o]);
-        jy += half_dt * rho * double(force[a.plane + o]);
+        jx += half_dt * rm * double(force[o]);
+        jy += half_dt * rm * double(force[a.plane + o]);
     }
-    ux = jx / rho;
-    uy = jy / rho;
+    ux = jx / rm;
+    uy = jy / rm;
 }
 
 template <class R>
@@ -190,6 +191,7 @@ StepArgs<R> view(fdlbm_ctx *h)
     a.plane = h->plane;
     a.gin = reinterpret_cast<const R *>(h->ws + h->lay.state[h->cur]);
     a.gout = reinterpret_cast<R *>(h->ws + h->lay.state[h->cur]);
+    a.c.incomp = h->incomp;
     return a;
 }
 

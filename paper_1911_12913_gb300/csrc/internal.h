@@ -59,6 +59,7 @@ struct fdlbm_ctx {
     double wall_u[4][2] = {};
     int precision = FDLBM_FP64;
     int scheme = FDLBM_SCHEME_T2S2_1;
+    int incomp = 0;                      // FDLBM_EQ_INCOMPRESSIBLE
     double nu = 0, tau = 0, dt = 0, cfl = 0, beta = 0, A = 0.5, rho0 = 1;
     int has_force = 0;
     int path = FDLBM_PATH_FUSED;

@@ -69,16 +69,18 @@ __device__ __forceinline__ void equilibrium_dev(R drho, R rho, R ux, R uy, R geq
     }
 }
 
-// Eq. 3.12: F_i = Fbar.(xi_i - u) f_i^eq / cs^2, with f_i^eq = w_i rho0 + geq_i.
+// Eq. 3.12: F_i = Fbar.(xi_i - u) f_i^eq / cs^2, with f_i^eq = w_i rho0 + geq_i
+// - w_i dshift.  dshift = 0 takes the equilibrium of the node (Eq. 3.2); under
+// the incompressible equilibrium dshift = rho - rho0, which takes it at rho0.
 template <class R>
 __device__ __forceinline__ void force_terms(R rho0, const R geq[9], R ux, R uy, R Fx, R Fy,
-                                            R F[9])
+                                            R F[9], R dshift = R(0))
 {
     const R base = -(ux * Fx + uy * Fy);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const R xf = base + xi_dot<R>(i, Fx, Fy);
-        F[i] = R(3) * xf * (wq<R>(i) * rho0 + geq[i]);
+        F[i] = R(3) * xf * (wq<R>(i) * (rho0 - dshift) + geq[i]);
     }
 }
 
@@ -123,6 +125,7 @@ struct Coeffs {
     R b_star, c_star;   // f* from fbar* (Eq. 2.32)
     R b_phys, c_phys;   // physical f from f~ (Eq. 2.19 inverted; Eq. 2.32 with h = dt)
     R half_dt, half_h;  // force shifts of the first moment (Eq. 3.3 and its h analogue)
+    int incomp;         // 1: incompressible equilibrium of He and Luo (cited in Sec. 2)
 };
 
 template <class R>
@@ -146,7 +149,25 @@ __host__ inline Coeffs<R> make_coeffs(double tau, double dt, double A, double rh
     c.c_phys = R(tau * dt / (2.0 * tau + dt));
     c.half_dt = R(0.5 * dt);
     c.half_h = R(0.5 * h);
+    c.incomp = 0;
     return c;
+}
+
+// The density that carries the momentum and multiplies the velocity terms of
+// the equilibrium: rho itself (Eqs. 3.2, 3.3), or the constant rho0 under the
+// incompressible equilibrium, f_i^eq = w_i [rho + rho0 (3 xi.u + 4.5 (xi.u)^2
+// - 1.5 u.u)] with rho0 u = sum xi f.
+template <class R>
+__host__ __device__ __forceinline__ R macro_density(const Coeffs<R> &c, R drho)
+{
+    return c.incomp ? c.rho0 : c.rho0 + drho;
+}
+
+// The argument of force_terms that selects the equilibrium of the forcing term.
+template <class R>
+__host__ __device__ __forceinline__ R force_dshift(const Coeffs<R> &c, R drho)
+{
+    return c.incomp ? drho : R(0);
 }
 
 __host__ __device__ __forceinline__ int wrap_index(int k, int n)

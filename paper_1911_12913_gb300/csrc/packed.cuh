@@ -48,6 +48,21 @@ __device__ __forceinline__ Macro moments2(const f2 g[9], f2 rho0)
     return m;
 }
 
+// The same under the incompressible equilibrium of He and Luo: rho0 u = sum xi
+// g, and rho0 (not rho) multiplies the velocity terms of the equilibrium.
+__device__ __forceinline__ Macro moments2_incomp(const f2 g[9], f2 rho0, f2 inv_rho0)
+{
+    Macro m;
+    m.drho = add2(add2(add2(g[0], g[1]), add2(g[2], g[3])),
+                  add2(add2(g[4], g[5]), add2(add2(g[6], g[7]), g[8])));
+    const f2 jx = add2(add2(sub2(g[1], g[3]), sub2(g[5], g[6])), sub2(g[8], g[7]));
+    const f2 jy = add2(sub2(g[2], g[4]), sub2(add2(g[5], g[6]), add2(g[7], g[8])));
+    m.rho = rho0;
+    m.ux = mul2(jx, inv_rho0);
+    m.uy = mul2(jy, inv_rho0);
+    return m;
+}
+
 // Eq. 3.2 minus w_i rho0, written pairwise for opposite velocities: with
 // e = xi_i.u,  f_i^eq - w_i rho0 = w_i drho + w_i rho (A +- 3e),
 // A = 4.5 e^2 - 1.5 u.u.

@@ -80,7 +80,7 @@ __device__ __forceinline__ void node_macro(const StepArgs<R> &a, const R g[9], R
 {
     R jx, jy;
     moments_dev(g, drho, jx, jy);
-    rho = a.c.rho0 + drho;
+    rho = macro_density(a.c, drho);
     Fx = R(0);
     Fy = R(0);
     if (FORCE && a.force) {
@@ -104,7 +104,7 @@ __device__ void prepare_node(const StepArgs<R> &a, int x, int y)
     R drho, rho, ux, uy, Fx, Fy;
     node_macro<R, FORCE>(a, g, a.c.half_dt, o, drho, rho, ux, uy, Fx, Fy);
     equilibrium_dev(drho, rho, ux, uy, geq);
-    if (FORCE) force_terms(a.c.rho0, geq, ux, uy, Fx, Fy, F);
+    if (FORCE) force_terms(a.c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(a.c, drho));
     const bool s2 = a.scheme == FDLBM_SCHEME_T2S2_2;
     const R bP = s2 ? a.c.b_phys : a.c.b_bar, cP = s2 ? a.c.c_phys : a.c.c_bar;
 #pragma unroll
@@ -134,7 +134,7 @@ __device__ void star_node(const StepArgs<R> &a, int x, int y)
     R drho, rho, ux, uy, Fx, Fy;
     node_macro<R, FORCE>(a, gs, a.c.half_h, o, drho, rho, ux, uy, Fx, Fy);
     equilibrium_dev(drho, rho, ux, uy, geq);
-    if (FORCE) force_terms(a.c.rho0, geq, ux, uy, Fx, Fy, F);
+    if (FORCE) force_terms(a.c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(a.c, drho));
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         R v = gs[i] + a.c.b_star * (geq[i] - gs[i]);

@@ -92,7 +92,7 @@ struct Sweep {
         {
             R drho, jx, jy;
             moments_dev(cur, drho, jx, jy);
-            const R rho = c.rho0 + drho;
+            const R rho = macro_density(c, drho);
             R Fx = R(0), Fy = R(0);
             if (FORCE) {
                 const size_t fo = (size_t)rA * a.pitch + gx;
@@ -105,7 +105,7 @@ struct Sweep {
             const R ux = jx * inv, uy = jy * inv;
             R geq[9], F[9];
             equilibrium_dev(drho, rho, ux, uy, geq);
-            if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F);
+            if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(c, drho));
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const R neq = geq[i] - cur[i];
@@ -144,7 +144,7 @@ struct Sweep {
                 }
                 R drho, jx, jy;
                 moments_dev(gs, drho, jx, jy);
-                const R rho = c.rho0 + drho;
+                const R rho = macro_density(c, drho);
                 R Fx = R(0), Fy = R(0);
                 if (FORCE) {
                     const size_t fo = (size_t)sg * a.pitch + gx;
@@ -157,7 +157,7 @@ struct Sweep {
                 const R ux = jx * inv, uy = jy * inv;
                 R geq[9], F[9];
                 equilibrium_dev(drho, rho, ux, uy, geq);
-                if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F);
+                if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(c, drho));
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     R gst = gs[i] + c.b_star * (geq[i] - gs[i]);

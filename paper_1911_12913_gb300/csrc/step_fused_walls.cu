@@ -61,7 +61,7 @@ __device__ __forceinline__ void node_eq(const Coeffs<R> &c, const R g[9], R Fx, 
 {
     R jx, jy;
     moments_dev(g, drho, jx, jy);
-    rho = c.rho0 + drho;
+    rho = macro_density(c, drho);
     if (FORCE) {
         jx += shift * rho * Fx;
         jy += shift * rho * Fy;
@@ -152,7 +152,7 @@ struct SweepW {
             force_at(r, Fx, Fy);
             R drho, rho, ux, uy, geq[9], F[9];
             node_eq<R, FORCE>(c, cur, Fx, Fy, c.half_dt, drho, rho, ux, uy, geq);
-            if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F);
+            if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(c, drho));
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const R neq = geq[i] - cur[i];
@@ -195,7 +195,7 @@ struct SweepW {
                 force_at(rb, Fx, Fy);
                 R drho, rho, ux, uy, geq[9], F[9];
                 node_eq<R, FORCE>(c, gs, Fx, Fy, c.half_h, drho, rho, ux, uy, geq);
-                if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F);
+                if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(c, drho));
                 R st[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {

@@ -87,6 +87,7 @@ struct ArgsW {
     float rho0, h, dt, b_bar, b_til, b_star;
     float w[4];  // wm1, w0, w1, w2
     int *err;
+    float inv_rho0;  // incompressible equilibrium only
 };
 
 // The taps other than the centre of sign(c) * D_m f in x for the lane's pair
@@ -118,6 +119,8 @@ __device__ __forceinline__ f2 ytaps(const f2 c[3], int sgn, f2 vm2, f2 vm1, f2 v
     return fma2(c[2], vp2, fma2(c[1], vp1, fma2(c[0], vm1, acc)));
 }
 
+// INC: the incompressible equilibrium of He and Luo (velocity from rho0 u).
+template <bool INC>
 __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     k_step_fused_warp(const __grid_constant__ ArgsW a)
 {
@@ -202,7 +205,7 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
 #pragma unroll
             for (int i = 0; i < 9; ++i)
                 g[i] = *reinterpret_cast<const f2 *>(src + i * kCols * sizeof(float));
-            const Macro m = moments2(g, rho0);
+            const Macro m = INC ? moments2_incomp(g, rho0, bc(a.inv_rho0)) : moments2(g, rho0);
             f2 geq[9];
             equilibrium2(m, geq);
 #pragma unroll
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 if (cy(i) != 0) acc = ytaps(ay, cy(i), Pw[i][p4], Pw[i][p3], Pw[i][p1], Pw[i][p0], acc);
                 gs[i] = acc;
             }
-            const Macro m = moments2(gs, rho0);
+            const Macro m = INC ? moments2_incomp(gs, rho0, bc(a.inv_rho0)) : moments2(gs, rho0);
             f2 geq[9];
             equilibrium2(m, geq);
 #pragma unroll
@@ -371,12 +374,13 @@ cudaError_t launch_fused_warp(const StepArgs<float> &s, const void *map_in, cuda
     a.w[2] = s.st.w1;
     a.w[3] = s.st.w2;
     a.err = s.err;
+    a.inv_rho0 = 1.0f / s.c.rho0;
     constexpr size_t smem = sizeof(WarpSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_step_fused_warp,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = s.c.incomp ? k_step_fused_warp<true> : k_step_fused_warp<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((s.nx + kW - 1) / kW, (s.ny + s.rows - 1) / s.rows);
-    k_step_fused_warp<<<grid, kLanes, smem, stream>>>(a);
+    kern<<<grid, kLanes, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -386,8 +390,8 @@ int fused_warp_blocks_per_sm()
 {
     int n = 0;
     constexpr size_t smem = sizeof(WarpSmem);
-    cudaFuncSetAttribute(k_step_fused_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_fused_warp, kLanes, smem) !=
+    cudaFuncSetAttribute(k_step_fused_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_fused_warp<false>, kLanes, smem) !=
         cudaSuccess)
         return 0;
     return n;

@@ -29,14 +29,16 @@ class FDLBM:
     difference.  ``precision``: ``"fp64"`` or ``"fp32"`` (FP32 deviation storage).
     ``scheme``: 1 = T2S2-FDLBM1 (Eq. 2.23, A = 0 gives T1S2), 2 = T2S2-FDLBM2 (Eq. 5.23).
     ``graph_steps``: > 0 replays a CUDA graph of that many steps inside ``step``
-    (small grids, where launch latency dominates).
+    (small grids, where launch latency dominates).  ``equilibrium``:
+    ``"standard"`` (Eq. 3.2) or ``"incompressible"`` (the equilibrium of He and
+    Luo that Sec. 2 cites; velocity from rho0 u = sum xi f).
     """
 
     def __init__(self, xa, ya, *, nu: float, cfl: float, blend: float, A: float = 0.5,
                  precision: str = "fp64", rho0: float = 1.0, has_force: bool = False,
                  wall_u=None, path: str = "auto", rows_per_cta: int = 0, variant: str = "auto",
                  scheme: int = 1, adjoint: bool = False, graph_steps: int = 0, stream=None,
-                 device=None):
+                 device=None, equilibrium: str = "standard"):
         self._L = L = B.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.nx, self.ny = xa.n, ya.n
@@ -55,6 +57,7 @@ class FDLBM:
         o.scheme = {1: B.SCHEME_T2S2_1, 2: B.SCHEME_T2S2_2}[scheme]
         o.adjoint = int(adjoint)
         o.graph_steps = graph_steps
+        o.equilibrium = {"standard": B.EQ_STANDARD, "incompressible": B.EQ_INCOMPRESSIBLE}[equilibrium]
         o.variant = {"auto": B.VARIANT_AUTO, "scalar": B.VARIANT_SCALAR,
                      "packed": B.VARIANT_PACKED, "tma": B.VARIANT_TMA,
                      "async": B.VARIANT_ASYNC, "warp": B.VARIANT_WARP}[variant]
@@ -244,7 +247,8 @@ class FDLBM:
 class FDLBMBatch:
     """Many independent cases stepped together (batched staged kernels, CUDA
     graph replay, autotuned block shape).  ``cases``: list of dicts with keys
-    ``xa, ya, nu, cfl, blend`` and optional ``wall_u, has_force, A, scheme``.
+    ``xa, ya, nu, cfl, blend`` and optional ``wall_u, has_force, A, scheme,
+    equilibrium``.
     ``batch.case(c)`` returns an ``FDLBM`` view of case c for initialisation and
     read-back; ``batch.step(n)`` advances every case."""
 
@@ -269,6 +273,8 @@ class FDLBMBatch:
             opts[c].has_force = int(cs.get("has_force", False))
             opts[c].A = cs.get("A", 0.5)
             opts[c].scheme = {1: B.SCHEME_T2S2_1, 2: B.SCHEME_T2S2_2}[cs.get("scheme", 1)]
+            opts[c].equilibrium = {"standard": B.EQ_STANDARD,
+                                   "incompressible": B.EQ_INCOMPRESSIBLE}[cs.get("equilibrium", "standard")]
         nu = np.ascontiguousarray([cs["nu"] for cs in cases], dtype=np.float64)
         cfl = np.ascontiguousarray([cs["cfl"] for cs in cases], dtype=np.float64)
         blend = np.ascontiguousarray([cs["blend"] for cs in cases], dtype=np.float64)

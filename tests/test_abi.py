@@ -130,6 +130,21 @@ def test_workspace_and_validation_without_gpu(B):
     mneg.dzeta_dx = B._dptr(neg)
     assert L.fdlbm_create(ctypes.byref(grid), ctypes.byref(mneg), 0.01, 0.5, 0.1, None,
                           ctypes.byref(h)) == -1
+    # the equilibrium option: unknown values are invalid; the incompressible
+    # equilibrium has no adjoint step and no TMA / ASYNC / PACKED variant
+    L.fdlbm_default_opts(ctypes.byref(o))
+    o.equilibrium = 2
+    assert L.fdlbm_create(ctypes.byref(grid), None, 0.01, 0.5, 0.1, ctypes.byref(o),
+                          ctypes.byref(h)) == -1
+    o.equilibrium = B.EQ_INCOMPRESSIBLE
+    for field, value in (("adjoint", 1), ("variant", B.VARIANT_TMA), ("variant", B.VARIANT_ASYNC),
+                         ("variant", B.VARIANT_PACKED)):
+        L.fdlbm_default_opts(ctypes.byref(o))
+        o.equilibrium = B.EQ_INCOMPRESSIBLE
+        o.precision = B.FP32_DEV
+        setattr(o, field, value)
+        assert L.fdlbm_create(ctypes.byref(grid), None, 0.01, 0.5, 0.1, ctypes.byref(o),
+                              ctypes.byref(h)) == -5, (field, value)
     assert L.fdlbm_status_string(-4) == b"non-finite result"
     assert L.fdlbm_last_error(None) == b"NULL handle"
     L.fdlbm_destroy(None)

@@ -547,3 +547,119 @@ def test_complex_build_is_the_same_arithmetic():
     eps = 1e-6
     fd = (real_step(f0 + eps * v) - real_step(f0 - eps * v)) / (2 * eps)
     assert np.linalg.norm(y.imag / 1e-20 - fd) <= 1e-9 * np.linalg.norm(fd)
+
+
+# ----------------------------------------------------------------- incompressible equilibrium (He and Luo)
+@pytest.mark.parametrize("rho,ux,uy", [(1.0, 0.0, 0.0), (1.03, 0.05, -0.02), (0.96, -0.1, 0.08)])
+def test_feq_incomp_moments(rho, ux, uy):
+    """The incompressible equilibrium carries density rho, momentum rho0 u and
+    the momentum flux rho cs^2 I + rho0 u u exactly on D2Q9; at rho = rho0 it
+    is Eq. 3.2, and at rest it is w_i rho."""
+    rho0, cs2 = 1.0, 1.0 / 3.0
+    fe = O.feq_incomp(rho, rho0, ux, uy)
+    assert fe.sum() == pytest.approx(rho, abs=1e-15)
+    assert (EX * fe).sum() == pytest.approx(rho0 * ux, abs=1e-15)
+    assert (EY * fe).sum() == pytest.approx(rho0 * uy, abs=1e-15)
+    assert (EX * EX * fe).sum() == pytest.approx(rho * cs2 + rho0 * ux * ux, abs=1e-15)
+    assert (EX * EY * fe).sum() == pytest.approx(rho0 * ux * uy, abs=1e-15)
+    assert (EY * EY * fe).sum() == pytest.approx(rho * cs2 + rho0 * uy * uy, abs=1e-15)
+    assert np.allclose(O.feq_incomp(rho0, rho0, ux, uy), O.feq(rho0, ux, uy), atol=1e-16)
+    assert np.allclose(O.feq_incomp(rho, rho0, 0.0, 0.0), rho * O.feq(1.0, 0.0, 0.0), atol=1e-16)
+
+
+def _incomp_state(nx, ny, seed, force=None, rho0=1.0):
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 1.3)
+    o = O.Oracle(xa, ya, nu=0.02, dt=0.05, beta=0.1, force=force, incomp=True, rho0=rho0)
+    r = I.random_fields(nx, ny, seed, drho=0.05)
+    o.init_fields(r["rho"], r["ux"], r["uy"], grad=[r["dudx"], r["dudy"], r["dvdx"], r["dvdy"]])
+    return o
+
+
+def test_incomp_uniform_state_is_fixed_point():
+    """f~ = f^eq(rho, U) of the incompressible model with rho != rho0 and no
+    force is a fixed point: the velocity is read back as U only when it is taken
+    from rho0 u = sum xi f~."""
+    xa = I.periodic_axis(6, 0.0, 1.0)
+    ya = I.periodic_axis(5, 0.0, 1.0)
+    o = O.Oracle(xa, ya, nu=0.01, dt=0.1, beta=0.3, incomp=True, rho0=1.0)
+    one = np.ones((5, 6))
+    o.init_fields(1.1 * one, 0.07 * one, -0.04 * one)
+    rho, ux, uy = o.moments()
+    assert np.abs(ux - 0.07).max() < 1e-15 and np.abs(uy + 0.04).max() < 1e-15
+    f0 = o.f.copy()
+    o.step(20)
+    assert np.abs(o.f - f0).max() < 1e-15
+
+
+def test_incomp_mass_and_momentum_budget():
+    """Periodic uniform grid, non-uniform force field, varying density: under
+    the incompressible model the mass is conserved and the total momentum
+    rho0 sum u grows by exactly dt rho0 sum F per step (the forcing term adds
+    rho0 F at every node), not by dt sum rho F as under Eq. 3.2."""
+    ny, nx = 7, 9
+    rng = np.random.default_rng(5)
+    force = 1e-3 * rng.normal(size=(2, ny, nx))
+    rho0 = 1.0
+    o = _incomp_state(nx, ny, 11, force=force, rho0=rho0)
+
+    def totals():
+        r, ux, uy = o.moments()
+        return r.sum(), rho0 * ux.sum(), rho0 * uy.sum(), r
+
+    M, px0, py0, r0 = totals()
+    assert r0.std() > 0.01                      # the density really varies
+    steps = 25
+    o.step(steps)
+    M1, px1, py1, _ = totals()
+    assert abs(M1 - M) < 1e-13 * M
+    gx = steps * o.dt * rho0 * force[0].sum()
+    gy = steps * o.dt * rho0 * force[1].sum()
+    assert px1 - px0 == pytest.approx(gx, rel=1e-10, abs=1e-16)
+    assert py1 - py0 == pytest.approx(gy, rel=1e-10, abs=1e-16)
+    # the budget of Eq. 3.2 (rho-weighted) is measurably different here
+    assert abs(steps * o.dt * (r0 * force[0]).sum() - gx) > 1e-4 * abs(gx)
+
+
+def test_incomp_nee_wall_moments():
+    """Eq. 3.10 under the incompressible model: wall nodes carry the interior
+    neighbour's density and exactly the wall velocity."""
+    nx, ny = 9, 8
+    xa = I.wall_axis(nx - 1, 0.0, 1.0)
+    ya = I.wall_axis(ny - 1, 0.0, 1.0)
+    o = O.Oracle(xa, ya, nu=0.01, dt=0.02, beta=0.1, incomp=True,
+                 wall_u=[(0, 0), (0, 0), (0, 0), (0.1, 0.0)])
+    r = I.random_fields(nx, ny, 2, drho=0.05)
+    o.init_fields(r["rho"], r["ux"], r["uy"])
+    o.step(3)
+    rho, ux, uy = o.moments()
+    for y in range(ny):
+        for x in range(nx):
+            if 0 < x < nx - 1 and 0 < y < ny - 1:
+                continue
+            jx = min(max(x, 1), nx - 2)
+            jy = min(max(y, 1), ny - 2)
+            lid = (y == ny - 1) and 0 < x < nx - 1
+            assert rho[y, x] == pytest.approx(rho[jy, jx], rel=1e-14)
+            assert ux[y, x] == pytest.approx(0.1 if lid else 0.0, abs=1e-15)
+            assert uy[y, x] == pytest.approx(0.0, abs=1e-15)
+
+
+def test_incomp_taylor_green_converges():
+    """The Taylor vortex under the incompressible model follows the closed form
+    of Eq. 3.4 with second-order convergence (32 -> 64 nodes, CFL fixed)."""
+    errs = []
+    for n in (32, 64):
+        xa = I.periodic_axis(n, 0.0, 2 * math.pi)
+        ya = I.periodic_axis(n, 0.0, 2 * math.pi)
+        dt = O.time_step(0.5, xa, ya)
+        o = O.Oracle(xa, ya, nu=0.01, dt=dt, beta=0.1, incomp=True, nthreads=oracle_threads())
+        f = I.taylor_green(xa, ya, u0=0.01)
+        o.init_fields(f["rho"], f["ux"], f["uy"], grad=[f["dudx"], f["dudy"], f["dvdx"], f["dvdy"]])
+        steps = int(round(10.0 / dt))
+        o.step(steps)
+        _, ux, uy = o.moments()
+        ua, va = I.taylor_green_velocity(xa, ya, steps * dt, u0=0.01, nu=0.01)
+        errs.append(O.gre(ux, uy, ua, va))
+    order = math.log2(errs[0] / errs[1])
+    assert errs[1] < 1e-3 and order > 1.7, (errs, order)
