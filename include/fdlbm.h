@@ -287,7 +287,18 @@ fdlbm_status fdlbm_batch_step(fdlbm_batch_t b, int n);
 enum { FDLBM_BATCH_FUSED = 0, FDLBM_BATCH_STAGED = 1, FDLBM_BATCH_PERSISTENT = 2 };
 fdlbm_status fdlbm_batch_set_mode(fdlbm_batch_t b, int mode);
 int fdlbm_batch_mode(fdlbm_batch_t b);               /* -1 for NULL */
+/* Synchronise the batch stream, then read the kernel-side failure flag of
+ * every case (set when a bounded wait gave up: a grid barrier of PERSISTENT, a
+ * row copy of a fused kernel).  Flags that are set are cleared and reported
+ * once, as ECUDA with the number of cases in fdlbm_batch_last_error(); the
+ * states of those cases are not valid (re-initialise them). */
 fdlbm_status fdlbm_batch_sync(fdlbm_batch_t b);
+/* Test hook for the failure path of PERSISTENT: the number of polls after which
+ * a block gives up waiting at a grid barrier (default 2^24, well over a second
+ * with the back-off sleeps).  0 makes every block but the last to arrive give
+ * up at the first barrier, which sets the cases' flags without any fault or
+ * hang.  Synchronises (fdlbm_batch_sync) and drops a captured graph. */
+fdlbm_status fdlbm_batch_set_spin_limit(fdlbm_batch_t b, unsigned polls);
 void *fdlbm_batch_stream(fdlbm_batch_t b);           /* cudaStream_t of the batch */
 const char *fdlbm_batch_describe(fdlbm_batch_t b);
 const char *fdlbm_batch_last_error(fdlbm_batch_t b);

@@ -38,6 +38,7 @@ struct fdlbm_batch_ctx {
     size_t d_ints_cap = 0;
     BatchTables tab{};
     void *bar = nullptr;       // grid barrier of the persistent kernel (in d_ints)
+    unsigned spin_limit = 1u << 24;  // polls before a persistent block gives up
     int mode = FDLBM_BATCH_STAGED;  // FDLBM_BATCH_FUSED / _STAGED / _PERSISTENT
     int fused_rows = 0;             // tile height of the fused sweep (0: staged tables)
     dim3 blk{32, 8, 1};
@@ -198,8 +199,10 @@ cudaError_t launch_steps(fdlbm_batch_ctx *b, int parity, int n)
         return e;
     }
     if (b->mode == FDLBM_BATCH_PERSISTENT)
-        return f32 ? launch_persistent<float>(b->tab, b->bar, parity, n, b->blk, b->stream)
-                   : launch_persistent<double>(b->tab, b->bar, parity, n, b->blk, b->stream);
+        return f32 ? launch_persistent<float>(b->tab, b->bar, parity, n, b->blk, b->stream,
+                                              b->spin_limit)
+                   : launch_persistent<double>(b->tab, b->bar, parity, n, b->blk, b->stream,
+                                               b->spin_limit);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < n && e == cudaSuccess; ++k)
         e = f32 ? launch_batched<float>(b->tab, (parity + k) & 1, b->blk, b->stream)
@@ -528,7 +531,38 @@ fdlbm_status fdlbm_batch_sync(fdlbm_batch_t b)
 {
     if (!b) return FDLBM_EINVAL;
     cudaError_t e = cudaStreamSynchronize(b->stream);
-    return e == cudaSuccess ? FDLBM_OK : bfail(b, FDLBM_ECUDA, cudaGetErrorString(e));
+    if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, cudaGetErrorString(e));
+    // the kernel-side failure flags of the cases (bounded waits that gave up):
+    // reported here once, then cleared
+    const int n = (int)b->cases.size();
+    std::vector<int> flags(n, 0);
+    for (int c = 0; c < n && e == cudaSuccess; ++c)
+        e = cudaMemcpyAsync(&flags[c], b->cases[c]->ws + b->cases[c]->lay.err, sizeof(int),
+                            cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, cudaGetErrorString(e));
+    int bad = 0;
+    for (int c = 0; c < n; ++c) bad += flags[c] != 0;
+    if (!bad) return FDLBM_OK;
+    for (int c = 0; c < n && e == cudaSuccess; ++c)
+        if (flags[c])
+            e = cudaMemsetAsync(b->cases[c]->ws + b->cases[c]->lay.err, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, cudaGetErrorString(e));
+    return bfail(b, FDLBM_ECUDA,
+                 "batch: a kernel gave up waiting (grid barrier or row copy) in " +
+                     std::to_string(bad) + " of " + std::to_string(n) +
+                     " cases; their states are not valid");
+}
+
+fdlbm_status fdlbm_batch_set_spin_limit(fdlbm_batch_t b, unsigned polls)
+{
+    if (!b) return FDLBM_EINVAL;
+    fdlbm_status st = fdlbm_batch_sync(b);
+    if (st != FDLBM_OK) return st;
+    drop_graph(b);  // a captured graph holds the old limit
+    b->spin_limit = polls;
+    return FDLBM_OK;
 }
 
 void *fdlbm_batch_stream(fdlbm_batch_t b) { return b ? (void *)b->stream : nullptr; }

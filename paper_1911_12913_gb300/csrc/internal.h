@@ -144,7 +144,7 @@ cudaError_t launch_batched(const BatchTables &t, int parity, dim3 blk, cudaStrea
 // step_persist.cu (one cooperative launch for many steps of all cases)
 template <class R>
 cudaError_t launch_persistent(const BatchTables &t, void *bar, int parity0, int nsteps, dim3 blk,
-                              cudaStream_t s);
+                              cudaStream_t s, unsigned spin_limit);
 template <class R>
 int persistent_blocks_per_sm(dim3 blk);
 size_t persistent_barrier_bytes();

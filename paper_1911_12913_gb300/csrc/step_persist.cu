@@ -18,9 +18,12 @@
 // The grid barrier is a generation counter: thread 0 of every block makes its
 // block's writes visible (fence), arrives on a global counter, and the last
 // arriver resets the counter and publishes the next generation; the others
-// wait for it.  Every wait is bounded: a block that waits longer than about a
-// second records the error flag of every case and leaves, and the blocks still
-// running then time out at their next barrier, so the launch always ends.
+// wait for it.  Every wait is bounded: a block that waits longer than its poll
+// limit (by default 2^24 polls, well over a second with the sleeps) records the
+// error flag of every case and leaves, and the blocks still running then time
+// out at their next barrier, so the launch always ends.  A limit of 0 makes
+// every block but the last to arrive give up at the first barrier: a way to
+// exercise this path without a fault (fdlbm_batch_set_spin_limit).
 #include <algorithm>
 
 #include <cuda_runtime.h>
@@ -39,8 +42,9 @@ __device__ __forceinline__ unsigned load_volatile(const unsigned *p)
     return *reinterpret_cast<const volatile unsigned *>(p);
 }
 
-// Block-uniform result: false when this block gave up waiting.
-__device__ bool grid_barrier(GridBarrier *bar, unsigned &gen)
+// Block-uniform result: false when this block gave up waiting, after `limit`
+// polls (the last block to arrive never waits).
+__device__ bool grid_barrier(GridBarrier *bar, unsigned &gen, unsigned limit)
 {
     __shared__ int ok_s;
     __syncthreads();
@@ -54,7 +58,7 @@ __device__ bool grid_barrier(GridBarrier *bar, unsigned &gen)
             atomicExch(&bar->gen, target);
         } else {
             for (unsigned k = 0; load_volatile(&bar->gen) != target; ++k) {
-                if (k >= (1u << 24)) {
+                if (k >= limit) {
                     ok = 0;
                     break;
                 }
@@ -74,6 +78,7 @@ struct PersistArgs {
     GridBarrier *bar;
     int parity0;  // ping-pong parity of the first step
     int nsteps;
+    unsigned spin_limit;  // polls before a block gives up at a grid barrier
 };
 
 // Copy one case's arguments into shared memory with all threads.
@@ -156,22 +161,22 @@ __global__ void k_persist(const PersistArgs p)
     for (int k = 0; k < p.nsteps; ++k) {
         const StepArgs<R> *cases = static_cast<const StepArgs<R> *>(t.args[(p.parity0 + k) & 1]);
         node_stage<R, 0>(t, cases, a);
-        if (!grid_barrier(p.bar, gen)) goto timeout;
+        if (!grid_barrier(p.bar, gen, p.spin_limit)) goto timeout;
         if (t.total_wall > 0 && t.any_scheme2) {
             wall_stage<R, 2>(t, cases);
-            if (!grid_barrier(p.bar, gen)) goto timeout;
+            if (!grid_barrier(p.bar, gen, p.spin_limit)) goto timeout;
         }
         node_stage<R, 1>(t, cases, a);
-        if (!grid_barrier(p.bar, gen)) goto timeout;
+        if (!grid_barrier(p.bar, gen, p.spin_limit)) goto timeout;
         if (t.total_wall > 0) {
             wall_stage<R, 0>(t, cases);
-            if (!grid_barrier(p.bar, gen)) goto timeout;
+            if (!grid_barrier(p.bar, gen, p.spin_limit)) goto timeout;
         }
         node_stage<R, 2>(t, cases, a);
-        if (!grid_barrier(p.bar, gen)) goto timeout;
+        if (!grid_barrier(p.bar, gen, p.spin_limit)) goto timeout;
         if (t.total_wall > 0) {
             wall_stage<R, 1>(t, cases);
-            if (!grid_barrier(p.bar, gen)) goto timeout;
+            if (!grid_barrier(p.bar, gen, p.spin_limit)) goto timeout;
         }
     }
     return;
@@ -195,10 +200,11 @@ int persistent_blocks_per_sm(dim3 blk)
 }
 
 // Zero the barrier, then one cooperative launch of nsteps steps.  `bar` is two
-// unsigned words of device memory owned by the caller.
+// unsigned words of device memory owned by the caller; spin_limit bounds every
+// wait at a grid barrier (in polls).
 template <class R>
 cudaError_t launch_persistent(const BatchTables &t, void *bar, int parity0, int nsteps, dim3 blk,
-                              cudaStream_t s)
+                              cudaStream_t s, unsigned spin_limit)
 {
     if (nsteps <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
@@ -210,7 +216,7 @@ cudaError_t launch_persistent(const BatchTables &t, void *bar, int parity0, int 
     const int grid = std::max(1, std::min(t.total_blocks, per_sm * sms));
     e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
     if (e != cudaSuccess) return e;
-    PersistArgs p{t, static_cast<GridBarrier *>(bar), parity0, nsteps};
+    PersistArgs p{t, static_cast<GridBarrier *>(bar), parity0, nsteps, spin_limit};
     void *params[] = {&p};
     return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_persist<R>), dim3(grid), blk,
                                        params, 0, s);
@@ -220,8 +226,9 @@ size_t persistent_barrier_bytes() { return sizeof(GridBarrier); }
 
 template int persistent_blocks_per_sm<float>(dim3);
 template int persistent_blocks_per_sm<double>(dim3);
-template cudaError_t launch_persistent<float>(const BatchTables &, void *, int, int, dim3, cudaStream_t);
+template cudaError_t launch_persistent<float>(const BatchTables &, void *, int, int, dim3, cudaStream_t,
+                                              unsigned);
 template cudaError_t launch_persistent<double>(const BatchTables &, void *, int, int, dim3,
-                                               cudaStream_t);
+                                               cudaStream_t, unsigned);
 
 }  // namespace fdlbm

@@ -324,6 +324,13 @@ class FDLBMBatch:
         if rc != 0:
             raise B.FdlbmError(rc, self._L.fdlbm_batch_last_error(self._h).decode())
 
+    def set_spin_limit(self, polls: int):
+        """Polls before a block of the persistent mode gives up at a grid
+        barrier (0 exercises the timeout path; the default is 2**24)."""
+        rc = self._L.fdlbm_batch_set_spin_limit(self._h, int(polls))
+        if rc != 0:
+            raise B.FdlbmError(rc, self._L.fdlbm_batch_last_error(self._h).decode())
+
     def close(self):
         if getattr(self, "_h", None):
             for cv in self._cases:

@@ -167,3 +167,29 @@ def test_sweep_64_cases_sampled_parity():
         m, _ = batch.case(c).reduce()       # raises on NaN/Inf
         assert math.isfinite(m)
     print(batch.describe)
+
+
+def test_persistent_barrier_timeout_is_reported():
+    """The failure path of a bounded wait, without a fault or a hang: with a
+    poll limit of 0 every block of the persistent kernel but the last to arrive
+    gives up at the first grid barrier and sets the cases' error flags;
+    fdlbm_batch_sync reports them once and clears them, and the context stays
+    usable: with the default limit and re-initialised states the same batch
+    matches the oracle again."""
+    cases = _mixed_cases()
+    batch = FDLBMBatch(cases, precision="fp64", graph_steps=4, autotune=False, mode="persistent")
+    _setup(batch, cases)
+    batch.set_spin_limit(0)
+    batch.step(3)
+    with pytest.raises(B.FdlbmError, match="gave up waiting"):
+        batch.sync()
+    batch.sync()                               # reported once, then cleared
+    batch.set_spin_limit(2 ** 24)
+    oracles = _setup(batch, cases)
+    for n in (5, 4):                           # direct launches, then a graph replay
+        batch.step(n)
+        for o in oracles:
+            o.step(n)
+    batch.sync()
+    for c, o in enumerate(oracles):
+        assert rel(batch.case(c).get_state(), o.f) <= 1e-12, c
