@@ -282,7 +282,9 @@ static void wall_partner(const oracle_cfg *c, int x, int y, int *px, int *py, do
 }
 
 /* Eq. 3.10: non-equilibrium extrapolation onto every wall node of f.
- * `shift` selects the first-moment convention of f (see moments_node). */
+ * `shift` selects the first-moment convention of f (see moments_node).
+ * Pinned by the exact wall moments and convergence under refinement; parity
+ * with the paper's Poiseuille error magnitudes unpinned. */
 static void apply_nee(const oracle_cfg *c, real_t *f, double shift)
 {
     size_t N = (size_t)c->nx * c->ny;
@@ -434,7 +436,10 @@ static void step_scheme1(const oracle_cfg *c, real_t *f, work_t *w)
     (void)tau;
 }
 
-/* One T2S2-FDLBM2 step (Sec. 2D, second sequence; Eq. 5.23, h = dt). */
+/* One T2S2-FDLBM2 step (Sec. 2D, second sequence; Eq. 5.23, h = dt).
+ * Pinned by its second-order time convergence and the exact invariants; parity
+ * with the paper's printed FDLBM2 errors (Table 4) unpinned: no reading of the
+ * sequence tried reproduces them. */
 static void step_scheme2(const oracle_cfg *c, real_t *f, work_t *w)
 {
     size_t N = (size_t)c->nx * c->ny;
