@@ -315,6 +315,39 @@ def run_sweep(dev, stream, sizes=(512, 1024, 2048, 4096)):
     return out
 
 
+# ----------------------------------------------------------------------- T2S2-FDLBM2
+def run_fdlbm2(dev, stream, n=N_GRID):
+    """T2S2-FDLBM2 (Eq. 5.23) on the throughput workload: the fused sweep in FP32
+    and FP64 against the staged kernels in FP32 (extra line, not the headline)."""
+    import torch
+    from paper_1911_12913_gb300.solver import FDLBM
+
+    hbm = peaks().get("hbm_gbs") or 6800.0
+    ax, f, _ = workload_fields(n)
+    grad = [f["dudx"], f["dudy"], f["dvdx"], f["dvdy"]]
+    out = {}
+    for name, prec, path, k in (("fused_fp32", "fp32", "fused", 200), ("staged_fp32", "fp32", "staged", 20),
+                                ("fused_fp64", "fp64", "fused", 10)):
+        s = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision=prec, scheme=2, path=path,
+                  stream=stream)
+        s.init_fields(f["rho"], f["ux"], f["uy"], grad)
+        s.step(3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+        t = e0.elapsed_time(e1) / 1e3 / k
+        out[name] = {"kernel": s.describe, "MLUPS": n * n / t / 1e6, "ms_per_step": t * 1e3,
+                     "hbm_frac": BYTES_PER_CELL[prec] * n * n / t / 1e9 / hbm, "steps": k}
+        del s
+        torch.cuda.empty_cache()
+    out["workload"] = f"{n}x{n} random-phase Taylor vortex, T2S2-FDLBM2 (h = dt)"
+    return out
+
+
 # ----------------------------------------------------------------------- lid-driven cavity
 def run_cavity(dev, n_cells=256, c=1.5, U=0.1, Re=1000.0, cfl=0.9, eta=0.1, tol=1e-8):
     """Sec. 3C cavity on the (n_cells + 1)^2 tanh grid: FP64 march to E(u) < tol
@@ -644,6 +677,11 @@ def run_ours(args):
     if not args.no_sweep:
         sweep = run_sweep(dev, stream)
 
+    # ---------------- T2S2-FDLBM2: fused sweep against the staged kernels
+    fdlbm2 = None
+    if not args.no_sweep and rank == 0:
+        fdlbm2 = run_fdlbm2(dev, stream, n)
+
     # ---------------- 257^2 lid-driven cavity at Re = 1000 to steady state
     cavity = None
     if not args.no_cavity and rank == 0:
@@ -697,7 +735,7 @@ def run_ours(args):
                "config": config(n, "fp32", args.steps), "clocks": clk.summary(),
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                "cpu_baseline": cpu, "fp64": fp64, "fp32_variants": variants, "batched": batched, "adjoint": adjoint,
-               "cavity": cavity, "sweep": sweep,
+               "cavity": cavity, "sweep": sweep, "fdlbm2": fdlbm2,
                "mass_drift_rel": mass_drift,
                "parallelism": "replicas" if world > 1 else "single"}
         print(json.dumps(out), flush=True)

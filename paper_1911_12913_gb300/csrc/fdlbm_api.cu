@@ -80,9 +80,11 @@ bool walled(const fdlbm_grid *g) { return g->bc_x == FDLBM_WALL || g->bc_y == FD
 // grids in FP64: there the work is bound by the FP64 units, and the halo rows
 // the sweep recomputes on small walled grids cost more than the staged
 // kernels' extra traffic (257^2 cavity: 198 against 81 us per step on GB300).
+// T2S2-FDLBM2 has a fused sweep for periodic grids only.
 int choose_path(const fdlbm_grid *g, const fdlbm_opts *o)
 {
-    const bool can_fuse = fused_ok(g) && o->scheme == FDLBM_SCHEME_T2S2_1;
+    const bool can_fuse =
+        fused_ok(g) && (o->scheme == FDLBM_SCHEME_T2S2_1 || !walled(g));
     if (o->path == FDLBM_PATH_STAGED) return FDLBM_PATH_STAGED;
     if (o->path == FDLBM_PATH_FUSED) return can_fuse ? FDLBM_PATH_FUSED : -1;
     if (walled(g) && o->precision == FDLBM_FP64) return FDLBM_PATH_STAGED;
@@ -93,14 +95,16 @@ int choose_path(const fdlbm_grid *g, const fdlbm_opts *o)
 // tiles waste less; the grid should also fill whole waves of resident CTAs.
 // Pick the height that minimises (waves) x (rows + 8), the modelled sweep time
 // (on small grids that is a short segment: more CTAs, each walking fewer rows).
-int choose_rows(int nx, int ny, int precision, int variant, bool walls)
+int choose_rows(int nx, int ny, int precision, int variant, bool walls, int scheme)
 {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool f32 = precision == FDLBM_FP32_DEV;
     int per_sm;
-    if (walls)
+    if (scheme == FDLBM_SCHEME_T2S2_2)
+        per_sm = f32 ? fused_s2_blocks_per_sm<float>() : fused_s2_blocks_per_sm<double>();
+    else if (walls)
         per_sm = f32 ? fused_walls_blocks_per_sm<float>() : fused_walls_blocks_per_sm<double>();
     else if (variant == FDLBM_VARIANT_PACKED)
         per_sm = fused_x2_blocks_per_sm();
@@ -172,6 +176,7 @@ cudaError_t launch_step(fdlbm_ctx *h, cudaStream_t s)
     if (h->precision == FDLBM_FP32_DEV) {
         auto a = step_args<float>(h);
         if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
+        if (h->scheme == FDLBM_SCHEME_T2S2_2) return launch_fused_s2(a, s);
         if (walls) return launch_fused_walls(a, s);
         if (h->variant == FDLBM_VARIANT_PACKED) return launch_fused_x2(a, a.err, s);
         if (h->variant == FDLBM_VARIANT_WARP) return launch_fused_warp(a, h->tmap[h->cur], s);
@@ -181,6 +186,7 @@ cudaError_t launch_step(fdlbm_ctx *h, cudaStream_t s)
     }
     auto a = step_args<double>(h);
     if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
+    if (h->scheme == FDLBM_SCHEME_T2S2_2) return launch_fused_s2(a, s);
     if (walls) return launch_fused_walls(a, s);
     if (h->variant == FDLBM_VARIANT_TMA) return launch_fused_tma(a, s);
     if (h->variant == FDLBM_VARIANT_ASYNC) return launch_fused_async(a, s);
@@ -350,15 +356,19 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     if (path < 0) return FDLBM_EUNSUPPORTED;
     const bool fused = path == FDLBM_PATH_FUSED;
     const bool f32 = o.precision == FDLBM_FP32_DEV;
-    const bool packed_ok = fused && !walled(g) && f32 && !o.has_force && fused_x2_ok(g->nx, g->ny);
-    const bool tma_ok = fused && !walled(g) && (f32 ? fused_tma_ok<float>(g->nx, g->ny)
-                                                    : fused_tma_ok<double>(g->nx, g->ny));
+    // the variants are T2S2-FDLBM1 kernels; T2S2-FDLBM2 fuses on the scalar layout only
+    const bool s1 = o.scheme == FDLBM_SCHEME_T2S2_1;
+    const bool packed_ok =
+        s1 && fused && !walled(g) && f32 && !o.has_force && fused_x2_ok(g->nx, g->ny);
+    const bool tma_ok = s1 && fused && !walled(g) &&
+                        (f32 ? fused_tma_ok<float>(g->nx, g->ny) : fused_tma_ok<double>(g->nx, g->ny));
     const bool periodic = !walled(g);
-    const bool warp_ok = fused && periodic && f32 && !o.has_force && fused_warp_ok(g->nx, g->ny);
+    const bool warp_ok =
+        s1 && fused && periodic && f32 && !o.has_force && fused_warp_ok(g->nx, g->ny);
     if ((o.variant == FDLBM_VARIANT_PACKED && !packed_ok) ||
         (o.variant == FDLBM_VARIANT_WARP && !warp_ok) ||
         (o.variant == FDLBM_VARIANT_TMA && !tma_ok) ||
-        (o.variant == FDLBM_VARIANT_ASYNC && (!fused || walled(g))))
+        (o.variant == FDLBM_VARIANT_ASYNC && (!s1 || !fused || walled(g))))
         return FDLBM_EUNSUPPORTED;
     int variant = o.variant;
     if (variant == FDLBM_VARIANT_AUTO) variant = warp_ok ? FDLBM_VARIANT_WARP : FDLBM_VARIANT_SCALAR;
@@ -398,7 +408,8 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     h->variant = variant;
     if (path == FDLBM_PATH_FUSED)
         h->rows = o.rows_per_cta > 0 ? std::min(o.rows_per_cta, g->ny)
-                                     : choose_rows(g->nx, g->ny, o.precision, variant, walled(g));
+                                     : choose_rows(g->nx, g->ny, o.precision, variant, walled(g),
+                                                   o.scheme);
     h->stream = static_cast<cudaStream_t>(o.stream);
     h->adjoint = o.adjoint != 0;
     h->graph_steps = o.graph_steps > 0 ? o.graph_steps + (o.graph_steps & 1) : 0;
@@ -802,7 +813,10 @@ const char *fdlbm_describe(fdlbm_t h)
     if (!h) return "NULL handle";
     const char *prec = h->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64";
     if (h->scheme == FDLBM_SCHEME_T2S2_2) {
-        h->desc = std::string("staged-scheme2 ") + prec;
+        h->desc = std::string(h->path == FDLBM_PATH_FUSED ? "fused-scheme2 " : "staged-scheme2 ") +
+                  prec;
+        if (h->path == FDLBM_PATH_FUSED) h->desc += " rows=" + std::to_string(h->rows);
+        if (h->graph_steps) h->desc += " graph_steps=" + std::to_string(h->graph_steps);
         if (h->incomp) h->desc += " incompressible";
         return h->desc.c_str();
     }

@@ -102,6 +102,11 @@ cudaError_t launch_fused(const StepArgs<R> &a, cudaStream_t s);
 int fused_tile_width();
 template <class R>
 int fused_blocks_per_sm();
+// step_fused_s2.cu (T2S2-FDLBM2, periodic grids)
+template <class R>
+cudaError_t launch_fused_s2(const StepArgs<R> &a, cudaStream_t s);
+template <class R>
+int fused_s2_blocks_per_sm();
 // step_fused_tma.cu (scalar sweep with bulk-copy row loads)
 template <class R>
 bool fused_tma_ok(int nx, int ny);

@@ -1,0 +1,292 @@
+// Fused T2S2-FDLBM2 step for grids periodic in x and y: the second computational
+// sequence of Sec. 2D in one kernel, one read and one write of the
+// distributions per node and step (the staged kernels move 9 x 7 values).
+//
+// Per node, with h = dt (Sec. 2D: fbar = f~ and fbar^{+,h} = f~+ at h = dt):
+//   f^n      = Eq. 2.52 on f~^n (with the force term of Eq. 2.32)
+//   f~+      = Eq. 2.20 on f~^n
+//   fbar     = f~+ - dt xi.grad f~+                 (Eqs. 2.33, 2.35)
+//   f^{n+1}  = Eq. 2.52 on fbar
+//   f~^{n+1} = f~+ + dt/2 [L(f^n) + L(f^{n+1})]    (Eq. 5.23, L of Eq. 2.27)
+//
+// The layout is that of the T2S2-FDLBM1 sweep (step_fused.cu): a CTA owns NT - 8
+// columns and a segment of rows, thread t owns one column and sweeps bottom to
+// top; differences in y read per-thread register windows of five rows, in x
+// shared-memory rings written by the neighbours.  Per row r:
+//   A (row r)     f^n and f~+ of the newly loaded row (windows and x-rings)
+//   B (row r-2)   L(f^n) (kept in a per-thread ring for stage C two rows on),
+//                 fbar from the differences of f~+, then f^{n+1} (window, x-ring)
+//   C (row r-4)   L(f^{n+1}) and the update of Eq. 5.23 with f~+ from the window
+// Stage B carries the two differences the scheme needs at a point (of f^n and
+// of f~+) against one in T2S2-FDLBM1.  One barrier per row: every ring slot a
+// stage reads was written two rows earlier, and is rewritten five rows after
+// it was written.
+#include <cstdint>
+
+#include "internal.h"
+
+namespace fdlbm {
+namespace {
+
+constexpr int kHalo2 = 4;
+constexpr int kRing2 = 5;
+
+template <class R, int NT>
+struct Smem2 {
+    R P[kRing2][6][NT];   // f^n of the x-moving populations
+    R Q[kRing2][6][NT];   // f~+ of the x-moving populations
+    R S[kRing2][6][NT];   // f^{n+1} of the x-moving populations
+    R LN[kRing2][9][NT];  // L(f^n), read back by the same thread two rows later
+};
+
+template <class R>
+__device__ __forceinline__ R recip2(R v)
+{
+    return R(1) / v;
+}
+template <>
+__device__ __forceinline__ float recip2<float>(float v)
+{
+    return __frcp_rn(v);
+}
+
+// Moments (Eq. 3.3 with the force shift `shift`), f^eq (Eq. 3.2 or the
+// incompressible one) and the forcing terms (Eq. 3.12) of a deviation vector.
+template <class R, bool FORCE>
+__device__ __forceinline__ void node_maps(const Coeffs<R> &c, const R g[9], R Fx, R Fy, R shift,
+                                          R geq[9], R F[9])
+{
+    R drho, jx, jy;
+    moments_dev(g, drho, jx, jy);
+    const R rho = macro_density(c, drho);
+    if (FORCE) {
+        jx += shift * rho * Fx;
+        jy += shift * rho * Fy;
+    }
+    const R inv = recip2(rho);
+    const R ux = jx * inv, uy = jy * inv;
+    equilibrium_dev(drho, rho, ux, uy, geq);
+    if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(c, drho));
+}
+
+template <class R, bool FORCE, int NT>
+struct Sweep2 {
+    const StepArgs<R> a;
+    Smem2<R, NT> &sm;
+    const int t, gx, xc;
+    const bool act1, act2;
+    const R mxc;
+    const Coeffs<R> c;
+    const Stencil<R> st;
+    R Pw[9][kRing2];  // f^n of this column, slot = row mod 5
+    R Qw[9][kRing2];  // f~+
+    R Sw[9][kRing2];  // f^{n+1}
+    R cur[9], nxt[9];
+    int rl, rs, rq;   // wrapped global rows of the next load, stage B, stage C
+
+    __device__ static int inc(int v, int n) { return v + 1 == n ? 0 : v + 1; }
+
+    __device__ void load(R *dst, int row) const
+    {
+        const size_t off = (size_t)row * a.pitch + gx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[i] = __ldg(a.gin + i * a.plane + off);
+    }
+
+    __device__ void force_at(int row, R &Fx, R &Fy) const
+    {
+        Fx = Fy = R(0);
+        if (FORCE) {
+            const size_t fo = (size_t)row * a.pitch + gx;
+            Fx = __ldg(a.force + fo);
+            Fy = __ldg(a.force + a.plane + fo);
+        }
+    }
+
+    // sign(c) D_m f of population i at the centre of this column, in x from
+    // the ring row `rw` and in y from the window w (slots of rows k-2 .. k+2).
+    __device__ __forceinline__ R dx_of(int i, const R *rw, R v0) const
+    {
+        return apply_stencil(st, cx(i), rw[t - 2], rw[t - 1], v0, rw[t + 1], rw[t + 2]);
+    }
+
+    template <int PH>
+    __device__ void row(int k, int iters)
+    {
+        constexpr int p0 = PH;                  // row r       (newest)
+        constexpr int p1 = (PH + 4) % kRing2;   // row r-1
+        constexpr int p2 = (PH + 3) % kRing2;   // row r-2  (stage B centre)
+        constexpr int p3 = (PH + 2) % kRing2;   // row r-3
+        constexpr int p4 = (PH + 1) % kRing2;   // row r-4  (stage C centre)
+        const int rA = rl;
+        if (k + 1 < iters) {
+            rl = inc(rl, a.ny);
+            load(nxt, rl);
+        }
+        // ------------------------------------------------------------ A (row r)
+        {
+            R Fx, Fy, geq[9], F[9];
+            force_at(rA, Fx, Fy);
+            node_maps<R, FORCE>(c, cur, Fx, Fy, c.half_dt, geq, F);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const R neq = geq[i] - cur[i];
+                R fn = cur[i] + c.b_phys * neq;  // Eq. 2.52, h = dt
+                R ft = cur[i] + c.b_til * neq;   // Eq. 2.20
+                if (FORCE) {
+                    fn += c.c_phys * F[i];
+                    ft += c.c_til * F[i];
+                }
+                Pw[i][p0] = fn;
+                Qw[i][p0] = ft;
+                if (xslot(i) >= 0) {
+                    sm.P[p0][xslot(i)][t] = fn;
+                    sm.Q[p0][xslot(i)][t] = ft;
+                }
+            }
+        }
+        __syncthreads();
+        // ------------------------------------------------------------ B (row r-2)
+        if (k >= 4) {
+            const int sg = rs;
+            rs = inc(rs, a.ny);
+            if (act1) {
+                const R myr = __ldg(a.my + sg);
+                const R hx = c.h * mxc, hy = c.h * myr;  // h = dt
+                R fb[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    // L(f^n) = -xi.grad f^n and fbar = f~+ - dt xi.grad f~+
+                    R dP = R(0), fbar = Qw[i][p2];
+                    if (cx(i) != 0) {
+                        dP += mxc * dx_of(i, sm.P[p2][xslot(i)], Pw[i][p2]);
+                        fbar -= hx * dx_of(i, sm.Q[p2][xslot(i)], Qw[i][p2]);
+                    }
+                    if (cy(i) != 0) {
+                        dP += myr * apply_stencil(st, cy(i), Pw[i][p4], Pw[i][p3], Pw[i][p2],
+                                                  Pw[i][p1], Pw[i][p0]);
+                        fbar -= hy * apply_stencil(st, cy(i), Qw[i][p4], Qw[i][p3], Qw[i][p2],
+                                                   Qw[i][p1], Qw[i][p0]);
+                    }
+                    sm.LN[p0][i][t] = -dP;
+                    fb[i] = fbar;
+                }
+                R Fx, Fy, geq[9], F[9];
+                force_at(sg, Fx, Fy);
+                node_maps<R, FORCE>(c, fb, Fx, Fy, c.half_h, geq, F);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    R fnew = fb[i] + c.b_star * (geq[i] - fb[i]);  // Eq. 2.52, h = dt
+                    if (FORCE) fnew += c.c_star * F[i];
+                    Sw[i][p0] = fnew;
+                    if (xslot(i) >= 0) sm.S[p0][xslot(i)][t] = fnew;
+                }
+            }
+        }
+        // ------------------------------------------------------------ C (row r-4)
+        // f^{n+1} rows r-6 .. r-2 sit in slots p4 .. p0 of Sw, the centre row r-4
+        // in slot p2; L(f^n) of row r-4 in ring slot p2; f~+ of row r-4 in Qw p4.
+        if (k >= 8) {
+            const int qg = rq;
+            rq = inc(rq, a.ny);
+            if (act2) {
+                const R myr = __ldg(a.my + qg);
+                const R hdt = c.half_dt;
+                const size_t off = (size_t)qg * a.pitch + xc;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    R dS = R(0);
+                    if (cx(i) != 0) dS += mxc * dx_of(i, sm.S[p2][xslot(i)], Sw[i][p2]);
+                    if (cy(i) != 0)
+                        dS += myr * apply_stencil(st, cy(i), Sw[i][p4], Sw[i][p3], Sw[i][p2],
+                                                  Sw[i][p1], Sw[i][p0]);
+                    a.gout[i * a.plane + off] = Qw[i][p4] + hdt * (sm.LN[p2][i][t] - dS);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cur[i] = nxt[i];
+    }
+};
+
+template <class R, bool FORCE, int NT>
+__global__ void __launch_bounds__(NT, 2) k_step_fused_s2(const StepArgs<R> a)
+{
+    constexpr int W = NT - 2 * kHalo2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem2<R, NT> &sm = *reinterpret_cast<Smem2<R, NT> *>(smem_raw);
+
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * W;
+    const int xc = x0 - kHalo2 + t;
+    const int y0 = blockIdx.y * a.rows;
+    if (y0 >= a.ny) return;  // uniform over the block
+    const int y1 = min(y0 + a.rows, a.ny);
+    const int gx = wrap_index(xc, a.nx);
+    Sweep2<R, FORCE, NT> sw{a,
+                            sm,
+                            t,
+                            gx,
+                            xc,
+                            (t >= 2) && (t < NT - 2),
+                            (t >= kHalo2) && (t < NT - kHalo2) && (xc < a.nx),
+                            a.mx[gx],
+                            a.c,
+                            a.st};
+    // iteration k loads row y0-4+k; stage B works on row y0-6+k (from k = 4),
+    // stage C on row y0-8+k (from k = 8)
+    sw.rl = wrap_index(y0 - kHalo2, a.ny);
+    sw.rs = wrap_index(y0 - 2, a.ny);
+    sw.rq = y0;
+    sw.load(sw.cur, sw.rl);
+    const int iters = (y1 - y0) + 2 * kHalo2;
+    for (int k = 0; k < iters; k += kRing2) {
+        sw.template row<0>(k, iters);
+        if (k + 1 < iters) sw.template row<1>(k + 1, iters);
+        if (k + 2 < iters) sw.template row<2>(k + 2, iters);
+        if (k + 3 < iters) sw.template row<3>(k + 3, iters);
+        if (k + 4 < iters) sw.template row<4>(k + 4, iters);
+    }
+}
+
+template <class R, bool FORCE>
+cudaError_t launch_s2(const StepArgs<R> &a, cudaStream_t s)
+{
+    constexpr int NT = 128;
+    constexpr int W = NT - 2 * kHalo2;
+    constexpr size_t smem = sizeof(Smem2<R, NT>);
+    cudaError_t e = cudaFuncSetAttribute(k_step_fused_s2<R, FORCE, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((a.nx + W - 1) / W, (a.ny + a.rows - 1) / a.rows);
+    k_step_fused_s2<R, FORCE, NT><<<grid, NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <class R>
+cudaError_t launch_fused_s2(const StepArgs<R> &a, cudaStream_t s)
+{
+    return a.force ? launch_s2<R, true>(a, s) : launch_s2<R, false>(a, s);
+}
+
+template <class R>
+int fused_s2_blocks_per_sm()
+{
+    int n = 0;
+    constexpr size_t smem = sizeof(Smem2<R, 128>);
+    cudaFuncSetAttribute(k_step_fused_s2<R, false, 128>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_fused_s2<R, false, 128>, 128,
+                                                      smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+template cudaError_t launch_fused_s2<float>(const StepArgs<float> &, cudaStream_t);
+template cudaError_t launch_fused_s2<double>(const StepArgs<double> &, cudaStream_t);
+template int fused_s2_blocks_per_sm<float>();
+template int fused_s2_blocks_per_sm<double>();
+
+}  // namespace fdlbm

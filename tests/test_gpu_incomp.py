@@ -134,14 +134,17 @@ def test_incomp_walls(precision, tol, path, bcx, bcy, nx, ny, rows):
     assert err <= tol
 
 
-def test_incomp_scheme2_fp64():
-    """T2S2-FDLBM2 (staged kernels) with the incompressible equilibrium."""
+@pytest.mark.parametrize("walls", [True, False])
+def test_incomp_scheme2_fp64(walls):
+    """T2S2-FDLBM2 with the incompressible equilibrium: the staged kernels on a
+    channel, the fused sweep on a periodic grid."""
     nx, ny = 24, 20
     xa = I.periodic_axis(nx, 0.0, 1.0)
-    ya = I.tanh_axis(ny - 1, 1.5)
+    ya = I.tanh_axis(ny - 1, 1.5) if walls else I.periodic_axis(ny, 0.0, 0.8)
     force = 1e-3 * np.random.default_rng(4).uniform(-1, 1, size=(2, ny, nx))
     s, o = _pair(xa, ya, nu=0.02, cfl=0.3, beta=0.2, force=force, scheme=2,
-                 wall_u=[(0, 0), (0, 0), (0, 0), (0.05, 0.0)])
+                 wall_u=[(0, 0), (0, 0), (0, 0), (0.05, 0.0)] if walls else None)
+    assert s.describe.startswith("staged-scheme2" if walls else "fused-scheme2"), s.describe
     _init_both(s, o, I.random_fields(nx, ny, 5, drho=0.05))
     s.step(15)
     o.step(15)

@@ -297,24 +297,56 @@ def test_scalar_fp32_fused_with_force():
     assert rel(s.get_state(), o.f) <= 1e-6
 
 
+@pytest.mark.parametrize("path", ["fused", "staged"])
 @pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 1e-6)])
-def test_t2s2_fdlbm2_periodic_force_metrics(precision, tol):
-    """T2S2-FDLBM2 (Eq. 5.23) on the staged kernels against the oracle's second
-    sequence: random state, force field, stretched metrics."""
+def test_t2s2_fdlbm2_periodic_force_metrics(precision, tol, path):
+    """T2S2-FDLBM2 (Eq. 5.23) on the fused sweep and on the staged kernels
+    against the oracle's second sequence: random state, force field, stretched
+    metrics."""
     nx, ny = 70, 45
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.periodic_axis(ny, 0.0, 0.7)
     xa.metric = I.random_metric(nx, 71, base=nx, spread=0.3)
     ya.metric = I.random_metric(ny, 72, base=ny / 0.7, spread=0.3)
     force = 1e-3 * np.random.default_rng(17).uniform(-1, 1, size=(2, ny, nx))
-    s = FDLBM(xa, ya, nu=0.02, cfl=0.3, blend=0.2, has_force=True, precision=precision, scheme=2)
-    assert s.describe.startswith("staged-scheme2"), s.describe
+    s = FDLBM(xa, ya, nu=0.02, cfl=0.3, blend=0.2, has_force=True, precision=precision, scheme=2,
+              path=path)
+    assert s.describe.startswith(f"{path}-scheme2"), s.describe
+    assert s.kernels_per_step == (1 if path == "fused" else 3)
     o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force, scheme=2)
     s.set_force(force)
     _init_both(s, o, I.random_fields(nx, ny, 37))
     s.step(25)
     o.step(25)
     assert rel(s.get_state(), o.f) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 1e-6)])
+@pytest.mark.parametrize("nx,ny,rows,force", [(133, 37, 0, False), (250, 21, 1, True), (4, 9, 0, True),
+                                              (128, 64, 5, False), (500, 13, 3, False)])
+def test_t2s2_fdlbm2_fused_ragged(precision, tol, nx, ny, rows, force):
+    """The fused T2S2-FDLBM2 sweep on ragged strips and row segments (tile
+    heights 1, 3, 5 and automatic, a grid narrower than the halo), with and
+    without a force field, random metrics: 1 + 11 steps against the oracle."""
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 0.7)
+    xa.metric = I.random_metric(nx, 11, base=nx, spread=0.4)
+    ya.metric = I.random_metric(ny, 12, base=ny / 0.7, spread=0.4)
+    F = 1e-3 * np.random.default_rng(nx + ny).uniform(-1, 1, size=(2, ny, nx)) if force else None
+    s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, has_force=force, precision=precision, scheme=2,
+              rows_per_cta=rows)
+    assert s.describe.startswith("fused-scheme2"), s.describe
+    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=F, scheme=2)
+    if force:
+        s.set_force(F)
+    _init_both(s, o, I.random_fields(nx, ny, 5))
+    for n in (1, 11):
+        s.step(n)
+        o.step(n)
+    s.sync()
+    err = rel(s.get_state(), o.f)
+    print(f"{s.describe} {nx}x{ny}: rel L2(f~) = {err:.3e}")
+    assert err <= tol
 
 
 def test_t2s2_fdlbm2_channel_walls_fp64():
