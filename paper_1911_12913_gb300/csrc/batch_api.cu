@@ -161,6 +161,14 @@ bool fused_eligible(const fdlbm_batch_ctx *b)
     return true;
 }
 
+// The fused sweep's tiles for FUSED, and for PERSISTENT where the fused sweep
+// applies (one grid barrier per step); node tiles of the staged kernels
+// otherwise.
+bool uses_fused_sweep(const fdlbm_batch_ctx *b)
+{
+    return b->mode == FDLBM_BATCH_FUSED || (b->mode == FDLBM_BATCH_PERSISTENT && fused_eligible(b));
+}
+
 // Tile height of the fused batch: minimise (waves) x (rows + 8) over the tiles
 // of all cases, as for a single grid.
 int fused_rows_model(const fdlbm_batch_ctx *b)
@@ -198,6 +206,11 @@ cudaError_t launch_steps(fdlbm_batch_ctx *b, int parity, int n)
                     : launch_batched_fused<double>(b->tab, (parity + k) & 1, b->stream);
         return e;
     }
+    if (b->mode == FDLBM_BATCH_PERSISTENT && b->fused_rows > 0)  // the fused sweep, persistent
+        return f32 ? launch_persistent_fused<float>(b->tab, b->bar, parity, n, b->stream,
+                                                    b->spin_limit)
+                   : launch_persistent_fused<double>(b->tab, b->bar, parity, n, b->stream,
+                                                     b->spin_limit);
     if (b->mode == FDLBM_BATCH_PERSISTENT)
         return f32 ? launch_persistent<float>(b->tab, b->bar, parity, n, b->blk, b->stream,
                                               b->spin_limit)
@@ -303,7 +316,7 @@ fdlbm_status autotune(fdlbm_batch_ctx *b)
         }
     }
     std::vector<TuneChoice> cand;
-    if (b->mode == FDLBM_BATCH_FUSED) {
+    if (uses_fused_sweep(b)) {
         const int r0 = fused_rows_model(b);
         for (int r : {r0, std::max(1, r0 / 2), std::max(1, 3 * r0 / 4), std::min(512, 2 * r0)})
             if (std::none_of(cand.begin(), cand.end(), [&](const TuneChoice &c) { return c.rows == r; }))
@@ -348,8 +361,8 @@ fdlbm_status autotune(fdlbm_batch_ctx *b)
 // Tables of the current mode with its default parameters.
 fdlbm_status default_tables(fdlbm_batch_ctx *b)
 {
-    return b->mode == FDLBM_BATCH_FUSED ? build_tables(b, dim3(128, 1), fused_rows_model(b))
-                                        : build_tables(b, dim3(32, 8));
+    return uses_fused_sweep(b) ? build_tables(b, dim3(128, 1), fused_rows_model(b))
+                               : build_tables(b, dim3(32, 8));
 }
 
 void release(fdlbm_batch_ctx *b)
@@ -575,6 +588,10 @@ const char *fdlbm_batch_describe(fdlbm_batch_t b)
     if (b->mode == FDLBM_BATCH_FUSED) {
         os << "batched-fused " << prec << " cases=" << b->cases.size() << " rows=" << b->fused_rows
            << " graph_steps=" << b->graph_steps << " launches_per_step=1";
+    } else if (b->mode == FDLBM_BATCH_PERSISTENT && b->fused_rows > 0) {
+        os << "batched-persistent-fused " << prec << " cases=" << b->cases.size()
+           << " rows=" << b->fused_rows << " graph_steps=" << b->graph_steps
+           << " grid_barriers_per_step=1";
     } else {
         const int per_step =
             3 + (b->tab.total_wall > 0 ? 2 : 0) + (b->tab.total_wall > 0 && b->tab.any_scheme2 ? 1 : 0);

@@ -152,6 +152,12 @@ cudaError_t launch_persistent(const BatchTables &t, void *bar, int parity0, int 
                               cudaStream_t s, unsigned spin_limit);
 template <class R>
 int persistent_blocks_per_sm(dim3 blk);
+// step_fused_walls.cu: the fused batch sweep as one cooperative launch
+template <class R>
+cudaError_t launch_persistent_fused(const BatchTables &t, void *bar, int parity0, int nsteps,
+                                    cudaStream_t s, unsigned spin_limit);
+template <class R>
+int persistent_fused_blocks_per_sm();
 size_t persistent_barrier_bytes();
 // adjoint.cu
 template <class R>

@@ -28,50 +28,11 @@
 
 #include <cuda_runtime.h>
 
+#include "grid_barrier.cuh"
 #include "staged_nodes.cuh"
 
 namespace fdlbm {
 namespace {
-
-struct GridBarrier {
-    unsigned count, gen;
-};
-
-__device__ __forceinline__ unsigned load_volatile(const unsigned *p)
-{
-    return *reinterpret_cast<const volatile unsigned *>(p);
-}
-
-// Block-uniform result: false when this block gave up waiting, after `limit`
-// polls (the last block to arrive never waits).
-__device__ bool grid_barrier(GridBarrier *bar, unsigned &gen, unsigned limit)
-{
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        int ok = 1;
-        const unsigned target = gen + 1u;
-        __threadfence();
-        if (atomicAdd(&bar->count, 1u) + 1u == gridDim.x) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicExch(&bar->gen, target);
-        } else {
-            for (unsigned k = 0; load_volatile(&bar->gen) != target; ++k) {
-                if (k >= limit) {
-                    ok = 0;
-                    break;
-                }
-                if (k > 32) __nanosleep(64);
-            }
-        }
-        __threadfence();
-        gen = target;
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
-}
 
 struct PersistArgs {
     BatchTables t;

@@ -82,17 +82,21 @@ def _setup(batch, cases):
 @pytest.mark.parametrize("precision,tol,autotune,mode",
                          [("fp64", 1e-12, False, "auto"), ("fp32", 2e-6, True, "auto"),
                           ("fp32", 2e-6, True, "fused"), ("fp32", 2e-6, False, "staged"),
-                          ("fp64", 1e-12, False, "persistent"), ("fp32", 2e-6, False, "persistent")])
+                          ("fp64", 1e-12, False, "persistent"), ("fp32", 2e-6, False, "persistent"),
+                          ("fp32", 2e-6, True, "persistent-fused")])
 def test_mixed_batch_matches_oracle(precision, tol, autotune, mode):
-    """The three batch modes: the fused sweep with walls (FP32, T2S2-FDLBM1 cases
+    """The batch modes: the fused sweep with walls (FP32, T2S2-FDLBM1 cases
     only, the default where it applies), per-stage launches of the staged
-    kernels, and the persistent cooperative launch."""
+    kernels, and the persistent cooperative launch (of the fused sweep where
+    it applies, one grid barrier per step; of the staged stages otherwise)."""
     cases = _mixed_cases()
-    if mode == "fused":
+    if mode in ("fused", "persistent-fused"):
         cases = [cs for cs in cases if cs.get("scheme", 1) == 1]
-    batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=autotune, mode=mode)
+    batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=autotune,
+                       mode="persistent" if mode == "persistent-fused" else mode)
     want = {"fused": "batched-fused", "staged": "batched-staged",
-            "persistent": "batched-persistent", "auto": "batched-staged"}[mode]
+            "persistent": "batched-persistent ", "auto": "batched-staged",
+            "persistent-fused": "batched-persistent-fused"}[mode]
     assert batch.describe.startswith(want), batch.describe
     oracles = _setup(batch, cases)
     # 11 steps: 4 + 4 by graph replay, 3 launched directly; then 1 more
@@ -169,7 +173,8 @@ def test_sweep_64_cases_sampled_parity():
     print(batch.describe)
 
 
-def test_persistent_barrier_timeout_is_reported():
+@pytest.mark.parametrize("precision,scheme1_only", [("fp64", False), ("fp32", True)])
+def test_persistent_barrier_timeout_is_reported(precision, scheme1_only):
     """The failure path of a bounded wait, without a fault or a hang: with a
     poll limit of 0 every block of the persistent kernel but the last to arrive
     gives up at the first grid barrier and sets the cases' error flags;
@@ -177,7 +182,11 @@ def test_persistent_barrier_timeout_is_reported():
     usable: with the default limit and re-initialised states the same batch
     matches the oracle again."""
     cases = _mixed_cases()
-    batch = FDLBMBatch(cases, precision="fp64", graph_steps=4, autotune=False, mode="persistent")
+    if scheme1_only:                           # the persistent fused sweep
+        cases = [cs for cs in cases if cs.get("scheme", 1) == 1]
+    batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=False, mode="persistent")
+    assert batch.describe.startswith("batched-persistent-fused" if scheme1_only
+                                     else "batched-persistent "), batch.describe
     _setup(batch, cases)
     batch.set_spin_limit(0)
     batch.step(3)
@@ -191,5 +200,6 @@ def test_persistent_barrier_timeout_is_reported():
         for o in oracles:
             o.step(n)
     batch.sync()
+    tol = 1e-12 if precision == "fp64" else 2e-6
     for c, o in enumerate(oracles):
-        assert rel(batch.case(c).get_state(), o.f) <= 1e-12, c
+        assert rel(batch.case(c).get_state(), o.f) <= tol, c
