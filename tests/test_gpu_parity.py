@@ -462,15 +462,21 @@ def test_device_side_arguments_and_zero_steps():
 
 
 # ------------------------------------------------------------------ full size, sampled
-@pytest.mark.parametrize("precision,tol", [("fp32", 2e-7), ("fp64", FP64_TOL)])
-def test_full_size_4096_sampled_patches(precision, tol):
+@pytest.mark.parametrize("precision,tol,scheme,eq", [("fp32", 2e-7, 1, "standard"),
+                                                     ("fp64", FP64_TOL, 1, "standard"),
+                                                     ("fp32", 2e-7, 2, "standard"),
+                                                     ("fp64", FP64_TOL, 2, "standard"),
+                                                     ("fp32", 2e-7, 1, "incompressible")])
+def test_full_size_4096_sampled_patches(precision, tol, scheme, eq):
     """4096^2 periodic grid in the launch configuration the benchmark times
-    (automatic tile height): after 2 steps, sampled 40x40 patches are checked
-    against the oracle run on the same patch.  One step reaches 4 nodes, so the
-    central 24x24 nodes of each patch are exact for the oracle."""
+    (automatic kernel and tile height; T2S2-FDLBM1 and T2S2-FDLBM2, and the
+    incompressible equilibrium): after 2 steps, sampled 40x40 patches are
+    checked against the oracle run on the same patch.  One step reaches 4
+    nodes, so the central 24x24 nodes of each patch are exact for the oracle."""
     n, steps, P = 4096, 2, 40
     xa = I.periodic_axis(n, 0.0, 2 * math.pi)
-    s = FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision=precision)
+    s = FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision=precision, scheme=scheme,
+              equilibrium=eq)
     assert s.path == "fused"
     print(s.describe)
     fld = I.taylor_green(xa, xa, u0=0.01, phase=(0.7, 2.1))
@@ -490,7 +496,8 @@ def test_full_size_4096_sampled_patches(precision, tol):
         xs = (x0 + np.arange(P)) % n
         ys = (y0 + np.arange(P)) % n
         pa = I.periodic_axis(P, 0.0, P * 2 * math.pi / n)
-        o = O.Oracle(pa, pa, nu=0.01, dt=s.dt, beta=0.1)
+        o = O.Oracle(pa, pa, nu=0.01, dt=s.dt, beta=0.1, scheme=scheme,
+                     incomp=eq == "incompressible")
         sub = {k: v[np.ix_(ys, xs)] for k, v in fld.items()}
         o.init_fields(sub["rho"], sub["ux"], sub["uy"],
                       [sub["dudx"], sub["dudy"], sub["dvdx"], sub["dvdy"]])
@@ -500,5 +507,5 @@ def test_full_size_4096_sampled_patches(precision, tol):
         ix = torch.tensor(xs[m:P - m], device=g.device)
         got = g[:, iy][:, :, ix].cpu().numpy()
         errs.append(rel(got, want))
-    print(f"{precision} 4096^2 sampled patches: max rel L2(f~) = {max(errs):.3e}")
+    print(f"{s.describe} 4096^2 sampled patches: max rel L2(f~) = {max(errs):.3e}")
     assert max(errs) <= tol
