@@ -113,10 +113,10 @@ typedef struct {
     double rho0;              /* reference density; FP32 storage keeps f~_i - w_i rho0 */
     int precision;            /* FDLBM_FP64 or FDLBM_FP32_DEV */
     int has_force;            /* 1: reserve a body-acceleration field (fdlbm_set_force), Eq. 3.12 */
-    int path;                 /* FDLBM_PATH_AUTO: the fused kernel for T2S2-FDLBM1 (periodic grids,
-                                 and walled grids in FP32) and for T2S2-FDLBM2 on periodic
-                                 grids; the staged kernels for walled grids in FP64 and for
-                                 T2S2-FDLBM2 on walled grids */
+    int path;                 /* FDLBM_PATH_AUTO: the fused kernel for both schemes on periodic
+                                 grids and on walled grids in FP32; the staged kernels for
+                                 walled grids in FP64 (bound by the FP64 units, where the
+                                 sweep's recomputed halo costs more than the extra traffic) */
     int rows_per_cta;         /* fused kernel tile height; 0 = automatic */
     int variant;              /* FDLBM_VARIANT_*; PACKED where it does not apply -> EUNSUPPORTED */
     int scheme;               /* FDLBM_SCHEME_T2S2_1 (default) or FDLBM_SCHEME_T2S2_2 */

@@ -80,11 +80,10 @@ bool walled(const fdlbm_grid *g) { return g->bc_x == FDLBM_WALL || g->bc_y == FD
 // grids in FP64: there the work is bound by the FP64 units, and the halo rows
 // the sweep recomputes on small walled grids cost more than the staged
 // kernels' extra traffic (257^2 cavity: 198 against 81 us per step on GB300).
-// T2S2-FDLBM2 has a fused sweep for periodic grids only.
+// Both schemes have fused sweeps, for periodic and walled grids.
 int choose_path(const fdlbm_grid *g, const fdlbm_opts *o)
 {
-    const bool can_fuse =
-        fused_ok(g) && (o->scheme == FDLBM_SCHEME_T2S2_1 || !walled(g));
+    const bool can_fuse = fused_ok(g);
     if (o->path == FDLBM_PATH_STAGED) return FDLBM_PATH_STAGED;
     if (o->path == FDLBM_PATH_FUSED) return can_fuse ? FDLBM_PATH_FUSED : -1;
     if (walled(g) && o->precision == FDLBM_FP64) return FDLBM_PATH_STAGED;

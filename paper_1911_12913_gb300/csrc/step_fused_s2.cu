@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "walls_nodes.cuh"
 
 namespace fdlbm {
 namespace {
@@ -249,6 +250,320 @@ __global__ void __launch_bounds__(NT, 2) k_step_fused_s2(const StepArgs<R> a)
     }
 }
 
+// ---------------------------------------------------------------- walled grids
+// The same sweep with Eq. 3.10 inside it, laid out like the FDLBM1 walls sweep
+// (step_fused_walls.cu): on a walled axis loads outside the domain read the
+// nearest row or column, stages B and C run at interior nodes only, and an
+// interior node whose upwind tap would leave the domain takes the central
+// difference.  The second sequence extrapolates three fields to the walls
+// (shift 0 for f^n and f^{n+1}, dt/2 with the force for the new f~), each from
+// the interior neighbour x_j:
+//   f^n      of a W/E wall column: by the x_j thread into the wall column's
+//            x-ring slot; of the S wall row: into the window slot of row 0 when
+//            stage A reaches row 1; of the N wall row: in place at stage A;
+//   f^{n+1}  as f* in the FDLBM1 walls sweep (x-ring slot, S-row window slot
+//            at stage B of row 1, N row from the window row ny-2);
+//   f~^{n+1} stored with x_j's own output at stage C (corners from the
+//            diagonal x_j with the W/E wall velocity).
+// f~+ of a wall node is its own (Eq. 2.20 on its f~), as in the staged path.
+template <class R, bool FORCE, int NT>
+struct SweepS2W {
+    const StepArgs<R> a;
+    Smem2<R, NT> &sm;
+    const int t, xc, gx;
+    const bool wx, wy;
+    const bool colB, colC;
+    const R mxc;
+    const Coeffs<R> c;
+    Stencil<R> sxp, sxn;  // x-differences at this column for sign + / -
+    R Pw[9][kRing2];
+    R Qw[9][kRing2];
+    R Sw[9][kRing2];
+    R cur[9], nxt[9];
+    int rA;  // logical row of cur (may lie outside [0, ny))
+    int y1;
+
+    __device__ int mem_row(int r) const
+    {
+        return wy ? min(max(r, 0), a.ny - 1) : wrap_index(r, a.ny);
+    }
+    __device__ void load(R *dst, int r) const
+    {
+        const size_t off = (size_t)mem_row(r) * a.pitch + gx;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[i] = __ldg(a.gin + i * a.plane + off);
+    }
+    __device__ void force_at(int r, R &Fx, R &Fy) const
+    {
+        Fx = Fy = R(0);
+        if (FORCE && a.force) {
+            const size_t fo = (size_t)mem_row(r) * a.pitch + gx;
+            Fx = __ldg(a.force + fo);
+            Fy = __ldg(a.force + a.plane + fo);
+        }
+    }
+    // wall velocities with constant indices only (see step_fused_walls.cu)
+    __device__ R uwx_side(bool west, int k) const
+    {
+        return west ? (k ? a.wall_u[FDLBM_WALL_W][1] : a.wall_u[FDLBM_WALL_W][0])
+                    : (k ? a.wall_u[FDLBM_WALL_E][1] : a.wall_u[FDLBM_WALL_E][0]);
+    }
+    __device__ R uwy_side(bool south, int k) const
+    {
+        return south ? (k ? a.wall_u[FDLBM_WALL_S][1] : a.wall_u[FDLBM_WALL_S][0])
+                     : (k ? a.wall_u[FDLBM_WALL_N][1] : a.wall_u[FDLBM_WALL_N][0]);
+    }
+    __device__ __forceinline__ R dx_of(int i, const R *rw, R v0) const
+    {
+        return apply_stencil(cx(i) > 0 ? sxp : sxn, cx(i), rw[t - 2], rw[t - 1], v0, rw[t + 1],
+                             rw[t + 2]);
+    }
+
+    template <int PH>
+    __device__ void row(bool load_next, bool doB, bool doC)
+    {
+        constexpr int p0 = PH;
+        constexpr int p1 = (PH + 4) % kRing2;
+        constexpr int p2 = (PH + 3) % kRing2;
+        constexpr int p3 = (PH + 2) % kRing2;
+        constexpr int p4 = (PH + 1) % kRing2;
+        const int r = rA;
+        if (load_next) load(nxt, r + 1);
+        const bool wallcol = wx && (xc == 0 || xc == a.nx - 1);
+        // ------------------------------------------------------------ A (row r)
+        {
+            R Fx, Fy, geq[9], F[9];
+            force_at(r, Fx, Fy);
+            node_maps<R, FORCE>(c, cur, Fx, Fy, c.half_dt, geq, F);
+            R fn[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const R neq = geq[i] - cur[i];
+                R p = cur[i] + c.b_phys * neq;  // Eq. 2.52, h = dt
+                R q = cur[i] + c.b_til * neq;   // Eq. 2.20
+                if (FORCE) {
+                    p += c.c_phys * F[i];
+                    q += c.c_til * F[i];
+                }
+                fn[i] = p;
+                Pw[i][p0] = p;
+                Qw[i][p0] = q;
+                if (xslot(i) >= 0) {
+                    sm.Q[p0][xslot(i)][t] = q;
+                    if (!wallcol) sm.P[p0][xslot(i)][t] = p;
+                }
+            }
+            // Eq. 3.10 for f^n of the wall column next to x_j (this column)
+            if (wx && (xc == 1 || xc == a.nx - 2)) {
+                R wv[9];
+                nee<R, false>(c, fn, R(0), R(0), R(0), uwx_side(xc == 1, 0), uwx_side(xc == 1, 1), wv);
+                const int tw = xc == 1 ? t - 1 : t + 1;
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (xslot(i) >= 0) sm.P[p0][xslot(i)][tw] = wv[i];
+            }
+            if (wy && r == 1) {  // the S wall row, into the window slot of row 0
+                R wv[9];
+                nee<R, false>(c, fn, R(0), R(0), R(0), uwy_side(true, 0), uwy_side(true, 1), wv);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Pw[i][p1] = wv[i];
+            } else if (wy && r == a.ny - 1) {  // the N wall row, from the window row ny-2
+                R pj[9], wv[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) pj[i] = Pw[i][p1];
+                nee<R, false>(c, pj, R(0), R(0), R(0), uwy_side(false, 0), uwy_side(false, 1), wv);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Pw[i][p0] = wv[i];
+            }
+        }
+        __syncthreads();
+        // ------------------------------------------------------------ B (row r-2)
+        if (doB) {
+            const int rb = r - 2;
+            const bool rowin = !wy || (rb >= 1 && rb <= a.ny - 2);
+            if (colB && rowin) {
+                const R myr = a.my[mem_row(rb)];
+                const R hx = c.h * mxc, hy = c.h * myr;  // h = dt
+                const Stencil<R> syp = (wy && rb == 1) ? a.stc : a.st;
+                const Stencil<R> syn = (wy && rb == a.ny - 2) ? a.stc : a.st;
+                R fb[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    R dP = R(0), fbar = Qw[i][p2];
+                    if (cx(i) != 0) {
+                        dP += mxc * dx_of(i, sm.P[p2][xslot(i)], Pw[i][p2]);
+                        fbar -= hx * dx_of(i, sm.Q[p2][xslot(i)], Qw[i][p2]);
+                    }
+                    if (cy(i) != 0) {
+                        const Stencil<R> &sy = cy(i) > 0 ? syp : syn;
+                        dP += myr * apply_stencil(sy, cy(i), Pw[i][p4], Pw[i][p3], Pw[i][p2],
+                                                  Pw[i][p1], Pw[i][p0]);
+                        fbar -= hy * apply_stencil(sy, cy(i), Qw[i][p4], Qw[i][p3], Qw[i][p2],
+                                                   Qw[i][p1], Qw[i][p0]);
+                    }
+                    sm.LN[p0][i][t] = -dP;
+                    fb[i] = fbar;
+                }
+                R Fx, Fy, geq[9], F[9];
+                force_at(rb, Fx, Fy);
+                node_maps<R, FORCE>(c, fb, Fx, Fy, c.half_h, geq, F);
+                R st[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    R v = fb[i] + c.b_star * (geq[i] - fb[i]);  // Eq. 2.52, h = dt
+                    if (FORCE) v += c.c_star * F[i];
+                    st[i] = v;
+                    Sw[i][p0] = v;
+                    if (xslot(i) >= 0) sm.S[p0][xslot(i)][t] = v;
+                }
+                if (wx && (xc == 1 || xc == a.nx - 2)) {
+                    R wv[9];
+                    nee<R, false>(c, st, R(0), R(0), R(0), uwx_side(xc == 1, 0), uwx_side(xc == 1, 1), wv);
+                    const int tw = xc == 1 ? t - 1 : t + 1;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        if (xslot(i) >= 0) sm.S[p0][xslot(i)][tw] = wv[i];
+                }
+                if (wy && rb == 1) {
+                    R wv[9];
+                    nee<R, false>(c, st, R(0), R(0), R(0), uwy_side(true, 0), uwy_side(true, 1), wv);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) Sw[i][p1] = wv[i];
+                }
+            } else if (colB && wy && rb == a.ny - 1) {
+                R sj[9], wv[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) sj[i] = Sw[i][p1];
+                nee<R, false>(c, sj, R(0), R(0), R(0), uwy_side(false, 0), uwy_side(false, 1), wv);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    Sw[i][p0] = wv[i];
+                    if (xslot(i) >= 0) sm.S[p0][xslot(i)][t] = wv[i];
+                    sm.LN[p0][i][t] = R(0);
+                }
+            } else {
+                // not evaluated here: finite zeros (wall columns keep the value
+                // their interior neighbour writes into the ring)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    Sw[i][p0] = R(0);
+                    if (xslot(i) >= 0 && !wallcol) sm.S[p0][xslot(i)][t] = R(0);
+                    sm.LN[p0][i][t] = R(0);
+                }
+            }
+        }
+        // ------------------------------------------------------------ C (row r-4)
+        if (doC) {
+            const int rc = r - 4;
+            const bool rowin = !wy || (rc >= 1 && rc <= a.ny - 2);
+            if (colC && rowin && rc < y1) {
+                const R myr = a.my[mem_row(rc)];
+                const Stencil<R> syp = (wy && rc == 1) ? a.stc : a.st;
+                const Stencil<R> syn = (wy && rc == a.ny - 2) ? a.stc : a.st;
+                R out[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    R dS = R(0);
+                    if (cx(i) != 0) dS += mxc * dx_of(i, sm.S[p2][xslot(i)], Sw[i][p2]);
+                    if (cy(i) != 0)
+                        dS += myr * apply_stencil(cy(i) > 0 ? syp : syn, cy(i), Sw[i][p4], Sw[i][p3],
+                                                  Sw[i][p2], Sw[i][p1], Sw[i][p0]);
+                    out[i] = Qw[i][p4] + c.half_dt * (sm.LN[p2][i][t] - dS);
+                }
+                const int my_row = mem_row(rc);
+                auto put = [&](int x, int y, const R *v) {
+                    const size_t o = (size_t)y * a.pitch + x;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) a.gout[i * a.plane + o] = v[i];
+                };
+                put(gx, my_row, out);
+                const bool bw = wy && rc == 1, tw = wy && rc == a.ny - 2;
+                const bool lw = wx && xc == 1, rw = wx && xc == a.nx - 2;
+                if (bw || tw || lw || rw) {
+                    R Fx, Fy;
+                    force_at(rc, Fx, Fy);
+                    R wv[9];
+                    if (bw) {
+                        nee<R, FORCE>(c, out, Fx, Fy, c.half_dt, uwy_side(true, 0), uwy_side(true, 1), wv);
+                        put(gx, 0, wv);
+                    }
+                    if (tw) {
+                        nee<R, FORCE>(c, out, Fx, Fy, c.half_dt, uwy_side(false, 0), uwy_side(false, 1), wv);
+                        put(gx, a.ny - 1, wv);
+                    }
+                    if (lw || rw) {
+                        const int xw = lw ? 0 : a.nx - 1;
+                        nee<R, FORCE>(c, out, Fx, Fy, c.half_dt, uwx_side(lw, 0), uwx_side(lw, 1), wv);
+                        put(xw, my_row, wv);
+                        if (bw) put(xw, 0, wv);
+                        if (tw) put(xw, a.ny - 1, wv);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cur[i] = nxt[i];
+        ++rA;
+    }
+};
+
+template <class R, bool FORCE, int NT>
+__global__ void __launch_bounds__(NT, 2) k_step_fused_s2_walls(const StepArgs<R> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem2<R, NT> &sm = *reinterpret_cast<Smem2<R, NT> *>(smem_raw);
+    const int t = threadIdx.x;
+    const int x0 = blockIdx.x * (NT - 2 * kHalo2);
+    const int y0 = blockIdx.y * a.rows;
+    if (y0 >= a.ny) return;  // uniform over the block
+    const int xc = x0 - kHalo2 + t;
+    const int y1 = min(y0 + a.rows, a.ny);
+    const bool wx = a.bc_x == FDLBM_WALL, wy = a.bc_y == FDLBM_WALL;
+    const bool inside = !wx || (xc >= 0 && xc < a.nx);
+    const int gx = wx ? min(max(xc, 0), a.nx - 1) : wrap_index(xc, a.nx);
+    const bool colint = !wx || (xc >= 1 && xc <= a.nx - 2);
+    const bool colB = (t >= 2) && (t < NT - 2) && inside && colint;
+    const bool colC = (t >= kHalo2) && (t < NT - kHalo2) && xc < a.nx && inside && colint;
+    SweepS2W<R, FORCE, NT> sw{a,
+                              sm,
+                              t,
+                              xc,
+                              gx,
+                              wx,
+                              wy,
+                              colB,
+                              colC,
+                              a.mx[gx],
+                              a.c,
+                              (wx && xc == 1) ? a.stc : a.st,
+                              (wx && xc == a.nx - 2) ? a.stc : a.st};
+    sw.y1 = y1;
+    sw.rA = y0 - kHalo2;
+    sw.load(sw.cur, sw.rA);
+    const int iters = (y1 - y0) + 2 * kHalo2;
+    for (int k = 0; k < iters; k += kRing2) {
+        sw.template row<0>(k + 1 < iters, k >= 4, k >= 8);
+        if (k + 1 < iters) sw.template row<1>(k + 2 < iters, k + 1 >= 4, k + 1 >= 8);
+        if (k + 2 < iters) sw.template row<2>(k + 3 < iters, k + 2 >= 4, k + 2 >= 8);
+        if (k + 3 < iters) sw.template row<3>(k + 4 < iters, k + 3 >= 4, k + 3 >= 8);
+        if (k + 4 < iters) sw.template row<4>(k + 5 < iters, k + 4 >= 4, k + 4 >= 8);
+    }
+}
+
+template <class R, bool FORCE>
+cudaError_t launch_s2_walls(const StepArgs<R> &a, cudaStream_t s)
+{
+    constexpr int NT = 128;
+    constexpr int W = NT - 2 * kHalo2;
+    constexpr size_t smem = sizeof(Smem2<R, NT>);
+    cudaError_t e = cudaFuncSetAttribute(k_step_fused_s2_walls<R, FORCE, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((a.nx + W - 1) / W, (a.ny + a.rows - 1) / a.rows);
+    k_step_fused_s2_walls<R, FORCE, NT><<<grid, NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <class R, bool FORCE>
 cudaError_t launch_s2(const StepArgs<R> &a, cudaStream_t s)
 {
@@ -268,6 +583,8 @@ cudaError_t launch_s2(const StepArgs<R> &a, cudaStream_t s)
 template <class R>
 cudaError_t launch_fused_s2(const StepArgs<R> &a, cudaStream_t s)
 {
+    if (a.bc_x == FDLBM_WALL || a.bc_y == FDLBM_WALL)
+        return a.force ? launch_s2_walls<R, true>(a, s) : launch_s2_walls<R, false>(a, s);
     return a.force ? launch_s2<R, true>(a, s) : launch_s2<R, false>(a, s);
 }
 

@@ -105,17 +105,19 @@ def test_workspace_and_validation_without_gpu(B):
     assert n64 > n32 >= 2 * 9 * 64 * 64 * 4
     o.path = B.PATH_STAGED
     assert L.fdlbm_workspace_bytes(ctypes.byref(grid), ctypes.byref(o)) > n32
-    # walled grids take the fused path (Eq. 3.10 inside the sweep); T2S2-FDLBM2
-    # does not
+    # walled grids take the fused path (Eq. 3.10 inside the sweep), for both
+    # schemes; the fused variants of T2S2-FDLBM1 do not run T2S2-FDLBM2
     wa = I.wall_axis(20, 0.0, 1.0)
     wgrid, keep2 = B.make_grid(xa, wa)
     o.path = B.PATH_FUSED
     assert L.fdlbm_workspace_bytes(ctypes.byref(wgrid), ctypes.byref(o)) > 0
     o.scheme = B.SCHEME_T2S2_2
-    assert L.fdlbm_workspace_bytes(ctypes.byref(wgrid), ctypes.byref(o)) == 0
+    assert L.fdlbm_workspace_bytes(ctypes.byref(wgrid), ctypes.byref(o)) > 0
     h = ctypes.c_void_p()
-    assert L.fdlbm_create(ctypes.byref(wgrid), None, 0.01, 0.5, 0.1, ctypes.byref(o),
+    o.variant = B.VARIANT_WARP
+    assert L.fdlbm_create(ctypes.byref(grid), None, 0.01, 0.5, 0.1, ctypes.byref(o),
                           ctypes.byref(h)) == -5
+    o.variant = B.VARIANT_AUTO
     # invalid arguments are rejected before any device work
     L.fdlbm_default_opts(ctypes.byref(o))
     for nu, cfl, blend in ((0.0, 0.5, 0.1), (0.01, -1.0, 0.1), (0.01, 0.5, 1.5)):

@@ -263,6 +263,34 @@ def test_fused_walls_match_oracle(precision, tol, bcx, bcy, nx, ny, rows):
     assert err <= tol
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 1e-6)])
+@pytest.mark.parametrize("bcx,bcy,nx,ny,rows", _WALL_CASES)
+def test_fused_walls_scheme2_match_oracle(precision, tol, bcx, bcy, nx, ny, rows):
+    """The fused T2S2-FDLBM2 sweep with Eq. 3.10 inside it (f^n, f^{n+1} and the
+    new f~ extrapolated to the walls) on the walled grids of the T2S2-FDLBM1
+    walls test: moving walls on every side, a force field, random state, 12
+    steps against the oracle's second sequence."""
+    xa = _axis(bcx, nx, 81, 1.0)
+    ya = _axis(bcy, ny, 82, 0.8)
+    rng = np.random.default_rng(nx * 1000 + ny + 7)
+    force = 1e-3 * rng.uniform(-1, 1, size=(2, ny, nx))
+    wall_u = [tuple(0.05 * rng.uniform(-1, 1, size=2)) for _ in range(4)]
+    s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, precision=precision, has_force=True,
+              wall_u=wall_u, rows_per_cta=rows, path="fused", scheme=2)
+    assert s.describe.startswith("fused-scheme2"), s.describe
+    assert s.kernels_per_step == 1
+    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force, wall_u=wall_u, scheme=2)
+    s.set_force(force)
+    _init_both(s, o, I.random_fields(nx, ny, 190 + nx))
+    for n in (1, 11):
+        s.step(n)
+        o.step(n)
+    s.sync()
+    err = rel(s.get_state(), o.f)
+    print(f"{s.describe} {bcx}/{bcy} {nx}x{ny}: rel L2(f~) = {err:.3e}")
+    assert err <= tol
+
+
 def test_variant_not_applicable_is_rejected():
     xa = I.periodic_axis(130, 0.0, 1.0)   # 130 % 4 != 0: no 16-byte FP32 row pieces
     with pytest.raises(Exception, match="EUNSUPPORTED"):
@@ -349,15 +377,22 @@ def test_t2s2_fdlbm2_fused_ragged(precision, tol, nx, ny, rows, force):
     assert err <= tol
 
 
-def test_t2s2_fdlbm2_channel_walls_fp64():
-    """T2S2-FDLBM2 with Eq. 3.10 walls on the stretched channel grid of Eq. 3.9."""
+@pytest.mark.parametrize("precision,tol,path", [("fp64", FP64_TOL, "auto"), ("fp64", FP64_TOL, "fused"),
+                                                ("fp32", 2e-6, "auto")])
+def test_t2s2_fdlbm2_channel_walls(precision, tol, path):
+    """T2S2-FDLBM2 with Eq. 3.10 walls on the stretched channel grid of Eq. 3.9
+    (FP64: the staged kernels by default, and the fused sweep; FP32: the fused
+    sweep by default)."""
     F = 0.01
     nu = math.sqrt(F / 80.0)
     xa = I.periodic_axis(10, 0.0, 1.0)
     ya = I.tanh_axis(20, 1.5)
     force = np.zeros((2, ya.n, xa.n))
     force[0] = F
-    s = FDLBM(xa, ya, nu=nu, cfl=0.5, blend=0.1, has_force=True, scheme=2)
+    s = FDLBM(xa, ya, nu=nu, cfl=0.5, blend=0.1, has_force=True, scheme=2, precision=precision,
+              path=path)
+    assert s.describe.startswith("staged-scheme2" if (precision, path) == ("fp64", "auto")
+                                 else "fused-scheme2"), s.describe
     o = O.Oracle(xa, ya, nu=nu, dt=s.dt, beta=0.1, force=force, scheme=2)
     s.set_force(force)
     one = np.ones((ya.n, xa.n))
@@ -365,7 +400,7 @@ def test_t2s2_fdlbm2_channel_walls_fp64():
     o.init_fields(one, 0 * one, 0 * one)
     s.step(200)
     o.step(200)
-    assert rel(s.get_state(), o.f) <= FP64_TOL
+    assert rel(s.get_state(), o.f) <= tol
 
 
 def test_t1s2_special_case_fp64():
