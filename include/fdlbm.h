@@ -273,14 +273,15 @@ long long fdlbm_batch_cells(fdlbm_batch_t b);        /* nodes of all cases */
 /* Advance every case by n steps (asynchronous on the batch stream). */
 fdlbm_status fdlbm_batch_step(fdlbm_batch_t b, int n);
 /* How fdlbm_batch_step advances the cases:
- *  FUSED       one launch per step of the fused sweep with Eq. 3.10 inside it,
- *              over tiles of every case (FP32 and T2S2-FDLBM1 only; the default
- *              where it applies);
+ *  FUSED       the fused sweeps with Eq. 3.10 inside them over tiles of every
+ *              case: one launch per step for the T2S2-FDLBM1 cases and one for
+ *              the T2S2-FDLBM2 cases (FP32 batches; the default there);
  *  STAGED      one launch per stage and step of the staged kernels (the default
  *              otherwise);
- *  PERSISTENT  the staged stages in one cooperative launch for all the steps of
- *              a call (or of a graph replay), separated by a grid-wide barrier
- *              with bounded waits (a timeout sets every case's error flag, which
+ *  PERSISTENT  one cooperative launch for all the steps of a call (or of a graph
+ *              replay): the fused sweep with one grid barrier per step where
+ *              every case is T2S2-FDLBM1 in FP32, else the staged stages
+ *              separated by grid barriers; every barrier wait is bounded (a timeout sets every case's error flag, which
  *              fdlbm_sync / fdlbm_reduce of a case report).
  * fdlbm_batch_set_mode synchronises the batch stream, drops a captured graph and
  * rebuilds the tables with the mode's default tile shape (no autotuning);

@@ -75,9 +75,15 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
 {
     const int n = (int)b->cases.size();
     std::vector<int> blk_start(n), tiles_x(n), wall_start(n), blk_case;
-    int total_wall = 0, total_blocks = 0;
+    int total_wall = 0, total_blocks = 0, blocks_s1 = 0;
     bool any2 = false;
-    for (int c = 0; c < n; ++c) {
+    // the tiles of T2S2-FDLBM1 cases first, then those of T2S2-FDLBM2 cases (the
+    // fused batch runs each group with its own kernel)
+    std::vector<int> order;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int c = 0; c < n; ++c)
+            if ((b->cases[c]->scheme == FDLBM_SCHEME_T2S2_2) == (pass == 1)) order.push_back(c);
+    for (int c : order) {
         fdlbm_ctx *h = b->cases[c];
         int tx, ty;
         if (fused_rows > 0) {
@@ -92,6 +98,7 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
         blk_start[c] = total_blocks;
         tiles_x[c] = tx;
         total_blocks += tx * ty;
+        if (h->scheme != FDLBM_SCHEME_T2S2_2) blocks_s1 = total_blocks;
         blk_case.insert(blk_case.end(), (size_t)tx * ty, c);
         wall_start[c] = total_wall;
         const bool wy = h->bc_y == FDLBM_WALL, wx = h->bc_x == FDLBM_WALL;
@@ -146,16 +153,20 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
     b->tab.total_blocks = total_blocks;
     b->tab.total_wall = total_wall;
     b->tab.any_scheme2 = any2;
+    b->tab.blocks_s1 = blocks_s1;
     b->blk = blk;
     b->fused_rows = fused_rows;
     return FDLBM_OK;
 }
 
-// Every case T2S2-FDLBM1 in FP32: the fused sweep applies (FP64 walled cases are
-// bound by the FP64 units, where the staged kernels do better).
-bool fused_eligible(const fdlbm_batch_ctx *b)
+// FP32: the fused sweeps apply, one kernel for the T2S2-FDLBM1 cases and one
+// for the T2S2-FDLBM2 cases (FP64 walled cases are bound by the FP64 units,
+// where the staged kernels do better).
+bool fused_eligible(const fdlbm_batch_ctx *b) { return b->precision == FDLBM_FP32_DEV; }
+
+// The persistent fused sweep runs T2S2-FDLBM1 cases only.
+bool all_scheme1(const fdlbm_batch_ctx *b)
 {
-    if (b->precision != FDLBM_FP32_DEV) return false;
     for (const fdlbm_ctx *h : b->cases)
         if (h->scheme != FDLBM_SCHEME_T2S2_1) return false;
     return true;
@@ -166,7 +177,8 @@ bool fused_eligible(const fdlbm_batch_ctx *b)
 // otherwise.
 bool uses_fused_sweep(const fdlbm_batch_ctx *b)
 {
-    return b->mode == FDLBM_BATCH_FUSED || (b->mode == FDLBM_BATCH_PERSISTENT && fused_eligible(b));
+    return b->mode == FDLBM_BATCH_FUSED ||
+           (b->mode == FDLBM_BATCH_PERSISTENT && fused_eligible(b) && all_scheme1(b));
 }
 
 // Tile height of the fused batch: minimise (waves) x (rows + 8) over the tiles
@@ -200,10 +212,17 @@ cudaError_t launch_steps(fdlbm_batch_ctx *b, int parity, int n)
 {
     const bool f32 = b->precision == FDLBM_FP32_DEV;
     if (b->mode == FDLBM_BATCH_FUSED) {
+        const int n1 = b->tab.blocks_s1, n2 = b->tab.total_blocks - n1;
         cudaError_t e = cudaSuccess;
-        for (int k = 0; k < n && e == cudaSuccess; ++k)
-            e = f32 ? launch_batched_fused<float>(b->tab, (parity + k) & 1, b->stream)
-                    : launch_batched_fused<double>(b->tab, (parity + k) & 1, b->stream);
+        for (int k = 0; k < n && e == cudaSuccess; ++k) {
+            const int p = (parity + k) & 1;
+            if (n1 > 0)
+                e = f32 ? launch_batched_fused<float>(b->tab, p, n1, b->stream)
+                        : launch_batched_fused<double>(b->tab, p, n1, b->stream);
+            if (e == cudaSuccess && n2 > 0)
+                e = f32 ? launch_batched_fused_s2<float>(b->tab, p, n1, n2, b->stream)
+                        : launch_batched_fused_s2<double>(b->tab, p, n1, n2, b->stream);
+        }
         return e;
     }
     if (b->mode == FDLBM_BATCH_PERSISTENT && b->fused_rows > 0)  // the fused sweep, persistent
@@ -529,7 +548,7 @@ fdlbm_status fdlbm_batch_set_mode(fdlbm_batch_t b, int mode)
     if (mode != FDLBM_BATCH_FUSED && mode != FDLBM_BATCH_STAGED && mode != FDLBM_BATCH_PERSISTENT)
         return bfail(b, FDLBM_EINVAL, "batch set_mode: unknown mode");
     if (mode == FDLBM_BATCH_FUSED && !fused_eligible(b))
-        return bfail(b, FDLBM_EUNSUPPORTED, "batch set_mode: the fused sweep needs FP32 and T2S2-FDLBM1");
+        return bfail(b, FDLBM_EUNSUPPORTED, "batch set_mode: the fused sweeps need FP32");
     fdlbm_status st = fdlbm_batch_sync(b);
     if (st != FDLBM_OK) return st;
     drop_graph(b);
@@ -586,8 +605,9 @@ const char *fdlbm_batch_describe(fdlbm_batch_t b)
     std::ostringstream os;
     const char *prec = b->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64";
     if (b->mode == FDLBM_BATCH_FUSED) {
+        const int n1 = b->tab.blocks_s1, n2 = b->tab.total_blocks - n1;
         os << "batched-fused " << prec << " cases=" << b->cases.size() << " rows=" << b->fused_rows
-           << " graph_steps=" << b->graph_steps << " launches_per_step=1";
+           << " graph_steps=" << b->graph_steps << " launches_per_step=" << (n1 > 0) + (n2 > 0);
     } else if (b->mode == FDLBM_BATCH_PERSISTENT && b->fused_rows > 0) {
         os << "batched-persistent-fused " << prec << " cases=" << b->cases.size()
            << " rows=" << b->fused_rows << " graph_steps=" << b->graph_steps

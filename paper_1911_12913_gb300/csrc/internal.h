@@ -42,6 +42,7 @@ struct BatchTables {
     const int *wall_start; // [ncases]
     int ncases, total_blocks, total_wall;
     bool any_scheme2;
+    int blocks_s1;         // fused tables: tiles of T2S2-FDLBM1 cases, which come first
 };
 
 struct Layout {
@@ -107,6 +108,9 @@ template <class R>
 cudaError_t launch_fused_s2(const StepArgs<R> &a, cudaStream_t s);
 template <class R>
 int fused_s2_blocks_per_sm();
+template <class R>
+cudaError_t launch_batched_fused_s2(const BatchTables &t, int parity, int blk_off, int nblocks,
+                                    cudaStream_t s);
 // step_fused_tma.cu (scalar sweep with bulk-copy row loads)
 template <class R>
 bool fused_tma_ok(int nx, int ny);
@@ -138,7 +142,7 @@ cudaError_t launch_fused_walls(const StepArgs<R> &a, cudaStream_t s);
 template <class R>
 int fused_walls_blocks_per_sm();
 template <class R>
-cudaError_t launch_batched_fused(const BatchTables &t, int parity, cudaStream_t s);
+cudaError_t launch_batched_fused(const BatchTables &t, int parity, int nblocks, cudaStream_t s);
 int fused_tile_width_walls();
 // step_staged.cu
 template <class R>

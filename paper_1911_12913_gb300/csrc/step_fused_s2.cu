@@ -507,15 +507,12 @@ struct SweepS2W {
     }
 };
 
+// One tile of the walls sweep: output columns x0 .. x0 + NT - 9, rows y0 .. y0 +
+// a.rows - 1 (periodic axes wrap, walled axes clamp).
 template <class R, bool FORCE, int NT>
-__global__ void __launch_bounds__(NT, 2) k_step_fused_s2_walls(const StepArgs<R> a)
+__device__ __forceinline__ void sweep_tile_s2(const StepArgs<R> &a, Smem2<R, NT> &sm, int x0, int y0)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem2<R, NT> &sm = *reinterpret_cast<Smem2<R, NT> *>(smem_raw);
     const int t = threadIdx.x;
-    const int x0 = blockIdx.x * (NT - 2 * kHalo2);
-    const int y0 = blockIdx.y * a.rows;
-    if (y0 >= a.ny) return;  // uniform over the block
     const int xc = x0 - kHalo2 + t;
     const int y1 = min(y0 + a.rows, a.ny);
     const bool wx = a.bc_x == FDLBM_WALL, wy = a.bc_y == FDLBM_WALL;
@@ -548,6 +545,44 @@ __global__ void __launch_bounds__(NT, 2) k_step_fused_s2_walls(const StepArgs<R>
         if (k + 3 < iters) sw.template row<3>(k + 4 < iters, k + 3 >= 4, k + 3 >= 8);
         if (k + 4 < iters) sw.template row<4>(k + 5 < iters, k + 4 >= 4, k + 4 >= 8);
     }
+}
+
+template <class R, bool FORCE, int NT>
+__global__ void __launch_bounds__(NT, 2) k_step_fused_s2_walls(const StepArgs<R> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem2<R, NT> &sm = *reinterpret_cast<Smem2<R, NT> *>(smem_raw);
+    const int y0 = blockIdx.y * a.rows;
+    if (y0 >= a.ny) return;  // uniform over the block
+    sweep_tile_s2<R, FORCE, NT>(a, sm, blockIdx.x * (NT - 2 * kHalo2), y0);
+}
+
+// Batched: block b is tile (b + blk_off - blk_start[c]) of case c =
+// blk_case[b + blk_off]; the T2S2-FDLBM2 cases' tiles follow those of the
+// T2S2-FDLBM1 cases in the batch's tables, from blk_off on.  The case's
+// arguments are copied into shared memory first.
+template <class R, int NT>
+__global__ void __launch_bounds__(NT, 2)
+    kb_step_fused_s2(const StepArgs<R> *cases, const int *blk_case, const int *blk_start,
+                     const int *strips, int blk_off)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem2<R, NT> &sm = *reinterpret_cast<Smem2<R, NT> *>(smem_raw);
+    __shared__ __align__(16) unsigned char abuf[sizeof(StepArgs<R>)];
+    static_assert(sizeof(StepArgs<R>) % 4 == 0, "argument block is copied as 32-bit words");
+    const int b = blockIdx.x + blk_off;
+    const int c = blk_case[b];
+    {
+        const int *src = reinterpret_cast<const int *>(cases + c);
+        int *dst = reinterpret_cast<int *>(abuf);
+        for (int q = threadIdx.x; q < (int)(sizeof(StepArgs<R>) / 4); q += blockDim.x) dst[q] = src[q];
+    }
+    __syncthreads();
+    const StepArgs<R> &a = *reinterpret_cast<const StepArgs<R> *>(abuf);
+    const int lb = b - blk_start[c], ns = strips[c];
+    const int y0 = (lb / ns) * a.rows;
+    if (y0 >= a.ny) return;  // uniform over the block
+    sweep_tile_s2<R, true, NT>(a, sm, (lb % ns) * (NT - 2 * kHalo2), y0);
 }
 
 template <class R, bool FORCE>
@@ -601,6 +636,25 @@ int fused_s2_blocks_per_sm()
     return n;
 }
 
+// The T2S2-FDLBM2 tiles of a batch (nblocks of them, from table entry blk_off).
+template <class R>
+cudaError_t launch_batched_fused_s2(const BatchTables &t, int parity, int blk_off, int nblocks,
+                                    cudaStream_t s)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    constexpr int NT = 128;
+    constexpr size_t smem = sizeof(Smem2<R, NT>);
+    cudaError_t e = cudaFuncSetAttribute(kb_step_fused_s2<R, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kb_step_fused_s2<R, NT><<<nblocks, NT, smem, s>>>(
+        static_cast<const StepArgs<R> *>(t.args[parity]), t.blk_case, t.blk_start, t.tiles_x,
+        blk_off);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_batched_fused_s2<float>(const BatchTables &, int, int, int, cudaStream_t);
+template cudaError_t launch_batched_fused_s2<double>(const BatchTables &, int, int, int, cudaStream_t);
 template cudaError_t launch_fused_s2<float>(const StepArgs<float> &, cudaStream_t);
 template cudaError_t launch_fused_s2<double>(const StepArgs<double> &, cudaStream_t);
 template int fused_s2_blocks_per_sm<float>();

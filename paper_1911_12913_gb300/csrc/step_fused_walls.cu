@@ -486,15 +486,17 @@ int fused_walls_blocks_per_sm()
     return n;
 }
 
-// One step of every case of a batch (all T2S2-FDLBM1): one launch.
+// One step of the T2S2-FDLBM1 cases of a batch (the first nblocks tiles of
+// its tables): one launch.
 template <class R>
-cudaError_t launch_batched_fused(const BatchTables &t, int parity, cudaStream_t s)
+cudaError_t launch_batched_fused(const BatchTables &t, int parity, int nblocks, cudaStream_t s)
 {
+    if (nblocks <= 0) return cudaSuccess;
     constexpr size_t smem = sizeof(Smem<R>);
     cudaError_t e = cudaFuncSetAttribute(kb_step_fused_walls<R>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kb_step_fused_walls<R><<<t.total_blocks, NT, smem, s>>>(
+    kb_step_fused_walls<R><<<nblocks, NT, smem, s>>>(
         static_cast<const StepArgs<R> *>(t.args[parity]), t.blk_case, t.blk_start, t.tiles_x);
     return cudaGetLastError();
 }
@@ -548,8 +550,8 @@ template cudaError_t launch_persistent_fused<float>(const BatchTables &, void *,
 template cudaError_t launch_persistent_fused<double>(const BatchTables &, void *, int, int,
                                                      cudaStream_t, unsigned);
 
-template cudaError_t launch_batched_fused<float>(const BatchTables &, int, cudaStream_t);
-template cudaError_t launch_batched_fused<double>(const BatchTables &, int, cudaStream_t);
+template cudaError_t launch_batched_fused<float>(const BatchTables &, int, int, cudaStream_t);
+template cudaError_t launch_batched_fused<double>(const BatchTables &, int, int, cudaStream_t);
 template cudaError_t launch_fused_walls<float>(const StepArgs<float> &, cudaStream_t);
 template cudaError_t launch_fused_walls<double>(const StepArgs<double> &, cudaStream_t);
 template int fused_walls_blocks_per_sm<float>();

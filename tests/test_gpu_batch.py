@@ -90,12 +90,13 @@ def test_mixed_batch_matches_oracle(precision, tol, autotune, mode):
     kernels, and the persistent cooperative launch (of the fused sweep where
     it applies, one grid barrier per step; of the staged stages otherwise)."""
     cases = _mixed_cases()
-    if mode in ("fused", "persistent-fused"):
+    if mode == "persistent-fused":
         cases = [cs for cs in cases if cs.get("scheme", 1) == 1]
     batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=autotune,
                        mode="persistent" if mode == "persistent-fused" else mode)
     want = {"fused": "batched-fused", "staged": "batched-staged",
-            "persistent": "batched-persistent ", "auto": "batched-staged",
+            "persistent": "batched-persistent ",
+            "auto": "batched-fused" if precision == "fp32" else "batched-staged",
             "persistent-fused": "batched-persistent-fused"}[mode]
     assert batch.describe.startswith(want), batch.describe
     oracles = _setup(batch, cases)
@@ -112,14 +113,16 @@ def test_mixed_batch_matches_oracle(precision, tol, autotune, mode):
     print(batch.describe)
 
 
-def test_batch_fused_mode_needs_fp32_scheme1():
+def test_batch_fused_mode_needs_fp32():
+    """FUSED runs FP32 batches, with one launch per step for the T2S2-FDLBM1
+    cases and one for the T2S2-FDLBM2 cases; FP64 batches stay staged."""
     cases = _mixed_cases()
     with pytest.raises(Exception, match="EUNSUPPORTED"):
-        FDLBMBatch(cases, precision="fp32", graph_steps=0, autotune=False, mode="fused")
-    with pytest.raises(Exception, match="EUNSUPPORTED"):
-        FDLBMBatch(cases[:5], precision="fp64", graph_steps=0, autotune=False, mode="fused")
+        FDLBMBatch(cases, precision="fp64", graph_steps=0, autotune=False, mode="fused")
     b = FDLBMBatch(cases[:5], precision="fp32", graph_steps=0, autotune=False)
-    assert b.describe.startswith("batched-fused"), b.describe
+    assert b.describe.startswith("batched-fused") and "launches_per_step=1" in b.describe, b.describe
+    b = FDLBMBatch(cases, precision="fp32", graph_steps=0, autotune=False)
+    assert b.describe.startswith("batched-fused") and "launches_per_step=2" in b.describe, b.describe
 
 
 def test_batch_case_restrictions():
