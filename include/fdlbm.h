@@ -234,6 +234,15 @@ fdlbm_status fdlbm_adjoint_step(fdlbm_t h, const void *state_n, const void *lam_
  * (if not NULL). */
 fdlbm_status fdlbm_moments_vjp(fdlbm_t h, const void *state, const double *du, void *lam,
                                double *dforce);
+/* Cotangents of the fields of an equilibrium initialisation
+ * (fdlbm_init_fields(rho, ux, uy, NULL), Eq. 3.2 or the incompressible
+ * equilibrium): given the cotangent lam (storage layout, device) of the state
+ * that those fields (device, FP64, [ny][nx] each) produce, ADD their
+ * cotangents to drho (may be NULL), dux and duy (device, FP64, [ny][nx]).
+ * With fdlbm_adjoint_step this differentiates a rollout with respect to its
+ * initial density and velocity.  Asynchronous on the stream. */
+fdlbm_status fdlbm_init_vjp(fdlbm_t h, const double *rho, const double *ux, const double *uy,
+                            const void *lam, double *drho, double *dux, double *duy);
 
 /* ---------------------------------------------------------------------------
  * Batched mode: many independent cases (uneven sizes, walls, forces, Reynolds

@@ -805,6 +805,22 @@ fdlbm_status fdlbm_moments_vjp(fdlbm_t h, const void *state, const double *du, v
     return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "moments_vjp");
 }
 
+fdlbm_status fdlbm_init_vjp(fdlbm_t h, const double *rho, const double *ux, const double *uy,
+                            const void *lam, double *drho, double *dux, double *duy)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (!rho || !ux || !uy || !lam || !dux || !duy)
+        return fail(h, FDLBM_EINVAL, "init_vjp: NULL buffer");
+    cudaError_t e;
+    if (h->precision == FDLBM_FP32_DEV)
+        e = launch_init_vjp<float>(step_args<float>(h), rho, ux, uy, static_cast<const float *>(lam),
+                                   drho, dux, duy, h->stream);
+    else
+        e = launch_init_vjp<double>(step_args<double>(h), rho, ux, uy,
+                                    static_cast<const double *>(lam), drho, dux, duy, h->stream);
+    return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "init_vjp");
+}
+
 const char *fdlbm_last_error(fdlbm_t h) { return h ? h->err.c_str() : "NULL handle"; }
 
 const char *fdlbm_describe(fdlbm_t h)

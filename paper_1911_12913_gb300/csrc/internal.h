@@ -168,6 +168,10 @@ template <class R>
 cudaError_t launch_adjoint(const StepArgs<R> &a, const R *lam_next, R *lam_prev, R *P, R *lgs,
                            double *fB, double *dforce, cudaStream_t s);
 template <class R>
+cudaError_t launch_init_vjp(const StepArgs<R> &a, const double *rho, const double *ux,
+                            const double *uy, const R *lam, double *drho, double *dux, double *duy,
+                            cudaStream_t s);
+template <class R>
 cudaError_t launch_moments_vjp(const StepArgs<R> &a, const double *du, R *lam, double *dforce,
                                cudaStream_t s);
 // fields.cu

@@ -236,6 +236,19 @@ class FDLBM:
                                         dforce.data_ptr() if dforce is not None else None)
         _check(self._L, self._h, rc, "adjoint_step")
 
+    def init_vjp(self, rho, ux, uy, lam, drho, dux, duy):
+        """Add the cotangents of the fields of an equilibrium initialisation to
+        drho (may be None), dux, duy, given the cotangent ``lam`` (storage
+        layout) of the state they produced (all CUDA tensors)."""
+        def ptr(t):
+            return None if t is None else t.data_ptr()
+        for t in (rho, ux, uy, drho, dux, duy):
+            assert t is None or (t.dtype == torch.float64 and t.is_contiguous() and t.is_cuda)
+        rc = self._L.fdlbm_init_vjp(self._h, ptr(rho), ptr(ux), ptr(uy), ptr(lam), ptr(drho),
+                                    ptr(dux), ptr(duy))
+        _check(self._L, self._h, rc, "init_vjp")
+        return self
+
     def moments_vjp(self, state, du, lam, dforce=None):
         du = du.detach().to(torch.float64).contiguous()
         rc = self._L.fdlbm_moments_vjp(self._h, state.data_ptr(), du.data_ptr(), lam.data_ptr(),
