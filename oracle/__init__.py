@@ -172,8 +172,9 @@ class Oracle:
 
     ``A``: the intermediate time fraction (0.5: T2S2-FDLBM1, 0: T1S2-FDLBM).
     ``beta``: upwind weight of the mixed difference.  ``scheme=2`` selects
-    T2S2-FDLBM2 (Eq. 5.23; pinned by its time order and invariants, parity
-    with the paper's printed FDLBM2 errors unpinned).  Walled axes use Eq. 3.10
+    T2S2-FDLBM2 (Eq. 5.23; pinned by the grid-convergence table of Sec. 3A,
+    its time order and invariants; parity with the paper's large-CFL FDLBM2
+    errors unpinned).  Walled axes use Eq. 3.10
     (parity with the paper's Poiseuille error magnitudes unpinned).  ``incomp=True`` selects the incompressible
     equilibrium of He and Luo with reference density ``rho0`` (velocity from
     rho0 u = sum xi f, forcing term at rho0).

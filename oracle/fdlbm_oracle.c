@@ -437,9 +437,10 @@ static void step_scheme1(const oracle_cfg *c, real_t *f, work_t *w)
 }
 
 /* One T2S2-FDLBM2 step (Sec. 2D, second sequence; Eq. 5.23, h = dt).
- * Pinned by its second-order time convergence and the exact invariants; parity
- * with the paper's printed FDLBM2 errors (Table 4) unpinned: no reading of the
- * sequence tried reproduces them. */
+ * Pinned by the printed FDLBM2 errors of the grid-convergence table of Sec. 3A
+ * (small time step), its second-order time convergence and the exact
+ * invariants; parity with the printed FDLBM2 errors at large CFL (Table 4)
+ * unpinned: no reading of the sequence tried reproduces them. */
 static void step_scheme2(const oracle_cfg *c, real_t *f, work_t *w)
 {
     size_t N = (size_t)c->nx * c->ny;
