@@ -133,15 +133,16 @@ def test_rollout_gradient_matches_central_differences():
         assert abs(fd - ad) <= 1e-6 * abs(fd), (k, fd, ad)
 
 
-@pytest.mark.parametrize("eq", ["standard", "incompressible"])
-def test_init_vjp_dot_product(eq):
+@pytest.mark.parametrize("eq,precision,tol", [("standard", "fp64", 1e-9), ("incompressible", "fp64", 1e-9),
+                                              ("standard", "fp32", 1e-4)])
+def test_init_vjp_dot_product(eq, precision, tol):
     """fdlbm_init_vjp is the transpose of the equilibrium initialisation:
     <J v, lam> = <v, J^T lam> with J v from central differences of
     fdlbm_init_fields (FP64, 16 x 12, random fields and directions)."""
     nx, ny = 16, 12
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.periodic_axis(ny, 0.0, 0.8)
-    s = FDLBM(xa, ya, nu=NU, cfl=CFL, blend=BETA, equilibrium=eq)
+    s = FDLBM(xa, ya, nu=NU, cfl=CFL, blend=BETA, equilibrium=eq, precision=precision)
     rng = np.random.default_rng(3)
     dev = s.device
     f = [torch.tensor(v, dtype=torch.float64, device=dev) for v in
@@ -149,21 +150,21 @@ def test_init_vjp_dot_product(eq):
           0.05 * rng.uniform(-1, 1, (ny, nx)))]
     v = [torch.tensor(rng.normal(size=(ny, nx)), dtype=torch.float64, device=dev) for _ in range(3)]
     lam = s.new_buffer()
-    lam[:, :, :nx] = torch.tensor(rng.normal(size=(9, ny, nx)), dtype=torch.float64, device=dev)
+    lam[:, :, :nx] = torch.tensor(rng.normal(size=(9, ny, nx)), dtype=lam.dtype, device=dev)
 
     def state_of(fields):
         s.init_fields(*fields)
-        return s.save_state(s.new_buffer())
+        return s.save_state(s.new_buffer()).to(torch.float64)
 
-    eps = 1e-5
+    eps = 1e-5 if precision == "fp64" else 1e-2
     jv = (state_of([a + eps * b for a, b in zip(f, v)]) -
           state_of([a - eps * b for a, b in zip(f, v)])) / (2 * eps)
     g = [torch.zeros_like(a) for a in f]
     s.init_vjp(*f, lam, *g)
     s.sync()
-    lhs = float((jv[:, :, :nx] * lam[:, :, :nx]).sum())
+    lhs = float((jv[:, :, :nx] * lam[:, :, :nx].to(torch.float64)).sum())
     rhs = float(sum((a * b).sum() for a, b in zip(v, g)))
-    assert abs(lhs - rhs) <= 1e-9 * abs(rhs), (lhs, rhs)
+    assert abs(lhs - rhs) <= tol * abs(rhs), (lhs, rhs)
 
 
 def test_rollout_gradient_wrt_initial_velocity():

@@ -134,21 +134,23 @@ def test_incomp_walls(precision, tol, path, bcx, bcy, nx, ny, rows):
     assert err <= tol
 
 
-@pytest.mark.parametrize("walls", [True, False])
-def test_incomp_scheme2_fp64(walls):
-    """T2S2-FDLBM2 with the incompressible equilibrium: the staged kernels on a
-    channel, the fused sweep on a periodic grid."""
+@pytest.mark.parametrize("walls,precision,tol", [(True, "fp64", FP64_TOL), (False, "fp64", FP64_TOL),
+                                                 (True, "fp32", 1e-6)])
+def test_incomp_scheme2(walls, precision, tol):
+    """T2S2-FDLBM2 with the incompressible equilibrium: the staged kernels on an
+    FP64 channel, the fused sweeps on an FP32 channel and a periodic grid."""
     nx, ny = 24, 20
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.tanh_axis(ny - 1, 1.5) if walls else I.periodic_axis(ny, 0.0, 0.8)
     force = 1e-3 * np.random.default_rng(4).uniform(-1, 1, size=(2, ny, nx))
-    s, o = _pair(xa, ya, nu=0.02, cfl=0.3, beta=0.2, force=force, scheme=2,
+    s, o = _pair(xa, ya, nu=0.02, cfl=0.3, beta=0.2, force=force, scheme=2, precision=precision,
                  wall_u=[(0, 0), (0, 0), (0, 0), (0.05, 0.0)] if walls else None)
-    assert s.describe.startswith("staged-scheme2" if walls else "fused-scheme2"), s.describe
+    staged = walls and precision == "fp64"
+    assert s.describe.startswith("staged-scheme2" if staged else "fused-scheme2"), s.describe
     _init_both(s, o, I.random_fields(nx, ny, 5, drho=0.05))
     s.step(15)
     o.step(15)
-    assert rel(s.get_state(), o.f) <= FP64_TOL
+    assert rel(s.get_state(), o.f) <= tol
 
 
 @pytest.mark.parametrize("precision,tol,mode", [("fp64", FP64_TOL, "staged"), ("fp32", 2e-6, "fused"),
