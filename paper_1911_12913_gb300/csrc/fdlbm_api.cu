@@ -241,8 +241,35 @@ fdlbm_status capture_step_graph(fdlbm_ctx *h)
     return FDLBM_OK;
 }
 
-// Copy `nfields` host or device fields ([ny][nx] FP64 each) through the staging
-// area in row chunks and hand each chunk to `kernel(ptr, row0, nrows, fstride)`.
+// The address under which the device reads and writes a host array directly:
+// pinned host memory is mapped into the device's address space (unified
+// addressing), so kernels can use it in place of a staged copy.  nullptr for
+// pageable memory (or on any query error, which is cleared).
+double *device_view(const double *p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return static_cast<double *>(at.devicePointer);
+}
+
+// Device views of all non-null host arrays, or false if any has none.
+bool device_views(const double *const *p, int n, double **out)
+{
+    for (int k = 0; k < n; ++k) {
+        out[k] = nullptr;
+        if (p[k] && !(out[k] = device_view(p[k]))) return false;
+    }
+    return true;
+}
+
+// Hand `nfields` host or device fields ([ny][nx] FP64 each) to
+// `kernel(ptr, row0, nrows, fstride)`: device fields and pinned host fields in
+// place (one pass; the call still waits for it, so host arrays are free on
+// return), pageable host fields through the staging area in row chunks.
 template <class K>
 fdlbm_status staged_in(fdlbm_ctx *h, const double *const *fields, int nfields, int where,
                        K kernel, const char *what)
@@ -252,6 +279,15 @@ fdlbm_status staged_in(fdlbm_ctx *h, const double *const *fields, int nfields, i
         // device fields: consecutive pointers are expected for multi-field args
         cudaError_t e = kernel(fields, h->ny, (size_t)h->nx * h->ny, 0);
         return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, what);
+    }
+    {
+        std::vector<double *> views(nfields);
+        if (device_views(fields, nfields, views.data())) {
+            std::vector<const double *> cv(views.begin(), views.end());
+            cudaError_t e = kernel(cv.data(), h->ny, (size_t)h->nx * h->ny, 0);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, what);
+        }
     }
     double *stage = reinterpret_cast<double *>(h->ws + h->lay.staging);
     const int rows = (int)std::max<size_t>(1, h->lay.staging_elems / ((size_t)nfields * h->nx));
@@ -612,6 +648,11 @@ fdlbm_status fdlbm_get_state(fdlbm_t h, double *f, int where)
         e = launch_convert_out(h, f, 0, h->ny, N);
         return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "get_state");
     }
+    if (double *v = device_view(f)) {  // pinned host memory: written in place
+        e = launch_convert_out(h, v, 0, h->ny, N);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "get_state");
+    }
     double *stage = reinterpret_cast<double *>(h->ws + h->lay.staging);
     const int rows = (int)std::max<size_t>(1, h->lay.staging_elems / (9 * (size_t)h->nx));
     for (int r0 = 0; r0 < h->ny; r0 += rows) {
@@ -666,6 +707,15 @@ fdlbm_status fdlbm_moments(fdlbm_t h, double *rho, double *ux, double *uy, int w
     if (where == FDLBM_MEM_DEVICE) {
         e = launch_moments(h, rho, ux, uy, 0, h->ny, N);
         return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "moments");
+    }
+    {
+        const double *outs[3] = {rho, ux, uy};
+        double *v[3];
+        if (device_views(outs, 3, v)) {  // pinned host memory: written in place
+            e = launch_moments(h, v[0], v[1], v[2], 0, h->ny, N);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "moments");
+        }
     }
     double *stage = reinterpret_cast<double *>(h->ws + h->lay.staging);
     const int rows = (int)std::max<size_t>(1, h->lay.staging_elems / (3 * (size_t)h->nx));
