@@ -9,6 +9,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 namespace fdlbm {
 
 // Velocity set of Sec. 3 with xi = 1 (population order 0..8 of the paper).
@@ -69,6 +71,39 @@ __device__ __forceinline__ void equilibrium_dev(R drho, R rho, R ux, R uy, R geq
     }
 }
 
+// The same deviation from the momentum j = rho u (with any force shift of
+// Eq. 3.3 already in it) and inv = 1/rho, or 1/rho0 under the incompressible
+// equilibrium (whose velocity terms rho0 (3 xi.u + 4.5 (xi.u)^2 - 1.5 u.u) are
+// the same expression in j = rho0 u):
+//   f_i^eq - w_i rho0 = w_i [ drho + 3 e_i + (4.5 e_i^2 - 1.5 j.j) inv ],  e_i = xi_i.j.
+// Only the quadratic term needs 1/rho, and opposite velocities share it.  The
+// linear coefficients 3 w_i are c1 = fl(1/3) (axis velocities) and c2 =
+// (1 - 2 c1)/4 (diagonals): 2 c1 + 4 c2 = 1 exactly, so the first moment of
+// the equilibrium is j with no rounding bias (a fixed bias would act like a
+// force proportional to u, which a slowly decaying flow accumulates).
+template <class R>
+struct LinearCoef {
+    static constexpr R c1 = R(1) / R(3);
+    static constexpr R c2 = (R(1) - R(2) * c1) * R(0.25);
+};
+
+template <class R>
+__device__ __forceinline__ void equilibrium_dev_j(R drho, R jx, R jy, R inv, R geq[9])
+{
+    const R qn = R(-1.5) * (jx * jx + jy * jy);
+    geq[0] = wq<R>(0) * (drho + qn * inv);
+    auto pair = [&](R e, R w, R c, int ip, int im) {
+        const R ws = w * (drho + (R(4.5) * e * e + qn) * inv);
+        const R lin = c * e;
+        geq[ip] = ws + lin;
+        geq[im] = ws - lin;
+    };
+    pair(jx, wq<R>(1), LinearCoef<R>::c1, 1, 3);
+    pair(jy, wq<R>(2), LinearCoef<R>::c1, 2, 4);
+    pair(jx + jy, wq<R>(5), LinearCoef<R>::c2, 5, 7);
+    pair(jy - jx, wq<R>(6), LinearCoef<R>::c2, 6, 8);
+}
+
 // Eq. 3.12: F_i = Fbar.(xi_i - u) f_i^eq / cs^2, with f_i^eq = w_i rho0 + geq_i
 // - w_i dshift.  dshift = 0 takes the equilibrium of the node (Eq. 3.2); under
 // the incompressible equilibrium dshift = rho - rho0, which takes it at rho0.
@@ -94,15 +129,49 @@ struct Stencil {
     R wm1, w0, w1, w2;
 };
 
+// The weights sum to zero, so the difference of a constant vanishes and the
+// update conserves mass and momentum on a periodic uniform grid.  Rounded
+// separately they would not (for beta = 0.1 in FP32 the sum is 1.9e-8), and
+// every step would then scale each moving population by 1 - CFL x that sum: a
+// damping that adds up linearly over a long run.  So the weights are put on a
+// grid of 2^-22 (FP32) or 2^-51 (FP64), fine enough to move beta by no more
+// than that, and coarse enough that w0 = -(wm1 + w1 + w2) and every partial sum
+// are exact (|w| <= 2).
 template <class R>
 __host__ inline Stencil<R> make_stencil(double beta)
 {
+    const double g = sizeof(R) == 4 ? 4194304.0 : 2251799813685248.0;  // 2^22, 2^51
+    auto on_grid = [g](double v) { return std::nearbyint(v * g) / g; };
+    const double wm1 = on_grid(0.5 * (1.0 - beta));
+    const double w1 = on_grid(-0.5 * (1.0 - beta) - 2.0 * beta);
+    const double w2 = on_grid(0.5 * beta);
     Stencil<R> s;
-    s.wm1 = R(0.5 * (1.0 - beta));
-    s.w0 = R(1.5 * beta);
-    s.w1 = R(-0.5 * (1.0 - beta) - 2.0 * beta);
-    s.w2 = R(0.5 * beta);
+    s.wm1 = R(wm1);
+    s.w1 = R(w1);
+    s.w2 = R(w2);
+    s.w0 = R(-(wm1 + w1 + w2));
     return s;
+}
+
+// Products s w of a weight (|w| <= 2) and a scale s != 0 (for instance -dt m)
+// rounded to a multiple of q = 2^(e - 21), where 2^e <= |s| < 2^(e+1).  The
+// rounding moves a product by at most 2^-22 |s|, and every sum of up to three
+// such products, or of two such sums with the same q, is exact in FP32.  So a
+// centre coefficient set to minus the sum of the taps gives a difference whose
+// coefficients sum to exactly zero, as the exact ones do.
+struct WeightGrid {
+    float q, inv_q;
+};
+
+__device__ __forceinline__ WeightGrid weight_grid(float s)
+{
+    const int b = (__float_as_int(s) & 0x7f800000) - (21 << 23);  // exponent field of q
+    return {__int_as_float(b), __int_as_float(0x7f000000 - b)};
+}
+
+__device__ __forceinline__ float on_weight_grid(float v, WeightGrid g)
+{
+    return rintf(v * g.inv_q) * g.q;
 }
 
 // Apply to values v(k-2..k+2) given as vm2..vp2 for a population moving in the

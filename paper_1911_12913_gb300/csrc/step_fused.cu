@@ -104,7 +104,7 @@ struct Sweep {
             const R inv = recip(rho);
             const R ux = jx * inv, uy = jy * inv;
             R geq[9], F[9];
-            equilibrium_dev(drho, rho, ux, uy, geq);
+            equilibrium_dev_j(drho, jx, jy, inv, geq);
             if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(c, drho));
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -156,7 +156,7 @@ struct Sweep {
                 const R inv = recip(rho);
                 const R ux = jx * inv, uy = jy * inv;
                 R geq[9], F[9];
-                equilibrium_dev(drho, rho, ux, uy, geq);
+                equilibrium_dev_j(drho, jx, jy, inv, geq);
                 if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(c, drho));
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {

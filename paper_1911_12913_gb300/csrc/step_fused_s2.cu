@@ -66,7 +66,7 @@ __device__ __forceinline__ void node_maps(const Coeffs<R> &c, const R g[9], R Fx
     }
     const R inv = recip2(rho);
     const R ux = jx * inv, uy = jy * inv;
-    equilibrium_dev(drho, rho, ux, uy, geq);
+    equilibrium_dev_j(drho, jx, jy, inv, geq);
     if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(c, drho));
 }
 

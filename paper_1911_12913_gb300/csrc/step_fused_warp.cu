@@ -29,7 +29,10 @@
 //
 // The x-differences use weights pre-multiplied by the column's metric and the
 // half step (stage B) or step (stage C), with the centre taps of the x and y
-// differences merged into one coefficient.
+// differences merged into one coefficient.  The equilibria are formed from the
+// momentum rho u (packed.cuh), so that only their quadratic term waits for
+// 1/rho, and stage B folds the relaxation of Eq. 2.52 into the equilibrium
+// (two packed FMAs per population).
 //
 // Every wait on an mbarrier is bounded: on timeout the warp records an error
 // flag, keeps its control flow, waits (bounded) for its copies in flight
@@ -41,6 +44,7 @@
 // 2^32 values, so that element offsets fit 32 bits.
 #include <cstddef>
 #include <cstdint>
+#include <cmath>
 #include <cstring>
 #include <type_traits>
 
@@ -88,7 +92,39 @@ struct ArgsW {
     float w[4];  // wm1, w0, w1, w2
     int *err;
     float inv_rho0;  // incompressible equilibrium only
+    RelaxK kstar;    // the relaxation of Eq. 2.52 (b = b_star) as packed weights
 };
+
+// The weights of the update's differences (stage C) for a scale s = -dt m:
+// the taps (offsets +1, -1, -2 for sgn > 0) in t[0..2] and the centre in c,
+// with c + t[0] + t[1] + t[2] = 0 exactly, as for the exact weights, so that
+// the update of a constant is zero and a periodic uniform grid conserves mass
+// and momentum to rounding (separately rounded weights leave a sum of order
+// 1e-8 s, a damping that adds up linearly over a long run).
+//   GRID = false (requires wm1 >= 0.55 |w1|, beta <= 0.16): t0 = s wm1,
+//     t1 = s w1 and c = s w0 rounded; t0 + t1 is exact by Sterbenz's lemma
+//     (t0 and -t1 within a factor 2), so is (t0 + t1) + c (ratio 3/4), and
+//     t2 = -((t0 + t1) + c) takes up their rounding (1e-8 |s| at most).
+//   GRID = true (any beta): each tap rounded to the weight grid of s and c
+//     minus their sum, exact on that grid.
+// Both sides of a square uniform grid get bit-identical weights, so the
+// merged centre of a diagonal population, c_x + c_y = 2c, is exact too.
+template <bool GRID>
+__device__ __forceinline__ void update_weights(float s, const float w[4], float t[3], float &c)
+{
+    if (GRID) {
+        const WeightGrid g = weight_grid(s);
+        t[0] = on_weight_grid(s * w[0], g);
+        t[1] = on_weight_grid(s * w[2], g);
+        t[2] = on_weight_grid(s * w[3], g);
+        c = -((t[0] + t[1]) + t[2]);
+    } else {
+        t[0] = s * w[0];
+        t[1] = s * w[2];
+        c = s * w[1];
+        t[2] = -((t[0] + t[1]) + c);
+    }
+}
 
 // The taps other than the centre of sign(c) * D_m f in x for the lane's pair
 // (Eq. 2.36 with Eqs. 2.37-2.38), weighted by c[0..2] = weights of the taps
@@ -120,7 +156,8 @@ __device__ __forceinline__ f2 ytaps(const f2 c[3], int sgn, f2 vm2, f2 vm1, f2 v
 }
 
 // INC: the incompressible equilibrium of He and Luo (velocity from rho0 u).
-template <bool INC>
+// GRID: how the update's weights are made to sum to zero (update_weights).
+template <bool INC, bool GRID>
 __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     k_step_fused_warp(const __grid_constant__ ArgsW a)
 {
@@ -152,9 +189,21 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     const f2 mx2 = make_float2(__ldg(a.mx + gx), __ldg(a.mx + gx + 1));
     const f2 nhx = mul2(bc(-a.h), mx2), ndx = mul2(bc(-a.dt), mx2);
     const f2 axB[3] = {mul2(nhx, bc(a.w[0])), mul2(nhx, bc(a.w[2])), mul2(nhx, bc(a.w[3]))};
-    const f2 axC[3] = {mul2(ndx, bc(a.w[0])), mul2(ndx, bc(a.w[2])), mul2(ndx, bc(a.w[3]))};
-    const f2 cxB = mul2(nhx, bc(a.w[1])), cxC = mul2(ndx, bc(a.w[1]));
-    const f2 bbar = bc(a.b_bar), btil = bc(a.b_til), bstar = bc(a.b_star);
+    // stage C: taps on the weight grid of each column and the centre as minus
+    // their sum, so that the x weights of the update sum to exactly zero
+    // (stage B needs no such care: its result enters the update only through
+    // differences)
+    f2 axC[3], cxC;
+    {
+        float tl[3], th[3];
+        update_weights<GRID>(ndx.x, a.w, tl, cxC.x);
+        update_weights<GRID>(ndx.y, a.w, th, cxC.y);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) axC[k] = make_float2(tl[k], th[k]);
+    }
+    const f2 cxB = mul2(nhx, bc(a.w[1]));
+    const f2 c_xB = add2(bc(1.f), cxB);
+    const f2 bbar = bc(a.b_bar), btil = bc(a.b_til);
 
     const uint32_t bar0 = smem_addr(&sm.bar[0]);
     const uint32_t ring0 = smem_addr(&sm.ring[0][0][0]), wrap0 = smem_addr(&sm.wrap[0][0][0]);
@@ -205,9 +254,8 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
 #pragma unroll
             for (int i = 0; i < 9; ++i)
                 g[i] = *reinterpret_cast<const f2 *>(src + i * kCols * sizeof(float));
-            const Macro m = INC ? moments2_incomp(g, rho0, bc(a.inv_rho0)) : moments2(g, rho0);
             f2 geq[9];
-            equilibrium2(m, geq);
+            equilibrium2_j(INC ? moments2_j_incomp(g, bc(a.inv_rho0)) : moments2_j(g, rho0), geq);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const f2 neq = sub2(geq[i], g[i]);
@@ -223,35 +271,38 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
             const f2 ay[3] = {bc(nhy * a.w[0]), bc(nhy * a.w[2]), bc(nhy * a.w[3])};
             // centre coefficients: 1 + the centre weights of the differences taken
             const f2 c_y = bc(1.f + nhy * a.w[1]);
-            const f2 c_x = add2(bc(1.f), cxB), c_d = add2(c_y, cxB);
+            const f2 c_d = add2(c_y, cxB);
             f2 gs[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const f2 v0 = Pw[i][p2];
                 f2 acc;
                 if (cx(i) != 0 && cy(i) != 0) acc = mul2(c_d, v0);
-                else if (cx(i) != 0) acc = mul2(c_x, v0);
+                else if (cx(i) != 0) acc = mul2(c_xB, v0);
                 else if (cy(i) != 0) acc = mul2(c_y, v0);
                 else acc = v0;
                 if (cx(i) != 0) acc = xtaps(axB, cx(i), v0, acc);
                 if (cy(i) != 0) acc = ytaps(ay, cy(i), Pw[i][p4], Pw[i][p3], Pw[i][p1], Pw[i][p0], acc);
                 gs[i] = acc;
             }
-            const Macro m = INC ? moments2_incomp(gs, rho0, bc(a.inv_rho0)) : moments2(gs, rho0);
-            f2 geq[9];
-            equilibrium2(m, geq);
+            // Eq. 2.52: f* = f-bar* + b* (f^eq* - f-bar*), folded into the equilibrium
+            f2 fs[9];
+            relax2_j(INC ? moments2_j_incomp(gs, bc(a.inv_rho0)) : moments2_j(gs, rho0), gs, a.kstar, fs);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) Sw[i][p0] = fma2(bstar, sub2(geq[i], gs[i]), gs[i]);
+            for (int i = 0; i < 9; ++i) Sw[i][p0] = fs[i];
         }
         // ------------------------------------------------------------ C (row r-4)
         // f* rows r-6 .. r-2 sit in slots p4, p3, p2, p1, p0 of Sw.
         {
-            const float ndy = -a.dt * myC;
             const int qg = rq;
             rq = rq + 1 == a.ny ? 0 : rq + 1;
+            const float ndy = -a.dt * myC;
             myC = __ldg(a.my + rq);
-            const f2 by[3] = {bc(ndy * a.w[0]), bc(ndy * a.w[2]), bc(ndy * a.w[3])};
-            const f2 c_y = bc(ndy * a.w[1]);
+            // the y weights of the update, summing to zero exactly
+            float ty[3], cyw;
+            update_weights<GRID>(ndy, a.w, ty, cyw);
+            const f2 by[3] = {bc(ty[0]), bc(ty[1]), bc(ty[2])};
+            const f2 c_y = bc(cyw);
             const f2 c_d = add2(c_y, cxC);
             // element offsets fit 32 bits (9 planes < 2^32 elements, checked on
             // the host): one wide multiply-add per store address
@@ -375,8 +426,12 @@ cudaError_t launch_fused_warp(const StepArgs<float> &s, const void *map_in, cuda
     a.w[3] = s.st.w2;
     a.err = s.err;
     a.inv_rho0 = 1.0f / s.c.rho0;
+    a.kstar = make_relax(s.c.b_star);
     constexpr size_t smem = sizeof(WarpSmem);
-    auto kern = s.c.incomp ? k_step_fused_warp<true> : k_step_fused_warp<false>;
+    // the Sterbenz-ordered update weights need wm1 >= 0.55 |w1| (beta <= 0.16)
+    const bool on_grid = !(s.st.wm1 >= 0.55f * std::fabs(s.st.w1));
+    auto kern = s.c.incomp ? (on_grid ? k_step_fused_warp<true, true> : k_step_fused_warp<true, false>)
+                           : (on_grid ? k_step_fused_warp<false, true> : k_step_fused_warp<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((s.nx + kW - 1) / kW, (s.ny + s.rows - 1) / s.rows);
@@ -390,8 +445,8 @@ int fused_warp_blocks_per_sm()
 {
     int n = 0;
     constexpr size_t smem = sizeof(WarpSmem);
-    cudaFuncSetAttribute(k_step_fused_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_fused_warp<false>, kLanes, smem) !=
+    cudaFuncSetAttribute(k_step_fused_warp<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_fused_warp<false, false>, kLanes, smem) !=
         cudaSuccess)
         return 0;
     return n;

@@ -35,7 +35,7 @@ __device__ __forceinline__ void node_eq(const Coeffs<R> &c, const R g[9], R Fx, 
     const R inv = recip(rho);
     ux = jx * inv;
     uy = jy * inv;
-    equilibrium_dev(drho, rho, ux, uy, geq);
+    equilibrium_dev_j(drho, jx, jy, inv, geq);
 }
 
 // Eq. 3.10: the wall value of every population from node x_j's vector g.
