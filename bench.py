@@ -39,6 +39,13 @@ N_GRID = 4096
 # unstable at the 4096^2 spacing (dt/tau = 0.026, nearly collisionless transport).
 NU, CFL, BLEND, U0, SEED = 0.001, 0.5, 0.1, 0.01, 2026
 BYTES_PER_CELL = {"fp32": 72, "fp64": 144}   # 9 populations read once + written once
+# FP64 is bound by the FP64 units, not HBM.  The FP64 fused step executes
+# 80.0 M DADD + 60.3 M DMUL + 212.5 M DFMA thread instructions per 1,474,560
+# thread-rows (ncu, 1024^2, 9 x 32 CTAs of 128 threads x 40 rows): 383 flop
+# per node of sweep work, the algorithmic figure per cell update (the halo
+# recompute of a given tiling comes on top).
+FP64_FLOP_PER_CELL = 383
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 nominal FP64 rate (non-tensor)
 SAMPLE_N = 512                                # oracle sample grid
 
 
@@ -145,7 +152,7 @@ class Clocks:
 TRAFFIC = {
     "fused-warp": ("warp_fp32_traffic.json",
                    ["step_fused_warp.cu", "packed.cuh", "tma.cuh", "lattice.cuh"]),
-    "fused": ("fused_fp32_traffic.json", ["step_fused.cu"]),
+    "fused": ("fused_fp32_traffic.json", ["step_fused.cu", "lattice.cuh"]),
 }
 
 
@@ -656,7 +663,12 @@ def run_ours(args):
         fp64 = {"value": N / t64 / 1e6, "unit": "MLUPS", "ms_per_step": ms64 / args.fp64_steps,
                 "steps": args.fp64_steps,
                 "hbm_achieved_gbs": BYTES_PER_CELL["fp64"] * N / t64 / 1e9,
-                "hbm_frac": BYTES_PER_CELL["fp64"] * N / t64 / 1e9 / hbm}
+                "hbm_frac": BYTES_PER_CELL["fp64"] * N / t64 / 1e9 / hbm,
+                "roofline": {"bound": "alu", "achieved": FP64_FLOP_PER_CELL * N / t64 / 1e12,
+                             "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                             "frac": FP64_FLOP_PER_CELL * N / t64 / 1e12 / FP64_NOMINAL_TFLOPS,
+                             "flop_per_cell": FP64_FLOP_PER_CELL,
+                             "peak_source": "nominal FP64 rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)"}}
         del s64
         torch.cuda.empty_cache()
 
