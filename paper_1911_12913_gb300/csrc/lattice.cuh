@@ -104,6 +104,34 @@ __device__ __forceinline__ void equilibrium_dev_j(R drho, R jx, R jy, R inv, R g
     pair(jy - jx, wq<R>(6), LinearCoef<R>::c2, 6, 8);
 }
 
+// 1/rho for the momentum-form equilibrium, where it scales only the O(u^2)
+// quadratic term, so a reciprocal within a few ulp serves.  FP32: the
+// hardware approximation (about one ulp for normal x).  FP64: the same
+// instruction's FP64 form as a seed, refined by two Newton-Raphson steps for
+// f(y) = 1/y - x, y <- y + y (1 - x y), each of which squares the relative
+// error (e.g. J.-M. Muller et al., Handbook of Floating-Point Arithmetic,
+// division by Newton-Raphson iteration); the density is O(1) and finite.
+template <class R>
+__device__ __forceinline__ R node_reciprocal(R x);
+
+template <>
+__device__ __forceinline__ float node_reciprocal<float>(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <>
+__device__ __forceinline__ double node_reciprocal<double>(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+#pragma unroll
+    for (int k = 0; k < 2; ++k) y = fma(y, fma(-x, y, 1.0), y);
+    return y;
+}
+
 // Eq. 3.12: F_i = Fbar.(xi_i - u) f_i^eq / cs^2, with f_i^eq = w_i rho0 + geq_i
 // - w_i dshift.  dshift = 0 takes the equilibrium of the node (Eq. 3.2); under
 // the incompressible equilibrium dshift = rho - rho0, which takes it at rho0.

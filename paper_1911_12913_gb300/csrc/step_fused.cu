@@ -32,17 +32,6 @@ namespace {
 constexpr int kHalo = 4;
 constexpr int kRing = 5;
 
-template <class R>
-__device__ __forceinline__ R recip(R v)
-{
-    return R(1) / v;
-}
-template <>
-__device__ __forceinline__ float recip<float>(float v)
-{
-    return __frcp_rn(v);
-}
-
 template <class R, int NT>
 struct Smem {
     R P[kRing][6][NT];   // fbar^{+,h} of the x-moving populations
@@ -101,7 +90,7 @@ struct Sweep {
                 jx += c.half_dt * rho * Fx;
                 jy += c.half_dt * rho * Fy;
             }
-            const R inv = recip(rho);
+            const R inv = node_reciprocal(rho);
             const R ux = jx * inv, uy = jy * inv;
             R geq[9], F[9];
             equilibrium_dev_j(drho, jx, jy, inv, geq);
@@ -153,7 +142,7 @@ struct Sweep {
                     jx += c.half_h * rho * Fx;
                     jy += c.half_h * rho * Fy;
                 }
-                const R inv = recip(rho);
+                const R inv = node_reciprocal(rho);
                 const R ux = jx * inv, uy = jy * inv;
                 R geq[9], F[9];
                 equilibrium_dev_j(drho, jx, jy, inv, geq);

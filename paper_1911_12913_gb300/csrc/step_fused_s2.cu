@@ -40,17 +40,6 @@ struct Smem2 {
     R LN[kRing2][9][NT];  // L(f^n), read back by the same thread two rows later
 };
 
-template <class R>
-__device__ __forceinline__ R recip2(R v)
-{
-    return R(1) / v;
-}
-template <>
-__device__ __forceinline__ float recip2<float>(float v)
-{
-    return __frcp_rn(v);
-}
-
 // Moments (Eq. 3.3 with the force shift `shift`), f^eq (Eq. 3.2 or the
 // incompressible one) and the forcing terms (Eq. 3.12) of a deviation vector.
 template <class R, bool FORCE>
@@ -64,7 +53,7 @@ __device__ __forceinline__ void node_maps(const Coeffs<R> &c, const R g[9], R Fx
         jx += shift * rho * Fx;
         jy += shift * rho * Fy;
     }
-    const R inv = recip2(rho);
+    const R inv = node_reciprocal(rho);
     const R ux = jx * inv, uy = jy * inv;
     equilibrium_dev_j(drho, jx, jy, inv, geq);
     if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F, force_dshift(c, drho));

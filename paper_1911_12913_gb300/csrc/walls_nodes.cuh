@@ -8,17 +8,6 @@
 namespace fdlbm {
 namespace {
 
-template <class R>
-__device__ __forceinline__ R recip(R v)
-{
-    return R(1) / v;
-}
-template <>
-__device__ __forceinline__ float recip<float>(float v)
-{
-    return __frcp_rn(v);
-}
-
 // Eq. 3.3 and Eq. 3.2 for a 9-vector of deviations; `shift` is the force
 // shift of its first moment (FORCE only).
 template <class R, bool FORCE>
@@ -32,7 +21,7 @@ __device__ __forceinline__ void node_eq(const Coeffs<R> &c, const R g[9], R Fx, 
         jx += shift * rho * Fx;
         jy += shift * rho * Fy;
     }
-    const R inv = recip(rho);
+    const R inv = node_reciprocal(rho);
     ux = jx * inv;
     uy = jy * inv;
     equilibrium_dev_j(drho, jx, jy, inv, geq);
