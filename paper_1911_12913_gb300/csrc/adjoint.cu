@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kAdjNT, sizeof(R) == 4 ? 2 : 1) k_adj_fused(co
             const R inv = node_recip(rho);
             const R ux = jx * inv, uy = jy * inv;
             R geq[9], F[9];
-            equilibrium_dev(drho, rho, ux, uy, geq);
+            equilibrium_dev_j(drho, jx, jy, inv, geq);
             if (FORCE) force_terms(c.rho0, geq, ux, uy, Fx, Fy, F);
 #pragma unroll
             for (int i = 0; i < 9; ++i) {

@@ -9,16 +9,12 @@ namespace fdlbm {
 
 // Node map of stage A or B: moments (with force shift `sh`), equilibrium and
 // forcing, and the derivatives needed by its vector-Jacobian product.
-// 1/rho: correctly rounded in FP32, a plain division in FP64.
+// 1/rho: the forward sweeps' fast reciprocal (within 1 ulp in FP32, equal to
+// 1/x on the samples tested in FP64).
 template <class R>
 __device__ __forceinline__ R node_recip(R v)
 {
-    return R(1) / v;
-}
-template <>
-__device__ __forceinline__ float node_recip<float>(float v)
-{
-    return __frcp_rn(v);
+    return node_reciprocal<R>(v);
 }
 
 template <class R>
