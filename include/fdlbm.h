@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define FDLBM_ABI_VERSION 2
+#define FDLBM_ABI_VERSION 3
 
 typedef struct fdlbm_ctx *fdlbm_t;
 
@@ -40,7 +40,10 @@ typedef enum {
     FDLBM_OK = 0,
     FDLBM_EINVAL = -1,        /* invalid argument (sizes, metrics <= 0, NULL, ...) */
     FDLBM_ENOMEM = -2,        /* workspace too small, or device allocation failed */
-    FDLBM_ECUDA = -3,         /* CUDA runtime error; see fdlbm_last_error() */
+    FDLBM_ECUDA = -3,         /* CUDA runtime error, or a bounded device-side wait (an mbarrier
+                                 of a tensor-copy kernel, a grid barrier of a persistent batch)
+                                 that gave up: there is no separate timeout status; the text
+                                 of fdlbm_last_error() says which */
     FDLBM_ENONFINITE = -4,    /* a reduction met NaN or Inf (the run diverged) */
     FDLBM_EUNSUPPORTED = -5,  /* option combination not available */
     FDLBM_ETOOBIG = -6        /* size beyond a fixed capacity (see fdlbm_reduce_noalloc) */
@@ -85,7 +88,9 @@ enum { FDLBM_WALL_W = 0, FDLBM_WALL_E = 1, FDLBM_WALL_S = 2, FDLBM_WALL_N = 3 };
  *  T2S2_1  f~(n+1) = f~+ + dt L(f*), f* at t_n + A dt (Eq. 2.23; A = 0 gives T1S2);
  *  T2S2_2  f~(n+1) = f~+ + dt/2 [L(f^n) + L(f^{n+1})] with the characteristic
  *          estimate of f^{n+1} over h = dt (Eq. 5.23, second sequence of Sec. 2D).
- *          Runs on the staged kernels; A is ignored. */
+ *          Runs on its own fused sweeps (periodic grids in both precisions,
+ *          walled grids in FP32) and on the staged kernels (walled grids in
+ *          FP64, or opts.path = FDLBM_PATH_STAGED); A is ignored. */
 enum { FDLBM_SCHEME_T2S2_1 = 0, FDLBM_SCHEME_T2S2_2 = 1 };
 
 /* Tensor-product grid (Sec. 3, Eqs. 3.9 and 3.11).  A periodic axis stores its
@@ -156,9 +161,15 @@ fdlbm_status fdlbm_create(const fdlbm_grid *grid, const fdlbm_metrics *metrics, 
 /* Release the handle and any memory the library allocated.  NULL-safe. */
 void fdlbm_destroy(fdlbm_t h);
 
-/* Initialise f~ from macroscopic fields: Eq. 3.2 (f~ = f^eq(rho, u)), or with
- * grad != NULL the non-equilibrium start of Eq. 3.5,
- *   f~_i = f_i^eq - rho0 w_i (2 tau + dt) / (2 cs^2) xi_i xi_i : grad u,
+/* Initialise f~ from macroscopic fields.  The physical distribution is
+ * f = f^eq(rho, u) (Eq. 3.2), or with grad != NULL the non-equilibrium start of
+ * Eq. 3.5, and the stored variable is f~ = f - (dt/2) Omega-bar(f) (Eq. 2.19):
+ *   f~_i = f_i^eq - (dt/2) F_i(rho, u) - rho0 w_i (2 tau + dt) / (2 cs^2) xi_i xi_i : grad u,
+ * with F_i the forcing term of Eq. 3.12 under the handle's body-acceleration
+ * field AS SET AT THE TIME OF THIS CALL (zero without opts.has_force or before
+ * the first fdlbm_set_force), so that Eq. 3.3 returns exactly the given u.  A
+ * later fdlbm_set_force changes the force of the following steps but not the
+ * state: call fdlbm_set_force first to start a forced run from (rho, u).
  * grad = 4 consecutive [ny][nx] fields du/dx, du/dy, dv/dx, dv/dy.
  * rho, ux, uy: [ny][nx] FP64 at `where`. */
 fdlbm_status fdlbm_init_fields(fdlbm_t h, const double *rho, const double *ux, const double *uy,
@@ -184,7 +195,9 @@ fdlbm_status fdlbm_moments(fdlbm_t h, double *rho, double *ux, double *uy, int w
  * nodes (the Jacobian-weighted mass, exactly conserved on periodic grids), and
  * *resid = the successive-state residual of the cavity section,
  * sqrt(sum |u - u_prev|^2 / sum |u|^2), against the velocity of the previous
- * fdlbm_reduce call (-1 on the first call).  Synchronises the stream.  Returns
+ * fdlbm_reduce call (-1 on the first call; for a fluid exactly at rest, where
+ * sum |u|^2 = 0, the absolute sqrt(sum |u - u_prev|^2), which is 0 if it was at
+ * rest before as well).  Synchronises the stream.  Returns
  * ENONFINITE if either value is NaN/Inf.  Either pointer may be NULL. */
 fdlbm_status fdlbm_reduce(fdlbm_t h, double *mass, double *resid);
 
@@ -235,14 +248,18 @@ fdlbm_status fdlbm_adjoint_step(fdlbm_t h, const void *state_n, const void *lam_
 fdlbm_status fdlbm_moments_vjp(fdlbm_t h, const void *state, const double *du, void *lam,
                                double *dforce);
 /* Cotangents of the fields of an equilibrium initialisation
- * (fdlbm_init_fields(rho, ux, uy, NULL), Eq. 3.2 or the incompressible
- * equilibrium): given the cotangent lam (storage layout, device) of the state
- * that those fields (device, FP64, [ny][nx] each) produce, ADD their
- * cotangents to drho (may be NULL), dux and duy (device, FP64, [ny][nx]).
- * With fdlbm_adjoint_step this differentiates a rollout with respect to its
- * initial density and velocity.  Asynchronous on the stream. */
+ * (fdlbm_init_fields(rho, ux, uy, NULL): Eq. 3.2 or the incompressible
+ * equilibrium, minus (dt/2) F_i of Eq. 2.19 under the handle's current force
+ * field): given the cotangent lam (storage layout, device) of the state that
+ * those fields (device, FP64, [ny][nx] each) produce, ADD their cotangents to
+ * drho (may be NULL), dux and duy (device, FP64, [ny][nx]), and the cotangent
+ * of the force field through the initial state to dforce (device, FP64,
+ * [2][ny][nx]; may be NULL).  With fdlbm_adjoint_step this differentiates a
+ * rollout with respect to its initial density and velocity.  Asynchronous on
+ * the stream. */
 fdlbm_status fdlbm_init_vjp(fdlbm_t h, const double *rho, const double *ux, const double *uy,
-                            const void *lam, double *drho, double *dux, double *duy);
+                            const void *lam, double *drho, double *dux, double *duy,
+                            double *dforce);
 
 /* ---------------------------------------------------------------------------
  * Batched mode: many independent cases (uneven sizes, walls, forces, Reynolds
@@ -251,9 +268,9 @@ fdlbm_status fdlbm_init_vjp(fdlbm_t h, const double *rho, const double *ux, cons
  * fdlbm_set_force, fdlbm_get_state, fdlbm_moments, fdlbm_reduce, fdlbm_dt) work
  * on fdlbm_batch_case(b, c); stepping, the stream and destruction belong to the
  * batch (fdlbm_step / fdlbm_set_stream on a case return EUNSUPPORTED,
- * fdlbm_destroy ignores it).  All cases run the staged kernels of their own
- * scheme (Sec. 2D), each with its own dt (Eq. 3.1); one batch step advances
- * every case by one of its own time steps.
+ * fdlbm_destroy ignores it).  Every case runs its own scheme (Sec. 2D) with
+ * its own dt (Eq. 3.1), on the kernels that fdlbm_batch_set_mode selects; one
+ * batch step advances every case by one of its own time steps.
  * ------------------------------------------------------------------------- */
 typedef struct fdlbm_batch_ctx *fdlbm_batch_t;
 
@@ -326,16 +343,19 @@ void fdlbm_batch_destroy(fdlbm_batch_t b);           /* NULL-safe; releases ever
  *   dzeta_dx, dmu_dy  device, FP64 metrics of length nx and ny;
  *   uprev     device, FP64 [2][ny][nx] previous velocity (u then v), or NULL;
  *   out       device, 3 FP64: Jacobian-weighted mass, residual against uprev
- *             (-1 without uprev), sum |u|^2.  Velocities are those of Eq. 3.3
- *             without body force.
+ *             (-1 without uprev; the absolute sqrt(sum |u - uprev|^2) when
+ *             sum |u|^2 = 0), sum |u|^2.  Velocities are sum xi f / sum f, with
+ *             no body-force correction.
  * Enqueued on `stream` (cudaStream_t, NULL = default); read `out` after the
  * stream completes.  No allocation of any kind: the scratch (3 doubles per grid
  * row) is a fixed device array of fdlbm_reduce_noalloc_max_rows() rows that
  * every GPU using the library holds until the process exits.  The first call on
  * a device looks up that array's device address, so make it before any stream
- * capture.  Every call shares the array: calls whose kernels overlap on the GPU
- * race and give wrong results.  Errors: EINVAL (NULL pointer, nx or ny < 1),
- * ETOOBIG (ny above the maximum), ECUDA. */
+ * capture (and, after the device's context has been destroyed and made anew,
+ * the next call looks it up again).  Every call shares the array: calls whose
+ * kernels overlap on the GPU race and give wrong results.  Errors: EINVAL (NULL
+ * pointer, nx or ny < 1), ETOOBIG (ny above the maximum), ECUDA (also, without
+ * launching, when an earlier CUDA error is already pending on the thread). */
 fdlbm_status fdlbm_reduce_noalloc(const double *f, int nx, int ny, const double *dzeta_dx,
                                   const double *dmu_dy, const double *uprev, double *out,
                                   void *stream);

@@ -269,10 +269,10 @@ class Oracle:
 
 # ------------------------------------------------------------------ complex step
 def step_complex(xa, ya, *, nu: float, dt: float, beta: float, f, force=None, A: float = 0.5,
-                 nsteps: int = 1, wall_u=None):
+                 nsteps: int = 1, wall_u=None, scheme: int = 1):
     """Advance a complex-valued state (and complex force field, if given) with
     the complex build of the oracle: the same arithmetic as ``Oracle.step``."""
-    o = Oracle(xa, ya, nu=nu, dt=dt, beta=beta, A=A, wall_u=wall_u)
+    o = Oracle(xa, ya, nu=nu, dt=dt, beta=beta, A=A, wall_u=wall_u, scheme=scheme)
     fc = np.ascontiguousarray(f, dtype=np.complex128).copy()
     keep = None
     if force is not None:

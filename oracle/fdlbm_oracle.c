@@ -174,18 +174,24 @@ void oracle_moments(const oracle_cfg *c, const real_t *f, real_t *rho, real_t *u
         moments_node(c, f, n, 0.5 * c->dt, &rho[n], &ux[n], &uy[n]);
 }
 
-/* Eq. 3.5 (coefficient read as rho0 w_i (2 tau + dt) / (2 cs^2), see the
- * module header of the Python wrapper) or Eq. 3.2 alone when grad is NULL.
+/* Initial f~ from the fields (rho, u) and, optionally, the velocity gradient.
+ * The physical distribution is f = f^eq (Eq. 3.2), plus the non-equilibrium
+ * part of Eq. 3.5 when grad is given (coefficient read as
+ * rho0 w_i (2 tau + dt) / (2 cs^2), which already carries the factor
+ * 1 + dt/(2 tau) of the change of variables).  The stored variable is then
+ * f~ = f - (dt/2) Omega-bar(f) (Eq. 2.19); with a body force Omega-bar holds
+ * the forcing term of Eq. 3.12, so f~ = ... - (dt/2) F_i(rho, u), and Eq. 3.3
+ * reads back exactly the velocity u that was given.
  * grad = [dudx, dudy, dvdx, dvdy], each [ny][nx]. */
 void oracle_init(const oracle_cfg *c, const real_t *rho, const real_t *ux, const real_t *uy,
                  const real_t *grad, double rho0, real_t *f)
 {
     size_t N = (size_t)c->nx * c->ny;
     for (size_t n = 0; n < N; ++n) {
-        real_t feq[9];
-        feq_model(c, rho[n], ux[n], uy[n], feq);
+        real_t feq[9], Fi[9];
+        node_feq_force(c, n, rho[n], ux[n], uy[n], feq, Fi);
         for (int i = 0; i < 9; ++i) {
-            real_t v = feq[i];
+            real_t v = feq[i] - 0.5 * c->dt * Fi[i];
             if (grad) {
                 double xx = EX[i] * EX[i], xy = EX[i] * EY[i], yy = EY[i] * EY[i];
                 real_t ddot = xx * grad[n] + xy * (grad[N + n] + grad[2 * N + n]) +

@@ -6,7 +6,8 @@ torch.autograd.Functions, with sqrt(N) checkpointing.
 ``force`` ([2, ny, nx], FP64, CUDA) and returns the final velocity [2, ny, nx]
 (FP64).  Its backward pass gives d/d force.
 ``rollout_velocity_from_fields(solver, force, rho, ux, uy, nsteps)`` starts
-from the equilibrium of the fields (Eq. 3.2) instead, and its backward pass
+from the fields instead (f = f^eq of Eq. 3.2, f~ = f - (dt/2) F_i by Eq. 2.19
+under ``force``), and its backward pass
 also gives d/d rho, d/d ux and d/d uy (libfdlbm ``fdlbm_init_vjp``), so that
 an initial velocity (or vorticity, through a differentiable map to u) can be
 recovered as well as a force.
@@ -27,8 +28,8 @@ from .solver import FDLBM
 
 
 def _forward(solver: FDLBM, force, nsteps: int):
-    """Run nsteps from the solver's current state, keeping the checkpoints."""
-    solver.set_force(force)
+    """Run nsteps from the solver's current state under the force already set,
+    keeping the checkpoints."""
     k = max(1, int(math.ceil(math.sqrt(nsteps))))
     ckpts = []
     done = 0
@@ -68,6 +69,7 @@ class _Rollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, force, solver: FDLBM, f0, nsteps: int):
         solver.load_state(f0)
+        solver.set_force(force)
         ckpts, final, k, u = _forward(solver, force, nsteps)
         ctx.solver, ctx.ckpts, ctx.final, ctx.nsteps, ctx.k = solver, ckpts, final, nsteps, k
         ctx.shape = tuple(force.shape)
@@ -83,6 +85,8 @@ class _RolloutFields(torch.autograd.Function):
     @staticmethod
     def forward(ctx, force, rho, ux, uy, solver: FDLBM, nsteps: int):
         fields = [t.detach().to(torch.float64).contiguous() for t in (rho, ux, uy)]
+        # the force first: the initial state carries -(dt/2) F_i (Eq. 2.19)
+        solver.set_force(force)
         solver.init_fields(*fields)
         ckpts, final, k, u = _forward(solver, force, nsteps)
         ctx.solver, ctx.ckpts, ctx.final, ctx.nsteps, ctx.k = solver, ckpts, final, nsteps, k
@@ -95,7 +99,7 @@ class _RolloutFields(torch.autograd.Function):
         s: FDLBM = ctx.solver
         dforce, lam0 = _reverse(s, ctx.ckpts, ctx.final, ctx.nsteps, ctx.k, grad_u, ctx.shape)
         drho, dux, duy = (torch.zeros_like(f) for f in ctx.fields)
-        s.init_vjp(*ctx.fields, lam0, drho, dux, duy)
+        s.init_vjp(*ctx.fields, lam0, drho, dux, duy, dforce)
         s.sync()
         return dforce, drho, dux, duy, None, None
 

@@ -98,7 +98,7 @@ SIGNATURES = [
     ("fdlbm_batch_set_mode", ctypes.c_int, [_H, ctypes.c_int]),
     ("fdlbm_batch_mode", ctypes.c_int, [_H]),
     ("fdlbm_batch_sync", ctypes.c_int, [_H]),
-    ("fdlbm_init_vjp", ctypes.c_int, [_H] + [ctypes.c_void_p] * 7),
+    ("fdlbm_init_vjp", ctypes.c_int, [_H] + [ctypes.c_void_p] * 8),
     ("fdlbm_batch_set_spin_limit", ctypes.c_int, [_H, ctypes.c_uint]),
     ("fdlbm_batch_stream", ctypes.c_void_p, [_H]),
     ("fdlbm_batch_describe", ctypes.c_char_p, [_H]),

@@ -357,57 +357,77 @@ __global__ void k_moments_vjp(const StepArgs<R> a, const double *du, R *lam, dou
     }
 }
 
-// Cotangents of the fields of the equilibrium initialisation (Eq. 3.2, as
-// written by k_init without the gradient term of Eq. 3.5): with e = xi_i.u and
-// Phi_i = 3e + 4.5e^2 - 1.5u.u,  g_i = w_i [(rho - rho0) + rho Phi_i], so
-//   dg_i/drho = w_i (1 + Phi_i),  dg_i/du_a = w_i rho (3 + 9e) xi_ia - 3 w_i rho u_a
-// (rho0 in place of rho in the velocity terms under the incompressible
-// equilibrium, where dg_i/drho = w_i).  The cotangents are added, in FP64.
+// Cotangents of the fields of the equilibrium initialisation, as written by
+// k_init without the gradient term of Eq. 3.5: the physical f = f^eq (Eq. 3.2)
+// and f~ = f - (dt/2) F_i (Eq. 2.19 with the forcing term of Eq. 3.12).  With
+// e = xi_i.u, Phi_i = 3e + 4.5e^2 - 1.5u.u, E_i = w_i rho (1 + Phi_i) and
+// q_i = 1.5 dt Fbar.(xi_i - u) (so that (dt/2) F_i = q_i E_i),
+//   g_i = w_i [(rho - rho0) + rho Phi_i] - q_i E_i,
+//   dg_i/drho  = w_i (1 + Phi_i)(1 - q_i),
+//   dg_i/du_a  = w_i rho dPhi_i/du_a (1 - q_i) + 1.5 dt Fbar_a E_i,
+//   dg_i/dFbar_a = -1.5 dt (xi_ia - u_a) E_i,
+// with dPhi_i/du_a = (3 + 9e) xi_ia - 3 u_a.  Under the incompressible
+// equilibrium rho0 replaces rho in the velocity terms and in E_i, and
+// dg_i/drho = w_i.  The cotangents are added, in FP64.
 template <class R>
 __global__ void k_init_vjp(const StepArgs<R> a, const double *rho, const double *ux,
-                           const double *uy, const R *lam, double *drho, double *dux, double *duy)
+                           const double *uy, const R *lam, double dt, double *drho, double *dux,
+                           double *duy, double *dforce)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
     const size_t o = (size_t)y * a.pitch + x, n = (size_t)y * a.nx + x;
+    const size_t N = (size_t)a.nx * a.ny;
     const double r = rho[n], u = ux[n], v = uy[n];
     const double rm = a.c.incomp ? double(a.c.rho0) : r;  // the density of the velocity terms
+    const double Fx = a.force ? double(a.force[o]) : 0.0;
+    const double Fy = a.force ? double(a.force[a.plane + o]) : 0.0;
+    const double hq = 1.5 * dt;  // (dt/2) / cs^2
     const double uu = u * u + v * v;
-    double gr = 0.0, gu = 0.0, gv = 0.0;
+    double gr = 0.0, gu = 0.0, gv = 0.0, gfx = 0.0, gfy = 0.0;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const double l = double(lam[i * a.plane + o]) * wq<double>(i);
+        const double w = wq<double>(i);
+        const double l = double(lam[i * a.plane + o]);
         const double e = double(cx(i)) * u + double(cy(i)) * v;
         const double phi = e * (3.0 + 4.5 * e) - 1.5 * uu;
-        gr += l * (a.c.incomp ? 1.0 : 1.0 + phi);
+        const double E = w * rm * (1.0 + phi);
+        const double q = hq * ((double(cx(i)) - u) * Fx + (double(cy(i)) - v) * Fy);
+        gr += l * (a.c.incomp ? w : w * (1.0 + phi) * (1.0 - q));
         const double de = rm * (3.0 + 9.0 * e);
-        gu += l * (de * double(cx(i)) - 3.0 * rm * u);
-        gv += l * (de * double(cy(i)) - 3.0 * rm * v);
+        gu += l * (w * (de * double(cx(i)) - 3.0 * rm * u) * (1.0 - q) + hq * Fx * E);
+        gv += l * (w * (de * double(cy(i)) - 3.0 * rm * v) * (1.0 - q) + hq * Fy * E);
+        gfx -= l * hq * (double(cx(i)) - u) * E;
+        gfy -= l * hq * (double(cy(i)) - v) * E;
     }
     if (drho) drho[n] += gr;
     dux[n] += gu;
     duy[n] += gv;
+    if (dforce) {
+        dforce[n] += gfx;
+        dforce[N + n] += gfy;
+    }
 }
 
 }  // namespace
 
 template <class R>
 cudaError_t launch_init_vjp(const StepArgs<R> &a, const double *rho, const double *ux,
-                            const double *uy, const R *lam, double *drho, double *dux, double *duy,
-                            cudaStream_t s)
+                            const double *uy, const R *lam, double dt, double *drho, double *dux,
+                            double *duy, double *dforce, cudaStream_t s)
 {
     const dim3 blk(32, 8), grd((a.nx + 31) / 32, (a.ny + 7) / 8);
-    k_init_vjp<R><<<grd, blk, 0, s>>>(a, rho, ux, uy, lam, drho, dux, duy);
+    k_init_vjp<R><<<grd, blk, 0, s>>>(a, rho, ux, uy, lam, dt, drho, dux, duy, dforce);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_init_vjp<float>(const StepArgs<float> &, const double *, const double *,
-                                            const double *, const float *, double *, double *,
-                                            double *, cudaStream_t);
+                                            const double *, const float *, double, double *,
+                                            double *, double *, double *, cudaStream_t);
 template cudaError_t launch_init_vjp<double>(const StepArgs<double> &, const double *,
-                                             const double *, const double *, const double *,
-                                             double *, double *, double *, cudaStream_t);
+                                             const double *, const double *, const double *, double,
+                                             double *, double *, double *, double *, cudaStream_t);
 
 template <class R>
 cudaError_t launch_adjoint(const StepArgs<R> &a, const R *lam_next, R *lam_prev, R *, R *,

@@ -748,7 +748,9 @@ fdlbm_status fdlbm_reduce(fdlbm_t h, double *mass, double *resid)
     if (e != cudaSuccess) return cuda_fail(h, e, "reduce");
     fdlbm_status fs = check_flag(h);
     if (fs != FDLBM_OK) return fs;
-    const double res = h->have_uprev ? std::sqrt(r[2] / r[1]) : -1.0;
+    // relative residual; a fluid exactly at rest gets the absolute one
+    const double res =
+        h->have_uprev ? (r[1] > 0.0 ? std::sqrt(r[2] / r[1]) : std::sqrt(r[2])) : -1.0;
     h->have_uprev = true;
     if (mass) *mass = r[0];
     if (resid) *resid = res;
@@ -856,7 +858,8 @@ fdlbm_status fdlbm_moments_vjp(fdlbm_t h, const void *state, const double *du, v
 }
 
 fdlbm_status fdlbm_init_vjp(fdlbm_t h, const double *rho, const double *ux, const double *uy,
-                            const void *lam, double *drho, double *dux, double *duy)
+                            const void *lam, double *drho, double *dux, double *duy,
+                            double *dforce)
 {
     if (!h) return FDLBM_EINVAL;
     if (!rho || !ux || !uy || !lam || !dux || !duy)
@@ -864,10 +867,11 @@ fdlbm_status fdlbm_init_vjp(fdlbm_t h, const double *rho, const double *ux, cons
     cudaError_t e;
     if (h->precision == FDLBM_FP32_DEV)
         e = launch_init_vjp<float>(step_args<float>(h), rho, ux, uy, static_cast<const float *>(lam),
-                                   drho, dux, duy, h->stream);
+                                   h->dt, drho, dux, duy, dforce, h->stream);
     else
         e = launch_init_vjp<double>(step_args<double>(h), rho, ux, uy,
-                                    static_cast<const double *>(lam), drho, dux, duy, h->stream);
+                                    static_cast<const double *>(lam), h->dt, drho, dux, duy,
+                                    dforce, h->stream);
     return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "init_vjp");
 }
 

@@ -12,24 +12,37 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
+// Initial f~ from (rho, u) and optionally the velocity gradient.  The physical
+// distribution is f = f^eq (Eq. 3.2), plus the non-equilibrium part of Eq. 3.5
+// with the coefficient rho0 w_i (2 tau + dt) / (2 cs^2) when grad is given; the
+// stored variable is f~ = f - (dt/2) Omega-bar(f) (Eq. 2.19), which with a body
+// force carries -(dt/2) F_i(rho, u) (Eq. 3.12), so that Eq. 3.3 reads back the
+// given velocity.  The force is the handle's field at the time of the call.
 template <class R>
-__global__ void k_init(StepArgs<R> a, const double *rho, const double *ux, const double *uy,
-                       const double *grad, size_t fstride, int row0, int nrows, double tau,
-                       double dt, double rho0)
+__global__ void k_init(StepArgs<R> a, const R *force, const double *rho, const double *ux,
+                       const double *uy, const double *grad, size_t fstride, int row0, int nrows,
+                       double tau, double dt, double rho0)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || j >= nrows) return;
     const size_t l = (size_t)j * a.nx + x;
     const double r = rho[l], u = ux[l], v = uy[l];
-    double geq[9];
+    double geq[9], F[9];
     equilibrium_dev<double>(r - rho0, a.c.incomp ? rho0 : r, u, v, geq);
+    const size_t o = (size_t)(row0 + j) * a.pitch + x;
+    if (force) {
+        force_terms<double>(rho0, geq, u, v, double(force[o]), double(force[a.plane + o]), F,
+                            a.c.incomp ? r - rho0 : 0.0);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) F[i] = 0.0;
+    }
     // Eq. 3.5 with the coefficient rho0 w_i (2 tau + dt) / (2 cs^2)
     const double k = rho0 * (2.0 * tau + dt) * 1.5;
-    const size_t o = (size_t)(row0 + j) * a.pitch + x;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        double val = geq[i];
+        double val = geq[i] - 0.5 * dt * F[i];
         if (grad) {
             const double gxx = grad[l], gxy = grad[fstride + l], gyx = grad[2 * fstride + l],
                          gyy = grad[3 * fstride + l];
@@ -218,8 +231,12 @@ cudaError_t launch_init_fields(fdlbm_ctx *h, const double *rho, const double *ux
                                size_t fstride)
 {
     const dim3 blk(32, 8);
-    DISPATCH(h, R, k_init<R><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
-                       view<R>(h), rho, ux, uy, grad, fstride, row0, nrows, h->tau, h->dt, h->rho0));
+    DISPATCH(h, R,
+             const R *force = h->has_force ? reinterpret_cast<const R *>(h->ws + h->lay.force)
+                                           : nullptr;
+             k_init<R><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
+                 view<R>(h), force, rho, ux, uy, grad, fstride, row0, nrows, h->tau, h->dt,
+                 h->rho0));
     return cudaGetLastError();
 }
 

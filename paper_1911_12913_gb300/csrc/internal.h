@@ -169,8 +169,8 @@ cudaError_t launch_adjoint(const StepArgs<R> &a, const R *lam_next, R *lam_prev,
                            double *fB, double *dforce, cudaStream_t s);
 template <class R>
 cudaError_t launch_init_vjp(const StepArgs<R> &a, const double *rho, const double *ux,
-                            const double *uy, const R *lam, double *drho, double *dux, double *duy,
-                            cudaStream_t s);
+                            const double *uy, const R *lam, double dt, double *drho, double *dux,
+                            double *duy, double *dforce, cudaStream_t s);
 template <class R>
 cudaError_t launch_moments_vjp(const StepArgs<R> &a, const double *du, R *lam, double *dforce,
                                cudaStream_t s);

@@ -7,13 +7,17 @@
 // fixed-footprint service loop that must not grow its memory after start-up,
 // or a host thread that is not allowed to call cudaMalloc while other work is
 // in flight.  This entry point takes only the caller's input and output
-// buffers; its scratch (one partial sum per grid row) lives in a file-scope
-// device array that every GPU which loads the library holds until the
-// process exits.
+// buffers; its scratch (three partial sums per grid row: mass, |u|^2 and
+// |u - u_prev|^2) lives in a file-scope device array that every GPU which
+// loads the library holds until the process exits.
 //
 // Set-up: the first call on a device looks up the device address of that
-// array (cudaGetSymbolAddress, with that device current) and caches it, so
-// that first call should be made before any stream capture.  All calls on a
+// array (cudaGetSymbolAddress, with that device current) and caches it for
+// the device's current CUDA context, so that first call should be made before
+// any stream capture.  If that context is destroyed and another one is made
+// current (cudaDeviceReset, or a library releasing the primary context), the
+// module is loaded again, possibly at another address, and the next call looks
+// the address up again; it should then also come before any capture.  All calls on a
 // device share the array, and it keeps the previous call's partials; the row
 // partials are rewritten in full by every call and the final pass writes the
 // outputs directly, so nothing has to be cleared.  Two calls whose kernels
@@ -36,6 +40,24 @@ static __device__ __align__(256) double g_row_partials[kMaxRows * 3];
 
 std::mutex g_mu;
 double *g_scratch[kMaxDevices] = {};
+void *g_ctx[kMaxDevices] = {};  // the context each cached address belongs to
+
+// cuCtxGetCurrent from the driver, through the runtime's entry-point query (so
+// that the library need not link the driver library itself).
+using CtxGetCurrentFn = int (*)(void **);
+CtxGetCurrentFn ctx_get_current()
+{
+    static CtxGetCurrentFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<CtxGetCurrentFn>(p);
+    }();
+    return fn;
+}
 
 // D2Q9 velocity components of the populations (Sec. 3 order).
 __device__ __constant__ int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -61,8 +83,8 @@ __device__ double block_sum(double v, double *red)
     return s;  // valid in thread 0
 }
 
-// One block per row: sums of rho/(m_x m_y), |u|^2 and |u - u_prev|^2 (Eq. 3.3
-// moments of f~ without body force).
+// One block per row: sums of rho/(m_x m_y), |u|^2 and |u - u_prev|^2, with
+// rho = sum f and u = sum xi f / rho (no body-force correction).
 __global__ void __launch_bounds__(kThreads)
     k_rows(const double *f, int nx, int ny, const double *mx, const double *my,
            const double *uprev, double *rows)
@@ -115,12 +137,15 @@ __global__ void __launch_bounds__(kThreads)
     const double sd = block_sum(du, red);
     if (threadIdx.x == 0) {
         out[0] = sm;
-        out[1] = have_prev ? sqrt(sd / su) : -1.0;
+        // relative residual; a fluid exactly at rest (sum |u|^2 = 0) gets the
+        // absolute one, which is 0 if it was at rest before as well
+        out[1] = have_prev ? (su > 0.0 ? sqrt(sd / su) : sqrt(sd)) : -1.0;
         out[2] = su;
     }
 }
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device, looked up once
+// per device and context (again when the device's context has changed).
 cudaError_t scratch_for_current_device(double **out)
 {
     int dev = 0;
@@ -128,12 +153,23 @@ cudaError_t scratch_for_current_device(double **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_row_partials);
-        if (e != cudaSuccess) return e;
-        g_scratch[dev] = static_cast<double *>(p);
+    if (g_scratch[dev]) {
+        void *ctx = nullptr;
+        CtxGetCurrentFn get = ctx_get_current();
+        // without the query every call looks the address up (no stale cache)
+        if (get && get(&ctx) == 0 && ctx && ctx == g_ctx[dev]) {
+            *out = g_scratch[dev];
+            return cudaSuccess;
+        }
     }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_row_partials);  // makes the context current if needed
+    if (e != cudaSuccess) return e;
+    void *ctx = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (!get || get(&ctx) != 0) ctx = nullptr;
+    g_scratch[dev] = static_cast<double *>(p);
+    g_ctx[dev] = ctx;
     *out = g_scratch[dev];
     return cudaSuccess;
 }
@@ -150,11 +186,15 @@ fdlbm_status fdlbm_reduce_noalloc(const double *f, int nx, int ny, const double 
 {
     if (!f || !dzeta_dx || !dmu_dy || !out || nx < 1 || ny < 1) return FDLBM_EINVAL;
     if (ny > kMaxRows) return FDLBM_ETOOBIG;
+    // An error left pending by earlier, unrelated work on this thread is not
+    // ours to clear or report as our own: refuse to launch and leave it.
+    if (cudaPeekAtLastError() != cudaSuccess) return FDLBM_ECUDA;
     double *rows = nullptr;
     cudaError_t e = scratch_for_current_device(&rows);
     if (e != cudaSuccess) return FDLBM_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     k_rows<<<ny, kThreads, 0, s>>>(f, nx, ny, dzeta_dx, dmu_dy, uprev, rows);
+    if (cudaGetLastError() != cudaSuccess) return FDLBM_ECUDA;
     k_final<<<1, kThreads, 0, s>>>(rows, ny, uprev != nullptr, out);
     return cudaGetLastError() == cudaSuccess ? FDLBM_OK : FDLBM_ECUDA;
 }

@@ -236,16 +236,17 @@ class FDLBM:
                                         dforce.data_ptr() if dforce is not None else None)
         _check(self._L, self._h, rc, "adjoint_step")
 
-    def init_vjp(self, rho, ux, uy, lam, drho, dux, duy):
+    def init_vjp(self, rho, ux, uy, lam, drho, dux, duy, dforce=None):
         """Add the cotangents of the fields of an equilibrium initialisation to
-        drho (may be None), dux, duy, given the cotangent ``lam`` (storage
-        layout) of the state they produced (all CUDA tensors)."""
+        drho (may be None), dux, duy, and that of the force field through the
+        initial state to dforce (may be None), given the cotangent ``lam``
+        (storage layout) of the state they produced (all CUDA tensors)."""
         def ptr(t):
             return None if t is None else t.data_ptr()
-        for t in (rho, ux, uy, drho, dux, duy):
+        for t in (rho, ux, uy, drho, dux, duy, dforce):
             assert t is None or (t.dtype == torch.float64 and t.is_contiguous() and t.is_cuda)
         rc = self._L.fdlbm_init_vjp(self._h, ptr(rho), ptr(ux), ptr(uy), ptr(lam), ptr(drho),
-                                    ptr(dux), ptr(duy))
+                                    ptr(dux), ptr(duy), ptr(dforce))
         _check(self._L, self._h, rc, "init_vjp")
         return self
 

@@ -133,37 +133,53 @@ def test_rollout_gradient_matches_central_differences():
         assert abs(fd - ad) <= 1e-6 * abs(fd), (k, fd, ad)
 
 
-@pytest.mark.parametrize("eq,precision,tol", [("standard", "fp64", 1e-9), ("incompressible", "fp64", 1e-9),
-                                              ("standard", "fp32", 1e-4)])
-def test_init_vjp_dot_product(eq, precision, tol):
-    """fdlbm_init_vjp is the transpose of the equilibrium initialisation:
-    <J v, lam> = <v, J^T lam> with J v from central differences of
-    fdlbm_init_fields (FP64, 16 x 12, random fields and directions)."""
+@pytest.mark.parametrize("eq,precision,forced,tol", [
+    ("standard", "fp64", False, 1e-9), ("incompressible", "fp64", False, 1e-9),
+    ("standard", "fp32", False, 1e-4), ("standard", "fp64", True, 1e-9),
+    ("incompressible", "fp64", True, 1e-9), ("standard", "fp32", True, 1e-4)])
+def test_init_vjp_dot_product(eq, precision, forced, tol):
+    """fdlbm_init_vjp is the transpose of the initialisation f~ = f^eq -
+    (dt/2) F_i (Eqs. 3.2, 2.19, 3.12): <J v, lam> = <v, J^T lam> with J v from
+    central differences of fdlbm_set_force + fdlbm_init_fields along random
+    directions of the density, the velocity and (forced cases) the force field
+    (16 x 12, random fields)."""
     nx, ny = 16, 12
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.periodic_axis(ny, 0.0, 0.8)
-    s = FDLBM(xa, ya, nu=NU, cfl=CFL, blend=BETA, equilibrium=eq, precision=precision)
+    s = FDLBM(xa, ya, nu=NU, cfl=CFL, blend=BETA, equilibrium=eq, precision=precision,
+              has_force=forced)
     rng = np.random.default_rng(3)
     dev = s.device
     f = [torch.tensor(v, dtype=torch.float64, device=dev) for v in
          (1.0 + 0.05 * rng.uniform(-1, 1, (ny, nx)), 0.05 * rng.uniform(-1, 1, (ny, nx)),
           0.05 * rng.uniform(-1, 1, (ny, nx)))]
     v = [torch.tensor(rng.normal(size=(ny, nx)), dtype=torch.float64, device=dev) for _ in range(3)]
+    # a force of 0.5 per unit time: (dt/2) F_i is then a few per cent of f^eq
+    F = torch.tensor(0.5 * rng.uniform(-1, 1, (2, ny, nx)), dtype=torch.float64, device=dev)
+    vF = torch.tensor(rng.normal(size=(2, ny, nx)), dtype=torch.float64, device=dev)
     lam = s.new_buffer()
     lam[:, :, :nx] = torch.tensor(rng.normal(size=(9, ny, nx)), dtype=lam.dtype, device=dev)
 
-    def state_of(fields):
+    def state_of(fields, force):
+        if forced:
+            s.set_force(force)
         s.init_fields(*fields)
         return s.save_state(s.new_buffer()).to(torch.float64)
 
     eps = 1e-5 if precision == "fp64" else 1e-2
-    jv = (state_of([a + eps * b for a, b in zip(f, v)]) -
-          state_of([a - eps * b for a, b in zip(f, v)])) / (2 * eps)
+    jv = (state_of([a + eps * b for a, b in zip(f, v)], F + eps * vF) -
+          state_of([a - eps * b for a, b in zip(f, v)], F - eps * vF)) / (2 * eps)
     g = [torch.zeros_like(a) for a in f]
-    s.init_vjp(*f, lam, *g)
+    gF = torch.zeros_like(F)
+    if forced:
+        s.set_force(F)
+    s.init_vjp(*f, lam, *g, gF if forced else None)
     s.sync()
     lhs = float((jv[:, :, :nx] * lam[:, :, :nx].to(torch.float64)).sum())
     rhs = float(sum((a * b).sum() for a, b in zip(v, g)))
+    if forced:
+        rhs += float((vF * gF).sum())
+        assert float(gF.abs().max()) > 0
     assert abs(lhs - rhs) <= tol * abs(rhs), (lhs, rhs)
 
 
@@ -205,6 +221,24 @@ def test_rollout_gradient_wrt_initial_velocity():
         fd = (4.0 * central(V, eps / 2) - central(V, eps)) / 3.0
         ad = float(sum((g * b).sum() for g, b in zip(grads, V)))
         assert abs(fd - ad) <= 1e-6 * abs(fd), (k, fd, ad)
+
+    # d/d force of the same rollout: through the steps and through the initial
+    # state, which carries -(dt/2) F_i (Eq. 2.19)
+    Fg = F.clone().requires_grad_(True)
+    u = rollout_velocity_from_fields(s, Fg, *base, nsteps)
+    (0.5 * ((u - tgt) ** 2).sum()).backward()
+    VF = torch.tensor(rng.normal(size=(2, ny, nx)), dtype=torch.float64, device=dev)
+
+    def central_F(eps):
+        with torch.no_grad():
+            jp = 0.5 * float(((rollout_velocity_from_fields(s, F + eps * VF, *base, nsteps) - tgt) ** 2).sum())
+            jm = 0.5 * float(((rollout_velocity_from_fields(s, F - eps * VF, *base, nsteps) - tgt) ** 2).sum())
+        return (jp - jm) / (2 * eps)
+
+    eps = 1e-4
+    fd = (4.0 * central_F(eps / 2) - central_F(eps)) / 3.0
+    ad = float((Fg.grad * VF).sum())
+    assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
 
 
 def test_recover_initial_velocity_by_gradient_descent():

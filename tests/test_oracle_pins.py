@@ -565,6 +565,90 @@ def test_poiseuille_converges_under_refinement():
     assert errs[-1] < 0.015 and min(orders) > 1.2, (errs, orders)
 
 
+def _poiseuille_channel(k, *, scheme=1, A=0.5, force_init=True):
+    """The channel of the Poiseuille section (10 x 20 cells, Eq. 3.9 with
+    c = 1.5, Re = 10, Fbar = 0.01, eta = 0.1, rho = 1, u = 0) marched to t = 20
+    with dt = 20 / round(20 / (k y1)), i.e. k y1 adjusted so that every run
+    ends at exactly t = 20.  Returns the velocity at t = 20."""
+    g = json.loads((GOLDEN / "paper_poiseuille_gre.json").read_text())
+    F, T = g["F"], g["t_end"]
+    nu = math.sqrt(F / (8.0 * g["Re"]))     # u0 = F H^2 / (8 nu), Re = H u0 / nu
+    xa = I.periodic_axis(g["grid_cells"][0], 0.0, 1.0)
+    ya = I.tanh_axis(g["grid_cells"][1], g["c"])
+    y1 = ya.coords[1]
+    n = int(round(T / (k * y1)))
+    force = np.zeros((2, ya.n, xa.n))
+    force[0] = F
+    o = O.Oracle(xa, ya, nu=nu, dt=T / n, beta=g["eta"], A=A, scheme=scheme, force=force,
+                 nthreads=oracle_threads())
+    one = np.ones((ya.n, xa.n))
+    o.init_fields(one, 0 * one, 0 * one)
+    o.step(n)
+    _, ux, uy = o.moments()
+    return ux, uy
+
+
+def test_forced_initialisation_reads_back_the_given_velocity():
+    """Sec. 3B initialises f by Eq. 3.2; the stored variable is f~ = f -
+    (dt/2) Omega-bar(f) (Eq. 2.19), which with a body force is f^eq -
+    (dt/2) F_i (Eq. 3.12).  Eq. 3.3 then returns exactly the given density and
+    velocity.  (Storing f~ = f^eq instead reads back u + (dt/2) Fbar.)"""
+    xa = I.periodic_axis(7, 0.0, 1.0)
+    ya = I.tanh_axis(6, 1.5)
+    r = I.random_fields(7, 7, 4, du=0.05, drho=0.03)
+    rng = np.random.default_rng(8)
+    force = rng.uniform(-0.5, 0.5, size=(2, 7, 7))
+    for incomp in (False, True):
+        o = O.Oracle(xa, ya, nu=0.01, dt=0.05, beta=0.1, force=force, incomp=incomp, rho0=1.0)
+        o.init_fields(r["rho"], r["ux"], r["uy"])
+        rho, ux, uy = o.moments()
+        assert np.allclose(rho, r["rho"], rtol=0, atol=1e-15)
+        assert np.allclose(ux, r["ux"], rtol=0, atol=1e-15)
+        assert np.allclose(uy, r["uy"], rtol=0, atol=1e-15)
+
+
+@pytest.mark.slow
+def test_poiseuille_time_step_table():
+    """The time-step table of the Poiseuille section: E(u) at t = 20 for dt =
+    0.2 ... 0.7 y1 on the stretched 10 x 20 channel, measured (Eq. 3.6 on the
+    velocity vector over all nodes) against the same scheme's run at dt =
+    0.02 y1.  T2S2-FDLBM1 reproduces every printed E(u) within 25 % (measured
+    ratios 0.80-0.89), every printed local order within 0.25 (measured
+    1.83-1.95 against the printed 1.82-2.06) and the order over the whole range
+    within 0.1 (1.90 against 1.94).  T1S2 (A = 0) and T2S2-FDLBM2 are measured
+    the same way; their printed rows are not reproduced (T1S2 about 8x above
+    the print with order 1.0-1.1, FDLBM2 about 30x below it with order 1.8-1.9)
+    and are checked only for their order in time: about 1 and about 2."""
+    g = json.loads((GOLDEN / "paper_poiseuille_gre.json").read_text())
+    ks = g["dt_over_y1"]
+
+    def row(**kw):
+        ur, vr = _poiseuille_channel(0.02, **kw)
+        errs = [O.gre(*_poiseuille_channel(k, **kw), ur, vr) for k in ks]
+        orders = [math.log(errs[i + 1] / errs[i]) / math.log(ks[i + 1] / ks[i])
+                  for i in range(len(ks) - 1)]
+        return errs, orders
+
+    e1, o1 = row(scheme=1)
+    p1 = g["T2S2_FDLBM1"]
+    print("FDLBM1 ratios", [round(a / b, 3) for a, b in zip(e1, p1["E_u"])], "orders", o1)
+    for a, b in zip(e1, p1["E_u"]):
+        assert a == pytest.approx(b, rel=0.25)
+    # the printed local orders scatter (1.82, 1.99, 1.94, 2.06, 2.02) about a
+    # smooth trend; each is matched within 0.25 and the order over the whole
+    # range 0.2 ... 0.7 y1 (printed 1.94) within 0.1
+    for a, b in zip(o1, p1["order"]):
+        assert abs(a - b) <= 0.25
+    span = math.log(ks[-1] / ks[0])
+    assert abs(math.log(e1[-1] / e1[0]) / span - math.log(p1["E_u"][-1] / p1["E_u"][0]) / span) <= 0.1
+    e0, o0 = row(scheme=1, A=0.0)
+    print("T1S2 ratios", [round(a / b, 3) for a, b in zip(e0, g["T1S2_FDLBM"]["E_u"])], "orders", o0)
+    assert all(0.9 < o < 1.2 for o in o0)
+    e2, o2 = row(scheme=2)
+    print("FDLBM2 ratios", [round(a / b, 3) for a, b in zip(e2, g["T2S2_FDLBM2"]["E_u"])], "orders", o2)
+    assert all(1.7 < o < 2.2 for o in o2)
+
+
 # ----------------------------------------------------------------- complex-step build
 def test_complex_build_is_the_same_arithmetic():
     """The complex-valued build of the oracle (used for exact complex-step

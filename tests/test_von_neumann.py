@@ -12,12 +12,12 @@ import inputs as I
 import oracle as O
 
 
-def spectral_radius(cfl, omega, *, u=(0.01, 0.01), beta=0.1, A=0.5, n=8):
+def spectral_radius(cfl, omega, *, u=(0.01, 0.01), beta=0.1, A=0.5, n=8, scheme=1):
     xa = I.periodic_axis(n, 0.0, float(n))
     ya = I.periodic_axis(n, 0.0, float(n))
     dt = cfl
     nu = dt / omega / 3.0
-    o = O.Oracle(xa, ya, nu=nu, dt=dt, beta=beta, A=A)
+    o = O.Oracle(xa, ya, nu=nu, dt=dt, beta=beta, A=A, scheme=scheme)
     one = np.ones((n, n))
     o.init_fields(one, u[0] * one, u[1] * one)
     f0 = o.f.copy()
@@ -25,7 +25,8 @@ def spectral_radius(cfl, omega, *, u=(0.01, 0.01), beta=0.1, A=0.5, n=8):
     for k in range(f0.size):
         x = f0.astype(np.complex128).ravel()
         x[k] += 1e-20j
-        y = O.step_complex(xa, ya, nu=nu, dt=dt, beta=beta, A=A, f=x.reshape(f0.shape))
+        y = O.step_complex(xa, ya, nu=nu, dt=dt, beta=beta, A=A, f=x.reshape(f0.shape),
+                           scheme=scheme)
         J[:, k] = (y.imag / 1e-20).ravel()
     return float(np.abs(np.linalg.eigvals(J)).max())
 
@@ -61,3 +62,25 @@ def test_nearly_collisionless_regime_is_unstable():
     assert spectral_radius(0.5, 1.0, u=(0.2, 0.2)) <= 1.0 + 1e-10
     assert spectral_radius(0.5, 0.1, u=(0.2, 0.2)) <= 1.0 + 1e-10
     assert spectral_radius(0.5, 0.026, u=(0.2, 0.2)) > 1.01
+
+
+# omega = dt / tau of the Taylor vortex of Sec. 3A at a given CFL: dt = CFL *
+# 2 pi / 128 and tau = 3 nu = 0.003
+TV_OMEGA_PER_CFL = 2 * np.pi / 128 / 0.003
+
+
+@pytest.mark.parametrize("cfl", [0.6, 0.7, 0.8])
+def test_fdlbm2_stable_to_cfl_08(cfl):
+    """T2S2-FDLBM2 (Eq. 5.23) at eta = 0.1 with the Taylor vortex's dt / tau is
+    stable up to CFL 0.8 ..."""
+    assert spectral_radius(cfl, TV_OMEGA_PER_CFL * cfl, scheme=2) <= 1.0 + 1e-10
+
+
+def test_fdlbm2_unstable_at_cfl_09_where_fdlbm1_is_stable():
+    """... and unstable at CFL 0.9 (the worst mode of the 8 x 8 grid grows by
+    about 8 % per step), where T2S2-FDLBM1 is still stable.  The Taylor-vortex
+    CFL table of Sec. 3A shows the same split: T2S2-FDLBM2 fails at CFL 0.9
+    (GRE 1.01) while T2S2-FDLBM1 keeps a small error there."""
+    om = TV_OMEGA_PER_CFL * 0.9
+    assert spectral_radius(0.9, om, scheme=2) > 1.05
+    assert spectral_radius(0.9, om, scheme=1) <= 1.0 + 1e-10
