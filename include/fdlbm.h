@@ -59,30 +59,24 @@ enum { FDLBM_MEM_HOST = 0, FDLBM_MEM_DEVICE = 1 };
  *   f_i^eq = w_i [rho + rho0 (xi.u / cs^2 + ((xi.u)^2 - cs^2 u.u) / (2 cs^4))],
  * with the velocity read from rho0 u = sum xi f~ + (dt/2) rho0 F (Eq. 3.3 with
  * rho0 for rho) and the forcing term of Eq. 3.12 taken with the equilibrium at
- * rho0.  It runs on the scalar, warp-tile, walls and staged kernels and in
- * batches; the TMA, ASYNC and PACKED variants and the adjoint step return
- * FDLBM_EUNSUPPORTED with it.  fdlbm_moments returns the density and this
- * velocity. */
+ * rho0.  It runs on every step kernel and in batches; the adjoint step
+ * returns FDLBM_EUNSUPPORTED with it.  fdlbm_moments returns the density and
+ * this velocity. */
 enum { FDLBM_EQ_STANDARD = 0, FDLBM_EQ_INCOMPRESSIBLE = 1 };
-/* Fused-kernel variant (periodic grids; a grid with a walled axis runs the
- * scalar sweep with Eq. 3.10 inside it, and any other variant is unsupported):
+/* Fused-kernel variant of T2S2-FDLBM1 on periodic grids (a grid with a walled
+ * axis runs the scalar sweep with Eq. 3.10 inside it, and WARP there is
+ * unsupported):
  *  SCALAR  one column per thread, rows loaded through registers (any nx >= 4);
- *  TMA     one column per thread, rows streamed into shared memory by bulk
- *          copies (nx a multiple of 16 bytes worth of values, nx >= 128);
- *  PACKED  FP32 only, two strips per thread in packed f32x2 arithmetic, bulk
- *          copies (no force field, nx % 4 == 0, nx >= 256);
- *  ASYNC   one column per thread, each thread prefetching its own column two
- *          rows ahead with cp.async (any nx >= 4);
  *  WARP    FP32 only, one independent warp per 56-column tile, two adjacent
  *          columns per lane in packed f32x2 arithmetic, x-neighbours by warp
- *          shuffle, rows by bulk copies into a per-warp ring; no block-level
- *          barrier (no force field, nx % 4 == 0, nx >= 64, fewer than 2^32
- *          values in the state).
+ *          shuffle, rows by bulk tensor copies into a per-warp ring; no
+ *          block-level barrier (no force field, nx % 4 == 0, nx >= 64, fewer
+ *          than 2^32 values in the state).
  * AUTO picks WARP where it applies (the fastest measured on GB300 for the
  * periodic 4096^2 throughput case) and SCALAR otherwise.  Asking for a
- * variant that does not apply returns FDLBM_EUNSUPPORTED. */
-enum { FDLBM_VARIANT_AUTO = 0, FDLBM_VARIANT_SCALAR = 1, FDLBM_VARIANT_PACKED = 2,
-       FDLBM_VARIANT_TMA = 3, FDLBM_VARIANT_ASYNC = 4, FDLBM_VARIANT_WARP = 5 };
+ * variant that does not apply returns FDLBM_EUNSUPPORTED; the values 2 to 4
+ * are not used. */
+enum { FDLBM_VARIANT_AUTO = 0, FDLBM_VARIANT_SCALAR = 1, FDLBM_VARIANT_WARP = 5 };
 enum { FDLBM_WALL_W = 0, FDLBM_WALL_E = 1, FDLBM_WALL_S = 2, FDLBM_WALL_N = 3 };
 /* Time-marching scheme (Sec. 2A):
  *  T2S2_1  f~(n+1) = f~+ + dt L(f*), f* at t_n + A dt (Eq. 2.23; A = 0 gives T1S2);
@@ -123,7 +117,7 @@ typedef struct {
                                  walled grids in FP64 (bound by the FP64 units, where the
                                  sweep's recomputed halo costs more than the extra traffic) */
     int rows_per_cta;         /* fused kernel tile height; 0 = automatic */
-    int variant;              /* FDLBM_VARIANT_*; PACKED where it does not apply -> EUNSUPPORTED */
+    int variant;              /* FDLBM_VARIANT_*; WARP where it does not apply -> EUNSUPPORTED */
     int scheme;               /* FDLBM_SCHEME_T2S2_1 (default) or FDLBM_SCHEME_T2S2_2 */
     int adjoint;              /* 1: reserve scratch for fdlbm_adjoint_step (periodic grids) */
     int graph_steps;          /* > 0: fdlbm_step replays a CUDA graph of this many steps (rounded
@@ -214,7 +208,7 @@ int fdlbm_path(fdlbm_t h);               /* FDLBM_PATH_FUSED or FDLBM_PATH_STAGE
 int fdlbm_kernels_per_step(fdlbm_t h);   /* kernel launches fdlbm_step makes per step */
 const char *fdlbm_last_error(fdlbm_t h); /* never NULL */
 /* Short description of the kernel the handle runs per step, e.g.
- * "fused-f32x2 rows=121" (never NULL; valid until the handle is destroyed). */
+ * "fused-warp fp32dev rows=121" (never NULL; valid until the handle is destroyed). */
 const char *fdlbm_describe(fdlbm_t h);
 const char *fdlbm_status_string(fdlbm_status s);
 
@@ -360,6 +354,16 @@ fdlbm_status fdlbm_reduce_noalloc(const double *f, int nx, int ny, const double 
                                   const double *dmu_dy, const double *uprev, double *out,
                                   void *stream);
 int fdlbm_reduce_noalloc_max_rows(void);
+
+/* Measurement utility (the paper has no counterpart): a launch of `blocks`
+ * blocks of independent FP64 fused multiply-add chains, `iters` FMAs per chain,
+ * enqueued on `stream` (cudaStream_t, NULL = default).  *flop (if not NULL) is
+ * set to the floating-point operations it performs (2 per FMA).  Time it with
+ * CUDA events on the same stream to measure the FP64 rate of the device, the
+ * roofline denominator of the FP64 step.  out: device pointer to `blocks`
+ * doubles (written only in a case that does not occur; it keeps the work).
+ * Errors: EINVAL, ECUDA. */
+fdlbm_status fdlbm_probe_fp64_fma(int blocks, int iters, double *out, void *stream, double *flop);
 
 #ifdef __cplusplus
 }

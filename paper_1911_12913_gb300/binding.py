@@ -21,7 +21,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 SCHEME_T2S2_1, SCHEME_T2S2_2 = 0, 1
 EQ_STANDARD, EQ_INCOMPRESSIBLE = 0, 1
 BATCH_FUSED, BATCH_STAGED, BATCH_PERSISTENT = 0, 1, 2
-VARIANT_AUTO, VARIANT_SCALAR, VARIANT_PACKED, VARIANT_TMA, VARIANT_ASYNC, VARIANT_WARP = 0, 1, 2, 3, 4, 5
+VARIANT_AUTO, VARIANT_SCALAR, VARIANT_WARP = 0, 1, 5
 STATUS = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENONFINITE", -5: "EUNSUPPORTED",
           -6: "ETOOBIG"}
 
@@ -108,6 +108,8 @@ SIGNATURES = [
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p]),
     ("fdlbm_reduce_noalloc_max_rows", ctypes.c_int, []),
+    ("fdlbm_probe_fp64_fma", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
 ]
 
 _lib = None

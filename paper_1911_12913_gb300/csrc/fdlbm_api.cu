@@ -105,21 +105,13 @@ int choose_rows(int nx, int ny, int precision, int variant, bool walls, int sche
         per_sm = f32 ? fused_s2_blocks_per_sm<float>() : fused_s2_blocks_per_sm<double>();
     else if (walls)
         per_sm = f32 ? fused_walls_blocks_per_sm<float>() : fused_walls_blocks_per_sm<double>();
-    else if (variant == FDLBM_VARIANT_PACKED)
-        per_sm = fused_x2_blocks_per_sm();
     else if (variant == FDLBM_VARIANT_WARP)
         per_sm = fused_warp_blocks_per_sm();
-    else if (variant == FDLBM_VARIANT_TMA)
-        per_sm = f32 ? fused_tma_blocks_per_sm<float>() : fused_tma_blocks_per_sm<double>();
-    else if (variant == FDLBM_VARIANT_ASYNC)
-        per_sm = f32 ? fused_async_blocks_per_sm<float>() : fused_async_blocks_per_sm<double>();
     else
         per_sm = f32 ? fused_blocks_per_sm<float>() : fused_blocks_per_sm<double>();
     if (per_sm <= 0) per_sm = 1;
     const long long slots = (long long)per_sm * sms;
-    const int W = variant == FDLBM_VARIANT_PACKED ? fused_x2_tile_width()
-                  : variant == FDLBM_VARIANT_WARP ? fused_warp_tile_width()
-                                                  : fused_tile_width();
+    const int W = variant == FDLBM_VARIANT_WARP ? fused_warp_tile_width() : fused_tile_width();
     const long long strips = (nx + W - 1) / W;
     int best = std::min(ny, 64);
     double best_cost = 1e300;
@@ -177,18 +169,13 @@ cudaError_t launch_step(fdlbm_ctx *h, cudaStream_t s)
         if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
         if (h->scheme == FDLBM_SCHEME_T2S2_2) return launch_fused_s2(a, s);
         if (walls) return launch_fused_walls(a, s);
-        if (h->variant == FDLBM_VARIANT_PACKED) return launch_fused_x2(a, a.err, s);
-        if (h->variant == FDLBM_VARIANT_WARP) return launch_fused_warp(a, h->tmap[h->cur], s);
-        if (h->variant == FDLBM_VARIANT_TMA) return launch_fused_tma(a, s);
-        if (h->variant == FDLBM_VARIANT_ASYNC) return launch_fused_async(a, s);
+        if (h->variant == FDLBM_VARIANT_WARP) return launch_fused_warp(a, h->wmaps, h->cur, s);
         return launch_fused(a, s);
     }
     auto a = step_args<double>(h);
     if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
     if (h->scheme == FDLBM_SCHEME_T2S2_2) return launch_fused_s2(a, s);
     if (walls) return launch_fused_walls(a, s);
-    if (h->variant == FDLBM_VARIANT_TMA) return launch_fused_tma(a, s);
-    if (h->variant == FDLBM_VARIANT_ASYNC) return launch_fused_async(a, s);
     return launch_fused(a, s);
 }
 
@@ -378,33 +365,22 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     if (!grid_ok(g) || !(nu > 0) || !(cfl > 0) || !(blend >= 0 && blend <= 1) ||
         !(o.A >= 0 && o.A <= 1) || !(o.rho0 > 0) ||
         (o.precision != FDLBM_FP64 && o.precision != FDLBM_FP32_DEV) || o.rows_per_cta < 0 || o.graph_steps < 0 ||
-        o.variant < FDLBM_VARIANT_AUTO || o.variant > FDLBM_VARIANT_WARP ||
+        (o.variant != FDLBM_VARIANT_AUTO && o.variant != FDLBM_VARIANT_SCALAR &&
+         o.variant != FDLBM_VARIANT_WARP) ||
         (o.scheme != FDLBM_SCHEME_T2S2_1 && o.scheme != FDLBM_SCHEME_T2S2_2) ||
         (o.equilibrium != FDLBM_EQ_STANDARD && o.equilibrium != FDLBM_EQ_INCOMPRESSIBLE))
         return FDLBM_EINVAL;
-    // the incompressible equilibrium runs on the default kernels only
-    if (o.equilibrium == FDLBM_EQ_INCOMPRESSIBLE &&
-        (o.adjoint || o.variant == FDLBM_VARIANT_TMA || o.variant == FDLBM_VARIANT_ASYNC ||
-         o.variant == FDLBM_VARIANT_PACKED))
-        return FDLBM_EUNSUPPORTED;
+    // the adjoint is written for the standard equilibrium only
+    if (o.equilibrium == FDLBM_EQ_INCOMPRESSIBLE && o.adjoint) return FDLBM_EUNSUPPORTED;
     const int path = force_staged ? FDLBM_PATH_STAGED : choose_path(g, &o);
     if (path < 0) return FDLBM_EUNSUPPORTED;
     const bool fused = path == FDLBM_PATH_FUSED;
     const bool f32 = o.precision == FDLBM_FP32_DEV;
-    // the variants are T2S2-FDLBM1 kernels; T2S2-FDLBM2 fuses on the scalar layout only
+    // the warp-tile kernel is a T2S2-FDLBM1 kernel; T2S2-FDLBM2 fuses on the scalar layout only
     const bool s1 = o.scheme == FDLBM_SCHEME_T2S2_1;
-    const bool packed_ok =
-        s1 && fused && !walled(g) && f32 && !o.has_force && fused_x2_ok(g->nx, g->ny);
-    const bool tma_ok = s1 && fused && !walled(g) &&
-                        (f32 ? fused_tma_ok<float>(g->nx, g->ny) : fused_tma_ok<double>(g->nx, g->ny));
     const bool periodic = !walled(g);
-    const bool warp_ok =
-        s1 && fused && periodic && f32 && !o.has_force && fused_warp_ok(g->nx, g->ny);
-    if ((o.variant == FDLBM_VARIANT_PACKED && !packed_ok) ||
-        (o.variant == FDLBM_VARIANT_WARP && !warp_ok) ||
-        (o.variant == FDLBM_VARIANT_TMA && !tma_ok) ||
-        (o.variant == FDLBM_VARIANT_ASYNC && (!s1 || !fused || walled(g))))
-        return FDLBM_EUNSUPPORTED;
+    const bool warp_ok = s1 && fused && periodic && f32 && fused_warp_ok(g->nx, g->ny);
+    if (o.variant == FDLBM_VARIANT_WARP && !warp_ok) return FDLBM_EUNSUPPORTED;
     int variant = o.variant;
     if (variant == FDLBM_VARIANT_AUTO) variant = warp_ok ? FDLBM_VARIANT_WARP : FDLBM_VARIANT_SCALAR;
     mx.assign(g->nx, 0.0);
@@ -561,11 +537,14 @@ fdlbm_status fdlbm_create(const fdlbm_grid *g, const fdlbm_metrics *metrics, dou
     }
     st = handle_upload(h, mx, my);
     if (st == FDLBM_OK && h->variant == FDLBM_VARIANT_WARP) {
-        // tensor maps of both ping-pong buffers for the warp-tile kernel
-        for (int b = 0; b < 2 && st == FDLBM_OK; ++b)
-            if (fused_warp_encode(h->tmap[b], reinterpret_cast<const float *>(h->ws + h->lay.state[b]),
-                                  h->nx, h->ny, h->pitch, h->plane) != cudaSuccess)
-                st = FDLBM_EUNSUPPORTED;
+        // tensor maps of both ping-pong buffers (and of the force field) for the
+        // warp-tile kernel
+        if (fused_warp_encode(&h->wmaps, reinterpret_cast<const float *>(h->ws + h->lay.state[0]),
+                              reinterpret_cast<const float *>(h->ws + h->lay.state[1]),
+                              h->has_force ? reinterpret_cast<const float *>(h->ws + h->lay.force)
+                                           : nullptr,
+                              h->nx, h->ny, h->pitch, h->plane) != cudaSuccess)
+            st = FDLBM_EUNSUPPORTED;
     }
     if (st != FDLBM_OK) {
         fdlbm_destroy(h);
@@ -892,10 +871,7 @@ const char *fdlbm_describe(fdlbm_t h)
     const bool walls = h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL;
     const char *kern = h->path == FDLBM_PATH_STAGED        ? "staged"
                        : walls                              ? "fused-walls"
-                       : h->variant == FDLBM_VARIANT_PACKED ? "fused-f32x2"
                        : h->variant == FDLBM_VARIANT_WARP   ? "fused-warp"
-                       : h->variant == FDLBM_VARIANT_TMA    ? "fused-tma"
-                       : h->variant == FDLBM_VARIANT_ASYNC  ? "fused-async"
                                                             : "fused";
     h->desc = std::string(kern) + " " + prec + " rows=" + std::to_string(h->rows);
     if (h->graph_steps) h->desc += " graph_steps=" + std::to_string(h->graph_steps);

@@ -133,7 +133,9 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 // Per-block partial sums of  J rho,  |u|^2,  |u - u_prev|^2  (J = 1/(m_x m_y)),
-// then u_prev <- u.  Grid-stride over nodes; fixed block count -> fixed order.
+// then u_prev <- u.  Rows are dealt to the blocks in a fixed stride and each
+// block's threads sweep a row's columns (coalesced, no index division); the
+// block count is fixed, so the order of the sums is too.
 template <class R>
 __global__ void __launch_bounds__(kRedThreads)
     k_reduce_partial(StepArgs<R> a, const R *force, const double *mxd, const double *myd,
@@ -142,20 +144,22 @@ __global__ void __launch_bounds__(kRedThreads)
     __shared__ double red[3][kRedThreads / 32];
     const size_t N = (size_t)a.nx * a.ny;
     double m = 0.0, uu = 0.0, du = 0.0;
-    for (size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x; n < N;
-         n += (size_t)gridDim.x * blockDim.x) {
-        const int y = (int)(n / a.nx), x = (int)(n % a.nx);
-        const size_t o = (size_t)y * a.pitch + x;
-        double r, u, v;
-        node_moments(a, force, o, rho0, half_dt, r, u, v);
-        m += r / (mxd[x] * myd[y]);
-        uu += u * u + v * v;
-        if (use_prev) {
-            const double eu = u - uprev[n], ev = v - uprev[N + n];
-            du += eu * eu + ev * ev;
+    for (int y = blockIdx.x; y < a.ny; y += gridDim.x) {
+        const double my = myd[y];
+        for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
+            const size_t n = (size_t)y * a.nx + x;
+            const size_t o = (size_t)y * a.pitch + x;
+            double r, u, v;
+            node_moments(a, force, o, rho0, half_dt, r, u, v);
+            m += r / (mxd[x] * my);
+            uu += u * u + v * v;
+            if (use_prev) {
+                const double eu = u - uprev[n], ev = v - uprev[N + n];
+                du += eu * eu + ev * ev;
+            }
+            uprev[n] = u;
+            uprev[N + n] = v;
         }
-        uprev[n] = u;
-        uprev[N + n] = v;
     }
     m = warp_sum(m);
     uu = warp_sum(uu);

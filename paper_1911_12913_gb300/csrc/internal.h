@@ -45,6 +45,16 @@ struct BatchTables {
     int blocks_s1;         // fused tables: tiles of T2S2-FDLBM1 cases, which come first
 };
 
+// Tensor maps (CUtensorMap, 128 bytes each) of the warp-tile kernel: the
+// ping-pong state buffers with boxes of 64 and 4 columns, and the force field.
+struct WarpMaps {
+    alignas(64) unsigned char state[2][128];
+    alignas(64) unsigned char side[2][128];
+    alignas(64) unsigned char force[128];
+    alignas(64) unsigned char force_side[128];
+    bool has_force = false;
+};
+
 struct Layout {
     size_t state[2], mx, my, mxd, myd, force, P, Q, S, uprev, partials, red, err, staging;
     size_t staging_elems, total;
@@ -68,7 +78,7 @@ struct fdlbm_ctx {
     bool in_batch = false;               // owned by a batch: stepped by fdlbm_batch_step
     bool adjoint = false;                // scratch for the adjoint step reserved
     int graph_steps = 0;                 // steps per replayed CUDA graph (even), 0 = none
-    unsigned char tmap[2][128] = {};     // tensor maps of state[0], state[1] (warp-tile kernel)
+    fdlbm::WarpMaps wmaps{};             // tensor maps of the warp-tile kernel
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int rows = 64;
@@ -111,29 +121,12 @@ int fused_s2_blocks_per_sm();
 template <class R>
 cudaError_t launch_batched_fused_s2(const BatchTables &t, int parity, int blk_off, int nblocks,
                                     cudaStream_t s);
-// step_fused_tma.cu (scalar sweep with bulk-copy row loads)
-template <class R>
-bool fused_tma_ok(int nx, int ny);
-template <class R>
-cudaError_t launch_fused_tma(const StepArgs<R> &a, cudaStream_t s);
-template <class R>
-int fused_tma_blocks_per_sm();
-// step_fused_async.cu (scalar sweep, per-thread cp.async row prefetch)
-template <class R>
-cudaError_t launch_fused_async(const StepArgs<R> &a, cudaStream_t s);
-template <class R>
-int fused_async_blocks_per_sm();
-// step_fused_x2.cu (FP32, two strips per CTA in packed f32x2, bulk-copy loads)
-bool fused_x2_ok(int nx, int ny);
-cudaError_t launch_fused_x2(const StepArgs<float> &a, int *err, cudaStream_t s);
-int fused_x2_tile_width();
-int fused_x2_blocks_per_sm();
 // step_fused_warp.cu (FP32, one independent warp per tile, packed f32x2)
 bool fused_warp_ok(int nx, int ny);
-size_t fused_warp_map_bytes();
-cudaError_t fused_warp_encode(void *map, const float *state, int nx, int ny, int pitch,
-                              size_t plane);
-cudaError_t launch_fused_warp(const StepArgs<float> &a, const void *map_in, cudaStream_t s);
+cudaError_t fused_warp_encode(WarpMaps *m, const float *state0, const float *state1,
+                              const float *force, int nx, int ny, int pitch, size_t plane);
+cudaError_t launch_fused_warp(const StepArgs<float> &a, const WarpMaps &maps, int cur,
+                              cudaStream_t s);
 int fused_warp_tile_width();
 int fused_warp_blocks_per_sm();
 // step_fused_walls.cu (scalar sweep with walled axes and Eq. 3.10 inside)

@@ -198,6 +198,57 @@ __device__ __forceinline__ void relax2_j(const MacroJ &m, const f2 g[9], const R
     pair(sub2(m.jy, m.jx), k.bw2, k.bc2, k.nbc2, 6, 8);
 }
 
+// The forcing term of Eq. 3.12 for the pair, premultiplied by k = 3 c for the
+// weight c of the transform it enters (Eqs. 2.20, 2.32, 2.34):
+//   k/3 F_i = k (xi_i.F - u.F) f_i^eq,   f_i^eq = w_i rf + geq_i,
+// with rf = rho0 (f^eq of Eq. 3.2; geq is its deviation from w_i rho0) or
+// rf = rho0 - drho under the incompressible equilibrium, whose forcing term
+// takes the equilibrium at rho0.  uF = u.F.  out_i += (k/3) F_i for two
+// transforms (k1, k2) at once; q returns f_i^eq for reuse.
+__device__ __forceinline__ void force_add2(const f2 geq[9], f2 rf, f2 Fx, f2 Fy, f2 uF, f2 k1,
+                                           f2 k2, f2 out1[9], f2 out2[9])
+{
+    const float w[3] = {4.f / 9.f, 1.f / 9.f, 1.f / 36.f};
+    auto one = [&](int i, f2 tF, int wc) {
+        const f2 q = fma2(bc(w[wc]), rf, geq[i]);
+        out1[i] = fma2(mul2(k1, tF), q, out1[i]);
+        out2[i] = fma2(mul2(k2, tF), q, out2[i]);
+    };
+    const f2 nuF = mul2(bc(-1.f), uF);
+    one(0, nuF, 0);
+    one(1, sub2(Fx, uF), 1);
+    one(3, sub2(nuF, Fx), 1);
+    one(2, sub2(Fy, uF), 1);
+    one(4, sub2(nuF, Fy), 1);
+    const f2 s = add2(Fx, Fy), d = sub2(Fy, Fx);
+    one(5, sub2(s, uF), 2);
+    one(7, sub2(nuF, s), 2);
+    one(6, sub2(d, uF), 2);
+    one(8, sub2(nuF, d), 2);
+}
+
+// The same for one transform.
+__device__ __forceinline__ void force_add1(const f2 geq[9], f2 rf, f2 Fx, f2 Fy, f2 uF, f2 k1,
+                                           f2 out1[9])
+{
+    const float w[3] = {4.f / 9.f, 1.f / 9.f, 1.f / 36.f};
+    auto one = [&](int i, f2 tF, int wc) {
+        const f2 q = fma2(bc(w[wc]), rf, geq[i]);
+        out1[i] = fma2(mul2(k1, tF), q, out1[i]);
+    };
+    const f2 nuF = mul2(bc(-1.f), uF);
+    one(0, nuF, 0);
+    one(1, sub2(Fx, uF), 1);
+    one(3, sub2(nuF, Fx), 1);
+    one(2, sub2(Fy, uF), 1);
+    one(4, sub2(nuF, Fy), 1);
+    const f2 s = add2(Fx, Fy), d = sub2(Fy, Fx);
+    one(5, sub2(s, uF), 2);
+    one(7, sub2(nuF, s), 2);
+    one(6, sub2(d, uF), 2);
+    one(8, sub2(nuF, d), 2);
+}
+
 // sign(c) * D_m f at the centre from f(k-2..k+2); w = {wm1, w0, w1, w2} of
 // make_stencil (lattice.cuh).
 __device__ __forceinline__ f2 stencil2(const float w[4], int sgn, f2 vm2, f2 vm1, f2 v0, f2 vp1,

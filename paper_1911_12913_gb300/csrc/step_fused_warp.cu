@@ -73,26 +73,54 @@ constexpr unsigned kFull = 0xffffffffu;
 #endif
 constexpr uint32_t kRowBytes = 9u * kCols * sizeof(float);
 
+// Columns of the other side of the seam that a seam window needs: 4 (the
+// x-halo); with a force field the side rings hold just these (a tensor copy
+// of box 4 x 1 x 9, or 4 x 1 x 2 for the force), which keeps the forced
+// kernel's shared memory within eight warps per SM.
+constexpr int kSide = 4;
+constexpr int kFRing = 5;                        // force rows r-2 .. r+2
+constexpr uint32_t kSideSlot = 256;              // bytes per side-ring slot (144 used)
+constexpr uint32_t kFSideSlot = 128;             // bytes per force side-ring slot (32 used)
+constexpr uint32_t kFRowBytes = 2u * kCols * sizeof(float);
+
+template <bool FORCE>
 struct WarpSmem {
-    float ring[kStages][9][kCols];  // f~ rows of the window, [pop][window column]
-    float wrap[kStages][9][kCols];  // the same rows at the other side of the seam
-    f2 Q[kQRing][9][kLanes];        // f~+ of the lane's two columns
+    float ring[kStages][9][kCols];                // f~ rows of the window, [pop][window column]
+    // the same rows at the other side of the seam: 64 columns, or with a force
+    // field the 4 columns next to the seam ([pop][4], one 256-byte slot per row)
+    float wrap[kStages][FORCE ? kSideSlot / 4 : 9 * kCols];
+    float fring[FORCE ? kFRing : 1][2][kCols];    // force rows, [component][window column]
+    float fwrap[FORCE ? kFRing : 1][kFSideSlot / 4];  // force columns next to the seam, [2][4]
+    f2 Q[kQRing][9][kLanes];                      // f~+ of the lane's two columns
     uint64_t bar[kStages];
 };
-static_assert(offsetof(WarpSmem, wrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
+static_assert(offsetof(WarpSmem<false>, wrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
+static_assert(offsetof(WarpSmem<true>, wrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
+static_assert(offsetof(WarpSmem<true>, fring) % 128 == 0, "tensor-copy destinations are 128-B aligned");
+static_assert(offsetof(WarpSmem<true>, fwrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
 
 struct ArgsW {
-    CUtensorMap tin;  // the input state: dims (nx, ny, 9), box (64, 1, 9)
+    CUtensorMap tin;    // the input state: dims (nx, ny, 9), box (64, 1, 9)
+    CUtensorMap tside;  // the same with box (4, 1, 9) (force field only)
+    CUtensorMap tf;     // the force field: dims (nx, ny, 2), box (64, 1, 2)
+    CUtensorMap tfside; // the same with box (4, 1, 2)
     float *gout;
     const float *mx, *my;
     int nx, ny, pitch;
     size_t plane;
     int rows;
+    // output rectangle: columns [xoff + 56 bx, ...) below xend, rows [yoff + rows by,
+    // ...) below yend (the whole grid on a periodic one)
+    int xoff, xend, yoff, yend;
     float rho0, h, dt, b_bar, b_til, b_star;
     float w[4];  // wm1, w0, w1, w2
     int *err;
     float inv_rho0;  // incompressible equilibrium only
     RelaxK kstar;    // the relaxation of Eq. 2.52 (b = b_star) as packed weights
+    // force field: shifts dt/2 and h/2 of the first moments (Eq. 3.3 and its
+    // analogue for fbar), and 3 x the weights of the forcing term in fbar^{+,h}
+    // (Eq. 2.34 after Eq. 2.19), f~+ (Eq. 2.20) and f* (Eq. 2.32)
+    float hdt, hh, k_bar, k_til, k_star;
 };
 
 // The weights of the update's differences (stage C) for a scale s = -dt m:
@@ -157,32 +185,50 @@ __device__ __forceinline__ f2 ytaps(const f2 c[3], int sgn, f2 vm2, f2 vm1, f2 v
 
 // INC: the incompressible equilibrium of He and Luo (velocity from rho0 u).
 // GRID: how the update's weights are made to sum to zero (update_weights).
-template <bool INC, bool GRID>
+// FORCE: a body-acceleration field (Eqs. 3.3 and 3.12), whose rows arrive by
+// tensor copy with the rows of f~ into a 5-row ring (stage B reads row r-2).
+template <bool INC, bool GRID, bool FORCE>
 __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     k_step_fused_warp(const __grid_constant__ ArgsW a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    WarpSmem &sm = *reinterpret_cast<WarpSmem *>(smem_raw);
+    WarpSmem<FORCE> &sm = *reinterpret_cast<WarpSmem<FORCE> *>(smem_raw);
 
     const int l = threadIdx.x;
-    const int x0 = blockIdx.x * kW;        // first output column
-    const int y0 = blockIdx.y * a.rows;
-    if (y0 >= a.ny) return;                // uniform over the warp
-    const int y1 = min(y0 + a.rows, a.ny);
+    const int x0 = a.xoff + blockIdx.x * kW;  // first output column
+    const int y0 = a.yoff + blockIdx.y * a.rows;
+    if (y0 >= a.yend) return;              // uniform over the warp
+    const int y1 = min(y0 + a.rows, a.yend);
     const int iters = (y1 - y0) + 2 * kHalo;
     const int xs = x0 - kHalo;             // window start before wrapping
     const int xc = xs + 2 * l;             // the lane's first column
     const int gx = wrap_index(xc, a.nx);   // even, and gx + 1 < nx
-    const bool store = (l >= 2) && (l < kLanes - 2) && (xc < a.nx);
+    const bool store = (l >= 2) && (l < kLanes - 2) && (xc < a.xend);
 
     // ---- where the lane's pair lands: the main ring, or the side ring filled
     // from x = nx - 4 (first window) or x = 0 (last window)
     const bool wrap_lo = xs < 0, wrap_hi = xs + kCols > a.nx;
     const int wrap_x = wrap_lo ? a.nx - kHalo : 0;
-    uint32_t rd = (uint32_t)offsetof(WarpSmem, ring) + 8u * (uint32_t)l;
-    if (xc < 0) rd = (uint32_t)offsetof(WarpSmem, wrap) + 4u * (uint32_t)(xc + kHalo);
-    if (xc >= a.nx) rd = (uint32_t)offsetof(WarpSmem, wrap) + 4u * (uint32_t)(xc - a.nx);
+    uint32_t rd = (uint32_t)offsetof(WarpSmem<FORCE>, ring) + 8u * (uint32_t)l;
+    uint32_t pstride = kCols * sizeof(float);  // bytes between populations
+    uint32_t frd = (uint32_t)offsetof(WarpSmem<FORCE>, fring) + 8u * (uint32_t)l;
+    uint32_t fstride = kCols * sizeof(float);  // bytes between force components
+    if (!FORCE) {
+        if (xc < 0) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc + kHalo);
+        if (xc >= a.nx) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc - a.nx);
+    } else {
+        // side rings of 4 columns; lanes further past the seam read the main
+        // ring's zero fill (their values reach no output)
+        const int side = xc < 0 ? xc + kHalo : (xc >= a.nx && xc < a.nx + kSide ? xc - a.nx : -1);
+        if (side >= 0) {
+            rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)side;
+            pstride = kSide * sizeof(float);
+            frd = (uint32_t)offsetof(WarpSmem<FORCE>, fwrap) + 4u * (uint32_t)side;
+            fstride = kSide * sizeof(float);
+        }
+    }
     const unsigned char *rd_base = smem_raw + rd;
+    const unsigned char *frd_base = smem_raw + frd;
 
     // ---- constants: the x weights carry -h m_x (stage B) and -dt m_x (stage C)
     const f2 rho0 = bc(a.rho0);
@@ -206,18 +252,31 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     const f2 bbar = bc(a.b_bar), btil = bc(a.b_til);
 
     const uint32_t bar0 = smem_addr(&sm.bar[0]);
-    const uint32_t ring0 = smem_addr(&sm.ring[0][0][0]), wrap0 = smem_addr(&sm.wrap[0][0][0]);
-    const uint32_t tx = (wrap_lo || wrap_hi) ? 2u * kRowBytes : kRowBytes;
+    const uint32_t ring0 = smem_addr(&sm.ring[0][0][0]), wrap0 = smem_addr(&sm.wrap[0][0]);
+    const uint32_t fring0 = smem_addr(&sm.fring[0][0][0]), fwrap0 = smem_addr(&sm.fwrap[0][0]);
+    const bool seam = wrap_lo || wrap_hi;
+    const uint32_t tx = FORCE ? kRowBytes + kFRowBytes + (seam ? 9u * kSide * 4u + 2u * kSide * 4u : 0u)
+                              : (seam ? 2u * kRowBytes : kRowBytes);
     int ld_row = wrap_index(y0 - kHalo, a.ny);  // next row to request
-    auto issue = [&](int slot) {
+    // rows into f~ slot `slot` and (force field) force slot `fslot`
+    auto issue = [&](int slot, int fslot) {
         if (l == 0) {
             fence_proxy_async();
             const uint32_t bar = bar0 + 8u * (uint32_t)slot;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx)
                          : "memory");
             tensor_copy_3d(ring0 + (uint32_t)slot * kRowBytes, &a.tin, xs, ld_row, 0, bar);
-            if (wrap_lo || wrap_hi)
-                tensor_copy_3d(wrap0 + (uint32_t)slot * kRowBytes, &a.tin, wrap_x, ld_row, 0, bar);
+            if (!FORCE) {
+                if (seam)
+                    tensor_copy_3d(wrap0 + (uint32_t)slot * kRowBytes, &a.tin, wrap_x, ld_row, 0, bar);
+            } else {
+                tensor_copy_3d(fring0 + (uint32_t)fslot * kFRowBytes, &a.tf, xs, ld_row, 0, bar);
+                if (seam) {
+                    tensor_copy_3d(wrap0 + (uint32_t)slot * kSideSlot, &a.tside, wrap_x, ld_row, 0, bar);
+                    tensor_copy_3d(fwrap0 + (uint32_t)fslot * kFSideSlot, &a.tfside, wrap_x, ld_row, 0,
+                                   bar);
+                }
+            }
         }
         ld_row = ld_row + 1 == a.ny ? 0 : ld_row + 1;
     };
@@ -227,7 +286,7 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
         mbar_init_fence();
     }
     __syncwarp();
-    for (int s = 0; s < kStages && s < iters; ++s) issue(s);
+    for (int s = 0; s < kStages && s < iters; ++s) issue(s, s);
 
     f2 Pw[9][5];  // fbar^{+,h} of the lane's columns, slot = iteration mod 5
     f2 Sw[9][5];  // f*
@@ -242,6 +301,14 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     uint32_t parity = 0;   // mbarrier phase parity of the current slot
     bool timed_out = false;
 
+    // force of the lane's pair from force slot fs (components x, y)
+    auto force_of = [&](int fs, f2 &Fx, f2 &Fy) {
+        const unsigned char *src = frd_base + fs * kFRowBytes;
+        if (FORCE && fstride != kCols * sizeof(float)) src = frd_base + fs * kFSideSlot;
+        Fx = *reinterpret_cast<const f2 *>(src);
+        Fy = *reinterpret_cast<const f2 *>(src + fstride);
+    };
+
     auto row = [&](auto PHc, int k) {
         constexpr int PH = decltype(PHc)::value;
         constexpr int p0 = PH, p1 = (PH + 4) % 5, p2 = (PH + 3) % 5, p3 = (PH + 2) % 5,
@@ -249,18 +316,47 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
         // ------------------------------------------------------------ A (row r)
         if (!mbar_wait_bounded(&sm.bar[slot], parity)) timed_out = true;
         {
-            const unsigned char *src = rd_base + slot * kRowBytes;
+            const unsigned char *src =
+                rd_base + slot * (FORCE && pstride != kCols * sizeof(float) ? kSideSlot : kRowBytes);
             f2 g[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i)
-                g[i] = *reinterpret_cast<const f2 *>(src + i * kCols * sizeof(float));
+                g[i] = *reinterpret_cast<const f2 *>(src + i * (FORCE ? pstride : kCols * sizeof(float)));
             f2 geq[9];
-            equilibrium2_j(INC ? moments2_j_incomp(g, bc(a.inv_rho0)) : moments2_j(g, rho0), geq);
+            if (!FORCE) {
+                equilibrium2_j(INC ? moments2_j_incomp(g, bc(a.inv_rho0)) : moments2_j(g, rho0), geq);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const f2 neq = sub2(geq[i], g[i]);
-                Pw[i][p0] = fma2(bbar, neq, g[i]);
-                sm.Q[PH][i][l] = fma2(btil, neq, g[i]);
+                for (int i = 0; i < 9; ++i) {
+                    const f2 neq = sub2(geq[i], g[i]);
+                    Pw[i][p0] = fma2(bbar, neq, g[i]);
+                    sm.Q[PH][i][l] = fma2(btil, neq, g[i]);
+                }
+            } else {
+                f2 Fx, Fy;
+                force_of(p0, Fx, Fy);
+                // Eq. 3.3: rho u = sum xi f~ + (dt/2) rho F
+                MacroJ m = INC ? moments2_j_incomp(g, bc(a.inv_rho0)) : moments2_j(g, rho0);
+                const f2 hr = mul2(bc(a.hdt), INC ? rho0 : add2(rho0, m.drho));
+                m.jx = fma2(hr, Fx, m.jx);
+                m.jy = fma2(hr, Fy, m.jy);
+                equilibrium2_j(m, geq);
+                const f2 uF = mul2(fma2(m.jx, Fx, mul2(m.jy, Fy)), m.inv);
+                f2 P[9], Qv[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const f2 neq = sub2(geq[i], g[i]);
+                    P[i] = fma2(bbar, neq, g[i]);
+                    Qv[i] = fma2(btil, neq, g[i]);
+                }
+                // Eq. 3.12 at the equilibrium of Eq. 3.2 (at rho0 under the
+                // incompressible one)
+                force_add2(geq, INC ? sub2(rho0, m.drho) : rho0, Fx, Fy, uF, bc(a.k_bar),
+                           bc(a.k_til), P, Qv);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    Pw[i][p0] = P[i];
+                    sm.Q[PH][i][l] = Qv[i];
+                }
             }
         }
         // ------------------------------------------------------------ B (row r-2)
@@ -285,9 +381,26 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 if (cy(i) != 0) acc = ytaps(ay, cy(i), Pw[i][p4], Pw[i][p3], Pw[i][p1], Pw[i][p0], acc);
                 gs[i] = acc;
             }
-            // Eq. 2.52: f* = f-bar* + b* (f^eq* - f-bar*), folded into the equilibrium
             f2 fs[9];
-            relax2_j(INC ? moments2_j_incomp(gs, bc(a.inv_rho0)) : moments2_j(gs, rho0), gs, a.kstar, fs);
+            if (!FORCE) {
+                // Eq. 2.52: f* = f-bar* + b* (f^eq* - f-bar*), folded into the equilibrium
+                relax2_j(INC ? moments2_j_incomp(gs, bc(a.inv_rho0)) : moments2_j(gs, rho0), gs, a.kstar, fs);
+            } else {
+                // Eq. 2.32 with the force of row r-2: rho u = sum xi fbar + (h/2) rho F
+                f2 Fx, Fy;
+                force_of(p2, Fx, Fy);
+                MacroJ m = INC ? moments2_j_incomp(gs, bc(a.inv_rho0)) : moments2_j(gs, rho0);
+                const f2 hr = mul2(bc(a.hh), INC ? rho0 : add2(rho0, m.drho));
+                m.jx = fma2(hr, Fx, m.jx);
+                m.jy = fma2(hr, Fy, m.jy);
+                f2 ge[9];
+                equilibrium2_j(m, ge);
+                const f2 uF = mul2(fma2(m.jx, Fx, mul2(m.jy, Fy)), m.inv);
+                const f2 bst = bc(a.b_star);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fs[i] = fma2(bst, sub2(ge[i], gs[i]), gs[i]);
+                force_add1(ge, INC ? sub2(rho0, m.drho) : rho0, Fx, Fy, uF, bc(a.k_star), fs);
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) Sw[i][p0] = fs[i];
         }
@@ -321,11 +434,12 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 if (st) *reinterpret_cast<f2 *>(a.gout + (roff + (unsigned)i * plane32)) = acc;
             }
         }
-        // every lane has read the slot: refill it three rows ahead.  The copy
-        // is issued at the end of the row so that its memory ordering does not
-        // split stages A and B, C into separately scheduled regions.
+        // every lane has read the slot: refill it three rows ahead (force slot
+        // (k + 3) mod 5, which stage B has just read).  The copy is issued at
+        // the end of the row so that its memory ordering does not split stages
+        // A and B, C into separately scheduled regions.
         __syncwarp();
-        if (k + kStages < iters) issue(slot);
+        if (k + kStages < iters) issue(slot, (PH + 3) % 5);
         if (++slot == kStages) {
             slot = 0;
             parity ^= 1u;
@@ -378,34 +492,76 @@ bool fused_warp_ok(int nx, int ny)
     return nx % 4 == 0 && nx >= kCols && ny >= 4 && 9ull * pitch * (unsigned long long)ny < (1ull << 32);
 }
 
-size_t fused_warp_map_bytes() { return sizeof(CUtensorMap); }
+namespace {
 
-// Tensor map of one FP32 state buffer [9][ny][pitch]: dims (nx, ny, 9), byte
-// strides (4 pitch, 4 plane), box (64, 1, 9).  Columns outside [0, nx) read
-// as zero (the kernel takes them from the wrapped copy).
-cudaError_t fused_warp_encode(void *map, const float *state, int nx, int ny, int pitch,
-                              size_t plane)
+// Tensor map of an FP32 field [depth][ny][pitch]: dims (nx, ny, depth), byte
+// strides (4 pitch, 4 plane), box (box_x, 1, depth).  Columns outside [0, nx)
+// read as zero (the kernel takes the wrapped ones from the side copies).
+cudaError_t encode(unsigned char *map, const float *base, int nx, int ny, int pitch, size_t plane,
+                   int depth, int box_x)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
     CUtensorMap m;
-    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, 9};
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)depth};
     const cuuint64_t strides[2] = {(cuuint64_t)pitch * sizeof(float), (cuuint64_t)plane * sizeof(float)};
-    const cuuint32_t box[3] = {kCols, 1, 9};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, 1, (cuuint32_t)depth};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                          const_cast<float *>(state), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     std::memcpy(map, &m, sizeof m);
     return cudaSuccess;
 }
 
-cudaError_t launch_fused_warp(const StepArgs<float> &s, const void *map_in, cudaStream_t stream)
+}  // namespace
+
+static_assert(sizeof(CUtensorMap) == sizeof(WarpMaps::state[0]), "tensor map size");
+
+// The tensor maps of both ping-pong buffers (and of the force field, if any).
+cudaError_t fused_warp_encode(WarpMaps *m, const float *state0, const float *state1,
+                              const float *force, int nx, int ny, int pitch, size_t plane)
+{
+    const float *st[2] = {state0, state1};
+    for (int b = 0; b < 2; ++b) {
+        cudaError_t e = encode(m->state[b], st[b], nx, ny, pitch, plane, 9, kCols);
+        if (e == cudaSuccess && force) e = encode(m->side[b], st[b], nx, ny, pitch, plane, 9, kSide);
+        if (e != cudaSuccess) return e;
+    }
+    m->has_force = force != nullptr;
+    if (force) {
+        cudaError_t e = encode(m->force, force, nx, ny, pitch, plane, 2, kCols);
+        if (e == cudaSuccess) e = encode(m->force_side, force, nx, ny, pitch, plane, 2, kSide);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <bool INC, bool GRID, bool FORCE>
+cudaError_t launch_t(const ArgsW &a, dim3 grid, cudaStream_t stream)
+{
+    constexpr size_t smem = sizeof(WarpSmem<FORCE>);
+    auto kern = k_step_fused_warp<INC, GRID, FORCE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kLanes, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused_warp(const StepArgs<float> &s, const WarpMaps &maps, int cur,
+                              cudaStream_t stream)
 {
     ArgsW a;
-    std::memcpy(&a.tin, map_in, sizeof(CUtensorMap));
+    std::memset(&a, 0, sizeof a);
+    const bool force = s.force != nullptr;
+    if (force && !maps.has_force) return cudaErrorInvalidValue;
+    std::memcpy(&a.tin, maps.state[cur], sizeof(CUtensorMap));
+    if (force) {
+        std::memcpy(&a.tside, maps.side[cur], sizeof(CUtensorMap));
+        std::memcpy(&a.tf, maps.force, sizeof(CUtensorMap));
+        std::memcpy(&a.tfside, maps.force_side, sizeof(CUtensorMap));
+    }
     a.gout = s.gout;
     a.mx = s.mx;
     a.my = s.my;
@@ -414,6 +570,10 @@ cudaError_t launch_fused_warp(const StepArgs<float> &s, const void *map_in, cuda
     a.pitch = s.pitch;
     a.plane = s.plane;
     a.rows = s.rows;
+    a.xoff = 0;
+    a.xend = s.nx;
+    a.yoff = 0;
+    a.yend = s.ny;
     a.rho0 = s.c.rho0;
     a.h = s.c.h;
     a.dt = s.c.dt;
@@ -427,16 +587,21 @@ cudaError_t launch_fused_warp(const StepArgs<float> &s, const void *map_in, cuda
     a.err = s.err;
     a.inv_rho0 = 1.0f / s.c.rho0;
     a.kstar = make_relax(s.c.b_star);
-    constexpr size_t smem = sizeof(WarpSmem);
+    a.hdt = s.c.half_dt;
+    a.hh = s.c.half_h;
+    a.k_bar = 3.0f * s.c.c_bar;
+    a.k_til = 3.0f * s.c.c_til;
+    a.k_star = 3.0f * s.c.c_star;
     // the Sterbenz-ordered update weights need wm1 >= 0.55 |w1| (beta <= 0.16)
     const bool on_grid = !(s.st.wm1 >= 0.55f * std::fabs(s.st.w1));
-    auto kern = s.c.incomp ? (on_grid ? k_step_fused_warp<true, true> : k_step_fused_warp<true, false>)
-                           : (on_grid ? k_step_fused_warp<false, true> : k_step_fused_warp<false, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((s.nx + kW - 1) / kW, (s.ny + s.rows - 1) / s.rows);
-    kern<<<grid, kLanes, smem, stream>>>(a);
-    return cudaGetLastError();
+    const dim3 grid((s.nx + kW - 1) / kW, (s.ny + s.rows - 1) / s.rows);
+    const bool inc = s.c.incomp != 0;
+    if (force) {
+        if (inc) return on_grid ? launch_t<true, true, true>(a, grid, stream) : launch_t<true, false, true>(a, grid, stream);
+        return on_grid ? launch_t<false, true, true>(a, grid, stream) : launch_t<false, false, true>(a, grid, stream);
+    }
+    if (inc) return on_grid ? launch_t<true, true, false>(a, grid, stream) : launch_t<true, false, false>(a, grid, stream);
+    return on_grid ? launch_t<false, true, false>(a, grid, stream) : launch_t<false, false, false>(a, grid, stream);
 }
 
 int fused_warp_tile_width() { return kW; }
@@ -444,11 +609,10 @@ int fused_warp_tile_width() { return kW; }
 int fused_warp_blocks_per_sm()
 {
     int n = 0;
-    constexpr size_t smem = sizeof(WarpSmem);
-    cudaFuncSetAttribute(k_step_fused_warp<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step_fused_warp<false, false>, kLanes, smem) !=
-        cudaSuccess)
-        return 0;
+    constexpr size_t smem = sizeof(WarpSmem<false>);
+    auto kern = k_step_fused_warp<false, false, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kLanes, smem) != cudaSuccess) return 0;
     return n;
 }
 

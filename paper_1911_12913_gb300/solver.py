@@ -59,8 +59,7 @@ class FDLBM:
         o.graph_steps = graph_steps
         o.equilibrium = {"standard": B.EQ_STANDARD, "incompressible": B.EQ_INCOMPRESSIBLE}[equilibrium]
         o.variant = {"auto": B.VARIANT_AUTO, "scalar": B.VARIANT_SCALAR,
-                     "packed": B.VARIANT_PACKED, "tma": B.VARIANT_TMA,
-                     "async": B.VARIANT_ASYNC, "warp": B.VARIANT_WARP}[variant]
+                     "warp": B.VARIANT_WARP}[variant]
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         o.stream = self.stream.cuda_stream
         nbytes = L.fdlbm_workspace_bytes(ctypes.byref(self._grid), ctypes.byref(o))

@@ -106,7 +106,7 @@ def test_workspace_and_validation_without_gpu(B):
     o.path = B.PATH_STAGED
     assert L.fdlbm_workspace_bytes(ctypes.byref(grid), ctypes.byref(o)) > n32
     # walled grids take the fused path (Eq. 3.10 inside the sweep), for both
-    # schemes; the fused variants of T2S2-FDLBM1 do not run T2S2-FDLBM2
+    # schemes; the warp-tile kernel does not run T2S2-FDLBM2
     wa = I.wall_axis(20, 0.0, 1.0)
     wgrid, keep2 = B.make_grid(xa, wa)
     o.path = B.PATH_FUSED
@@ -133,20 +133,23 @@ def test_workspace_and_validation_without_gpu(B):
     assert L.fdlbm_create(ctypes.byref(grid), ctypes.byref(mneg), 0.01, 0.5, 0.1, None,
                           ctypes.byref(h)) == -1
     # the equilibrium option: unknown values are invalid; the incompressible
-    # equilibrium has no adjoint step and no TMA / ASYNC / PACKED variant
+    # equilibrium has no adjoint step
     L.fdlbm_default_opts(ctypes.byref(o))
     o.equilibrium = 2
     assert L.fdlbm_create(ctypes.byref(grid), None, 0.01, 0.5, 0.1, ctypes.byref(o),
                           ctypes.byref(h)) == -1
+    L.fdlbm_default_opts(ctypes.byref(o))
     o.equilibrium = B.EQ_INCOMPRESSIBLE
-    for field, value in (("adjoint", 1), ("variant", B.VARIANT_TMA), ("variant", B.VARIANT_ASYNC),
-                         ("variant", B.VARIANT_PACKED)):
+    o.precision = B.FP32_DEV
+    o.adjoint = 1
+    assert L.fdlbm_create(ctypes.byref(grid), None, 0.01, 0.5, 0.1, ctypes.byref(o),
+                          ctypes.byref(h)) == -5
+    # variant values that name no kernel are invalid
+    for value in (2, 3, 4, 6, -1):
         L.fdlbm_default_opts(ctypes.byref(o))
-        o.equilibrium = B.EQ_INCOMPRESSIBLE
-        o.precision = B.FP32_DEV
-        setattr(o, field, value)
+        o.variant = value
         assert L.fdlbm_create(ctypes.byref(grid), None, 0.01, 0.5, 0.1, ctypes.byref(o),
-                              ctypes.byref(h)) == -5, (field, value)
+                              ctypes.byref(h)) == -1, value
     assert L.fdlbm_status_string(-4) == b"non-finite result"
     assert L.fdlbm_last_error(None) == b"NULL handle"
     L.fdlbm_destroy(None)

@@ -7,6 +7,7 @@ import pytest
 
 import inputs as I
 import oracle as O
+from conftest import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -16,6 +17,19 @@ if not torch.cuda.is_available():
 
 from paper_1911_12913_gb300 import binding as B  # noqa: E402
 from paper_1911_12913_gb300.solver import FDLBMBatch  # noqa: E402
+
+
+# FP32 bounds, about 10x the largest errors measured on GB300 over these tests
+# (relative L2 of f~ up to 1.5e-8 after 12-25 steps from random states, 3e-8
+# after 400 cavity steps; L-infinity of the error relative to the largest
+# deviation f~ - w_i rho0 up to 1.9e-6).  The deviations are O(u) ~ 1e-2 and
+# each step rounds them to 2^-24 relative, so a few steps leave errors of a
+# few 1e-8 of the deviation at most nodes and the largest of about 1e-6.
+# FP64: the L2 bound the benchmark spec fixes, and 1e-11 on the deviation
+# (measured up to 4.7e-13).
+FP32_L2 = 1e-7
+FP32_DEV = 2e-5
+FP64_DEV = 1e-11
 
 
 def rel(a, b):
@@ -80,10 +94,10 @@ def _setup(batch, cases):
 
 
 @pytest.mark.parametrize("precision,tol,autotune,mode",
-                         [("fp64", 1e-12, False, "auto"), ("fp32", 2e-6, True, "auto"),
-                          ("fp32", 2e-6, True, "fused"), ("fp32", 2e-6, False, "staged"),
-                          ("fp64", 1e-12, False, "persistent"), ("fp32", 2e-6, False, "persistent"),
-                          ("fp32", 2e-6, True, "persistent-fused")])
+                         [("fp64", 1e-12, False, "auto"), ("fp32", FP32_L2, True, "auto"),
+                          ("fp32", FP32_L2, True, "fused"), ("fp32", FP32_L2, False, "staged"),
+                          ("fp64", 1e-12, False, "persistent"), ("fp32", FP32_L2, False, "persistent"),
+                          ("fp32", FP32_L2, True, "persistent-fused")])
 def test_mixed_batch_matches_oracle(precision, tol, autotune, mode):
     """The batch modes: the fused sweep with walls (FP32, T2S2-FDLBM1 cases
     only, the default where it applies), per-stage launches of the staged
@@ -108,8 +122,9 @@ def test_mixed_batch_matches_oracle(precision, tol, autotune, mode):
             o.step(n)
     batch.sync()
     for c, o in enumerate(oracles):
-        err = rel(batch.case(c).get_state(), o.f)
-        assert err <= tol, (c, err, batch.describe)
+        assert_parity(batch.case(c).get_state(), o.f, l2=tol,
+                      dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                      label=f"{batch.describe} case {c}")
     print(batch.describe)
 
 
@@ -168,8 +183,8 @@ def test_sweep_64_cases_sampled_parity():
         one = np.ones((p["ya"].n, p["xa"].n))
         o.init_fields(one, 0 * one, 0 * one)
         o.step(steps)
-        err = rel(batch.case(c).get_state(), o.f)
-        assert err <= 2e-6, (c, specs[c], err)
+        assert_parity(batch.case(c).get_state(), o.f, l2=FP32_L2, dev=FP32_DEV,
+                      label=f"64-case sweep case {c} {specs[c]}")
     for c in range(len(specs)):
         m, _ = batch.case(c).reduce()       # raises on NaN/Inf
         assert math.isfinite(m)
@@ -203,6 +218,7 @@ def test_persistent_barrier_timeout_is_reported(precision, scheme1_only):
         for o in oracles:
             o.step(n)
     batch.sync()
-    tol = 1e-12 if precision == "fp64" else 2e-6
+    tol = 1e-12 if precision == "fp64" else FP32_L2
     for c, o in enumerate(oracles):
-        assert rel(batch.case(c).get_state(), o.f) <= tol, c
+        assert_parity(batch.case(c).get_state(), o.f, l2=tol,
+                      dev=FP64_DEV if precision == "fp64" else FP32_DEV, label=f"case {c}")

@@ -13,6 +13,7 @@ import pytest
 
 import inputs as I
 import oracle as O
+from conftest import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +46,7 @@ def _solver(precision, graph_steps=100):
     return ax, s
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-7)])
 def test_cavity_257_matches_oracle_through_graph_replay(precision, tol):
     from conftest import oracle_threads
     ax, s = _solver(precision)
@@ -58,9 +59,8 @@ def test_cavity_257_matches_oracle_through_graph_replay(precision, tol):
         s.step(n)
         o.step(n)
     s.sync()
-    err = rel(s.get_state(), o.f)
-    print(f"cavity 257^2 {precision}: rel L2 of f~ after 1000 steps {err:.2e}")
-    assert err <= tol
+    assert_parity(s.get_state(), o.f, l2=tol, dev=1e-11 if precision == "fp64" else 5e-6,
+                  label=f"cavity 257^2 {precision} after 1000 steps")
 
 
 def _centres(ax, s):

@@ -10,6 +10,7 @@ import pytest
 
 import inputs as I
 import oracle as O
+from conftest import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -20,6 +21,17 @@ if not torch.cuda.is_available():
 from paper_1911_12913_gb300.solver import FDLBM, FDLBMBatch  # noqa: E402
 
 FP64_TOL = 1e-12
+# FP32 bounds, about 10x the largest errors measured on GB300 over these tests
+# (relative L2 of f~ up to 1.5e-8 after 12-25 steps from random states, 3e-8
+# after 400 cavity steps; L-infinity of the error relative to the largest
+# deviation f~ - w_i rho0 up to 1.9e-6).  The deviations are O(u) ~ 1e-2 and
+# each step rounds them to 2^-24 relative, so a few steps leave errors of a
+# few 1e-8 of the deviation at most nodes and the largest of about 1e-6.
+# FP64: the L2 bound the benchmark spec fixes, and 1e-11 on the deviation
+# (measured up to 4.7e-13).
+FP32_L2 = 1e-7
+FP32_DEV = 2e-5
+FP64_DEV = 1e-11
 
 
 def rel(a, b):
@@ -82,13 +94,14 @@ def test_incomp_fp32_fused(variant, nx, ny, rows):
     s.step(25)
     o.step(25)
     s.sync()
-    err = rel(s.get_state(), o.f)
-    print(f"{s.describe} {nx}x{ny}: rel L2(f~) = {err:.3e}")
-    assert err <= 1e-6
+    assert_parity(s.get_state(), o.f, l2=FP32_L2, dev=FP32_DEV, label=f"{s.describe} {nx}x{ny}")
 
 
-def test_incomp_fp32_scalar_with_force():
-    nx, ny = 130, 20
+@pytest.mark.parametrize("nx", [130, 128])
+def test_incomp_fp32_with_force(nx):
+    """The incompressible equilibrium with a body-force field on the scalar
+    sweep (nx = 130) and the warp-tile kernel (nx = 128)."""
+    ny = 20
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.periodic_axis(ny, 0.0, 0.5)
     force = 1e-3 * np.random.default_rng(3).uniform(-1, 1, size=(2, ny, nx))
@@ -96,7 +109,7 @@ def test_incomp_fp32_scalar_with_force():
     _init_both(s, o, I.random_fields(nx, ny, 29, drho=0.05))
     s.step(25)
     o.step(25)
-    assert rel(s.get_state(), o.f) <= 1e-6
+    assert_parity(s.get_state(), o.f, l2=FP32_L2, dev=FP32_DEV, label=f"{s.describe} forced")
 
 
 _WALLS = [("wall", "wall", 40, 33, 3), ("periodic", "wall", 96, 24, 0), ("wall", "periodic", 33, 40, 4)]
@@ -112,7 +125,7 @@ def _axis(kind, n, seed, length):
 
 @pytest.mark.parametrize("precision,tol,path", [("fp64", FP64_TOL, "fused"),
                                                 ("fp64", FP64_TOL, "staged"),
-                                                ("fp32", 1e-6, "fused")])
+                                                ("fp32", FP32_L2, "fused")])
 @pytest.mark.parametrize("bcx,bcy,nx,ny,rows", _WALLS)
 def test_incomp_walls(precision, tol, path, bcx, bcy, nx, ny, rows):
     """Eq. 3.10 under the incompressible equilibrium (the fused walls sweep and
@@ -129,13 +142,12 @@ def test_incomp_walls(precision, tol, path, bcx, bcy, nx, ny, rows):
         s.step(n)
         o.step(n)
     s.sync()
-    err = rel(s.get_state(), o.f)
-    print(f"{s.describe} {bcx}/{bcy} {nx}x{ny}: rel L2(f~) = {err:.3e}")
-    assert err <= tol
+    assert_parity(s.get_state(), o.f, l2=tol, dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                  label=f"{s.describe} {bcx}/{bcy} {nx}x{ny}")
 
 
 @pytest.mark.parametrize("walls,precision,tol", [(True, "fp64", FP64_TOL), (False, "fp64", FP64_TOL),
-                                                 (True, "fp32", 1e-6)])
+                                                 (True, "fp32", FP32_L2)])
 def test_incomp_scheme2(walls, precision, tol):
     """T2S2-FDLBM2 with the incompressible equilibrium: the staged kernels on an
     FP64 channel, the fused sweeps on an FP32 channel and a periodic grid."""
@@ -150,11 +162,12 @@ def test_incomp_scheme2(walls, precision, tol):
     _init_both(s, o, I.random_fields(nx, ny, 5, drho=0.05))
     s.step(15)
     o.step(15)
-    assert rel(s.get_state(), o.f) <= tol
+    assert_parity(s.get_state(), o.f, l2=tol, dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                  label=f"{s.describe} scheme2")
 
 
-@pytest.mark.parametrize("precision,tol,mode", [("fp64", FP64_TOL, "staged"), ("fp32", 2e-6, "fused"),
-                                                ("fp32", 2e-6, "persistent")])
+@pytest.mark.parametrize("precision,tol,mode", [("fp64", FP64_TOL, "staged"), ("fp32", FP32_L2, "fused"),
+                                                ("fp32", FP32_L2, "persistent")])
 def test_incomp_batch(precision, tol, mode):
     """A batch of a cavity, a forced channel and a periodic case, all with the
     incompressible equilibrium, in three batch modes."""
@@ -193,8 +206,9 @@ def test_incomp_batch(precision, tol, mode):
             o.step(n)
     batch.sync()
     for c, o in enumerate(oracles):
-        err = rel(batch.case(c).get_state(), o.f)
-        assert err <= tol, (c, err, batch.describe)
+        assert_parity(batch.case(c).get_state(), o.f, l2=tol,
+                      dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                      label=f"{batch.describe} case {c}")
 
 
 def test_incomp_differs_from_standard():

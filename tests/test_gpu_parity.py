@@ -3,10 +3,12 @@ element by element on the same seeded inputs.
 
 Tolerances: FP64 paths must match the oracle's f~ to 1e-12 relative L2 (the
 only differences are rounding order; one step changes f~ by a few ulps).  The
-FP32-deviation path reports its error against the FP64 oracle; its bound here
-is derived from FP32 rounding of deviations of size |u| ~ 1e-2 (relative
-rounding 6e-8 per operation, a few hundred operations per step, errors that
-random-walk over the steps).
+FP32-deviation path reports its error against the FP64 oracle in two norms:
+the relative L2 of f~, dominated by the O(1) rest populations, and the
+L-infinity of the error relative to the largest deviation f~ - w_i rho0 (see
+conftest.parity_errors), which sees a defect confined to one population, a
+seam window or a wall column.  Both bounds sit about 10x above the errors
+measured on GB300 (FP32_L2, FP32_DEV below).
 """
 import math
 
@@ -15,7 +17,7 @@ import pytest
 
 import inputs as I
 import oracle as O
-from conftest import oracle_threads
+from conftest import assert_parity, oracle_threads, parity_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -26,6 +28,17 @@ if not torch.cuda.is_available():
 from paper_1911_12913_gb300.solver import FDLBM  # noqa: E402
 
 FP64_TOL = 1e-12
+# FP32 bounds, about 10x the largest errors measured on GB300 over these tests
+# (relative L2 of f~ up to 1.5e-8 after 12-25 steps from random states, 3e-8
+# after 400 cavity steps; L-infinity of the error relative to the largest
+# deviation f~ - w_i rho0 up to 1.9e-6).  The deviations are O(u) ~ 1e-2 and
+# each step rounds them to 2^-24 relative, so a few steps leave errors of a
+# few 1e-8 of the deviation at most nodes and the largest of about 1e-6.
+# FP64: the L2 bound the benchmark spec fixes, and 1e-11 on the deviation
+# (measured up to 4.7e-13).
+FP32_L2 = 1e-7
+FP32_DEV = 2e-5
+FP64_DEV = 1e-11
 
 
 def rel(a, b):
@@ -82,9 +95,9 @@ def test_taylor_green_64_fp32_error_vs_fp64_oracle():
     _, ux, uy = s.moments()
     _, oux, ouy = o.moments()
     err_u = O.gre(ux, uy, oux, ouy)
-    err_f = rel(s.get_state(), o.f)
-    print(f"FP32-deviation vs FP64 oracle after 1000 steps: rel L2 u = {err_u:.3e}, f~ = {err_f:.3e}")
-    assert err_u < 1e-4 and err_f < 1e-6
+    print(f"FP32-deviation vs FP64 oracle after 1000 steps: rel L2 u = {err_u:.3e}")
+    assert err_u < 1e-5      # measured 1.25e-6
+    assert_parity(s.get_state(), o.f, l2=5e-8, dev=FP32_DEV, label="tg64 fp32 1000")
 
 
 def test_taylor_green_64_fp32_10k_steps():
@@ -133,13 +146,13 @@ def test_random_state_force_stretched_fp64(path, rows, nx, ny):
     assert rel(s.get_state(), o.f) <= FP64_TOL
 
 
-@pytest.mark.parametrize("variant", ["packed", "tma", "scalar", "async", "warp"])
+@pytest.mark.parametrize("variant", ["scalar", "warp"])
 @pytest.mark.parametrize("nx,ny,rows", [(500, 37, 0), (256, 21, 7), (964, 40, 0), (4096, 9, 0),
                                         (260, 12, 1)])
 def test_fp32_fused_variants(variant, nx, ny, rows):
-    """FP32 fused kernels (scalar; bulk-copy rows; packed two-strip f32x2):
-    ragged strips, a strip beyond the domain, wrapped halos, stretched metrics;
-    25 steps against the FP64 oracle, with the error flag checked."""
+    """FP32 fused kernels (scalar sweep; warp-tile kernel): ragged strips, a
+    strip beyond the domain, wrapped halos, stretched metrics; 25 steps
+    against the FP64 oracle, with the error flag checked."""
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.periodic_axis(ny, 0.0, 0.7)
     xa.metric = I.random_metric(nx, 41, base=nx, spread=0.3)
@@ -147,79 +160,61 @@ def test_fp32_fused_variants(variant, nx, ny, rows):
     s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, precision="fp32", rows_per_cta=rows,
               variant=variant)
     o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2)
-    assert s.describe.split()[0] == {"packed": "fused-f32x2", "tma": "fused-tma",
-                                     "scalar": "fused", "async": "fused-async",
-                                     "warp": "fused-warp"}[variant], s.describe
+    assert s.describe.split()[0] == {"scalar": "fused", "warp": "fused-warp"}[variant], s.describe
     _init_both(s, o, I.random_fields(nx, ny, 23))
     s.step(25)
     o.step(25)
     s.sync()
-    err = rel(s.get_state(), o.f)
-    print(f"{s.describe} {nx}x{ny}: rel L2(f~) = {err:.3e}")
-    assert err <= 1e-6
+    assert_parity(s.get_state(), o.f, l2=FP32_L2, dev=FP32_DEV, label=f"{s.describe} {nx}x{ny}")
 
 
-@pytest.mark.parametrize("variant", ["tma", "async"])
-@pytest.mark.parametrize("nx,ny,rows", [(256, 37, 0), (132, 21, 3), (130, 9, 1)])
-def test_fp64_tma_variant_force_stretched(variant, nx, ny, rows):
-    """FP64 bulk-copy and cp.async variants with a force field and stretched metrics."""
-    xa = I.periodic_axis(nx, 0.0, 1.0)
-    ya = I.periodic_axis(ny, 0.0, 0.7)
-    xa.metric = I.random_metric(nx, 51, base=nx, spread=0.4)
-    ya.metric = I.random_metric(ny, 52, base=ny / 0.7, spread=0.4)
-    force = 1e-3 * np.random.default_rng(11).uniform(-1, 1, size=(2, ny, nx))
-    s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, has_force=True, rows_per_cta=rows,
-              variant=variant)
-    assert s.describe.startswith(f"fused-{variant} fp64"), s.describe
-    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force)
-    s.set_force(force)
-    _init_both(s, o, I.random_fields(nx, ny, 19))
-    s.step(25)
-    o.step(25)
-    s.sync()
-    assert rel(s.get_state(), o.f) <= FP64_TOL
-
-
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-6), ("fp64", FP64_TOL)])
+@pytest.mark.parametrize("precision,tol", [("fp32", FP32_L2), ("fp64", FP64_TOL)])
 @pytest.mark.parametrize("nx,ny,rows", [(133, 37, 0), (4, 9, 0), (250, 21, 1)])
-def test_async_variant_odd_sizes_with_force(precision, tol, nx, ny, rows):
-    """cp.async variant on sizes the bulk-copy kernels reject, with a force field."""
+def test_scalar_sweep_odd_sizes_with_force(precision, tol, nx, ny, rows):
+    """The scalar sweep on odd sizes (below the warp-tile kernel's 64-column
+    window, not a multiple of 4), with a force field and a stretched x axis."""
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.periodic_axis(ny, 0.0, 0.7)
     xa.metric = I.random_metric(nx, 61, base=nx, spread=0.3)
     force = 1e-3 * np.random.default_rng(13).uniform(-1, 1, size=(2, ny, nx))
     s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, has_force=True, rows_per_cta=rows,
-              precision=precision, variant="async")
+              precision=precision, variant="scalar")
     o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force)
     s.set_force(force)
     _init_both(s, o, I.random_fields(nx, ny, 31))
     s.step(25)
     o.step(25)
     s.sync()
-    assert rel(s.get_state(), o.f) <= tol
+    assert_parity(s.get_state(), o.f, l2=tol, dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                  label=f"{s.describe} {nx}x{ny}")
 
 
+@pytest.mark.parametrize("force", [False, True])
 @pytest.mark.parametrize("nx,ny,rows", [(64, 9, 0), (68, 13, 2), (120, 21, 0), (112, 7, 3),
-                                        (124, 40, 5)])
-def test_fp32_warp_variant_small_windows(nx, ny, rows):
+                                        (124, 40, 5), (4096, 6, 0)])
+def test_fp32_warp_variant_small_windows(nx, ny, rows, force):
     """Warp-tile kernel where every 64-column window wraps (nx = 64, 68), where
-    the last tile is mostly outside the domain (120 = 2 x 56 + 8), and with
-    row segments of 2..5 rows: 25 steps against the FP64 oracle."""
+    the last tile is mostly outside the domain (120 = 2 x 56 + 8), with row
+    segments of 2..5 rows, and on a 4096-wide strip (73 windows, the last one
+    with 52 columns past the seam), with and without a body-force field (whose
+    seam windows read the 4 columns next to the seam from side rings): 25 steps
+    against the FP64 oracle."""
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.periodic_axis(ny, 0.0, 0.7)
     xa.metric = I.random_metric(nx, 71, base=nx, spread=0.3)
     ya.metric = I.random_metric(ny, 72, base=ny / 0.7, spread=0.3)
+    F = 1e-3 * np.random.default_rng(nx + 3 * ny).uniform(-1, 1, size=(2, ny, nx)) if force else None
     s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, precision="fp32", rows_per_cta=rows,
-              variant="warp")
+              variant="warp", has_force=force)
     assert s.describe.startswith("fused-warp fp32dev"), s.describe
-    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2)
+    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=F)
+    if force:
+        s.set_force(F)
     _init_both(s, o, I.random_fields(nx, ny, 37))
     s.step(25)
     o.step(25)
     s.sync()
-    err = rel(s.get_state(), o.f)
-    print(f"{s.describe} {nx}x{ny}: rel L2(f~) = {err:.3e}")
-    assert err <= 1e-6
+    assert_parity(s.get_state(), o.f, l2=FP32_L2, dev=FP32_DEV, label=f"{s.describe} {nx}x{ny}")
 
 
 # ------------------------------------------------------------------ walls in the fused sweep
@@ -240,7 +235,7 @@ def _axis(kind, n, seed, length):
     return I.tanh_axis(n - 1, 1.5) if length == 1.0 else I.wall_axis(n - 1, 0.0, length)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 1e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_L2)])
 @pytest.mark.parametrize("bcx,bcy,nx,ny,rows", _WALL_CASES)
 def test_fused_walls_match_oracle(precision, tol, bcx, bcy, nx, ny, rows):
     """The fused sweep with Eq. 3.10 inside it, on walled grids (tanh-stretched
@@ -260,12 +255,11 @@ def test_fused_walls_match_oracle(precision, tol, bcx, bcy, nx, ny, rows):
         s.step(n)
         o.step(n)
     s.sync()
-    err = rel(s.get_state(), o.f)
-    print(f"{s.describe} {bcx}/{bcy} {nx}x{ny}: rel L2(f~) = {err:.3e}")
-    assert err <= tol
+    assert_parity(s.get_state(), o.f, l2=tol, dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                  label=f"{s.describe} {bcx}/{bcy} {nx}x{ny}")
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 1e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_L2)])
 @pytest.mark.parametrize("bcx,bcy,nx,ny,rows", _WALL_CASES)
 def test_fused_walls_scheme2_match_oracle(precision, tol, bcx, bcy, nx, ny, rows):
     """The fused T2S2-FDLBM2 sweep with Eq. 3.10 inside it (f^n, f^{n+1} and the
@@ -288,17 +282,12 @@ def test_fused_walls_scheme2_match_oracle(precision, tol, bcx, bcy, nx, ny, rows
         s.step(n)
         o.step(n)
     s.sync()
-    err = rel(s.get_state(), o.f)
-    print(f"{s.describe} {bcx}/{bcy} {nx}x{ny}: rel L2(f~) = {err:.3e}")
-    assert err <= tol
+    assert_parity(s.get_state(), o.f, l2=tol, dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                  label=f"{s.describe} {bcx}/{bcy} {nx}x{ny}")
 
 
 def test_variant_not_applicable_is_rejected():
     xa = I.periodic_axis(130, 0.0, 1.0)   # 130 % 4 != 0: no 16-byte FP32 row pieces
-    with pytest.raises(Exception, match="EUNSUPPORTED"):
-        FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="tma")
-    with pytest.raises(Exception, match="EUNSUPPORTED"):
-        FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="packed")
     with pytest.raises(Exception, match="EUNSUPPORTED"):
         FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="warp")
     xs = I.periodic_axis(60, 0.0, 1.0)    # narrower than one 64-column window
@@ -307,28 +296,31 @@ def test_variant_not_applicable_is_rejected():
     x4 = I.periodic_axis(128, 0.0, 1.0)
     with pytest.raises(Exception, match="EUNSUPPORTED"):
         FDLBM(x4, x4, nu=0.01, cfl=0.5, blend=0.1, precision="fp64", variant="warp")
-    with pytest.raises(Exception, match="EUNSUPPORTED"):
-        FDLBM(x4, x4, nu=0.01, cfl=0.5, blend=0.1, precision="fp32", variant="warp",
-              has_force=True)
 
 
-def test_scalar_fp32_fused_with_force():
-    """FP32 fused scalar kernel (body force present) against the FP64 oracle."""
+@pytest.mark.parametrize("variant", ["scalar", "auto"])
+def test_fp32_fused_with_force(variant):
+    """FP32 fused kernels with a body-force field against the FP64 oracle: the
+    scalar sweep, and the automatic choice, which is the warp-tile kernel."""
     nx, ny = 300, 33
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.periodic_axis(ny, 0.0, 0.7)
     force = 1e-3 * np.random.default_rng(3).uniform(-1, 1, size=(2, ny, nx))
-    s, o = _pair(xa, ya, nu=0.02, cfl=0.4, beta=0.2, precision="fp32", force=force)
-    assert s.describe.startswith("fused fp32dev"), s.describe
+    s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, precision="fp32", has_force=True,
+              variant=variant)
+    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force)
+    s.set_force(force)
+    assert s.describe.startswith("fused fp32dev" if variant == "scalar" else "fused-warp fp32dev"), \
+        s.describe
     _init_both(s, o, I.random_fields(nx, ny, 29))
     s.step(25)
     o.step(25)
     s.sync()
-    assert rel(s.get_state(), o.f) <= 1e-6
+    assert_parity(s.get_state(), o.f, l2=FP32_L2, dev=FP32_DEV, label=f"{s.describe} forced")
 
 
 @pytest.mark.parametrize("path", ["fused", "staged"])
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 1e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_L2)])
 def test_t2s2_fdlbm2_periodic_force_metrics(precision, tol, path):
     """T2S2-FDLBM2 (Eq. 5.23) on the fused sweep and on the staged kernels
     against the oracle's second sequence: random state, force field, stretched
@@ -348,10 +340,11 @@ def test_t2s2_fdlbm2_periodic_force_metrics(precision, tol, path):
     _init_both(s, o, I.random_fields(nx, ny, 37))
     s.step(25)
     o.step(25)
-    assert rel(s.get_state(), o.f) <= tol
+    assert_parity(s.get_state(), o.f, l2=tol, dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                  label=f"{s.describe} {nx}x{ny}")
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 1e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_L2)])
 @pytest.mark.parametrize("nx,ny,rows,force", [(133, 37, 0, False), (250, 21, 1, True), (4, 9, 0, True),
                                               (128, 64, 5, False), (500, 13, 3, False)])
 def test_t2s2_fdlbm2_fused_ragged(precision, tol, nx, ny, rows, force):
@@ -374,13 +367,12 @@ def test_t2s2_fdlbm2_fused_ragged(precision, tol, nx, ny, rows, force):
         s.step(n)
         o.step(n)
     s.sync()
-    err = rel(s.get_state(), o.f)
-    print(f"{s.describe} {nx}x{ny}: rel L2(f~) = {err:.3e}")
-    assert err <= tol
+    assert_parity(s.get_state(), o.f, l2=tol, dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                  label=f"{s.describe} {nx}x{ny}")
 
 
 @pytest.mark.parametrize("precision,tol,path", [("fp64", FP64_TOL, "auto"), ("fp64", FP64_TOL, "fused"),
-                                                ("fp32", 2e-6, "auto")])
+                                                ("fp32", 1e-7, "auto")])
 def test_t2s2_fdlbm2_channel_walls(precision, tol, path):
     """T2S2-FDLBM2 with Eq. 3.10 walls on the stretched channel grid of Eq. 3.9
     (FP64: the staged kernels by default, and the fused sweep; FP32: the fused
@@ -402,7 +394,8 @@ def test_t2s2_fdlbm2_channel_walls(precision, tol, path):
     o.init_fields(one, 0 * one, 0 * one)
     s.step(200)
     o.step(200)
-    assert rel(s.get_state(), o.f) <= tol
+    assert_parity(s.get_state(), o.f, l2=tol, dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                  label=f"{s.describe} channel")
 
 
 def test_t1s2_special_case_fp64():
@@ -437,7 +430,7 @@ def test_poiseuille_stretched_walls_fp64(path):
 
 
 @pytest.mark.parametrize("path", ["fused", "staged"])
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 2e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", 3e-7)])
 def test_cavity_stretched_walls(precision, tol, path):
     """Lid-driven cavity on a tanh grid (walls on all sides, lid U = 0.1)."""
     n = 24
@@ -451,7 +444,8 @@ def test_cavity_stretched_walls(precision, tol, path):
     o.init_fields(one, 0 * one, 0 * one)
     s.step(400)
     o.step(400)
-    assert rel(s.get_state(), o.f) <= tol
+    assert_parity(s.get_state(), o.f, l2=tol, dev=FP64_DEV if precision == "fp64" else FP32_DEV,
+                  label=f"{s.describe} cavity")
 
 
 # ------------------------------------------------------------------ reductions, misc
@@ -531,21 +525,23 @@ def test_device_side_arguments_and_zero_steps():
 
 
 # ------------------------------------------------------------------ full size, sampled
-@pytest.mark.parametrize("precision,tol,scheme,eq", [("fp32", 2e-7, 1, "standard"),
-                                                     ("fp64", FP64_TOL, 1, "standard"),
-                                                     ("fp32", 2e-7, 2, "standard"),
-                                                     ("fp64", FP64_TOL, 2, "standard"),
-                                                     ("fp32", 2e-7, 1, "incompressible")])
-def test_full_size_4096_sampled_patches(precision, tol, scheme, eq):
+@pytest.mark.parametrize("precision,tol,scheme,eq,force", [("fp32", 1e-8, 1, "standard", False),
+                                                           ("fp64", FP64_TOL, 1, "standard", False),
+                                                           ("fp32", 1e-8, 2, "standard", False),
+                                                           ("fp64", FP64_TOL, 2, "standard", False),
+                                                           ("fp32", 1e-8, 1, "incompressible", False),
+                                                           ("fp32", 1e-8, 1, "standard", True)])
+def test_full_size_4096_sampled_patches(precision, tol, scheme, eq, force):
     """4096^2 periodic grid in the launch configuration the benchmark times
-    (automatic kernel and tile height; T2S2-FDLBM1 and T2S2-FDLBM2, and the
-    incompressible equilibrium): after 2 steps, sampled 40x40 patches are
-    checked against the oracle run on the same patch.  One step reaches 4
-    nodes, so the central 24x24 nodes of each patch are exact for the oracle."""
+    (automatic kernel and tile height; T2S2-FDLBM1 and T2S2-FDLBM2, the
+    incompressible equilibrium, and a smooth body-force field): after 2
+    steps, sampled 40x40 patches are checked against the oracle run on the
+    same patch.  One step reaches 4 nodes, so the central 24x24 nodes of each
+    patch are exact for the oracle."""
     n, steps, P = 4096, 2, 40
     xa = I.periodic_axis(n, 0.0, 2 * math.pi)
     s = FDLBM(xa, xa, nu=0.01, cfl=0.5, blend=0.1, precision=precision, scheme=scheme,
-              equilibrium=eq)
+              equilibrium=eq, has_force=force)
     assert s.path == "fused"
     print(s.describe)
     fld = I.taylor_green(xa, xa, u0=0.01, phase=(0.7, 2.1))
@@ -553,6 +549,11 @@ def test_full_size_4096_sampled_patches(precision, tol, scheme, eq):
     for k in fld:
         fld[k] = fld[k] + (pert[k] - (1.0 if k == "rho" else 0.0))
     grad = [fld["dudx"], fld["dudy"], fld["dvdx"], fld["dvdy"]]
+    F = None
+    if force:
+        h = I.spectral_vorticity_velocity(n, 12, kmax=8, umax=1e-4)
+        F = np.stack([h["ux"], h["uy"]])
+        s.set_force(F)
     s.init_fields(fld["rho"], fld["ux"], fld["uy"], grad)
     s.step(steps)
     s.sync()
@@ -566,7 +567,8 @@ def test_full_size_4096_sampled_patches(precision, tol, scheme, eq):
         ys = (y0 + np.arange(P)) % n
         pa = I.periodic_axis(P, 0.0, P * 2 * math.pi / n)
         o = O.Oracle(pa, pa, nu=0.01, dt=s.dt, beta=0.1, scheme=scheme,
-                     incomp=eq == "incompressible")
+                     incomp=eq == "incompressible",
+                     force=None if F is None else F[:, ys][:, :, xs])
         sub = {k: v[np.ix_(ys, xs)] for k, v in fld.items()}
         o.init_fields(sub["rho"], sub["ux"], sub["uy"],
                       [sub["dudx"], sub["dudy"], sub["dvdx"], sub["dvdy"]])
@@ -575,6 +577,10 @@ def test_full_size_4096_sampled_patches(precision, tol, scheme, eq):
         iy = torch.tensor(ys[m:P - m], device=g.device)
         ix = torch.tensor(xs[m:P - m], device=g.device)
         got = g[:, iy][:, :, ix].cpu().numpy()
-        errs.append(rel(got, want))
-    print(f"{s.describe} 4096^2 sampled patches: max rel L2(f~) = {max(errs):.3e}")
-    assert max(errs) <= tol
+        errs.append(parity_errors(got, want))
+    e_l2 = max(e[0] for e in errs)
+    e_dev = max(e[1] for e in errs)
+    print(f"{s.describe} 4096^2 sampled patches: max rel L2(f~) = {e_l2:.3e}, "
+          f"max rel Linf(deviation) = {e_dev:.3e}")
+    assert e_l2 <= tol
+    assert e_dev <= (FP64_DEV if precision == "fp64" else 3e-6)
