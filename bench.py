@@ -45,7 +45,7 @@ BYTES_PER_CELL = {"fp32": 72, "fp64": 144}   # 9 populations read once + written
 # per node of sweep work, the algorithmic figure per cell update (the halo
 # recompute of a given tiling comes on top).
 FP64_FLOP_PER_CELL = 383
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 nominal FP64 rate (non-tensor)
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 nominal FP64 rate (non-tensor), context only
 SAMPLE_N = 512                                # oracle sample grid
 
 
@@ -102,6 +102,7 @@ class Clocks:
         self.uuid = uuid
         self.proc = None
         self.lines = []
+        self.bracket = 0
 
     def __enter__(self):
         try:
@@ -128,6 +129,19 @@ class Clocks:
                 self.proc.kill()
             self.t.join(timeout=2)
 
+    def snapshot(self):
+        """One sample now (used right before and right after a short timed
+        region, which the 200 ms sampler may miss)."""
+        try:
+            r = subprocess.run(["nvidia-smi", f"--id={self.uuid}", f"--query-gpu={self.Q}",
+                                "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                               timeout=10)
+            if r.returncode == 0 and r.stdout.strip():
+                self.lines.append(r.stdout.strip().splitlines()[0])
+                self.bracket += 1
+        except (OSError, subprocess.TimeoutExpired):
+            pass
+
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -144,7 +158,9 @@ class Clocks:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "bracketing_samples": self.bracket, "reasons": sorted(reasons),
+                "window": "200 ms sampler over the whole GPU part of the run, plus one sample "
+                          "right before and one right after the timed region"}
 
 
 # ----------------------------------------------------------------------- helpers
@@ -183,6 +199,31 @@ def peaks():
         return json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
     except (OSError, ValueError):
         return {}
+
+
+def fp64_peak(stream):
+    """Measured FP64 FMA rate (TFLOP/s) of this GPU: independent FMA chains
+    (libfdlbm's fdlbm_probe_fp64_fma), best of 3 launches of about 0.1 s,
+    timed with CUDA events on the launching stream."""
+    import ctypes
+    import torch
+    from paper_1911_12913_gb300 import binding as B
+    L = B.load()
+    blocks = 152 * 8
+    out = torch.zeros(blocks, dtype=torch.float64, device="cuda")
+    flop = ctypes.c_double()
+    best = None
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = L.fdlbm_probe_fp64_fma(blocks, 20000, out.data_ptr(), ctypes.c_void_p(stream.cuda_stream),
+                                    ctypes.byref(flop))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert rc == 0
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    return flop.value / best / 1e12
 
 
 def cpu_oracle_rate(n, target_s=12.0, nthreads=None, steps=None):
@@ -581,6 +622,12 @@ def run_ours(args):
     grad = [f["dudx"], f["dudy"], f["dvdx"], f["dvdy"]]
     stream = torch.cuda.current_stream(dev)
 
+    # the clock sampler runs over the whole GPU part of the run (it starts before
+    # the warm-up); one sample is also taken right before and right after the
+    # timed region, which at a few steps is shorter than the sampling period
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    clk = Clocks(uuid).__enter__()
+
     # ---------------- device-resident timing (FP32 deviation, the headline)
     s = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream,
               variant=args.variant, rows_per_cta=args.rows)
@@ -589,15 +636,15 @@ def run_ours(args):
     m0, _ = s.reduce()
     s.step(args.warmup)
     torch.cuda.synchronize()
-    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
+    clk.snapshot()
     torch.cuda.synchronize()
-    with Clocks(uuid) as clk:
-        ev0.record(stream)
-        s.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
+    ev0.record(stream)
+    s.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk.snapshot()
     barrier()
     ms = ev0.elapsed_time(ev1)
     ms_max = max_over_ranks(ms)
@@ -647,6 +694,32 @@ def run_ours(args):
             torch.cuda.empty_cache()
 
     # ---------------- FP64 beside it (same workload, shorter run)
+    # ---------------- the same workload with a body-force field (warp-tile kernel
+    # with Eqs. 3.3 and 3.12; 80 B per cell: the force field is read once more)
+    forced = None
+    if not args.no_variants:
+        import inputs as I
+        hF = I.spectral_vorticity_velocity(n, 12, kmax=8, umax=1e-5)
+        sf = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream,
+                   has_force=True)
+        sf.set_force(np.stack([hF["ux"], hF["uy"]]))
+        sf.init_fields(f["rho"], f["ux"], f["uy"], grad)
+        sf.step(5)
+        kv = max(100, args.steps // 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sf.step(kv)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sf.sync()
+        tv = e0.elapsed_time(e1) / 1e3 / kv
+        forced = {"kernel": sf.describe, "MLUPS": N / tv / 1e6, "ms_per_step": tv * 1e3,
+                  "bytes_per_cell": 80, "hbm_frac": 80 * N / tv / 1e9 / hbm, "steps": kv,
+                  "force": "smooth field, k^-3 spectrum up to k = 8, max 1e-5"}
+        del sf
+        torch.cuda.empty_cache()
+
     fp64 = None
     if args.fp64_steps > 0:
         s64 = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp64", stream=stream)
@@ -660,15 +733,18 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
         t64 = ms64 / 1e3 / args.fp64_steps
+        peak64 = fp64_peak(stream)
         fp64 = {"value": N / t64 / 1e6, "unit": "MLUPS", "ms_per_step": ms64 / args.fp64_steps,
                 "steps": args.fp64_steps,
                 "hbm_achieved_gbs": BYTES_PER_CELL["fp64"] * N / t64 / 1e9,
                 "hbm_frac": BYTES_PER_CELL["fp64"] * N / t64 / 1e9 / hbm,
                 "roofline": {"bound": "alu", "achieved": FP64_FLOP_PER_CELL * N / t64 / 1e12,
-                             "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                             "frac": FP64_FLOP_PER_CELL * N / t64 / 1e12 / FP64_NOMINAL_TFLOPS,
+                             "peak": peak64, "unit": "TFLOP/s",
+                             "frac": FP64_FLOP_PER_CELL * N / t64 / 1e12 / peak64,
                              "flop_per_cell": FP64_FLOP_PER_CELL,
-                             "peak_source": "nominal FP64 rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)"}}
+                             "peak_source": "measured in this run: independent FP64 FMA chains "
+                                            "(fdlbm_probe_fp64_fma), best of 4 launches",
+                             "nominal_tflops": FP64_NOMINAL_TFLOPS}}
         del s64
         torch.cuda.empty_cache()
 
@@ -701,38 +777,77 @@ def run_ours(args):
         torch.cuda.empty_cache()
 
     # ---------------- end to end through the C ABI with pinned host buffers
-    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in f.items()}
-    out_host = [torch.empty((n, n), dtype=torch.float64).pin_memory() for _ in range(3)]
+    # The job a user runs: upload the initial fields, K steps, the mass /
+    # residual reduction, read the moments back.  Headline: FP32 fields (the
+    # density as rho - rho0), the storage precision of the solver; beside it
+    # the same job with FP64 fields.
+    import ctypes
     s = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision="fp32", stream=stream)
     L, h = s._L, s._h
-    gpin = torch.stack([pin["dudx"], pin["dudy"], pin["dvdx"], pin["dvdy"]]).pin_memory()
-    import ctypes
     mass, resid = ctypes.c_double(), ctypes.c_double()
+    gkeys = ("dudx", "dudy", "dvdx", "dvdy")
 
-    def e2e_job(k):
-        rc = L.fdlbm_init_fields(h, pin["rho"].data_ptr(), pin["ux"].data_ptr(),
-                                 pin["uy"].data_ptr(), gpin.data_ptr(), 0)
+    def pinned(a, dt):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()
+
+    io = {}
+    for dt, tag in ((np.float32, "f32"), (np.float64, "f64")):
+        r0 = f["rho"] - 1.0 if tag == "f32" else f["rho"]
+        fin = [pinned(r0, dt), pinned(f["ux"], dt), pinned(f["uy"], dt)]
+        gin = pinned(np.stack([f[k] for k in gkeys]), dt)
+        outs = [torch.empty((n, n), dtype=torch.float32 if tag == "f32" else torch.float64).pin_memory()
+                for _ in range(3)]
+        init = L.fdlbm_init_fields_f32 if tag == "f32" else L.fdlbm_init_fields
+        mom = L.fdlbm_moments_f32 if tag == "f32" else L.fdlbm_moments
+        io[tag] = (fin, gin, outs, init, mom, np.dtype(dt).itemsize)
+
+    def e2e_job(tag, k, ev=None):
+        fin, gin, outs, init, mom, _ = io[tag]
+        if ev: ev[0].record(stream)
+        rc = init(h, *(t.data_ptr() for t in fin), gin.data_ptr(), 0)
+        if ev: ev[1].record(stream)
         rc |= L.fdlbm_step(h, k)
+        if ev: ev[2].record(stream)
         rc |= L.fdlbm_reduce(h, ctypes.byref(mass), ctypes.byref(resid))
-        rc |= L.fdlbm_moments(h, *(o.data_ptr() for o in out_host), 0)
+        if ev: ev[3].record(stream)
+        rc |= mom(h, *(o.data_ptr() for o in outs), 0)
+        if ev: ev[4].record(stream)
         assert rc == 0, L.fdlbm_last_error(h)
 
-    e2e_job(args.warmup)
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_job(args.steps)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    barrier()
-    e2e_s = max_over_ranks(e2e_s)
-    e2e = {"value": ranks.aggregate(N * args.steps, e2e_s) / 1e6, "unit": "MLUPS",
-           "h2d_bytes_per_step": 7 * N * 8 / args.steps,
-           "d2h_bytes_per_step": (3 * N * 8 + 3 * 8) / args.steps,
-           "job": "init_fields(host rho,u,grad u) + K steps + reduce + moments(host), per rank"}
+    e2e = None
+    for tag in ("f32", "f64"):
+        e2e_job(tag, args.warmup)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_job(tag, args.steps)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        barrier()
+        e2e_s = max_over_ranks(e2e_s)
+        # the same job once more with CUDA events between its phases
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e2e_job(tag, args.steps, ev)
+        torch.cuda.synchronize()
+        names = ("init_fields", "steps", "reduce", "moments")
+        brk = {nm: ev[i].elapsed_time(ev[i + 1]) for i, nm in enumerate(names)}
+        b = io[tag][5]
+        rec = {"value": ranks.aggregate(N * args.steps, e2e_s) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": 7 * N * b / args.steps,
+               "d2h_bytes_per_step": (3 * N * b + 3 * 8) / args.steps,
+               "job_ms": e2e_s * 1e3, "breakdown_ms": brk,
+               "job": f"init_fields{'_f32' if tag == 'f32' else ''}(pinned host drho|rho, u, grad u; "
+                      f"{'FP32' if tag == 'f32' else 'FP64'}) + K steps + reduce + "
+                      f"moments{'_f32' if tag == 'f32' else ''}(pinned host), per rank"}
+        if tag == "f32":
+            e2e = rec
+        else:
+            e2e["fp64_fields"] = rec
     del s
 
+    clk.__exit__(None, None, None)
+    clocks = clk.summary()
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
@@ -744,9 +859,10 @@ def run_ours(args):
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                "dtype": "f32", "data": "synthetic",
-               "config": config(n, "fp32", args.steps), "clocks": clk.summary(),
+               "config": config(n, "fp32", args.steps), "clocks": clocks,
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-               "cpu_baseline": cpu, "fp64": fp64, "fp32_variants": variants, "batched": batched, "adjoint": adjoint,
+               "cpu_baseline": cpu, "fp64": fp64, "fp32_variants": variants, "fp32_forced": forced,
+               "batched": batched, "adjoint": adjoint,
                "cavity": cavity, "sweep": sweep, "fdlbm2": fdlbm2,
                "mass_drift_rel": mass_drift,
                "parallelism": "replicas" if world > 1 else "single"}

@@ -168,6 +168,13 @@ void fdlbm_destroy(fdlbm_t h);
  * rho, ux, uy: [ny][nx] FP64 at `where`. */
 fdlbm_status fdlbm_init_fields(fdlbm_t h, const double *rho, const double *ux, const double *uy,
                                const double *grad, int where);
+/* The same from FP32 fields ([ny][nx] float at `where`), the density given as
+ * its deviation drho = rho - rho0 so that FP32 keeps its small variations.
+ * For a handle with FP32 storage nothing is lost against the FP64 call (the
+ * arithmetic runs in the storage precision either way) and half the bytes
+ * move. */
+fdlbm_status fdlbm_init_fields_f32(fdlbm_t h, const float *drho, const float *ux, const float *uy,
+                                   const float *grad, int where);
 
 /* Copy f~ ([9][ny][nx] FP64 at `where`) into / out of the handle. */
 fdlbm_status fdlbm_set_state(fdlbm_t h, const double *f, int where);
@@ -182,8 +189,11 @@ fdlbm_status fdlbm_set_force(fdlbm_t h, const double *force, int where);
  * the stream; returns ECUDA if a launch fails. */
 fdlbm_status fdlbm_step(fdlbm_t h, int n);
 
-/* Density and velocity of Eq. 3.3 into [ny][nx] FP64 arrays at `where`. */
+/* Density and velocity of Eq. 3.3 into [ny][nx] FP64 arrays at `where`,
+ * computed in the storage precision of the handle. */
 fdlbm_status fdlbm_moments(fdlbm_t h, double *rho, double *ux, double *uy, int where);
+/* The same into FP32 arrays, the density as its deviation rho - rho0. */
+fdlbm_status fdlbm_moments_f32(fdlbm_t h, float *drho, float *ux, float *uy, int where);
 
 /* FP64 reductions (warp shuffles, fixed order): *mass = sum rho / (m_x m_y) over all
  * nodes (the Jacobian-weighted mass, exactly conserved on periodic grids), and

@@ -61,12 +61,16 @@ SIGNATURES = [
     ("fdlbm_destroy", None, [_H]),
     ("fdlbm_init_fields", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_int]),
+    ("fdlbm_init_fields_f32", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_int]),
     ("fdlbm_set_state", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
     ("fdlbm_get_state", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
     ("fdlbm_set_force", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int]),
     ("fdlbm_step", ctypes.c_int, [_H, ctypes.c_int]),
     ("fdlbm_moments", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_int]),
+    ("fdlbm_moments_f32", ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int]),
     ("fdlbm_reduce", ctypes.c_int, [_H, _dp, _dp]),
     ("fdlbm_set_stream", ctypes.c_int, [_H, ctypes.c_void_p]),
     ("fdlbm_sync", ctypes.c_int, [_H]),

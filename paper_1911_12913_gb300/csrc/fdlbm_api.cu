@@ -103,10 +103,10 @@ int choose_rows(int nx, int ny, int precision, int variant, bool walls, int sche
     int per_sm;
     if (scheme == FDLBM_SCHEME_T2S2_2)
         per_sm = f32 ? fused_s2_blocks_per_sm<float>() : fused_s2_blocks_per_sm<double>();
-    else if (walls)
-        per_sm = f32 ? fused_walls_blocks_per_sm<float>() : fused_walls_blocks_per_sm<double>();
     else if (variant == FDLBM_VARIANT_WARP)
         per_sm = fused_warp_blocks_per_sm();
+    else if (walls)
+        per_sm = f32 ? fused_walls_blocks_per_sm<float>() : fused_walls_blocks_per_sm<double>();
     else
         per_sm = f32 ? fused_blocks_per_sm<float>() : fused_blocks_per_sm<double>();
     if (per_sm <= 0) per_sm = 1;
@@ -168,8 +168,8 @@ cudaError_t launch_step(fdlbm_ctx *h, cudaStream_t s)
         auto a = step_args<float>(h);
         if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
         if (h->scheme == FDLBM_SCHEME_T2S2_2) return launch_fused_s2(a, s);
-        if (walls) return launch_fused_walls(a, s);
         if (h->variant == FDLBM_VARIANT_WARP) return launch_fused_warp(a, h->wmaps, h->cur, s);
+        if (walls) return launch_fused_walls(a, s);
         return launch_fused(a, s);
     }
     auto a = step_args<double>(h);
@@ -232,7 +232,8 @@ fdlbm_status capture_step_graph(fdlbm_ctx *h)
 // pinned host memory is mapped into the device's address space (unified
 // addressing), so kernels can use it in place of a staged copy.  nullptr for
 // pageable memory (or on any query error, which is cleared).
-double *device_view(const double *p)
+template <class T>
+T *device_view(const T *p)
 {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -240,11 +241,12 @@ double *device_view(const double *p)
         return nullptr;
     }
     if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
-    return static_cast<double *>(at.devicePointer);
+    return static_cast<T *>(at.devicePointer);
 }
 
 // Device views of all non-null host arrays, or false if any has none.
-bool device_views(const double *const *p, int n, double **out)
+template <class T>
+bool device_views(const T *const *p, int n, T **out)
 {
     for (int k = 0; k < n; ++k) {
         out[k] = nullptr;
@@ -253,35 +255,36 @@ bool device_views(const double *const *p, int n, double **out)
     return true;
 }
 
-// Hand `nfields` host or device fields ([ny][nx] FP64 each) to
+// Hand `nfields` host or device fields ([ny][nx] of T each) to
 // `kernel(ptr, row0, nrows, fstride)`: device fields and pinned host fields in
 // place (one pass; the call still waits for it, so host arrays are free on
 // return), pageable host fields through the staging area in row chunks.
-template <class K>
-fdlbm_status staged_in(fdlbm_ctx *h, const double *const *fields, int nfields, int where,
-                       K kernel, const char *what)
+template <class T, class K>
+fdlbm_status staged_in(fdlbm_ctx *h, const T *const *fields, int nfields, int where, K kernel,
+                       const char *what)
 {
-    const size_t row_bytes = (size_t)h->nx * sizeof(double);
+    const size_t row_bytes = (size_t)h->nx * sizeof(T);
     if (where == FDLBM_MEM_DEVICE) {
         // device fields: consecutive pointers are expected for multi-field args
         cudaError_t e = kernel(fields, h->ny, (size_t)h->nx * h->ny, 0);
         return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, what);
     }
     {
-        std::vector<double *> views(nfields);
+        std::vector<T *> views(nfields);
         if (device_views(fields, nfields, views.data())) {
-            std::vector<const double *> cv(views.begin(), views.end());
+            std::vector<const T *> cv(views.begin(), views.end());
             cudaError_t e = kernel(cv.data(), h->ny, (size_t)h->nx * h->ny, 0);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
             return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, what);
         }
     }
-    double *stage = reinterpret_cast<double *>(h->ws + h->lay.staging);
-    const int rows = (int)std::max<size_t>(1, h->lay.staging_elems / ((size_t)nfields * h->nx));
+    T *stage = reinterpret_cast<T *>(h->ws + h->lay.staging);
+    const size_t stage_elems = h->lay.staging_elems * (sizeof(double) / sizeof(T));
+    const int rows = (int)std::max<size_t>(1, stage_elems / ((size_t)nfields * h->nx));
     for (int r0 = 0; r0 < h->ny; r0 += rows) {
         const int nr = std::min(rows, h->ny - r0);
         const size_t fstride = (size_t)nr * h->nx;
-        std::vector<const double *> ptrs(nfields);
+        std::vector<const T *> ptrs(nfields);
         for (int k = 0; k < nfields; ++k) {
             if (!fields[k]) {
                 ptrs[k] = nullptr;
@@ -297,6 +300,68 @@ fdlbm_status staged_in(fdlbm_ctx *h, const double *const *fields, int nfields, i
         // the staging area is reused by the next chunk
         e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, what);
+    }
+    return FDLBM_OK;
+}
+
+// Initialisation from fields of type T (see fdlbm_init_fields / _f32).
+template <class T>
+fdlbm_status init_fields_t(fdlbm_t h, const T *rho, const T *ux, const T *uy, const T *grad,
+                           int where)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (!rho || !ux || !uy || (where != FDLBM_MEM_HOST && where != FDLBM_MEM_DEVICE))
+        return fail(h, FDLBM_EINVAL, "init_fields: NULL field or bad `where`");
+    const size_t N = (size_t)h->nx * h->ny;
+    const T *f[7] = {rho, ux, uy, grad, grad ? grad + N : nullptr, grad ? grad + 2 * N : nullptr,
+                     grad ? grad + 3 * N : nullptr};
+    h->have_uprev = false;
+    return staged_in<T>(
+        h, f, grad ? 7 : 3, where,
+        [&](const T *const *p, int nr, size_t fstride, int r0) {
+            return launch_init_fields<T>(h, p[0], p[1], p[2], grad ? p[3] : nullptr, r0, nr, fstride);
+        },
+        "init_fields");
+}
+
+// Moments into fields of type T (see fdlbm_moments / _f32).
+template <class T>
+fdlbm_status moments_t(fdlbm_t h, T *rho, T *ux, T *uy, int where)
+{
+    if (!h) return FDLBM_EINVAL;
+    if (!rho || !ux || !uy || (where != FDLBM_MEM_HOST && where != FDLBM_MEM_DEVICE))
+        return fail(h, FDLBM_EINVAL, "moments: NULL or bad `where`");
+    const size_t N = (size_t)h->nx * h->ny;
+    cudaError_t e;
+    if (where == FDLBM_MEM_DEVICE) {
+        e = launch_moments<T>(h, rho, ux, uy, 0, h->ny, N);
+        return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "moments");
+    }
+    {
+        const T *outs[3] = {rho, ux, uy};
+        T *v[3];
+        if (device_views(outs, 3, v)) {  // pinned host memory: written in place
+            e = launch_moments<T>(h, v[0], v[1], v[2], 0, h->ny, N);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "moments");
+        }
+    }
+    T *stage = reinterpret_cast<T *>(h->ws + h->lay.staging);
+    const size_t stage_elems = h->lay.staging_elems * (sizeof(double) / sizeof(T));
+    const int rows = (int)std::max<size_t>(1, stage_elems / (3 * (size_t)h->nx));
+    for (int r0 = 0; r0 < h->ny; r0 += rows) {
+        const int nr = std::min(rows, h->ny - r0);
+        const size_t fs = (size_t)nr * h->nx;
+        e = launch_moments<T>(h, stage, stage + fs, stage + 2 * fs, r0, nr, fs);
+        if (e != cudaSuccess) return cuda_fail(h, e, "moments");
+        T *dst[3] = {rho, ux, uy};
+        for (int k = 0; k < 3; ++k) {
+            e = cudaMemcpyAsync(dst[k] + (size_t)r0 * h->nx, stage + k * fs, fs * sizeof(T),
+                                cudaMemcpyDeviceToHost, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "moments");
+        }
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "moments");
     }
     return FDLBM_OK;
 }
@@ -378,8 +443,7 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     const bool f32 = o.precision == FDLBM_FP32_DEV;
     // the warp-tile kernel is a T2S2-FDLBM1 kernel; T2S2-FDLBM2 fuses on the scalar layout only
     const bool s1 = o.scheme == FDLBM_SCHEME_T2S2_1;
-    const bool periodic = !walled(g);
-    const bool warp_ok = s1 && fused && periodic && f32 && fused_warp_ok(g->nx, g->ny);
+    const bool warp_ok = s1 && fused && f32 && fused_warp_ok(g->nx, g->ny, g->bc_x == FDLBM_WALL);
     if (o.variant == FDLBM_VARIANT_WARP && !warp_ok) return FDLBM_EUNSUPPORTED;
     int variant = o.variant;
     if (variant == FDLBM_VARIANT_AUTO) variant = warp_ok ? FDLBM_VARIANT_WARP : FDLBM_VARIANT_SCALAR;
@@ -568,19 +632,13 @@ void fdlbm_destroy(fdlbm_t h)
 fdlbm_status fdlbm_init_fields(fdlbm_t h, const double *rho, const double *ux, const double *uy,
                                const double *grad, int where)
 {
-    if (!h) return FDLBM_EINVAL;
-    if (!rho || !ux || !uy || (where != FDLBM_MEM_HOST && where != FDLBM_MEM_DEVICE))
-        return fail(h, FDLBM_EINVAL, "init_fields: NULL field or bad `where`");
-    const size_t N = (size_t)h->nx * h->ny;
-    const double *f[7] = {rho, ux, uy, grad, grad ? grad + N : nullptr,
-                          grad ? grad + 2 * N : nullptr, grad ? grad + 3 * N : nullptr};
-    h->have_uprev = false;
-    return staged_in(
-        h, f, grad ? 7 : 3, where,
-        [&](const double *const *p, int nr, size_t fstride, int r0) {
-            return launch_init_fields(h, p[0], p[1], p[2], grad ? p[3] : nullptr, r0, nr, fstride);
-        },
-        "init_fields");
+    return init_fields_t<double>(h, rho, ux, uy, grad, where);
+}
+
+fdlbm_status fdlbm_init_fields_f32(fdlbm_t h, const float *drho, const float *ux, const float *uy,
+                                   const float *grad, int where)
+{
+    return init_fields_t<float>(h, drho, ux, uy, grad, where);
 }
 
 fdlbm_status fdlbm_set_state(fdlbm_t h, const double *f, int where)
@@ -678,41 +736,12 @@ fdlbm_status fdlbm_step(fdlbm_t h, int n)
 
 fdlbm_status fdlbm_moments(fdlbm_t h, double *rho, double *ux, double *uy, int where)
 {
-    if (!h) return FDLBM_EINVAL;
-    if (!rho || !ux || !uy || (where != FDLBM_MEM_HOST && where != FDLBM_MEM_DEVICE))
-        return fail(h, FDLBM_EINVAL, "moments: NULL or bad `where`");
-    const size_t N = (size_t)h->nx * h->ny;
-    cudaError_t e;
-    if (where == FDLBM_MEM_DEVICE) {
-        e = launch_moments(h, rho, ux, uy, 0, h->ny, N);
-        return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "moments");
-    }
-    {
-        const double *outs[3] = {rho, ux, uy};
-        double *v[3];
-        if (device_views(outs, 3, v)) {  // pinned host memory: written in place
-            e = launch_moments(h, v[0], v[1], v[2], 0, h->ny, N);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-            return e == cudaSuccess ? FDLBM_OK : cuda_fail(h, e, "moments");
-        }
-    }
-    double *stage = reinterpret_cast<double *>(h->ws + h->lay.staging);
-    const int rows = (int)std::max<size_t>(1, h->lay.staging_elems / (3 * (size_t)h->nx));
-    for (int r0 = 0; r0 < h->ny; r0 += rows) {
-        const int nr = std::min(rows, h->ny - r0);
-        const size_t fs = (size_t)nr * h->nx;
-        e = launch_moments(h, stage, stage + fs, stage + 2 * fs, r0, nr, fs);
-        if (e != cudaSuccess) return cuda_fail(h, e, "moments");
-        double *dst[3] = {rho, ux, uy};
-        for (int k = 0; k < 3; ++k) {
-            e = cudaMemcpyAsync(dst[k] + (size_t)r0 * h->nx, stage + k * fs, fs * sizeof(double),
-                                cudaMemcpyDeviceToHost, h->stream);
-            if (e != cudaSuccess) return cuda_fail(h, e, "moments");
-        }
-        e = cudaStreamSynchronize(h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "moments");
-    }
-    return FDLBM_OK;
+    return moments_t<double>(h, rho, ux, uy, where);
+}
+
+fdlbm_status fdlbm_moments_f32(fdlbm_t h, float *drho, float *ux, float *uy, int where)
+{
+    return moments_t<float>(h, drho, ux, uy, where);
 }
 
 fdlbm_status fdlbm_reduce(fdlbm_t h, double *mass, double *resid)
@@ -870,10 +899,11 @@ const char *fdlbm_describe(fdlbm_t h)
     }
     const bool walls = h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL;
     const char *kern = h->path == FDLBM_PATH_STAGED        ? "staged"
-                       : walls                              ? "fused-walls"
                        : h->variant == FDLBM_VARIANT_WARP   ? "fused-warp"
+                       : walls                              ? "fused-walls"
                                                             : "fused";
     h->desc = std::string(kern) + " " + prec + " rows=" + std::to_string(h->rows);
+    if (walls && h->path == FDLBM_PATH_FUSED && h->variant == FDLBM_VARIANT_WARP) h->desc += " walls";
     if (h->graph_steps) h->desc += " graph_steps=" + std::to_string(h->graph_steps);
     if (h->incomp) h->desc += " incompressible";
     return h->desc.c_str();

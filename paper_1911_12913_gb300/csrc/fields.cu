@@ -18,39 +18,43 @@ constexpr int kRedThreads = 256;
 // stored variable is f~ = f - (dt/2) Omega-bar(f) (Eq. 2.19), which with a body
 // force carries -(dt/2) F_i(rho, u) (Eq. 3.12), so that Eq. 3.3 reads back the
 // given velocity.  The force is the handle's field at the time of the call.
-template <class R>
-__global__ void k_init(StepArgs<R> a, const R *force, const double *rho, const double *ux,
-                       const double *uy, const double *grad, size_t fstride, int row0, int nrows,
-                       double tau, double dt, double rho0)
+// Fields of type T (FP64, or FP32 with DEV: the density given as rho - rho0,
+// so that FP32 keeps its small variations); the arithmetic is in the storage
+// precision R, whose rounding the stored deviations take anyway.
+template <class R, class T, bool DEV>
+__global__ void k_init(StepArgs<R> a, const R *force, const T *rho, const T *ux, const T *uy,
+                       const T *grad, size_t fstride, int row0, int nrows, double tau, double dt,
+                       double rho0)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || j >= nrows) return;
     const size_t l = (size_t)j * a.nx + x;
-    const double r = rho[l], u = ux[l], v = uy[l];
-    double geq[9], F[9];
-    equilibrium_dev<double>(r - rho0, a.c.incomp ? rho0 : r, u, v, geq);
+    const R drho = DEV ? R(rho[l]) : R(double(rho[l]) - rho0);
+    const R r0 = R(rho0), u = R(ux[l]), v = R(uy[l]);
+    const R r = r0 + drho;
+    R geq[9], F[9];
+    equilibrium_dev<R>(drho, a.c.incomp ? r0 : r, u, v, geq);
     const size_t o = (size_t)(row0 + j) * a.pitch + x;
     if (force) {
-        force_terms<double>(rho0, geq, u, v, double(force[o]), double(force[a.plane + o]), F,
-                            a.c.incomp ? r - rho0 : 0.0);
+        force_terms<R>(r0, geq, u, v, force[o], force[a.plane + o], F, a.c.incomp ? drho : R(0));
     } else {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) F[i] = 0.0;
+        for (int i = 0; i < 9; ++i) F[i] = R(0);
     }
     // Eq. 3.5 with the coefficient rho0 w_i (2 tau + dt) / (2 cs^2)
-    const double k = rho0 * (2.0 * tau + dt) * 1.5;
+    const R k = R(rho0 * (2.0 * tau + dt) * 1.5);
+    const R hdt = R(0.5 * dt);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        double val = geq[i] - 0.5 * dt * F[i];
+        R val = geq[i] - hdt * F[i];
         if (grad) {
-            const double gxx = grad[l], gxy = grad[fstride + l], gyx = grad[2 * fstride + l],
-                         gyy = grad[3 * fstride + l];
-            const double d = double(cx(i) * cx(i)) * gxx + double(cx(i) * cy(i)) * (gxy + gyx) +
-                             double(cy(i) * cy(i)) * gyy;
-            val -= k * wq<double>(i) * d;
+            const R gxx = R(grad[l]), gxy = R(grad[fstride + l]), gyx = R(grad[2 * fstride + l]),
+                    gyy = R(grad[3 * fstride + l]);
+            const R d = R(cx(i) * cx(i)) * gxx + R(cx(i) * cy(i)) * (gxy + gyx) + R(cy(i) * cy(i)) * gyy;
+            val -= k * wq<R>(i) * d;
         }
-        a.gout[i * a.plane + o] = R(val);
+        a.gout[i * a.plane + o] = val;
     }
 }
 
@@ -90,39 +94,41 @@ __global__ void k_set_force(StepArgs<R> a, R *force, const double *src, size_t f
     force[a.plane + o] = R(src[fstride + l]);
 }
 
-// Eq. 3.3 in FP64 from the stored deviations.
+// Eq. 3.3 in the storage precision R: rho - rho0 and u.
 template <class R>
-__device__ void node_moments(const StepArgs<R> &a, const R *force, size_t o, double rho0,
-                             double half_dt, double &rho, double &ux, double &uy)
+__device__ void node_moments_r(const StepArgs<R> &a, const R *force, size_t o, R rho0, R half_dt,
+                               R &drho, R &ux, R &uy)
 {
-    double g[9];
+    R g[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) g[i] = double(a.gin[i * a.plane + o]);
-    double drho, jx, jy;
-    moments_dev<double>(g, drho, jx, jy);
-    rho = rho0 + drho;
-    const double rm = a.c.incomp ? rho0 : rho;  // the density of the momentum
+    for (int i = 0; i < 9; ++i) g[i] = a.gin[i * a.plane + o];
+    R jx, jy;
+    moments_dev<R>(g, drho, jx, jy);
+    const R rm = a.c.incomp ? rho0 : rho0 + drho;
     if (force) {
-        jx += half_dt * rm * double(force[o]);
-        jy += half_dt * rm * double(force[a.plane + o]);
+        jx += half_dt * rm * force[o];
+        jy += half_dt * rm * force[a.plane + o];
     }
-    ux = jx / rm;
-    uy = jy / rm;
+    const R inv = node_reciprocal<R>(rm);
+    ux = jx * inv;
+    uy = jy * inv;
 }
 
-template <class R>
-__global__ void k_moments(StepArgs<R> a, const R *force, double *rho, double *ux, double *uy,
-                          int row0, int nrows, double rho0, double half_dt)
+// Density (or with DEV its deviation rho - rho0) and velocity into fields of
+// type T, computed in the storage precision.
+template <class R, class T, bool DEV>
+__global__ void k_moments(StepArgs<R> a, const R *force, T *rho, T *ux, T *uy, int row0, int nrows,
+                          double rho0, double half_dt)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || j >= nrows) return;
     const size_t l = (size_t)j * a.nx + x, o = (size_t)(row0 + j) * a.pitch + x;
-    double r, u, v;
-    node_moments(a, force, o, rho0, half_dt, r, u, v);
-    rho[l] = r;
-    ux[l] = u;
-    uy[l] = v;
+    R dr, u, v;
+    node_moments_r<R>(a, force, o, R(rho0), R(half_dt), dr, u, v);
+    rho[l] = DEV ? T(dr) : T(rho0 + double(dr));
+    ux[l] = T(u);
+    uy[l] = T(v);
 }
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -149,8 +155,11 @@ __global__ void __launch_bounds__(kRedThreads)
         for (int x = threadIdx.x; x < a.nx; x += blockDim.x) {
             const size_t n = (size_t)y * a.nx + x;
             const size_t o = (size_t)y * a.pitch + x;
-            double r, u, v;
-            node_moments(a, force, o, rho0, half_dt, r, u, v);
+            // moments in the storage precision (FP32 states carry no more), sums
+            // in FP64
+            R dr, ur, vr;
+            node_moments_r<R>(a, force, o, R(rho0), R(half_dt), dr, ur, vr);
+            const double r = rho0 + double(dr), u = double(ur), v = double(vr);
             m += r / (mxd[x] * my);
             uu += u * u + v * v;
             if (use_prev) {
@@ -230,19 +239,24 @@ inline dim3 grid2(int nx, int nrows, dim3 blk)
         }                                             \
     } while (0)
 
-cudaError_t launch_init_fields(fdlbm_ctx *h, const double *rho, const double *ux,
-                               const double *uy, const double *grad, int row0, int nrows,
-                               size_t fstride)
+template <class T>
+cudaError_t launch_init_fields(fdlbm_ctx *h, const T *rho, const T *ux, const T *uy, const T *grad,
+                               int row0, int nrows, size_t fstride)
 {
     const dim3 blk(32, 8);
+    constexpr bool dev = sizeof(T) == 4;  // FP32 fields give the density as rho - rho0
     DISPATCH(h, R,
              const R *force = h->has_force ? reinterpret_cast<const R *>(h->ws + h->lay.force)
                                            : nullptr;
-             k_init<R><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
+             k_init<R, T, dev><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
                  view<R>(h), force, rho, ux, uy, grad, fstride, row0, nrows, h->tau, h->dt,
                  h->rho0));
     return cudaGetLastError();
 }
+template cudaError_t launch_init_fields<double>(fdlbm_ctx *, const double *, const double *,
+                                                const double *, const double *, int, int, size_t);
+template cudaError_t launch_init_fields<float>(fdlbm_ctx *, const float *, const float *,
+                                               const float *, const float *, int, int, size_t);
 
 cudaError_t launch_convert_in(fdlbm_ctx *h, const double *f, int row0, int nrows, size_t fstride)
 {
@@ -270,17 +284,22 @@ cudaError_t launch_set_force(fdlbm_ctx *h, const double *force, int row0, int nr
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(fdlbm_ctx *h, double *rho, double *ux, double *uy, int row0,
-                           int nrows, size_t /*fstride*/)
+template <class T>
+cudaError_t launch_moments(fdlbm_ctx *h, T *rho, T *ux, T *uy, int row0, int nrows,
+                           size_t /*fstride*/)
 {
     const dim3 blk(32, 8);
+    constexpr bool dev = sizeof(T) == 4;  // FP32 fields get the density as rho - rho0
     DISPATCH(h, R,
              const R *force = h->has_force ? reinterpret_cast<const R *>(h->ws + h->lay.force)
                                            : nullptr;
-             k_moments<R><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
+             k_moments<R, T, dev><<<grid2(h->nx, nrows, blk), blk, 0, h->stream>>>(
                  view<R>(h), force, rho, ux, uy, row0, nrows, h->rho0, 0.5 * h->dt));
     return cudaGetLastError();
 }
+template cudaError_t launch_moments<double>(fdlbm_ctx *, double *, double *, double *, int, int,
+                                            size_t);
+template cudaError_t launch_moments<float>(fdlbm_ctx *, float *, float *, float *, int, int, size_t);
 
 cudaError_t launch_reduce(fdlbm_ctx *h, int use_prev)
 {

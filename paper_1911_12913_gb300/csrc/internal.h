@@ -122,7 +122,7 @@ template <class R>
 cudaError_t launch_batched_fused_s2(const BatchTables &t, int parity, int blk_off, int nblocks,
                                     cudaStream_t s);
 // step_fused_warp.cu (FP32, one independent warp per tile, packed f32x2)
-bool fused_warp_ok(int nx, int ny);
+bool fused_warp_ok(int nx, int ny, bool wall_x);
 cudaError_t fused_warp_encode(WarpMaps *m, const float *state0, const float *state1,
                               const float *force, int nx, int ny, int pitch, size_t plane);
 cudaError_t launch_fused_warp(const StepArgs<float> &a, const WarpMaps &maps, int cur,
@@ -168,16 +168,17 @@ template <class R>
 cudaError_t launch_moments_vjp(const StepArgs<R> &a, const double *du, R *lam, double *dforce,
                                cudaStream_t s);
 // fields.cu
-cudaError_t launch_init_fields(fdlbm_ctx *h, const double *rho, const double *ux,
-                               const double *uy, const double *grad, int row0, int nrows,
-                               size_t src_pitch_rows);
+template <class T>
+cudaError_t launch_init_fields(fdlbm_ctx *h, const T *rho, const T *ux, const T *uy, const T *grad,
+                               int row0, int nrows, size_t src_pitch_rows);
 cudaError_t launch_convert_in(fdlbm_ctx *h, const double *f, int row0, int nrows,
                               size_t src_plane);
 cudaError_t launch_convert_out(fdlbm_ctx *h, double *f, int row0, int nrows, size_t dst_plane);
 cudaError_t launch_set_force(fdlbm_ctx *h, const double *force, int row0, int nrows,
                              size_t src_plane);
-cudaError_t launch_moments(fdlbm_ctx *h, double *rho, double *ux, double *uy, int row0,
-                           int nrows, size_t dst_plane);
+template <class T>
+cudaError_t launch_moments(fdlbm_ctx *h, T *rho, T *ux, T *uy, int row0, int nrows,
+                           size_t dst_plane);
 cudaError_t launch_reduce(fdlbm_ctx *h, int use_prev);
 
 }  // namespace fdlbm

@@ -106,6 +106,7 @@ struct ArgsW {
     CUtensorMap tfside; // the same with box (4, 1, 2)
     float *gout;
     const float *mx, *my;
+    const float *force;  // [2][ny][pitch] (walled grids read it directly at Eq. 3.10)
     int nx, ny, pitch;
     size_t plane;
     int rows;
@@ -121,6 +122,9 @@ struct ArgsW {
     // analogue for fbar), and 3 x the weights of the forcing term in fbar^{+,h}
     // (Eq. 2.34 after Eq. 2.19), f~+ (Eq. 2.20) and f* (Eq. 2.32)
     float hdt, hh, k_bar, k_til, k_star;
+    // walled axes (WALLS instances): the velocities of the W, E, S, N walls (Eq. 3.10)
+    int wx, wy;
+    float uw[4][2];
 };
 
 // The weights of the update's differences (stage C) for a scale s = -dt m:
@@ -176,6 +180,36 @@ __device__ __forceinline__ f2 xtaps(const f2 c[3], int sgn, f2 v0, f2 acc)
     return fma2(c[2], make_float2(Rlo, Rhi), acc);
 }
 
+// xtaps next to a wall of x (Eq. 3.10 grids): an interior node whose upwind
+// tap would reach past the wall takes the central difference alone.  With the
+// value past the wall replaced by the quadratic extrapolation 3 f(0) - 3 f(1) +
+// f(2) of the three nearest values, the mixed weights of Eq. 2.36 give exactly
+// the central difference (the upwind part is exact on quadratics), so the
+// weights stay those of every other node.  west: the lane holds columns 0 (the
+// wall) and 1; east: columns nx-2 and nx-1 (the wall; nx even); eastg:
+// columns nx-3 and nx-2 (nx odd, the wall is the next lane's first column).
+__device__ __forceinline__ f2 xtaps_w(const f2 c[3], int sgn, f2 v0, f2 acc, bool west, bool east,
+                                      bool eastg)
+{
+    if (sgn > 0) {
+        const float Llo = __shfl_up_sync(kFull, v0.x, 1);
+        float Lhi = __shfl_up_sync(kFull, v0.y, 1);
+        const float Rlo = __shfl_down_sync(kFull, v0.x, 1);
+        if (west) Lhi = fmaf(3.f, v0.x - v0.y, Rlo);   // column -1
+        acc = fma2(c[0], make_float2(v0.y, Rlo), acc);
+        acc = fma2(c[1], make_float2(Lhi, v0.x), acc);
+        return fma2(c[2], make_float2(Llo, Lhi), acc);
+    }
+    const float Lhi = __shfl_up_sync(kFull, v0.y, 1);
+    float Rlo = __shfl_down_sync(kFull, v0.x, 1);
+    float Rhi = __shfl_down_sync(kFull, v0.y, 1);
+    if (east) Rlo = fmaf(3.f, v0.y - v0.x, Lhi);       // column nx
+    if (eastg) Rhi = fmaf(3.f, Rlo - v0.y, v0.x);      // column nx
+    acc = fma2(c[0], make_float2(Lhi, v0.x), acc);
+    acc = fma2(c[1], make_float2(v0.y, Rlo), acc);
+    return fma2(c[2], make_float2(Rlo, Rhi), acc);
+}
+
 // The same in y from the lane's own window (rows k-2 .. k+2 as vm2 .. vp2).
 __device__ __forceinline__ f2 ytaps(const f2 c[3], int sgn, f2 vm2, f2 vm1, f2 vp1, f2 vp2, f2 acc)
 {
@@ -187,7 +221,14 @@ __device__ __forceinline__ f2 ytaps(const f2 c[3], int sgn, f2 vm2, f2 vm1, f2 v
 // GRID: how the update's weights are made to sum to zero (update_weights).
 // FORCE: a body-acceleration field (Eqs. 3.3 and 3.12), whose rows arrive by
 // tensor copy with the rows of f~ into a 5-row ring (stage B reads row r-2).
-template <bool INC, bool GRID, bool FORCE>
+// WALLS: walled axes (a.wx, a.wy) with Eq. 3.10, by the rules of the scalar
+// walls sweep: wall nodes take no part in stages B and C, their f* and new f~
+// come from Eq. 3.10 at the nearest interior node (the diagonal one at
+// corners, with the W/E wall velocity), and interior nodes whose upwind tap
+// would reach past a wall take the central difference alone (here through a
+// quadratic ghost value, xtaps_w).  Rows and columns past a wall arrive as
+// the tensor copy's zero fill and feed no stored value.
+template <bool INC, bool GRID, bool FORCE, bool WALLS>
 __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     k_step_fused_warp(const __grid_constant__ ArgsW a)
 {
@@ -202,24 +243,34 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     const int iters = (y1 - y0) + 2 * kHalo;
     const int xs = x0 - kHalo;             // window start before wrapping
     const int xc = xs + 2 * l;             // the lane's first column
+    const bool wxl = WALLS && a.wx, wyl = WALLS && a.wy;
     const int gx = wrap_index(xc, a.nx);   // even, and gx + 1 < nx
     const bool store = (l >= 2) && (l < kLanes - 2) && (xc < a.xend);
+    // lanes at a wall of x: west holds columns (0, 1); with nx even east holds
+    // (nx-2, nx-1); with nx odd eastg holds (nx-3, nx-2) and easto (nx-1, nx),
+    // whose interior neighbour x_j = nx-2 sits in the previous lane (the window
+    // that holds column nx-1 shuffles it over: hase)
+    const bool odd = (a.nx & 1) != 0;
+    const bool west = wxl && xc == 0, east = wxl && !odd && xc == a.nx - 2;
+    const bool eastg = wxl && odd && xc == a.nx - 3, easto = wxl && odd && xc == a.nx - 1;
+    const bool hase = wxl && odd && xs <= a.nx - 1 && a.nx - 1 < xs + kCols;
 
     // ---- where the lane's pair lands: the main ring, or the side ring filled
-    // from x = nx - 4 (first window) or x = 0 (last window)
-    const bool wrap_lo = xs < 0, wrap_hi = xs + kCols > a.nx;
+    // from x = nx - 4 (first window) or x = 0 (last window); a walled x axis
+    // has no seam
+    const bool wrap_lo = !wxl && xs < 0, wrap_hi = !wxl && xs + kCols > a.nx;
     const int wrap_x = wrap_lo ? a.nx - kHalo : 0;
     uint32_t rd = (uint32_t)offsetof(WarpSmem<FORCE>, ring) + 8u * (uint32_t)l;
     uint32_t pstride = kCols * sizeof(float);  // bytes between populations
     uint32_t frd = (uint32_t)offsetof(WarpSmem<FORCE>, fring) + 8u * (uint32_t)l;
     uint32_t fstride = kCols * sizeof(float);  // bytes between force components
     if (!FORCE) {
-        if (xc < 0) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc + kHalo);
-        if (xc >= a.nx) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc - a.nx);
+        if (!wxl && xc < 0) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc + kHalo);
+        if (!wxl && xc >= a.nx) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc - a.nx);
     } else {
         // side rings of 4 columns; lanes further past the seam read the main
         // ring's zero fill (their values reach no output)
-        const int side = xc < 0 ? xc + kHalo : (xc >= a.nx && xc < a.nx + kSide ? xc - a.nx : -1);
+        const int side = wxl ? -1 : (xc < 0 ? xc + kHalo : (xc >= a.nx && xc < a.nx + kSide ? xc - a.nx : -1));
         if (side >= 0) {
             rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)side;
             pstride = kSide * sizeof(float);
@@ -232,7 +283,7 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
 
     // ---- constants: the x weights carry -h m_x (stage B) and -dt m_x (stage C)
     const f2 rho0 = bc(a.rho0);
-    const f2 mx2 = make_float2(__ldg(a.mx + gx), __ldg(a.mx + gx + 1));
+    const f2 mx2 = make_float2(__ldg(a.mx + gx), __ldg(a.mx + (gx + 1 < a.nx ? gx + 1 : gx)));
     const f2 nhx = mul2(bc(-a.h), mx2), ndx = mul2(bc(-a.dt), mx2);
     const f2 axB[3] = {mul2(nhx, bc(a.w[0])), mul2(nhx, bc(a.w[2])), mul2(nhx, bc(a.w[3]))};
     // stage C: taps on the weight grid of each column and the centre as minus
@@ -257,7 +308,9 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     const bool seam = wrap_lo || wrap_hi;
     const uint32_t tx = FORCE ? kRowBytes + kFRowBytes + (seam ? 9u * kSide * 4u + 2u * kSide * 4u : 0u)
                               : (seam ? 2u * kRowBytes : kRowBytes);
-    int ld_row = wrap_index(y0 - kHalo, a.ny);  // next row to request
+    // next row to request (a walled y axis: the logical row, whose copies
+    // past the walls are zero-filled)
+    int ld_row = wyl ? y0 - kHalo : wrap_index(y0 - kHalo, a.ny);
     // rows into f~ slot `slot` and (force field) force slot `fslot`
     auto issue = [&](int slot, int fslot) {
         if (l == 0) {
@@ -278,7 +331,7 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 }
             }
         }
-        ld_row = ld_row + 1 == a.ny ? 0 : ld_row + 1;
+        ld_row = (!wyl && ld_row + 1 == a.ny) ? 0 : ld_row + 1;
     };
 
     if (l == 0) {
@@ -294,12 +347,16 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     for (int i = 0; i < 9; ++i)
 #pragma unroll
         for (int j = 0; j < 5; ++j) Pw[i][j] = Sw[i][j] = bc(0.f);
-    // rows of stage B (y0 - 6 + k) and C (y0 - 8 + k) at iteration k
+    // rows of stage B (y0 - 6 + k) and C (y0 - 8 + k) at iteration k: wrapped
+    // (metric and store rows) and logical (walls)
     int rs = wrap_index(y0 - 6, a.ny), rq = wrap_index(y0 - 8, a.ny);
+    int rbL = y0 - 6, rcL = y0 - 8;
     float myB = __ldg(a.my + rs), myC = __ldg(a.my + rq);
     int slot = 0;          // iteration mod 3
     uint32_t parity = 0;   // mbarrier phase parity of the current slot
     bool timed_out = false;
+    // wall velocities as pairs (both halves alike; corner halves get their own)
+    auto uwp = [&](int side, int k) { return bc(a.uw[side][k]); };
 
     // force of the lane's pair from force slot fs (components x, y)
     auto force_of = [&](int fs, f2 &Fx, f2 &Fy) {
@@ -313,6 +370,22 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
         constexpr int PH = decltype(PHc)::value;
         constexpr int p0 = PH, p1 = (PH + 4) % 5, p2 = (PH + 3) % 5, p3 = (PH + 2) % 5,
                       p4 = (PH + 1) % 5;
+        // Eq. 3.10 on the new f~ needs the force at the stage-C row (row r-4,
+        // no longer in the ring): fetched now for the lanes and rows that use it
+        const bool neeC = (wxl && (west || east || easto)) || (wyl && (rcL == 1 || rcL == a.ny - 2));
+        f2 FCx = bc(0.f), FCy = bc(0.f);
+        // (in-domain lanes only: xc even and xc + 1 < nx keep the pair loads
+        // aligned and in bounds)
+        if (WALLS && FORCE && neeC && rcL >= 0 && rcL < a.ny && xc >= 0 && xc < a.nx) {
+            const size_t fo = (size_t)rcL * a.pitch + xc;
+            if (easto) {  // the force of x_j = nx-2 (the lane's second column is padding)
+                FCx = bc(__ldg(a.force + fo - 1));
+                FCy = bc(__ldg(a.force + a.plane + fo - 1));
+            } else {
+                FCx = __ldg(reinterpret_cast<const float2 *>(a.force + fo));
+                FCy = __ldg(reinterpret_cast<const float2 *>(a.force + a.plane + fo));
+            }
+        }
         // ------------------------------------------------------------ A (row r)
         if (!mbar_wait_bounded(&sm.bar[slot], parity)) timed_out = true;
         {
@@ -368,6 +441,8 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
             // centre coefficients: 1 + the centre weights of the differences taken
             const f2 c_y = bc(1.f + nhy * a.w[1]);
             const f2 c_d = add2(c_y, cxB);
+            // rows next to a wall of y: the quadratic ghost row past it (xtaps_w)
+            const bool gS = wyl && rbL == 1, gN = wyl && rbL == a.ny - 2;
             f2 gs[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -377,8 +452,13 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 else if (cx(i) != 0) acc = mul2(c_xB, v0);
                 else if (cy(i) != 0) acc = mul2(c_y, v0);
                 else acc = v0;
-                if (cx(i) != 0) acc = xtaps(axB, cx(i), v0, acc);
-                if (cy(i) != 0) acc = ytaps(ay, cy(i), Pw[i][p4], Pw[i][p3], Pw[i][p1], Pw[i][p0], acc);
+                if (cx(i) != 0) acc = WALLS ? xtaps_w(axB, cx(i), v0, acc, west, east, eastg) : xtaps(axB, cx(i), v0, acc);
+                if (cy(i) != 0) {
+                    f2 vm2 = Pw[i][p4], vp2 = Pw[i][p0];
+                    if (WALLS && cy(i) > 0 && gS) vm2 = fma2(bc(3.f), sub2(Pw[i][p3], v0), Pw[i][p1]);
+                    if (WALLS && cy(i) < 0 && gN) vp2 = fma2(bc(3.f), sub2(Pw[i][p1], v0), Pw[i][p3]);
+                    acc = ytaps(ay, cy(i), vm2, Pw[i][p3], Pw[i][p1], vp2, acc);
+                }
                 gs[i] = acc;
             }
             f2 fs[9];
@@ -401,8 +481,49 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 for (int i = 0; i < 9; ++i) fs[i] = fma2(bst, sub2(ge[i], gs[i]), gs[i]);
                 force_add1(ge, INC ? sub2(rho0, m.drho) : rho0, Fx, Fy, uF, bc(a.k_star), fs);
             }
+            if (WALLS) {
+                // Eq. 3.10 for f* (physical distribution: no force shift)
+                const f2 z = bc(0.f), ir0 = bc(a.inv_rho0);
+                if (wyl && rbL == a.ny - 1) {
+                    // the N wall row, from the window row ny-2
 #pragma unroll
-            for (int i = 0; i < 9; ++i) Sw[i][p0] = fs[i];
+                    for (int i = 0; i < 9; ++i) fs[i] = Sw[i][p1];
+                    nee2<INC, false>(fs, rho0, ir0, z, z, z, uwp(FDLBM_WALL_N, 0), uwp(FDLBM_WALL_N, 1));
+                }
+                if (west || east || hase) {
+                    // the W (E) wall column from column 1 (nx-2): the same lane,
+                    // or for nx odd the previous one
+                    f2 t[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const float nb = hase ? __shfl_up_sync(kFull, fs[i].y, 1) : 0.f;
+                        t[i] = west ? bc(fs[i].y) : (east ? bc(fs[i].x) : bc(nb));
+                    }
+                    if (west || east || easto) {
+                        const int sd = west ? FDLBM_WALL_W : FDLBM_WALL_E;
+                        nee2<INC, false>(t, rho0, ir0, z, z, z, uwp(sd, 0), uwp(sd, 1));
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            if (east) fs[i].y = t[i].y;
+                            else fs[i].x = t[i].x;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Sw[i][p0] = fs[i];
+                if (wyl && rbL == 1) {
+                    // the S wall row into the window slot of row 0
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) fs[i] = Sw[i][p0];
+                    nee2<INC, false>(fs, rho0, ir0, z, z, z, uwp(FDLBM_WALL_S, 0), uwp(FDLBM_WALL_S, 1));
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) Sw[i][p1] = fs[i];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Sw[i][p0] = fs[i];
+            }
+            ++rbL;
         }
         // ------------------------------------------------------------ C (row r-4)
         // f* rows r-6 .. r-2 sit in slots p4, p3, p2, p1, p0 of Sw.
@@ -421,7 +542,10 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
             // the host): one wide multiply-add per store address
             const unsigned roff = (unsigned)qg * (unsigned)a.pitch + (unsigned)xc;
             const unsigned plane32 = (unsigned)a.plane;
-            const bool st = store && k >= 8;
+            const bool rowin = !wyl || (rcL >= 1 && rcL <= a.ny - 2);
+            const bool st = store && k >= 8 && rowin;
+            const bool gS = wyl && rcL == 1, gN = wyl && rcL == a.ny - 2;
+            f2 out[WALLS ? 9 : 1];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const f2 v0 = Sw[i][p2];
@@ -429,10 +553,68 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 if (cx(i) != 0 && cy(i) != 0) acc = fma2(c_d, v0, acc);
                 else if (cx(i) != 0) acc = fma2(cxC, v0, acc);
                 else if (cy(i) != 0) acc = fma2(c_y, v0, acc);
-                if (cx(i) != 0) acc = xtaps(axC, cx(i), v0, acc);
-                if (cy(i) != 0) acc = ytaps(by, cy(i), Sw[i][p4], Sw[i][p3], Sw[i][p1], Sw[i][p0], acc);
-                if (st) *reinterpret_cast<f2 *>(a.gout + (roff + (unsigned)i * plane32)) = acc;
+                if (cx(i) != 0) acc = WALLS ? xtaps_w(axC, cx(i), v0, acc, west, east, eastg) : xtaps(axC, cx(i), v0, acc);
+                if (cy(i) != 0) {
+                    f2 vm2 = Sw[i][p4], vp2 = Sw[i][p0];
+                    if (WALLS && cy(i) > 0 && gS) vm2 = fma2(bc(3.f), sub2(Sw[i][p3], v0), Sw[i][p1]);
+                    if (WALLS && cy(i) < 0 && gN) vp2 = fma2(bc(3.f), sub2(Sw[i][p1], v0), Sw[i][p3]);
+                    acc = ytaps(by, cy(i), vm2, Sw[i][p3], Sw[i][p1], vp2, acc);
+                }
+                if (WALLS) out[i] = acc;
+                else if (st) *reinterpret_cast<f2 *>(a.gout + (roff + (unsigned)i * plane32)) = acc;
             }
+            if (WALLS) {
+                // Eq. 3.10 on the new f~ (force shift dt/2, the force of x_j) of
+                // the wall nodes whose x_j is this node: the W (E) column from
+                // column 1 (nx-2) of the same lane, then the S (N) row from
+                // row 1 (ny-2); corners take the W/E value of their diagonal
+                // node, which is the value just put into the wall column
+                const f2 ir0 = bc(a.inv_rho0), hd = bc(a.hdt);
+                if (west || east || hase) {
+                    f2 t[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const float nb = hase ? __shfl_up_sync(kFull, out[i].y, 1) : 0.f;
+                        t[i] = west ? bc(out[i].y) : (east ? bc(out[i].x) : bc(nb));
+                    }
+                    if (west || east || easto) {
+                        const f2 Fx = west ? bc(FCx.y) : bc(FCx.x), Fy = west ? bc(FCy.y) : bc(FCy.x);
+                        const int sd = west ? FDLBM_WALL_W : FDLBM_WALL_E;
+                        nee2<INC, FORCE>(t, rho0, ir0, hd, Fx, Fy, uwp(sd, 0), uwp(sd, 1));
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            if (east) out[i].y = t[i].y;
+                            else out[i].x = t[i].x;
+                        }
+                    }
+                }
+                // the lane past the last column of an odd grid stores one value
+                auto put = [&](unsigned off, int i, f2 v) {
+                    if (easto) a.gout[off + (unsigned)i * plane32] = v.x;
+                    else *reinterpret_cast<f2 *>(a.gout + (off + (unsigned)i * plane32)) = v;
+                };
+                if (st) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) put(roff, i, out[i]);
+                }
+                if ((gS || gN) && store && k >= 8) {
+                    float corner[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) corner[i] = east ? out[i].y : out[i].x;
+                    const int sd = gS ? FDLBM_WALL_S : FDLBM_WALL_N;
+                    nee2<INC, FORCE>(out, rho0, ir0, hd, FCx, FCy, uwp(sd, 0), uwp(sd, 1));
+                    const unsigned wrow = gS ? 0u : (unsigned)(a.ny - 1);
+                    const unsigned woff = wrow * (unsigned)a.pitch + (unsigned)xc;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        f2 v = out[i];
+                        if (west || easto) v.x = corner[i];
+                        if (east) v.y = corner[i];
+                        put(woff, i, v);
+                    }
+                }
+            }
+            ++rcL;
         }
         // every lane has read the slot: refill it three rows ahead (force slot
         // (k + 3) mod 5, which stage B has just read).  The copy is issued at
@@ -486,10 +668,14 @@ EncodeTiledFn encode_fn()
 
 }  // namespace
 
-bool fused_warp_ok(int nx, int ny)
+bool fused_warp_ok(int nx, int ny, bool wall_x)
 {
+    // periodic x: every copy starts on a 16-byte boundary, a window crosses the
+    // seam at most once and a lane's pair never straddles it (nx % 4 == 0);
+    // walled x: any width (the lanes at the east wall handle either parity)
     const unsigned long long pitch = (nx + 31ull) / 32ull * 32ull;
-    return nx % 4 == 0 && nx >= kCols && ny >= 4 && 9ull * pitch * (unsigned long long)ny < (1ull << 32);
+    const bool cols = wall_x || nx % 4 == 0;
+    return cols && nx >= kCols && ny >= 4 && 9ull * pitch * (unsigned long long)ny < (1ull << 32);
 }
 
 namespace {
@@ -538,15 +724,25 @@ cudaError_t fused_warp_encode(WarpMaps *m, const float *state0, const float *sta
     return cudaSuccess;
 }
 
-template <bool INC, bool GRID, bool FORCE>
+template <bool INC, bool GRID, bool FORCE, bool WALLS>
 cudaError_t launch_t(const ArgsW &a, dim3 grid, cudaStream_t stream)
 {
     constexpr size_t smem = sizeof(WarpSmem<FORCE>);
-    auto kern = k_step_fused_warp<INC, GRID, FORCE>;
+    auto kern = k_step_fused_warp<INC, GRID, FORCE, WALLS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kLanes, smem, stream>>>(a);
     return cudaGetLastError();
+}
+
+template <bool INC, bool GRID>
+cudaError_t launch_fw(const ArgsW &a, bool force, bool walls, dim3 grid, cudaStream_t stream)
+{
+    if (force)
+        return walls ? launch_t<INC, GRID, true, true>(a, grid, stream)
+                     : launch_t<INC, GRID, true, false>(a, grid, stream);
+    return walls ? launch_t<INC, GRID, false, true>(a, grid, stream)
+                 : launch_t<INC, GRID, false, false>(a, grid, stream);
 }
 
 cudaError_t launch_fused_warp(const StepArgs<float> &s, const WarpMaps &maps, int cur,
@@ -565,6 +761,7 @@ cudaError_t launch_fused_warp(const StepArgs<float> &s, const WarpMaps &maps, in
     a.gout = s.gout;
     a.mx = s.mx;
     a.my = s.my;
+    a.force = s.force;
     a.nx = s.nx;
     a.ny = s.ny;
     a.pitch = s.pitch;
@@ -592,16 +789,21 @@ cudaError_t launch_fused_warp(const StepArgs<float> &s, const WarpMaps &maps, in
     a.k_bar = 3.0f * s.c.c_bar;
     a.k_til = 3.0f * s.c.c_til;
     a.k_star = 3.0f * s.c.c_star;
+    a.wx = s.bc_x == FDLBM_WALL;
+    a.wy = s.bc_y == FDLBM_WALL;
+    for (int k = 0; k < 4; ++k) {
+        a.uw[k][0] = s.wall_u[k][0];
+        a.uw[k][1] = s.wall_u[k][1];
+    }
+    const bool walls = a.wx || a.wy;
     // the Sterbenz-ordered update weights need wm1 >= 0.55 |w1| (beta <= 0.16)
     const bool on_grid = !(s.st.wm1 >= 0.55f * std::fabs(s.st.w1));
     const dim3 grid((s.nx + kW - 1) / kW, (s.ny + s.rows - 1) / s.rows);
-    const bool inc = s.c.incomp != 0;
-    if (force) {
-        if (inc) return on_grid ? launch_t<true, true, true>(a, grid, stream) : launch_t<true, false, true>(a, grid, stream);
-        return on_grid ? launch_t<false, true, true>(a, grid, stream) : launch_t<false, false, true>(a, grid, stream);
-    }
-    if (inc) return on_grid ? launch_t<true, true, false>(a, grid, stream) : launch_t<true, false, false>(a, grid, stream);
-    return on_grid ? launch_t<false, true, false>(a, grid, stream) : launch_t<false, false, false>(a, grid, stream);
+    if (s.c.incomp)
+        return on_grid ? launch_fw<true, true>(a, force, walls, grid, stream)
+                       : launch_fw<true, false>(a, force, walls, grid, stream);
+    return on_grid ? launch_fw<false, true>(a, force, walls, grid, stream)
+                   : launch_fw<false, false>(a, force, walls, grid, stream);
 }
 
 int fused_warp_tile_width() { return kW; }
@@ -610,7 +812,7 @@ int fused_warp_blocks_per_sm()
 {
     int n = 0;
     constexpr size_t smem = sizeof(WarpSmem<false>);
-    auto kern = k_step_fused_warp<false, false, false>;
+    auto kern = k_step_fused_warp<false, false, false, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kLanes, smem) != cudaSuccess) return 0;
     return n;

@@ -158,6 +158,51 @@ class FDLBM:
         _check(self._L, self._h, rc, "init_fields")
         return self
 
+    def init_fields_f32(self, drho, ux, uy, grad=None):
+        """As init_fields, from FP32 fields with the density given as rho - rho0
+        (numpy arrays or CUDA tensors, all on one side)."""
+        sh = (self.ny, self.nx)
+        # grad: a list of 4 fields, or one [4, ny, nx] array (kept as it is, so
+        # that a pinned one is read in place)
+        whole = grad is not None and not isinstance(grad, (list, tuple))
+        fields = [drho, ux, uy] + (list(grad) if grad is not None and not whole else [])
+        dev = isinstance(fields[0], torch.Tensor) and fields[0].is_cuda
+        if dev:
+            keep = [torch.as_tensor(v).detach().to(torch.float32).contiguous() for v in fields]
+            ptrs = [t.data_ptr() for t in keep[:3]]
+            g = None
+            if grad is not None:
+                g = grad.detach().to(torch.float32).contiguous() if whole else torch.stack(keep[3:])
+        else:
+            def host(v):
+                return np.ascontiguousarray(np.asarray(v.cpu() if isinstance(v, torch.Tensor) else v),
+                                            dtype=np.float32)
+            keep = [host(v) for v in fields]
+            ptrs = [a.ctypes.data for a in keep[:3]]
+            g = None
+            if grad is not None:
+                g = host(grad) if whole else np.ascontiguousarray(np.stack(keep[3:]))
+        if g is not None:
+            assert tuple(g.shape) == (4,) + sh, (g.shape, sh)
+        for a in keep[:3]:
+            assert tuple(a.shape) == sh, (a.shape, sh)
+        gp = None if g is None else (g.data_ptr() if dev else g.ctypes.data)
+        rc = self._L.fdlbm_init_fields_f32(self._h, *ptrs, gp, B.MEM_DEVICE if dev else B.MEM_HOST)
+        _check(self._L, self._h, rc, "init_fields_f32")
+        return self
+
+    def moments_f32(self, device: bool = False):
+        """(rho - rho0, ux, uy) as FP32 arrays (CUDA tensors with device=True)."""
+        sh = (self.ny, self.nx)
+        if device:
+            outs = [torch.empty(sh, dtype=torch.float32, device=self.device) for _ in range(3)]
+            rc = self._L.fdlbm_moments_f32(self._h, *(o.data_ptr() for o in outs), B.MEM_DEVICE)
+        else:
+            outs = [np.empty(sh, dtype=np.float32) for _ in range(3)]
+            rc = self._L.fdlbm_moments_f32(self._h, *(o.ctypes.data for o in outs), B.MEM_HOST)
+        _check(self._L, self._h, rc, "moments_f32")
+        return tuple(outs)
+
     def set_state(self, f):
         p, where, keep = self._arg(f, (9, self.ny, self.nx))
         _check(self._L, self._h, self._L.fdlbm_set_state(self._h, p, where), "set_state")

@@ -224,7 +224,15 @@ _WALL_CASES = [
     ("wall", "wall", 17, 17, 0), ("wall", "wall", 40, 33, 3), ("wall", "wall", 257, 21, 1),
     ("wall", "wall", 130, 9, 2), ("periodic", "wall", 96, 24, 5), ("periodic", "wall", 250, 13, 0),
     ("wall", "periodic", 33, 40, 4), ("wall", "periodic", 125, 11, 0), ("wall", "wall", 5, 6, 1),
+    # widths for the warp-tile kernel's walls: even and odd east walls, one
+    # and several windows, walls on x only and on y only, row segments 1..5
+    ("wall", "wall", 64, 40, 5), ("wall", "wall", 129, 33, 0), ("periodic", "wall", 128, 21, 3),
+    ("wall", "periodic", 66, 24, 2), ("wall", "wall", 200, 12, 1), ("wall", "wall", 115, 10, 4),
 ]
+
+
+def _warp_walls_ok(bcx, nx):
+    return nx >= 64 and (bcx == "wall" or nx % 4 == 0)
 
 
 def _axis(kind, n, seed, length):
@@ -235,20 +243,32 @@ def _axis(kind, n, seed, length):
     return I.tanh_axis(n - 1, 1.5) if length == 1.0 else I.wall_axis(n - 1, 0.0, length)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_L2)])
+@pytest.mark.parametrize("precision,tol,variant", [("fp64", FP64_TOL, "scalar"), ("fp32", FP32_L2, "scalar"),
+                                                   ("fp32", FP32_L2, "warp")])
+@pytest.mark.parametrize("force_on", [True, False])
 @pytest.mark.parametrize("bcx,bcy,nx,ny,rows", _WALL_CASES)
-def test_fused_walls_match_oracle(precision, tol, bcx, bcy, nx, ny, rows):
-    """The fused sweep with Eq. 3.10 inside it, on walled grids (tanh-stretched
-    or uniform), with moving walls on every side, a random force field and a
-    random state: 12 steps against the oracle."""
+def test_fused_walls_match_oracle(precision, tol, variant, force_on, bcx, bcy, nx, ny, rows):
+    """The fused sweeps with Eq. 3.10 inside them, on walled grids (tanh-stretched
+    or uniform), with moving walls on every side, a random force field (or
+    none) and a random state: 12 steps against the oracle.  variant: the
+    scalar walls sweep, or the warp-tile kernel's walls (FP32; widths of 64
+    and more, even and odd)."""
+    if variant == "warp" and not _warp_walls_ok(bcx, nx):
+        pytest.skip("narrower than the warp-tile window, or a periodic width not a multiple of 4")
     xa = _axis(bcx, nx, 81, 1.0)
     ya = _axis(bcy, ny, 82, 0.8)
     rng = np.random.default_rng(nx * 1000 + ny)
-    force = 1e-3 * rng.uniform(-1, 1, size=(2, ny, nx))
+    force = 1e-3 * rng.uniform(-1, 1, size=(2, ny, nx)) if force_on else None
     wall_u = [tuple(0.05 * rng.uniform(-1, 1, size=2)) for _ in range(4)]
-    s, o = _pair(xa, ya, nu=0.02, cfl=0.4, beta=0.2, precision=precision, force=force,
-                 wall_u=wall_u, rows=rows, path="fused")
-    assert s.describe.startswith("fused-walls"), s.describe
+    s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, precision=precision, has_force=force_on,
+              wall_u=wall_u, path="fused", rows_per_cta=rows, variant=variant)
+    o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force, wall_u=wall_u)
+    if force_on:
+        s.set_force(force)
+    if variant == "warp":
+        assert s.describe.startswith("fused-warp") and s.describe.endswith("walls"), s.describe
+    else:
+        assert s.describe.startswith("fused-walls"), s.describe
     assert s.kernels_per_step == 1
     _init_both(s, o, I.random_fields(nx, ny, 90 + nx))
     for n in (1, 11):
@@ -522,6 +542,58 @@ def test_device_side_arguments_and_zero_steps():
     orr, oux, ouy = o.moments()
     assert rel(r.cpu().numpy(), orr) < 1e-14
     assert O.gre(ux.cpu().numpy(), uy.cpu().numpy(), oux, ouy) < 1e-11
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("where", ["host", "pinned", "device"])
+def test_fp32_field_io_matches_fp64(precision, where):
+    """fdlbm_init_fields_f32 / fdlbm_moments_f32 (FP32 fields, the density as
+    rho - rho0): on an FP32 handle, whose arithmetic runs in FP32 either way,
+    the state is bit for bit that of the FP64 call and the FP32 moments are
+    the FP64 ones rounded; on an FP64 handle they agree to FP32 rounding of
+    the inputs.  Pageable, pinned and device fields, with a force field."""
+    nx, ny = 200, 37
+    xa = I.periodic_axis(nx, 0.0, 1.0)
+    ya = I.periodic_axis(ny, 0.0, 0.4)
+    r = I.random_fields(nx, ny, 43, du=0.02, drho=0.01)
+    force = 1e-3 * np.random.default_rng(5).uniform(-1, 1, size=(2, ny, nx))
+    keys = ("dudx", "dudy", "dvdx", "dvdy")
+    f32 = [(r["rho"] - 1.0).astype(np.float32), r["ux"].astype(np.float32), r["uy"].astype(np.float32)]
+    g32 = [r[k].astype(np.float32) for k in keys]
+    ref = [np.float64(f32[0]) + 1.0, np.float64(f32[1]), np.float64(f32[2])]
+    gref = [np.float64(v) for v in g32]
+
+    def side(a):
+        if where == "device":
+            return torch.tensor(a, device="cuda")
+        if where == "pinned":
+            return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return a
+
+    s1 = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, precision=precision, has_force=True)
+    s2 = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, precision=precision, has_force=True)
+    for s in (s1, s2):
+        s.set_force(force)
+    s1.init_fields(*[side(v) for v in ref], [side(v) for v in gref])
+    s2.init_fields_f32(*[side(v) for v in f32], side(np.stack(g32)))
+    a, b = s1.get_state(), s2.get_state()
+    if precision == "fp32":
+        assert np.array_equal(a, b)
+    else:
+        assert rel(b, a) < 1e-15
+    s1.step(3)
+    s2.step(3)
+    m64 = s1.moments()
+    m32 = s2.moments_f32(device=where == "device")
+    m32 = [np.asarray(v.cpu()) if isinstance(v, torch.Tensor) else v for v in m32]
+    assert m32[0].dtype == np.float32
+    if precision == "fp32":
+        assert np.array_equal(m32[0], (m64[0] - 1.0).astype(np.float32))
+        assert np.array_equal(m32[1], m64[1].astype(np.float32))
+        assert np.array_equal(m32[2], m64[2].astype(np.float32))
+    else:
+        assert np.allclose(m32[0], m64[0] - 1.0, rtol=0, atol=1e-9)
+        assert np.allclose(m32[1], m64[1], rtol=1e-6, atol=1e-12)
 
 
 # ------------------------------------------------------------------ full size, sampled
