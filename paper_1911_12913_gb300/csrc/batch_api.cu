@@ -48,6 +48,17 @@ struct fdlbm_batch_ctx {
     long long steps = 0;
     bool tuned = false;
     double tuned_ms = -1.0;
+    // FUSED mode: cases of T2S2-FDLBM1 on the warp-tile kernel, in groups of
+    // one kernel instance each (tiles [off, off + count) of the tables), then
+    // the walls sweep for the other T2S2-FDLBM1 cases (tiles [walls_off,
+    // blocks_s1)), then the T2S2-FDLBM2 cases
+    void *d_wargs = nullptr;  // 2 x ncases warp-tile argument blocks (tensor maps, scalars)
+    struct WGroup {
+        WarpKind kind;
+        int off, count;
+    };
+    std::vector<WGroup> wgroups;
+    int walls_off = 0;
     std::string err, desc;
 };
 
@@ -77,16 +88,47 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
     std::vector<int> blk_start(n), tiles_x(n), wall_start(n), blk_case;
     int total_wall = 0, total_blocks = 0, blocks_s1 = 0;
     bool any2 = false;
-    // the tiles of T2S2-FDLBM1 cases first, then those of T2S2-FDLBM2 cases (the
-    // fused batch runs each group with its own kernel)
+    // the tiles of T2S2-FDLBM1 cases first (in FUSED mode those on the
+    // warp-tile kernel, grouped by kernel instance, then those on the walls
+    // sweep), then those of T2S2-FDLBM2 cases; the fused batch runs each group
+    // with its own launch
+    const bool warp = fused_rows > 0 && b->mode == FDLBM_BATCH_FUSED;
+    auto on_warp = [&](const fdlbm_ctx *h) {
+        return warp && h->scheme == FDLBM_SCHEME_T2S2_1 && h->variant == FDLBM_VARIANT_WARP;
+    };
+    std::vector<WarpKind> kinds(n);
+    for (int c = 0; c < n; ++c)
+        if (on_warp(b->cases[c])) {
+            fdlbm_ctx *h = b->cases[c];
+            h->rows = std::min(fused_rows, h->ny);
+            kinds[c] = warp_kind(handle_step_args<float>(h));
+        }
     std::vector<int> order;
+    b->wgroups.clear();
+    for (int c = 0; c < n; ++c) {
+        if (!on_warp(b->cases[c])) continue;
+        if (std::find(order.begin(), order.end(), c) != order.end()) continue;
+        for (int d = c; d < n; ++d)
+            if (on_warp(b->cases[d]) && kinds[d] == kinds[c]) order.push_back(d);
+    }
+    const int nwarp_cases = (int)order.size();
     for (int pass = 0; pass < 2; ++pass)
         for (int c = 0; c < n; ++c)
-            if ((b->cases[c]->scheme == FDLBM_SCHEME_T2S2_2) == (pass == 1)) order.push_back(c);
-    for (int c : order) {
+            if (!on_warp(b->cases[c]) && (b->cases[c]->scheme == FDLBM_SCHEME_T2S2_2) == (pass == 1))
+                order.push_back(c);
+    int walls_off = -1;
+    for (int k = 0; k < (int)order.size(); ++k) {
+        const int c = order[k];
         fdlbm_ctx *h = b->cases[c];
+        if (k == nwarp_cases) walls_off = total_blocks;
         int tx, ty;
-        if (fused_rows > 0) {
+        if (k < nwarp_cases) {
+            tx = (h->nx + fused_warp_tile_width() - 1) / fused_warp_tile_width();
+            ty = (h->ny + h->rows - 1) / h->rows;
+            if (b->wgroups.empty() || !(b->wgroups.back().kind == kinds[c]))
+                b->wgroups.push_back({kinds[c], total_blocks, 0});
+            b->wgroups.back().count += tx * ty;
+        } else if (fused_rows > 0) {
             h->rows = std::min(fused_rows, h->ny);
             tx = (h->nx + fused_tile_width_walls() - 1) / fused_tile_width_walls();
             ty = (h->ny + h->rows - 1) / h->rows;
@@ -100,10 +142,15 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
         total_blocks += tx * ty;
         if (h->scheme != FDLBM_SCHEME_T2S2_2) blocks_s1 = total_blocks;
         blk_case.insert(blk_case.end(), (size_t)tx * ty, c);
+        any2 = any2 || h->scheme == FDLBM_SCHEME_T2S2_2;
+    }
+    // wall nodes in case order (the wall kernels find a node's case by a binary
+    // search over these prefix sums, whatever the order of the tiles)
+    for (int c = 0; c < n; ++c) {
+        const fdlbm_ctx *h = b->cases[c];
         wall_start[c] = total_wall;
         const bool wy = h->bc_y == FDLBM_WALL, wx = h->bc_x == FDLBM_WALL;
         total_wall += (wy ? 2 * h->nx : 0) + (wx ? 2 * (wy ? h->ny - 2 : h->ny) : 0);
-        any2 = any2 || h->scheme == FDLBM_SCHEME_T2S2_2;
     }
     const size_t nbar = (persistent_barrier_bytes() + sizeof(int) - 1) / sizeof(int);
     const size_t nints = 3 * (size_t)n + nbar + blk_case.size();
@@ -142,6 +189,24 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
         }
     if (cudaMemcpy(b->d_args, host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return bfail(b, FDLBM_ECUDA, "batch: argument upload failed");
+    // the warp-tile argument blocks (tensor maps of each parity's input state)
+    if (nwarp_cases > 0) {
+        const size_t ws = fused_warp_args_bytes();
+        std::vector<unsigned char> wh(2 * n * ws, 0);
+        for (int p = 0; p < 2; ++p)
+            for (int k = 0; k < nwarp_cases; ++k) {
+                const int c = order[k];
+                fdlbm_ctx *h = b->cases[c];
+                const int saved = h->cur;
+                h->cur = p;
+                const cudaError_t e = fused_warp_args(&wh[(p * n + c) * ws], handle_step_args<float>(h),
+                                                      h->wmaps, p);
+                h->cur = saved;
+                if (e != cudaSuccess) return bfail(b, FDLBM_ECUDA, "batch: warp-tile arguments");
+            }
+        if (cudaMemcpy(b->d_wargs, wh.data(), wh.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bfail(b, FDLBM_ECUDA, "batch: argument upload failed");
+    }
     b->tab.args[0] = b->d_args;
     b->tab.args[1] = static_cast<char *>(b->d_args) + n * as;
     b->tab.blk_start = b->d_ints;
@@ -154,6 +219,7 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
     b->tab.total_wall = total_wall;
     b->tab.any_scheme2 = any2;
     b->tab.blocks_s1 = blocks_s1;
+    b->walls_off = walls_off >= 0 ? std::min(walls_off, blocks_s1) : blocks_s1;
     b->blk = blk;
     b->fused_rows = fused_rows;
     return FDLBM_OK;
@@ -182,22 +248,29 @@ bool uses_fused_sweep(const fdlbm_batch_ctx *b)
 }
 
 // Tile height of the fused batch: minimise (waves) x (rows + 8) over the tiles
-// of all cases, as for a single grid.
+// of all cases, as for a single grid, with the waves of the warp-tile launches
+// and of the walls sweep counted separately (they run one after the other).
 int fused_rows_model(const fdlbm_batch_ctx *b)
 {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = std::max(1, fused_walls_blocks_per_sm<float>());
-    const long long slots = (long long)per_sm * sms;
-    const int W = fused_tile_width_walls();
+    const long long slots = (long long)std::max(1, fused_walls_blocks_per_sm<float>()) * sms;
+    const long long wslots = (long long)std::max(1, fused_warp_blocks_per_sm()) * sms;
+    const int W = fused_tile_width_walls(), WW = fused_warp_tile_width();
+    const bool warp = b->mode == FDLBM_BATCH_FUSED;
     int best = 64;
     double best_cost = 1e300;
     for (int rows = 1; rows <= 512; ++rows) {
-        long long ctas = 0;
-        for (const fdlbm_ctx *h : b->cases)
-            ctas += (long long)((h->nx + W - 1) / W) * ((h->ny + std::min(rows, h->ny) - 1) / std::min(rows, h->ny));
-        const double cost = (double)((ctas + slots - 1) / slots) * (rows + 8);
+        long long ctas = 0, wtiles = 0;
+        for (const fdlbm_ctx *h : b->cases) {
+            const int r = std::min(rows, h->ny), ty = (h->ny + r - 1) / r;
+            if (warp && h->scheme == FDLBM_SCHEME_T2S2_1 && h->variant == FDLBM_VARIANT_WARP)
+                wtiles += (long long)((h->nx + WW - 1) / WW) * ty;
+            else
+                ctas += (long long)((h->nx + W - 1) / W) * ty;
+        }
+        const double cost = (double)((ctas + slots - 1) / slots + (wtiles + wslots - 1) / wslots) * (rows + 8);
         if (cost < best_cost - 1e-9) {
             best_cost = cost;
             best = rows;
@@ -213,12 +286,20 @@ cudaError_t launch_steps(fdlbm_batch_ctx *b, int parity, int n)
     const bool f32 = b->precision == FDLBM_FP32_DEV;
     if (b->mode == FDLBM_BATCH_FUSED) {
         const int n1 = b->tab.blocks_s1, n2 = b->tab.total_blocks - n1;
+        const int nw = n1 - b->walls_off;
+        const size_t wsz = fused_warp_args_bytes() * b->cases.size();
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < n && e == cudaSuccess; ++k) {
             const int p = (parity + k) & 1;
-            if (n1 > 0)
-                e = f32 ? launch_batched_fused<float>(b->tab, p, n1, b->stream)
-                        : launch_batched_fused<double>(b->tab, p, n1, b->stream);
+            for (const auto &g : b->wgroups) {
+                if (e != cudaSuccess) break;
+                e = launch_batched_warp(static_cast<const char *>(b->d_wargs) + p * wsz, b->tab.blk_case,
+                                        b->tab.blk_start, b->tab.tiles_x, g.off, g.count, g.kind,
+                                        b->stream);
+            }
+            if (e == cudaSuccess && nw > 0)
+                e = f32 ? launch_batched_fused<float>(b->tab, p, b->walls_off, nw, b->stream)
+                        : launch_batched_fused<double>(b->tab, p, b->walls_off, nw, b->stream);
             if (e == cudaSuccess && n2 > 0)
                 e = f32 ? launch_batched_fused_s2<float>(b->tab, p, n1, n2, b->stream)
                         : launch_batched_fused_s2<double>(b->tab, p, n1, n2, b->stream);
@@ -390,6 +471,7 @@ void release(fdlbm_batch_ctx *b)
     drop_graph(b);
     for (fdlbm_ctx *h : b->cases) delete h;
     if (b->d_args) cudaFree(b->d_args);
+    if (b->d_wargs) cudaFree(b->d_wargs);
     if (b->d_ints) cudaFree(b->d_ints);
     if (b->owns_ws && b->ws) cudaFree(b->ws);
     if (b->owns_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -490,6 +572,25 @@ fdlbm_status fdlbm_batch_create(int ncases, const fdlbm_grid *grids, const fdlbm
     if (cudaMalloc(&b->d_args, 2 * ncases * args_size(b->precision)) != cudaSuccess) {
         release(b);
         return FDLBM_ENOMEM;
+    }
+    // FP32 T2S2-FDLBM1 cases that the warp-tile kernel takes (FUSED mode): the
+    // tensor maps of their state buffers and force field
+    if (b->precision == FDLBM_FP32_DEV) {
+        for (fdlbm_ctx *h : b->cases) {
+            h->variant = FDLBM_VARIANT_SCALAR;
+            if (h->scheme != FDLBM_SCHEME_T2S2_1 || !fused_warp_ok(h->nx, h->ny, h->bc_x == FDLBM_WALL))
+                continue;
+            if (fused_warp_encode(&h->wmaps, reinterpret_cast<const float *>(h->ws + h->lay.state[0]),
+                                  reinterpret_cast<const float *>(h->ws + h->lay.state[1]),
+                                  h->has_force ? reinterpret_cast<const float *>(h->ws + h->lay.force)
+                                               : nullptr,
+                                  h->nx, h->ny, h->pitch, h->plane) == cudaSuccess)
+                h->variant = FDLBM_VARIANT_WARP;
+        }
+        if (cudaMalloc(&b->d_wargs, 2 * ncases * fused_warp_args_bytes()) != cudaSuccess) {
+            release(b);
+            return FDLBM_ENOMEM;
+        }
     }
     b->graph_steps = graph_steps + (graph_steps & 1);  // even: starts and ends on the same parity
     b->mode = fused_eligible(b) ? FDLBM_BATCH_FUSED : FDLBM_BATCH_STAGED;
@@ -605,9 +706,10 @@ const char *fdlbm_batch_describe(fdlbm_batch_t b)
     std::ostringstream os;
     const char *prec = b->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64";
     if (b->mode == FDLBM_BATCH_FUSED) {
-        const int n1 = b->tab.blocks_s1, n2 = b->tab.total_blocks - n1;
+        const int n1 = b->tab.blocks_s1, n2 = b->tab.total_blocks - n1, nw = n1 - b->walls_off;
         os << "batched-fused " << prec << " cases=" << b->cases.size() << " rows=" << b->fused_rows
-           << " graph_steps=" << b->graph_steps << " launches_per_step=" << (n1 > 0) + (n2 > 0);
+           << " graph_steps=" << b->graph_steps << " warp_tiles=" << b->walls_off
+           << " launches_per_step=" << (int)b->wgroups.size() + (nw > 0) + (n2 > 0);
     } else if (b->mode == FDLBM_BATCH_PERSISTENT && b->fused_rows > 0) {
         os << "batched-persistent-fused " << prec << " cases=" << b->cases.size()
            << " rows=" << b->fused_rows << " graph_steps=" << b->graph_steps

@@ -127,6 +127,22 @@ cudaError_t fused_warp_encode(WarpMaps *m, const float *state0, const float *sta
                               const float *force, int nx, int ny, int pitch, size_t plane);
 cudaError_t launch_fused_warp(const StepArgs<float> &a, const WarpMaps &maps, int cur,
                               cudaStream_t s);
+// The instance of the warp-tile kernel a grid needs.
+struct WarpKind {
+    bool inc = false, grid = false, force = false, walls = false;
+    bool operator==(const WarpKind &o) const
+    {
+        return inc == o.inc && grid == o.grid && force == o.force && walls == o.walls;
+    }
+};
+WarpKind warp_kind(const StepArgs<float> &s);
+// Batches: the per-case argument blocks (tensor maps and scalars) in a device
+// table, and one launch over tiles of cases of one kind.
+size_t fused_warp_args_bytes();
+cudaError_t fused_warp_args(void *dst, const StepArgs<float> &s, const WarpMaps &maps, int cur);
+cudaError_t launch_batched_warp(const void *args, const int *blk_case, const int *blk_start,
+                                const int *tiles_x, int blk_off, int nblocks, WarpKind k,
+                                cudaStream_t s);
 int fused_warp_tile_width();
 int fused_warp_blocks_per_sm();
 // step_fused_walls.cu (scalar sweep with walled axes and Eq. 3.10 inside)
@@ -135,7 +151,8 @@ cudaError_t launch_fused_walls(const StepArgs<R> &a, cudaStream_t s);
 template <class R>
 int fused_walls_blocks_per_sm();
 template <class R>
-cudaError_t launch_batched_fused(const BatchTables &t, int parity, int nblocks, cudaStream_t s);
+cudaError_t launch_batched_fused(const BatchTables &t, int parity, int blk_off, int nblocks,
+                                 cudaStream_t s);
 int fused_tile_width_walls();
 // step_staged.cu
 template <class R>

@@ -257,9 +257,14 @@ __device__ __forceinline__ void force_add1(const f2 geq[9], f2 rf, f2 Fx, f2 Fy,
 // equilibria share rho_j, so their difference is formed directly (momentum
 // form, j_w = rho_j u_w, or rho0 u_w under the incompressible equilibrium):
 //   w_i [3 (e_w - e_j) + (4.5 (e_w^2 - e_j^2) - 1.5 (j_w.j_w - j_j.j_j)) / rho].
+#ifdef FDLBM_NEE_NOINLINE
+#define FDLBM_NEE_INLINE __noinline__
+#else
+#define FDLBM_NEE_INLINE __forceinline__
+#endif
 template <bool INC, bool FORCE>
-__device__ __forceinline__ void nee2(f2 g[9], f2 rho0, f2 inv_rho0, f2 shift, f2 Fx, f2 Fy,
-                                     f2 uwx, f2 uwy)
+__device__ FDLBM_NEE_INLINE void nee2(f2 g[9], f2 rho0, f2 inv_rho0, f2 shift, f2 Fx, f2 Fy,
+                                      f2 uwx, f2 uwy)
 {
     MacroJ m = INC ? moments2_j_incomp(g, inv_rho0) : moments2_j(g, rho0);
     const f2 rm = INC ? rho0 : add2(rho0, m.drho);

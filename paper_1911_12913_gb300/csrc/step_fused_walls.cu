@@ -334,13 +334,14 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2) k_step_fused_walls
 template <class R>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2)
     kb_step_fused_walls(const StepArgs<R> *cases, const int *blk_case, const int *blk_start,
-                        const int *strips)
+                        const int *strips, int blk_off)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<R> &sm = *reinterpret_cast<Smem<R> *>(smem_raw);
     __shared__ __align__(16) unsigned char abuf[sizeof(StepArgs<R>)];
     static_assert(sizeof(StepArgs<R>) % 4 == 0, "argument block is copied as 32-bit words");
-    const int c = blk_case[blockIdx.x];
+    const int bid = blk_off + blockIdx.x;
+    const int c = blk_case[bid];
     {
         const int *src = reinterpret_cast<const int *>(cases + c);
         int *dst = reinterpret_cast<int *>(abuf);
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2)
     }
     __syncthreads();
     const StepArgs<R> &a = *reinterpret_cast<const StepArgs<R> *>(abuf);
-    const int lb = blockIdx.x - blk_start[c], ns = strips[c];
+    const int lb = bid - blk_start[c], ns = strips[c];
     const int y0 = (lb / ns) * a.rows;
     if (y0 >= a.ny) return;  // uniform over the block
     sweep_tile<R, true>(a, sm, (lb % ns) * (NT - 2 * kHalo), y0);
@@ -486,10 +487,11 @@ int fused_walls_blocks_per_sm()
     return n;
 }
 
-// One step of the T2S2-FDLBM1 cases of a batch (the first nblocks tiles of
-// its tables): one launch.
+// One step of T2S2-FDLBM1 cases of a batch on the walls sweep (tiles
+// [blk_off, blk_off + nblocks) of its tables): one launch.
 template <class R>
-cudaError_t launch_batched_fused(const BatchTables &t, int parity, int nblocks, cudaStream_t s)
+cudaError_t launch_batched_fused(const BatchTables &t, int parity, int blk_off, int nblocks,
+                                 cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     constexpr size_t smem = sizeof(Smem<R>);
@@ -497,7 +499,7 @@ cudaError_t launch_batched_fused(const BatchTables &t, int parity, int nblocks, 
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kb_step_fused_walls<R><<<nblocks, NT, smem, s>>>(
-        static_cast<const StepArgs<R> *>(t.args[parity]), t.blk_case, t.blk_start, t.tiles_x);
+        static_cast<const StepArgs<R> *>(t.args[parity]), t.blk_case, t.blk_start, t.tiles_x, blk_off);
     return cudaGetLastError();
 }
 
@@ -550,8 +552,8 @@ template cudaError_t launch_persistent_fused<float>(const BatchTables &, void *,
 template cudaError_t launch_persistent_fused<double>(const BatchTables &, void *, int, int,
                                                      cudaStream_t, unsigned);
 
-template cudaError_t launch_batched_fused<float>(const BatchTables &, int, int, cudaStream_t);
-template cudaError_t launch_batched_fused<double>(const BatchTables &, int, int, cudaStream_t);
+template cudaError_t launch_batched_fused<float>(const BatchTables &, int, int, int, cudaStream_t);
+template cudaError_t launch_batched_fused<double>(const BatchTables &, int, int, int, cudaStream_t);
 template cudaError_t launch_fused_walls<float>(const StepArgs<float> &, cudaStream_t);
 template cudaError_t launch_fused_walls<double>(const StepArgs<double> &, cudaStream_t);
 template int fused_walls_blocks_per_sm<float>();

@@ -99,11 +99,8 @@ static_assert(offsetof(WarpSmem<true>, wrap) % 128 == 0, "tensor-copy destinatio
 static_assert(offsetof(WarpSmem<true>, fring) % 128 == 0, "tensor-copy destinations are 128-B aligned");
 static_assert(offsetof(WarpSmem<true>, fwrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
 
-struct ArgsW {
-    CUtensorMap tin;    // the input state: dims (nx, ny, 9), box (64, 1, 9)
-    CUtensorMap tside;  // the same with box (4, 1, 9) (force field only)
-    CUtensorMap tf;     // the force field: dims (nx, ny, 2), box (64, 1, 2)
-    CUtensorMap tfside; // the same with box (4, 1, 2)
+// Scalars and pointers of one step of one grid.
+struct ArgsS {
     float *gout;
     const float *mx, *my;
     const float *force;  // [2][ny][pitch] (walled grids read it directly at Eq. 3.10)
@@ -125,6 +122,16 @@ struct ArgsW {
     // walled axes (WALLS instances): the velocities of the W, E, S, N walls (Eq. 3.10)
     int wx, wy;
     float uw[4][2];
+};
+
+// The arguments of one grid: its tensor maps (kernel parameters, or entries
+// of a table in global memory for a batch) and the scalars.
+struct ArgsW {
+    CUtensorMap tin;    // the input state: dims (nx, ny, 9), box (64, 1, 9)
+    CUtensorMap tside;  // the same with box (4, 1, 9) (force field only)
+    CUtensorMap tf;     // the force field: dims (nx, ny, 2), box (64, 1, 2)
+    CUtensorMap tfside; // the same with box (4, 1, 2)
+    ArgsS s;
 };
 
 // The weights of the update's differences (stage C) for a scale s = -dt m:
@@ -180,34 +187,27 @@ __device__ __forceinline__ f2 xtaps(const f2 c[3], int sgn, f2 v0, f2 acc)
     return fma2(c[2], make_float2(Rlo, Rhi), acc);
 }
 
-// xtaps next to a wall of x (Eq. 3.10 grids): an interior node whose upwind
-// tap would reach past the wall takes the central difference alone.  With the
-// value past the wall replaced by the quadratic extrapolation 3 f(0) - 3 f(1) +
-// f(2) of the three nearest values, the mixed weights of Eq. 2.36 give exactly
-// the central difference (the upwind part is exact on quadratics), so the
-// weights stay those of every other node.  west: the lane holds columns 0 (the
-// wall) and 1; east: columns nx-2 and nx-1 (the wall; nx even); eastg:
-// columns nx-3 and nx-2 (nx odd, the wall is the next lane's first column).
-__device__ __forceinline__ f2 xtaps_w(const f2 c[3], int sgn, f2 v0, f2 acc, bool west, bool east,
-                                      bool eastg)
+// Next to a wall (Eq. 3.10 grids) an interior node whose upwind tap would
+// reach past the wall takes the central difference alone.  With the value
+// past the wall replaced by the quadratic extrapolation 3 f(0) - 3 f(1) + f(2)
+// of the three nearest values, the mixed weights of Eq. 2.36 give exactly the
+// central difference (the upwind part is exact on quadratics), so every node
+// keeps the same weights and the stencil loops the same code.  ghost_x puts
+// that value into the column past a wall of x, held by a lane outside the
+// grid (or, for an odd width, the padding column of the lane at the east
+// wall); all lanes take part in the shuffles.  gw: the lane holds columns -2
+// and -1; ge: nx and nx+1 (nx even); go: nx-1 and nx (nx odd).
+__device__ __forceinline__ void ghost_x(f2 &v, bool gw, bool ge, bool go)
 {
-    if (sgn > 0) {
-        const float Llo = __shfl_up_sync(kFull, v0.x, 1);
-        float Lhi = __shfl_up_sync(kFull, v0.y, 1);
-        const float Rlo = __shfl_down_sync(kFull, v0.x, 1);
-        if (west) Lhi = fmaf(3.f, v0.x - v0.y, Rlo);   // column -1
-        acc = fma2(c[0], make_float2(v0.y, Rlo), acc);
-        acc = fma2(c[1], make_float2(Lhi, v0.x), acc);
-        return fma2(c[2], make_float2(Llo, Lhi), acc);
-    }
-    const float Lhi = __shfl_up_sync(kFull, v0.y, 1);
-    float Rlo = __shfl_down_sync(kFull, v0.x, 1);
-    float Rhi = __shfl_down_sync(kFull, v0.y, 1);
-    if (east) Rlo = fmaf(3.f, v0.y - v0.x, Lhi);       // column nx
-    if (eastg) Rhi = fmaf(3.f, Rlo - v0.y, v0.x);      // column nx
-    acc = fma2(c[0], make_float2(Lhi, v0.x), acc);
-    acc = fma2(c[1], make_float2(v0.y, Rlo), acc);
-    return fma2(c[2], make_float2(Rlo, Rhi), acc);
+    const float d0 = __shfl_down_sync(kFull, v.x, 1);   // columns xc+2, xc+3, xc+4
+    const float d1 = __shfl_down_sync(kFull, v.y, 1);
+    const float d2 = __shfl_down_sync(kFull, v.x, 2);
+    const float u0 = __shfl_up_sync(kFull, v.x, 1);     // columns xc-2, xc-1, xc-3
+    const float u1 = __shfl_up_sync(kFull, v.y, 1);
+    const float u2 = __shfl_up_sync(kFull, v.y, 2);
+    if (gw) v.y = fmaf(3.f, d0 - d1, d2);   // column -1 from columns 0, 1, 2
+    if (ge) v.x = fmaf(3.f, u1 - u0, u2);   // column nx from columns nx-1, nx-2, nx-3
+    if (go) v.y = fmaf(3.f, v.x - u1, u0);  // column nx from columns nx-1, nx-2, nx-3
 }
 
 // The same in y from the lane's own window (rows k-2 .. k+2 as vm2 .. vp2).
@@ -226,18 +226,19 @@ __device__ __forceinline__ f2 ytaps(const f2 c[3], int sgn, f2 vm2, f2 vm1, f2 v
 // come from Eq. 3.10 at the nearest interior node (the diagonal one at
 // corners, with the W/E wall velocity), and interior nodes whose upwind tap
 // would reach past a wall take the central difference alone (here through a
-// quadratic ghost value, xtaps_w).  Rows and columns past a wall arrive as
+// quadratic ghost value, ghost_x).  Rows and columns past a wall arrive as
 // the tensor copy's zero fill and feed no stored value.
 template <bool INC, bool GRID, bool FORCE, bool WALLS>
-__global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
-    k_step_fused_warp(const __grid_constant__ ArgsW a)
+__device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin,
+                                          const CUtensorMap *tside, const CUtensorMap *tf,
+                                          const CUtensorMap *tfside, int bx, int by,
+                                          unsigned char *smem_raw)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
     WarpSmem<FORCE> &sm = *reinterpret_cast<WarpSmem<FORCE> *>(smem_raw);
 
     const int l = threadIdx.x;
-    const int x0 = a.xoff + blockIdx.x * kW;  // first output column
-    const int y0 = a.yoff + blockIdx.y * a.rows;
+    const int x0 = a.xoff + bx * kW;  // first output column
+    const int y0 = a.yoff + by * a.rows;
     if (y0 >= a.yend) return;              // uniform over the warp
     const int y1 = min(y0 + a.rows, a.yend);
     const int iters = (y1 - y0) + 2 * kHalo;
@@ -247,13 +248,18 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     const int gx = wrap_index(xc, a.nx);   // even, and gx + 1 < nx
     const bool store = (l >= 2) && (l < kLanes - 2) && (xc < a.xend);
     // lanes at a wall of x: west holds columns (0, 1); with nx even east holds
-    // (nx-2, nx-1); with nx odd eastg holds (nx-3, nx-2) and easto (nx-1, nx),
+    // (nx-2, nx-1); with nx odd easto holds (nx-1, nx),
     // whose interior neighbour x_j = nx-2 sits in the previous lane (the window
     // that holds column nx-1 shuffles it over: hase)
     const bool odd = (a.nx & 1) != 0;
     const bool west = wxl && xc == 0, east = wxl && !odd && xc == a.nx - 2;
-    const bool eastg = wxl && odd && xc == a.nx - 3, easto = wxl && odd && xc == a.nx - 1;
+    const bool easto = wxl && odd && xc == a.nx - 1;
     const bool hase = wxl && odd && xs <= a.nx - 1 && a.nx - 1 < xs + kCols;
+    // the window holds a wall column (warp-uniform: the wall code that needs
+    // every lane, shuffles and warp barriers, runs under these)
+    const bool winx = wxl && ((xs <= 0 && 0 < xs + kCols) || (xs <= a.nx - 1 && a.nx - 1 < xs + kCols));
+    // lanes that hold the ghost column past a wall of x (ghost_x)
+    const bool gw = wxl && xc == -2, ge = wxl && !odd && xc == a.nx, go = easto;
 
     // ---- where the lane's pair lands: the main ring, or the side ring filled
     // from x = nx - 4 (first window) or x = 0 (last window); a walled x axis
@@ -318,15 +324,15 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
             const uint32_t bar = bar0 + 8u * (uint32_t)slot;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx)
                          : "memory");
-            tensor_copy_3d(ring0 + (uint32_t)slot * kRowBytes, &a.tin, xs, ld_row, 0, bar);
+            tensor_copy_3d(ring0 + (uint32_t)slot * kRowBytes, tin, xs, ld_row, 0, bar);
             if (!FORCE) {
                 if (seam)
-                    tensor_copy_3d(wrap0 + (uint32_t)slot * kRowBytes, &a.tin, wrap_x, ld_row, 0, bar);
+                    tensor_copy_3d(wrap0 + (uint32_t)slot * kRowBytes, tin, wrap_x, ld_row, 0, bar);
             } else {
-                tensor_copy_3d(fring0 + (uint32_t)fslot * kFRowBytes, &a.tf, xs, ld_row, 0, bar);
+                tensor_copy_3d(fring0 + (uint32_t)fslot * kFRowBytes, tf, xs, ld_row, 0, bar);
                 if (seam) {
-                    tensor_copy_3d(wrap0 + (uint32_t)slot * kSideSlot, &a.tside, wrap_x, ld_row, 0, bar);
-                    tensor_copy_3d(fwrap0 + (uint32_t)fslot * kFSideSlot, &a.tfside, wrap_x, ld_row, 0,
+                    tensor_copy_3d(wrap0 + (uint32_t)slot * kSideSlot, tside, wrap_x, ld_row, 0, bar);
+                    tensor_copy_3d(fwrap0 + (uint32_t)fslot * kFSideSlot, tfside, wrap_x, ld_row, 0,
                                    bar);
                 }
             }
@@ -370,22 +376,6 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
         constexpr int PH = decltype(PHc)::value;
         constexpr int p0 = PH, p1 = (PH + 4) % 5, p2 = (PH + 3) % 5, p3 = (PH + 2) % 5,
                       p4 = (PH + 1) % 5;
-        // Eq. 3.10 on the new f~ needs the force at the stage-C row (row r-4,
-        // no longer in the ring): fetched now for the lanes and rows that use it
-        const bool neeC = (wxl && (west || east || easto)) || (wyl && (rcL == 1 || rcL == a.ny - 2));
-        f2 FCx = bc(0.f), FCy = bc(0.f);
-        // (in-domain lanes only: xc even and xc + 1 < nx keep the pair loads
-        // aligned and in bounds)
-        if (WALLS && FORCE && neeC && rcL >= 0 && rcL < a.ny && xc >= 0 && xc < a.nx) {
-            const size_t fo = (size_t)rcL * a.pitch + xc;
-            if (easto) {  // the force of x_j = nx-2 (the lane's second column is padding)
-                FCx = bc(__ldg(a.force + fo - 1));
-                FCy = bc(__ldg(a.force + a.plane + fo - 1));
-            } else {
-                FCx = __ldg(reinterpret_cast<const float2 *>(a.force + fo));
-                FCy = __ldg(reinterpret_cast<const float2 *>(a.force + a.plane + fo));
-            }
-        }
         // ------------------------------------------------------------ A (row r)
         if (!mbar_wait_bounded(&sm.bar[slot], parity)) timed_out = true;
         {
@@ -441,8 +431,24 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
             // centre coefficients: 1 + the centre weights of the differences taken
             const f2 c_y = bc(1.f + nhy * a.w[1]);
             const f2 c_d = add2(c_y, cxB);
-            // rows next to a wall of y: the quadratic ghost row past it (xtaps_w)
-            const bool gS = wyl && rbL == 1, gN = wyl && rbL == a.ny - 2;
+            // next to a wall: the quadratic ghost values past it (ghost_x); the
+            // slots they overwrite (rows -1 and ny, columns past the walls) feed
+            // no stored value otherwise
+            if (WALLS && wyl && rbL == 1) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (cy(i) > 0) Pw[i][p4] = fma2(bc(3.f), sub2(Pw[i][p3], Pw[i][p2]), Pw[i][p1]);
+            }
+            if (WALLS && wyl && rbL == a.ny - 2) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (cy(i) < 0) Pw[i][p0] = fma2(bc(3.f), sub2(Pw[i][p1], Pw[i][p2]), Pw[i][p3]);
+            }
+            if (WALLS && winx) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (cx(i) != 0) ghost_x(Pw[i][p2], gw, ge, go);
+            }
             f2 gs[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -452,13 +458,8 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 else if (cx(i) != 0) acc = mul2(c_xB, v0);
                 else if (cy(i) != 0) acc = mul2(c_y, v0);
                 else acc = v0;
-                if (cx(i) != 0) acc = WALLS ? xtaps_w(axB, cx(i), v0, acc, west, east, eastg) : xtaps(axB, cx(i), v0, acc);
-                if (cy(i) != 0) {
-                    f2 vm2 = Pw[i][p4], vp2 = Pw[i][p0];
-                    if (WALLS && cy(i) > 0 && gS) vm2 = fma2(bc(3.f), sub2(Pw[i][p3], v0), Pw[i][p1]);
-                    if (WALLS && cy(i) < 0 && gN) vp2 = fma2(bc(3.f), sub2(Pw[i][p1], v0), Pw[i][p3]);
-                    acc = ytaps(ay, cy(i), vm2, Pw[i][p3], Pw[i][p1], vp2, acc);
-                }
+                if (cx(i) != 0) acc = xtaps(axB, cx(i), v0, acc);
+                if (cy(i) != 0) acc = ytaps(ay, cy(i), Pw[i][p4], Pw[i][p3], Pw[i][p1], Pw[i][p0], acc);
                 gs[i] = acc;
             }
             f2 fs[9];
@@ -481,47 +482,48 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 for (int i = 0; i < 9; ++i) fs[i] = fma2(bst, sub2(ge[i], gs[i]), gs[i]);
                 force_add1(ge, INC ? sub2(rho0, m.drho) : rho0, Fx, Fy, uF, bc(a.k_star), fs);
             }
-            if (WALLS) {
-                // Eq. 3.10 for f* (physical distribution: no force shift)
-                const f2 z = bc(0.f), ir0 = bc(a.inv_rho0);
-                if (wyl && rbL == a.ny - 1) {
-                    // the N wall row, from the window row ny-2
+            if (WALLS && wyl && rbL == a.ny - 1) {
+                // the N wall row's f*, from the window row ny-2 (Eq. 3.10 on the
+                // physical distribution: no force shift)
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) fs[i] = Sw[i][p1];
-                    nee2<INC, false>(fs, rho0, ir0, z, z, z, uwp(FDLBM_WALL_N, 0), uwp(FDLBM_WALL_N, 1));
+                for (int i = 0; i < 9; ++i) fs[i] = Sw[i][p1];
+                const f2 z = bc(0.f);
+                nee2<INC, false>(fs, rho0, bc(a.inv_rho0), z, z, z, uwp(FDLBM_WALL_N, 0),
+                                 uwp(FDLBM_WALL_N, 1));
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) Sw[i][p0] = fs[i];
+            if (WALLS && winx) {
+                // the W (E) wall column's f* from column 1 (nx-2): the same lane,
+                // or for nx odd the previous one (a shuffle over the whole warp:
+                // winx is uniform)
+                f2 t[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const float nb = __shfl_up_sync(kFull, Sw[i][p0].y, 1);
+                    t[i] = west ? bc(Sw[i][p0].y) : (east ? bc(Sw[i][p0].x) : bc(nb));
                 }
-                if (west || east || hase) {
-                    // the W (E) wall column from column 1 (nx-2): the same lane,
-                    // or for nx odd the previous one
-                    f2 t[9];
+                if (west || east || easto) {
+                    const f2 z = bc(0.f);
+                    const int sd = west ? FDLBM_WALL_W : FDLBM_WALL_E;
+                    nee2<INC, false>(t, rho0, bc(a.inv_rho0), z, z, z, uwp(sd, 0), uwp(sd, 1));
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        const float nb = hase ? __shfl_up_sync(kFull, fs[i].y, 1) : 0.f;
-                        t[i] = west ? bc(fs[i].y) : (east ? bc(fs[i].x) : bc(nb));
-                    }
-                    if (west || east || easto) {
-                        const int sd = west ? FDLBM_WALL_W : FDLBM_WALL_E;
-                        nee2<INC, false>(t, rho0, ir0, z, z, z, uwp(sd, 0), uwp(sd, 1));
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) {
-                            if (east) fs[i].y = t[i].y;
-                            else fs[i].x = t[i].x;
-                        }
+                        if (east) Sw[i][p0].y = t[i].y;
+                        else Sw[i][p0].x = t[i].x;
                     }
                 }
+            }
+            if (WALLS && wyl && rbL == 1) {
+                // the S wall row's f* into the window slot of row 0
+                f2 t[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) Sw[i][p0] = fs[i];
-                if (wyl && rbL == 1) {
-                    // the S wall row into the window slot of row 0
+                for (int i = 0; i < 9; ++i) t[i] = Sw[i][p0];
+                const f2 z = bc(0.f);
+                nee2<INC, false>(t, rho0, bc(a.inv_rho0), z, z, z, uwp(FDLBM_WALL_S, 0),
+                                 uwp(FDLBM_WALL_S, 1));
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) fs[i] = Sw[i][p0];
-                    nee2<INC, false>(fs, rho0, ir0, z, z, z, uwp(FDLBM_WALL_S, 0), uwp(FDLBM_WALL_S, 1));
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) Sw[i][p1] = fs[i];
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) Sw[i][p0] = fs[i];
+                for (int i = 0; i < 9; ++i) Sw[i][p1] = t[i];
             }
             ++rbL;
         }
@@ -545,7 +547,26 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
             const bool rowin = !wyl || (rcL >= 1 && rcL <= a.ny - 2);
             const bool st = store && k >= 8 && rowin;
             const bool gS = wyl && rcL == 1, gN = wyl && rcL == a.ny - 2;
-            f2 out[WALLS ? 9 : 1];
+            // (the lane at the east wall of an odd grid stores its second value
+            // into the padding column nx, which nothing reads)
+            auto put = [&](unsigned off, int i, f2 v) {
+                *reinterpret_cast<f2 *>(a.gout + (off + (unsigned)i * plane32)) = v;
+            };
+            if (WALLS && gS) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (cy(i) > 0) Sw[i][p4] = fma2(bc(3.f), sub2(Sw[i][p3], Sw[i][p2]), Sw[i][p1]);
+            }
+            if (WALLS && gN) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (cy(i) < 0) Sw[i][p0] = fma2(bc(3.f), sub2(Sw[i][p1], Sw[i][p2]), Sw[i][p3]);
+            }
+            if (WALLS && winx) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    if (cx(i) != 0) ghost_x(Sw[i][p2], gw, ge, go);
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const f2 v0 = Sw[i][p2];
@@ -553,61 +574,57 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
                 if (cx(i) != 0 && cy(i) != 0) acc = fma2(c_d, v0, acc);
                 else if (cx(i) != 0) acc = fma2(cxC, v0, acc);
                 else if (cy(i) != 0) acc = fma2(c_y, v0, acc);
-                if (cx(i) != 0) acc = WALLS ? xtaps_w(axC, cx(i), v0, acc, west, east, eastg) : xtaps(axC, cx(i), v0, acc);
-                if (cy(i) != 0) {
-                    f2 vm2 = Sw[i][p4], vp2 = Sw[i][p0];
-                    if (WALLS && cy(i) > 0 && gS) vm2 = fma2(bc(3.f), sub2(Sw[i][p3], v0), Sw[i][p1]);
-                    if (WALLS && cy(i) < 0 && gN) vp2 = fma2(bc(3.f), sub2(Sw[i][p1], v0), Sw[i][p3]);
-                    acc = ytaps(by, cy(i), vm2, Sw[i][p3], Sw[i][p1], vp2, acc);
-                }
-                if (WALLS) out[i] = acc;
-                else if (st) *reinterpret_cast<f2 *>(a.gout + (roff + (unsigned)i * plane32)) = acc;
+                if (cx(i) != 0) acc = xtaps(axC, cx(i), v0, acc);
+                if (cy(i) != 0) acc = ytaps(by, cy(i), Sw[i][p4], Sw[i][p3], Sw[i][p1], Sw[i][p0], acc);
+                if (st) put(roff, i, acc);
             }
-            if (WALLS) {
-                // Eq. 3.10 on the new f~ (force shift dt/2, the force of x_j) of
-                // the wall nodes whose x_j is this node: the W (E) column from
-                // column 1 (nx-2) of the same lane, then the S (N) row from
-                // row 1 (ny-2); corners take the W/E value of their diagonal
-                // node, which is the value just put into the wall column
+            if (WALLS && (winx || gS || gN) && k >= 8) {
+                // Eq. 3.10 on the new f~ (force shift dt/2, the force of x_j),
+                // from the values just stored: first the W (E) column from
+                // column 1 (nx-2), then the S (N) row from row 1 (ny-2); the
+                // corners take the value of the wall column at that row (its
+                // diagonal x_j with the W/E velocity).  The condition is uniform
+                // over the warp, so every lane reaches the warp barriers.
+                __syncwarp();
                 const f2 ir0 = bc(a.inv_rho0), hd = bc(a.hdt);
-                if (west || east || hase) {
+                if (st && (west || east || easto)) {
+                    const int jx = west ? 1 : a.nx - 2, bx = west ? 0 : a.nx - 1;
+                    const unsigned oj = (unsigned)qg * (unsigned)a.pitch + (unsigned)jx;
                     f2 t[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        const float nb = hase ? __shfl_up_sync(kFull, out[i].y, 1) : 0.f;
-                        t[i] = west ? bc(out[i].y) : (east ? bc(out[i].x) : bc(nb));
+                    for (int i = 0; i < 9; ++i) t[i] = bc(a.gout[oj + (unsigned)i * plane32]);
+                    f2 Fx = bc(0.f), Fy = bc(0.f);
+                    if (FORCE) {
+                        Fx = bc(__ldg(a.force + oj));
+                        Fy = bc(__ldg(a.force + a.plane + oj));
                     }
-                    if (west || east || easto) {
-                        const f2 Fx = west ? bc(FCx.y) : bc(FCx.x), Fy = west ? bc(FCy.y) : bc(FCy.x);
-                        const int sd = west ? FDLBM_WALL_W : FDLBM_WALL_E;
-                        nee2<INC, FORCE>(t, rho0, ir0, hd, Fx, Fy, uwp(sd, 0), uwp(sd, 1));
+                    const int sd = west ? FDLBM_WALL_W : FDLBM_WALL_E;
+                    nee2<INC, FORCE>(t, rho0, ir0, hd, Fx, Fy, uwp(sd, 0), uwp(sd, 1));
+                    const unsigned ob = (unsigned)qg * (unsigned)a.pitch + (unsigned)bx;
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) {
-                            if (east) out[i].y = t[i].y;
-                            else out[i].x = t[i].x;
-                        }
+                    for (int i = 0; i < 9; ++i) a.gout[ob + (unsigned)i * plane32] = t[i].x;
+                }
+                if (gS || gN) __syncwarp();
+                if ((gS || gN) && store) {
+                    f2 t[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        t[i] = *reinterpret_cast<const f2 *>(a.gout + (roff + (unsigned)i * plane32));
+                    f2 Fx = bc(0.f), Fy = bc(0.f);
+                    if (FORCE) {  // (the force field's padding column reads as any finite value)
+                        Fx = __ldg(reinterpret_cast<const float2 *>(a.force + roff));
+                        Fy = __ldg(reinterpret_cast<const float2 *>(a.force + a.plane + roff));
                     }
-                }
-                // the lane past the last column of an odd grid stores one value
-                auto put = [&](unsigned off, int i, f2 v) {
-                    if (easto) a.gout[off + (unsigned)i * plane32] = v.x;
-                    else *reinterpret_cast<f2 *>(a.gout + (off + (unsigned)i * plane32)) = v;
-                };
-                if (st) {
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) put(roff, i, out[i]);
-                }
-                if ((gS || gN) && store && k >= 8) {
                     float corner[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) corner[i] = east ? out[i].y : out[i].x;
+                    for (int i = 0; i < 9; ++i) corner[i] = east ? t[i].y : t[i].x;
                     const int sd = gS ? FDLBM_WALL_S : FDLBM_WALL_N;
-                    nee2<INC, FORCE>(out, rho0, ir0, hd, FCx, FCy, uwp(sd, 0), uwp(sd, 1));
+                    nee2<INC, FORCE>(t, rho0, ir0, hd, Fx, Fy, uwp(sd, 0), uwp(sd, 1));
                     const unsigned wrow = gS ? 0u : (unsigned)(a.ny - 1);
                     const unsigned woff = wrow * (unsigned)a.pitch + (unsigned)xc;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        f2 v = out[i];
+                        f2 v = t[i];
                         if (west || easto) v.x = corner[i];
                         if (east) v.y = corner[i];
                         put(woff, i, v);
@@ -644,6 +661,44 @@ __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
         }
         if (l == 0) atomicOr(a.err, 1);
     }
+}
+
+template <bool INC, bool GRID, bool FORCE, bool WALLS>
+__global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
+    k_step_fused_warp(const __grid_constant__ ArgsW w)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    warp_tile<INC, GRID, FORCE, WALLS>(w.s, &w.tin, &w.tside, &w.tf, &w.tfside, blockIdx.x,
+                                       blockIdx.y, smem_raw);
+}
+
+// Shared-memory offset of a batch case's scalars, after the rings.
+template <bool FORCE>
+constexpr size_t kArgsOff = (sizeof(WarpSmem<FORCE>) + 15) / 16 * 16;
+
+// Batched: block blk_off + b is tile (b' - blk_start[c]) of case c = blk_case[b']
+// (tiles_x[c] windows per row of tiles); the case's tensor maps are read from
+// the table in global memory, its scalars from a copy in shared memory.
+template <bool INC, bool GRID, bool FORCE, bool WALLS>
+__global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
+    kb_step_fused_warp(const ArgsW *args, const int *blk_case, const int *blk_start,
+                       const int *tiles_x, int blk_off)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int b = blk_off + blockIdx.x;
+    const int c = blk_case[b];
+    const ArgsW &w = args[c];
+    ArgsS *sa = reinterpret_cast<ArgsS *>(smem_raw + kArgsOff<FORCE>);
+    static_assert(sizeof(ArgsS) % 4 == 0, "scalars are copied as 32-bit words");
+    {
+        const int *src = reinterpret_cast<const int *>(&w.s);
+        int *dst = reinterpret_cast<int *>(sa);
+        for (int k = threadIdx.x; k < (int)(sizeof(ArgsS) / 4); k += kLanes) dst[k] = src[k];
+    }
+    __syncwarp();
+    const int lb = b - blk_start[c], ns = tiles_x[c];
+    warp_tile<INC, GRID, FORCE, WALLS>(*sa, &w.tin, &w.tside, &w.tf, &w.tfside, lb % ns, lb / ns,
+                                       smem_raw);
 }
 
 // cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link).
@@ -735,29 +790,33 @@ cudaError_t launch_t(const ArgsW &a, dim3 grid, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-template <bool INC, bool GRID>
-cudaError_t launch_fw(const ArgsW &a, bool force, bool walls, dim3 grid, cudaStream_t stream)
+// Call f with the four instance flags of k as compile-time constants.
+template <class F>
+cudaError_t dispatch(const WarpKind &k, F &&f)
 {
-    if (force)
-        return walls ? launch_t<INC, GRID, true, true>(a, grid, stream)
-                     : launch_t<INC, GRID, true, false>(a, grid, stream);
-    return walls ? launch_t<INC, GRID, false, true>(a, grid, stream)
-                 : launch_t<INC, GRID, false, false>(a, grid, stream);
+    using T = std::true_type;
+    using N = std::false_type;
+    auto w = [&](auto inc, auto gr, auto fo) {
+        return k.walls ? f(inc, gr, fo, T{}) : f(inc, gr, fo, N{});
+    };
+    auto fo = [&](auto inc, auto gr) { return k.force ? w(inc, gr, T{}) : w(inc, gr, N{}); };
+    auto gr = [&](auto inc) { return k.grid ? fo(inc, T{}) : fo(inc, N{}); };
+    return k.inc ? gr(T{}) : gr(N{});
 }
 
-cudaError_t launch_fused_warp(const StepArgs<float> &s, const WarpMaps &maps, int cur,
-                              cudaStream_t stream)
+// The argument block of one grid at ping-pong parity `cur`.
+ArgsW make_args(const StepArgs<float> &s, const WarpMaps &maps, int cur)
 {
-    ArgsW a;
-    std::memset(&a, 0, sizeof a);
+    ArgsW w;
+    std::memset(&w, 0, sizeof w);
     const bool force = s.force != nullptr;
-    if (force && !maps.has_force) return cudaErrorInvalidValue;
-    std::memcpy(&a.tin, maps.state[cur], sizeof(CUtensorMap));
+    std::memcpy(&w.tin, maps.state[cur], sizeof(CUtensorMap));
     if (force) {
-        std::memcpy(&a.tside, maps.side[cur], sizeof(CUtensorMap));
-        std::memcpy(&a.tf, maps.force, sizeof(CUtensorMap));
-        std::memcpy(&a.tfside, maps.force_side, sizeof(CUtensorMap));
+        std::memcpy(&w.tside, maps.side[cur], sizeof(CUtensorMap));
+        std::memcpy(&w.tf, maps.force, sizeof(CUtensorMap));
+        std::memcpy(&w.tfside, maps.force_side, sizeof(CUtensorMap));
     }
+    ArgsS &a = w.s;
     a.gout = s.gout;
     a.mx = s.mx;
     a.my = s.my;
@@ -795,15 +854,61 @@ cudaError_t launch_fused_warp(const StepArgs<float> &s, const WarpMaps &maps, in
         a.uw[k][0] = s.wall_u[k][0];
         a.uw[k][1] = s.wall_u[k][1];
     }
-    const bool walls = a.wx || a.wy;
-    // the Sterbenz-ordered update weights need wm1 >= 0.55 |w1| (beta <= 0.16)
-    const bool on_grid = !(s.st.wm1 >= 0.55f * std::fabs(s.st.w1));
+    return w;
+}
+
+// Which instance a grid needs: the Sterbenz-ordered update weights need
+// wm1 >= 0.55 |w1| (beta <= 0.16), else the weights go on their grid.
+WarpKind warp_kind(const StepArgs<float> &s)
+{
+    WarpKind k;
+    k.inc = s.c.incomp != 0;
+    k.grid = !(s.st.wm1 >= 0.55f * std::fabs(s.st.w1));
+    k.force = s.force != nullptr;
+    k.walls = s.bc_x == FDLBM_WALL || s.bc_y == FDLBM_WALL;
+    return k;
+}
+
+cudaError_t launch_fused_warp(const StepArgs<float> &s, const WarpMaps &maps, int cur,
+                              cudaStream_t stream)
+{
+    if (s.force && !maps.has_force) return cudaErrorInvalidValue;
+    const ArgsW a = make_args(s, maps, cur);
+    const WarpKind k = warp_kind(s);
     const dim3 grid((s.nx + kW - 1) / kW, (s.ny + s.rows - 1) / s.rows);
-    if (s.c.incomp)
-        return on_grid ? launch_fw<true, true>(a, force, walls, grid, stream)
-                       : launch_fw<true, false>(a, force, walls, grid, stream);
-    return on_grid ? launch_fw<false, true>(a, force, walls, grid, stream)
-                   : launch_fw<false, false>(a, force, walls, grid, stream);
+    return dispatch(k, [&](auto inc, auto gr, auto fo, auto wa) {
+        return launch_t<decltype(inc)::value, decltype(gr)::value, decltype(fo)::value,
+                        decltype(wa)::value>(a, grid, stream);
+    });
+}
+
+size_t fused_warp_args_bytes() { return sizeof(ArgsW); }
+
+cudaError_t fused_warp_args(void *dst, const StepArgs<float> &s, const WarpMaps &maps, int cur)
+{
+    if (s.force && !maps.has_force) return cudaErrorInvalidValue;
+    const ArgsW a = make_args(s, maps, cur);
+    std::memcpy(dst, &a, sizeof a);
+    return cudaSuccess;
+}
+
+// A batch's tiles [blk_off, blk_off + nblocks) of the table, all of kind k.
+cudaError_t launch_batched_warp(const void *args, const int *blk_case, const int *blk_start,
+                                const int *tiles_x, int blk_off, int nblocks, WarpKind k,
+                                cudaStream_t stream)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    return dispatch(k, [&](auto inc, auto gr, auto fo, auto wa) {
+        constexpr bool I = decltype(inc)::value, G = decltype(gr)::value, F = decltype(fo)::value,
+                       W = decltype(wa)::value;
+        constexpr size_t smem = kArgsOff<F> + sizeof(ArgsS);
+        auto kern = kb_step_fused_warp<I, G, F, W>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<nblocks, kLanes, smem, stream>>>(static_cast<const ArgsW *>(args), blk_case, blk_start,
+                                                tiles_x, blk_off);
+        return cudaGetLastError();
+    });
 }
 
 int fused_warp_tile_width() { return kW; }

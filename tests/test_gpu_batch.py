@@ -58,6 +58,19 @@ def _mixed_cases():
              blend=0.1, wall_u=lid, init="rest"),
         dict(xa=I.periodic_axis(24, 0.0, 1.0), ya=I.periodic_axis(20, 0.0, 1.0), nu=0.02,
              cfl=0.3, blend=0.2, scheme=2, init="random"),
+        # cases the warp-tile kernel takes in FUSED mode (64 columns and more),
+        # of several kernel instances: walls with and without a force field,
+        # periodic with and without one, update weights of either construction
+        dict(xa=I.tanh_axis(68, 1.5), ya=I.tanh_axis(40, 1.5), nu=0.1 / 100, cfl=0.5, blend=0.1,
+             wall_u=lid, init="random"),
+        dict(xa=I.periodic_axis(64, 0.0, 1.0), ya=I.tanh_axis(30, 1.5), nu=math.sqrt(F / 80), cfl=0.5,
+             blend=0.1, has_force=True, force="channel", init="rest"),
+        dict(xa=I.periodic_axis(68, 0.0, 1.0), ya=I.periodic_axis(30, 0.0, 0.5), nu=0.02, cfl=0.4,
+             blend=0.2, has_force=True, force="random", init="random"),
+        dict(xa=I.periodic_axis(128, 0.0, 2 * math.pi), ya=I.periodic_axis(45, 0.0, 2 * math.pi),
+             nu=0.01, cfl=0.5, blend=0.1, init="random"),
+        dict(xa=I.wall_axis(70, 0.0, 1.0), ya=I.wall_axis(26, 0.0, 1.0), nu=0.001, cfl=0.5,
+             blend=0.1, wall_u=[(0, 0.02), (0, -0.01), (0.03, 0), (0.1, 0.0)], init="random"),
     ]
     return cases
 
@@ -136,8 +149,13 @@ def test_batch_fused_mode_needs_fp32():
         FDLBMBatch(cases, precision="fp64", graph_steps=0, autotune=False, mode="fused")
     b = FDLBMBatch(cases[:5], precision="fp32", graph_steps=0, autotune=False)
     assert b.describe.startswith("batched-fused") and "launches_per_step=1" in b.describe, b.describe
-    b = FDLBMBatch(cases, precision="fp32", graph_steps=0, autotune=False)
+    assert "warp_tiles=0" in b.describe, b.describe
+    b = FDLBMBatch(cases[:6], precision="fp32", graph_steps=0, autotune=False)
     assert b.describe.startswith("batched-fused") and "launches_per_step=2" in b.describe, b.describe
+    # the cases of 64 columns and more go to the warp-tile kernel, one launch
+    # per kernel instance (walls / force / weight construction)
+    b = FDLBMBatch(cases, precision="fp32", graph_steps=0, autotune=False)
+    assert "warp_tiles=0" not in b.describe and "launches_per_step=6" in b.describe, b.describe
 
 
 def test_batch_case_restrictions():
