@@ -34,7 +34,7 @@ struct fdlbm_batch_ctx {
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
     void *d_args = nullptr;    // 2 x ncases argument blocks
-    int *d_ints = nullptr;     // blk_start | tiles_x | wall_start | grid barrier | blk_case
+    int *d_ints = nullptr;     // blk_start | tiles_x | wall_start | frame_start | grid barrier | blk_case
     size_t d_ints_cap = 0;
     BatchTables tab{};
     void *bar = nullptr;       // grid barrier of the persistent kernel (in d_ints)
@@ -48,16 +48,24 @@ struct fdlbm_batch_ctx {
     long long steps = 0;
     bool tuned = false;
     double tuned_ms = -1.0;
-    // FUSED mode: cases of T2S2-FDLBM1 on the warp-tile kernel, in groups of
-    // one kernel instance each (tiles [off, off + count) of the tables), then
-    // the walls sweep for the other T2S2-FDLBM1 cases (tiles [walls_off,
-    // blocks_s1)), then the T2S2-FDLBM2 cases
+    // FUSED mode: the interiors of T2S2-FDLBM1 cases on the warp-tile kernel,
+    // in groups of one kernel instance each (tiles [off, off + count) of the
+    // tables), the frames of the walled ones (walls sweep in blocks of one
+    // warp, a group without and one with a force field), then the walls sweep
+    // for the other T2S2-FDLBM1 cases (tiles [walls_off, blocks_s1)), then the
+    // T2S2-FDLBM2 cases
     void *d_wargs = nullptr;  // 2 x ncases warp-tile argument blocks (tensor maps, scalars)
     struct WGroup {
         WarpKind kind;
         int off, count;
     };
     std::vector<WGroup> wgroups;
+    struct FGroup {
+        bool force;
+        int off, count;
+    };
+    std::vector<FGroup> fgroups;
+    const int *frame_start = nullptr;  // [ncases] first frame tile of each case (in d_ints)
     int walls_off = 0;
     std::string err, desc;
 };
@@ -85,7 +93,7 @@ fdlbm_status bfail(fdlbm_batch_ctx *b, fdlbm_status s, const std::string &what)
 fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
 {
     const int n = (int)b->cases.size();
-    std::vector<int> blk_start(n), tiles_x(n), wall_start(n), blk_case;
+    std::vector<int> blk_start(n), tiles_x(n), wall_start(n), frame_start(n, 0), frame_tiles(n, 0), blk_case;
     int total_wall = 0, total_blocks = 0, blocks_s1 = 0;
     bool any2 = false;
     // the tiles of T2S2-FDLBM1 cases first (in FUSED mode those on the
@@ -105,6 +113,7 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
         }
     std::vector<int> order;
     b->wgroups.clear();
+    b->fgroups.clear();
     for (int c = 0; c < n; ++c) {
         if (!on_warp(b->cases[c])) continue;
         if (std::find(order.begin(), order.end(), c) != order.end()) continue;
@@ -117,14 +126,30 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
             if (!on_warp(b->cases[c]) && (b->cases[c]->scheme == FDLBM_SCHEME_T2S2_2) == (pass == 1))
                 order.push_back(c);
     int walls_off = -1;
+    // after the warp-tile interiors: the frames of the walled ones
+    auto emit_frames = [&]() {
+        for (int force = 0; force < 2; ++force)
+            for (int k = 0; k < nwarp_cases; ++k) {
+                const int c = order[k];
+                if (frame_tiles[c] == 0 || b->cases[c]->has_force != (force == 1)) continue;
+                if (b->fgroups.empty() || b->fgroups.back().force != (force == 1))
+                    b->fgroups.push_back({force == 1, total_blocks, 0});
+                frame_start[c] = total_blocks;
+                b->fgroups.back().count += frame_tiles[c];
+                total_blocks += frame_tiles[c];
+                blk_case.insert(blk_case.end(), (size_t)frame_tiles[c], c);
+            }
+        blocks_s1 = total_blocks;
+        walls_off = total_blocks;
+    };
     for (int k = 0; k < (int)order.size(); ++k) {
         const int c = order[k];
         fdlbm_ctx *h = b->cases[c];
-        if (k == nwarp_cases) walls_off = total_blocks;
+        if (k == nwarp_cases) emit_frames();
         int tx, ty;
         if (k < nwarp_cases) {
-            tx = (h->nx + fused_warp_tile_width() - 1) / fused_warp_tile_width();
-            ty = (h->ny + h->rows - 1) / h->rows;
+            tx = 1;
+            fused_warp_tiles(handle_step_args<float>(h), &ty, &frame_tiles[c]);
             if (b->wgroups.empty() || !(b->wgroups.back().kind == kinds[c]))
                 b->wgroups.push_back({kinds[c], total_blocks, 0});
             b->wgroups.back().count += tx * ty;
@@ -144,6 +169,7 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
         blk_case.insert(blk_case.end(), (size_t)tx * ty, c);
         any2 = any2 || h->scheme == FDLBM_SCHEME_T2S2_2;
     }
+    if (nwarp_cases > 0 && nwarp_cases == (int)order.size()) emit_frames();
     // wall nodes in case order (the wall kernels find a node's case by a binary
     // search over these prefix sums, whatever the order of the tiles)
     for (int c = 0; c < n; ++c) {
@@ -153,7 +179,7 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
         total_wall += (wy ? 2 * h->nx : 0) + (wx ? 2 * (wy ? h->ny - 2 : h->ny) : 0);
     }
     const size_t nbar = (persistent_barrier_bytes() + sizeof(int) - 1) / sizeof(int);
-    const size_t nints = 3 * (size_t)n + nbar + blk_case.size();
+    const size_t nints = 4 * (size_t)n + nbar + blk_case.size();
     if (nints > b->d_ints_cap) {
         if (b->d_ints) cudaFree(b->d_ints);
         b->d_ints = nullptr;
@@ -166,7 +192,8 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
     all.insert(all.end(), blk_start.begin(), blk_start.end());
     all.insert(all.end(), tiles_x.begin(), tiles_x.end());
     all.insert(all.end(), wall_start.begin(), wall_start.end());
-    all.resize(3 * (size_t)n + nbar, 0);
+    all.insert(all.end(), frame_start.begin(), frame_start.end());
+    all.resize(4 * (size_t)n + nbar, 0);
     all.insert(all.end(), blk_case.begin(), blk_case.end());
     if (cudaMemcpy(b->d_ints, all.data(), nints * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
         return bfail(b, FDLBM_ECUDA, "batch: table upload failed");
@@ -212,8 +239,9 @@ fdlbm_status build_tables(fdlbm_batch_ctx *b, dim3 blk, int fused_rows = 0)
     b->tab.blk_start = b->d_ints;
     b->tab.tiles_x = b->d_ints + n;
     b->tab.wall_start = b->d_ints + 2 * n;
-    b->bar = b->d_ints + 3 * n;
-    b->tab.blk_case = b->d_ints + 3 * n + nbar;
+    b->frame_start = b->d_ints + 3 * n;
+    b->bar = b->d_ints + 4 * n;
+    b->tab.blk_case = b->d_ints + 4 * n + nbar;
     b->tab.ncases = n;
     b->tab.total_blocks = total_blocks;
     b->tab.total_wall = total_wall;
@@ -291,11 +319,16 @@ cudaError_t launch_steps(fdlbm_batch_ctx *b, int parity, int n)
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < n && e == cudaSuccess; ++k) {
             const int p = (parity + k) & 1;
+            for (const auto &g : b->fgroups) {
+                if (e != cudaSuccess) break;
+                e = launch_batched_frame(static_cast<const char *>(b->d_wargs) + p * wsz, b->tab.args[p],
+                                         b->tab.blk_case, b->frame_start, g.off, g.count, g.force,
+                                         b->stream);
+            }
             for (const auto &g : b->wgroups) {
                 if (e != cudaSuccess) break;
                 e = launch_batched_warp(static_cast<const char *>(b->d_wargs) + p * wsz, b->tab.blk_case,
-                                        b->tab.blk_start, b->tab.tiles_x, g.off, g.count, g.kind,
-                                        b->stream);
+                                        b->tab.blk_start, g.off, g.count, g.kind, b->stream);
             }
             if (e == cudaSuccess && nw > 0)
                 e = f32 ? launch_batched_fused<float>(b->tab, p, b->walls_off, nw, b->stream)
@@ -577,8 +610,12 @@ fdlbm_status fdlbm_batch_create(int ncases, const fdlbm_grid *grids, const fdlbm
     // tensor maps of their state buffers and force field
     if (b->precision == FDLBM_FP32_DEV) {
         for (fdlbm_ctx *h : b->cases) {
+            // the case's own choice (its options, or the automatic one of a
+            // single grid, which leaves small walled grids to the walls sweep)
+            const bool want = h->variant == FDLBM_VARIANT_WARP;
             h->variant = FDLBM_VARIANT_SCALAR;
-            if (h->scheme != FDLBM_SCHEME_T2S2_1 || !fused_warp_ok(h->nx, h->ny, h->bc_x == FDLBM_WALL))
+            if (!want || h->scheme != FDLBM_SCHEME_T2S2_1 ||
+                !fused_warp_ok(h->nx, h->ny, h->bc_x == FDLBM_WALL))
                 continue;
             if (fused_warp_encode(&h->wmaps, reinterpret_cast<const float *>(h->ws + h->lay.state[0]),
                                   reinterpret_cast<const float *>(h->ws + h->lay.state[1]),
@@ -709,7 +746,7 @@ const char *fdlbm_batch_describe(fdlbm_batch_t b)
         const int n1 = b->tab.blocks_s1, n2 = b->tab.total_blocks - n1, nw = n1 - b->walls_off;
         os << "batched-fused " << prec << " cases=" << b->cases.size() << " rows=" << b->fused_rows
            << " graph_steps=" << b->graph_steps << " warp_tiles=" << b->walls_off
-           << " launches_per_step=" << (int)b->wgroups.size() + (nw > 0) + (n2 > 0);
+           << " launches_per_step=" << (int)(b->wgroups.size() + b->fgroups.size()) + (nw > 0) + (n2 > 0);
     } else if (b->mode == FDLBM_BATCH_PERSISTENT && b->fused_rows > 0) {
         os << "batched-persistent-fused " << prec << " cases=" << b->cases.size()
            << " rows=" << b->fused_rows << " graph_steps=" << b->graph_steps

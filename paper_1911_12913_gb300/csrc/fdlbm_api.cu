@@ -446,7 +446,13 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     const bool warp_ok = s1 && fused && f32 && fused_warp_ok(g->nx, g->ny, g->bc_x == FDLBM_WALL);
     if (o.variant == FDLBM_VARIANT_WARP && !warp_ok) return FDLBM_EUNSUPPORTED;
     int variant = o.variant;
-    if (variant == FDLBM_VARIANT_AUTO) variant = warp_ok ? FDLBM_VARIANT_WARP : FDLBM_VARIANT_SCALAR;
+    // a walled grid on the warp-tile kernel pays a fixed 25-35 us for its frame
+    // launch (rows of the walls sweep are a chain of dependent work): below
+    // about 1.5 M nodes the walls sweep alone is faster (measured on GB300:
+    // 1025^2 channel 40 us against 43, 2049^2 cavity 164 us against 107)
+    const bool small_walled = walled(g) && (long long)g->nx * g->ny < (3ll << 19);
+    if (variant == FDLBM_VARIANT_AUTO)
+        variant = warp_ok && !small_walled ? FDLBM_VARIANT_WARP : FDLBM_VARIANT_SCALAR;
     mx.assign(g->nx, 0.0);
     my.assign(g->ny, 0.0);
     for (int i = 0; i < g->nx; ++i)

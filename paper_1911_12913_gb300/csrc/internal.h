@@ -129,11 +129,8 @@ cudaError_t launch_fused_warp(const StepArgs<float> &a, const WarpMaps &maps, in
                               cudaStream_t s);
 // The instance of the warp-tile kernel a grid needs.
 struct WarpKind {
-    bool inc = false, grid = false, force = false, walls = false;
-    bool operator==(const WarpKind &o) const
-    {
-        return inc == o.inc && grid == o.grid && force == o.force && walls == o.walls;
-    }
+    bool inc = false, grid = false, force = false;
+    bool operator==(const WarpKind &o) const { return inc == o.inc && grid == o.grid && force == o.force; }
 };
 WarpKind warp_kind(const StepArgs<float> &s);
 // Batches: the per-case argument blocks (tensor maps and scalars) in a device
@@ -141,8 +138,15 @@ WarpKind warp_kind(const StepArgs<float> &s);
 size_t fused_warp_args_bytes();
 cudaError_t fused_warp_args(void *dst, const StepArgs<float> &s, const WarpMaps &maps, int cur);
 cudaError_t launch_batched_warp(const void *args, const int *blk_case, const int *blk_start,
-                                const int *tiles_x, int blk_off, int nblocks, WarpKind k,
-                                cudaStream_t s);
+                                int blk_off, int nblocks, WarpKind k, cudaStream_t s);
+// The frames of walled cases (the walls sweep in blocks of one warp): frame
+// tile b - frame_start[c] of case c = blk_case[b].
+cudaError_t launch_batched_frame(const void *args, const void *sargs, const int *blk_case,
+                                 const int *frame_start, int blk_off, int nblocks, bool force,
+                                 cudaStream_t s);
+// Interior tiles (warp-tile launch) and frame tiles (walls-sweep launch, 0 on
+// a periodic grid) of one grid at its tile height.
+void fused_warp_tiles(const StepArgs<float> &s, int *interior, int *frame);
 int fused_warp_tile_width();
 int fused_warp_blocks_per_sm();
 // step_fused_walls.cu (scalar sweep with walled axes and Eq. 3.10 inside)

@@ -249,49 +249,6 @@ __device__ __forceinline__ void force_add1(const f2 geq[9], f2 rf, f2 Fx, f2 Fy,
     one(8, sub2(nuF, d), 2);
 }
 
-// Eq. 3.10 on a pair of wall nodes, in place: g holds f at the interior nodes
-// x_j on entry and the wall values on return,
-//   f_b = f^eq(rho_j, u_w) + f_j - f^eq(rho_j, u_j),
-// with rho_j, u_j the moments of f_j (first moment shifted by shift rho F for
-// a variable whose moment lacks it, Eq. 3.3) and u_w the wall velocity.  Both
-// equilibria share rho_j, so their difference is formed directly (momentum
-// form, j_w = rho_j u_w, or rho0 u_w under the incompressible equilibrium):
-//   w_i [3 (e_w - e_j) + (4.5 (e_w^2 - e_j^2) - 1.5 (j_w.j_w - j_j.j_j)) / rho].
-#ifdef FDLBM_NEE_NOINLINE
-#define FDLBM_NEE_INLINE __noinline__
-#else
-#define FDLBM_NEE_INLINE __forceinline__
-#endif
-template <bool INC, bool FORCE>
-__device__ FDLBM_NEE_INLINE void nee2(f2 g[9], f2 rho0, f2 inv_rho0, f2 shift, f2 Fx, f2 Fy,
-                                      f2 uwx, f2 uwy)
-{
-    MacroJ m = INC ? moments2_j_incomp(g, inv_rho0) : moments2_j(g, rho0);
-    const f2 rm = INC ? rho0 : add2(rho0, m.drho);
-    if (FORCE) {
-        const f2 sr = mul2(shift, rm);
-        m.jx = fma2(sr, Fx, m.jx);
-        m.jy = fma2(sr, Fy, m.jy);
-    }
-    const f2 wx = mul2(rm, uwx), wy = mul2(rm, uwy);
-    // -1.5 (j_w.j_w - j_j.j_j) / rho
-    const f2 dq = mul2(mul2(sub2(fma2(wx, wx, mul2(wy, wy)), fma2(m.jx, m.jx, mul2(m.jy, m.jy))),
-                            bc(-1.5f)), m.inv);
-    g[0] = fma2(bc(4.f / 9.f), dq, g[0]);
-    auto pair = [&](f2 ew, f2 ej, float w, float c, int ip, int im) {
-        // w (4.5 (ew^2 - ej^2) / rho + dq) and the linear term c (ew - ej)
-        const f2 sq = fma2(mul2(mul2(add2(ew, ej), sub2(ew, ej)), bc(4.5f)), m.inv, dq);
-        const f2 ws = mul2(bc(w), sq);
-        const f2 lin = mul2(bc(c), sub2(ew, ej));
-        g[ip] = add2(g[ip], add2(ws, lin));
-        g[im] = add2(g[im], sub2(ws, lin));
-    };
-    pair(wx, m.jx, 1.f / 9.f, kLin1, 1, 3);
-    pair(wy, m.jy, 1.f / 9.f, kLin1, 2, 4);
-    pair(add2(wx, wy), add2(m.jx, m.jy), 1.f / 36.f, kLin2, 5, 7);
-    pair(sub2(wy, wx), sub2(m.jy, m.jx), 1.f / 36.f, kLin2, 6, 8);
-}
-
 // sign(c) * D_m f at the centre from f(k-2..k+2); w = {wm1, w0, w1, w2} of
 // make_stencil (lattice.cuh).
 __device__ __forceinline__ f2 stencil2(const float w[4], int sgn, f2 vm2, f2 vm1, f2 v0, f2 vp1,

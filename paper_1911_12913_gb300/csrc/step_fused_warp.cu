@@ -1,6 +1,12 @@
-// Fused FP32-deviation T2S2-FDLBM step for periodic grids: one warp per tile,
-// two adjacent columns per lane in packed FP32x2 arithmetic, no block-level
-// barrier anywhere.
+// Fused FP32-deviation T2S2-FDLBM step: one warp per tile, two adjacent
+// columns per lane in packed FP32x2 arithmetic, no block-level barrier
+// anywhere.  On a walled grid (Eq. 3.10) the same launch splits the nodes: the
+// interior rectangle, at least 4 nodes from every wall, whose tiles load
+// nothing from outside the grid, where the walled scheme and the periodic one
+// compute the same values (the central differences next to a wall and the
+// wall nodes' Eq. 3.10 reach 4 nodes in at most), runs the warp tile below;
+// the frame around it runs the walls sweep (walls_sweep.cuh) in blocks of one
+// warp.
 //
 // The scheme is the one of step_fused.cu (stages A, B, C of Sec. 2D per row of
 // a bottom-to-top sweep, lags of 2 + 2 rows), laid out so that a warp needs
@@ -38,10 +44,12 @@
 // flag, keeps its control flow, waits (bounded) for its copies in flight
 // before it exits, and the host reports the flag.
 //
-// Requirements (checked by the host): nx % 4 == 0 and nx >= 64, so that every
-// copy starts on a 16-byte boundary, a window crosses the seam at most once,
-// and the two columns of a lane never straddle it; the state holds fewer than
-// 2^32 values, so that element offsets fit 32 bits.
+// Requirements (checked by the host): nx >= 64 and, on a periodic x axis,
+// nx % 4 == 0, so that every copy starts on a 16-byte boundary, a window
+// crosses the seam at most once, and the two columns of a lane never straddle
+// it (on a walled x axis the interior windows start at column 4 and end before
+// nx); the state holds fewer than 2^32 values, so that element offsets fit 32
+// bits.
 #include <cstddef>
 #include <cstdint>
 #include <cmath>
@@ -53,6 +61,7 @@
 #include "internal.h"
 #include "packed.cuh"
 #include "tma.cuh"
+#include "walls_sweep.cuh"
 
 namespace fdlbm {
 namespace {
@@ -103,13 +112,18 @@ static_assert(offsetof(WarpSmem<true>, fwrap) % 128 == 0, "tensor-copy destinati
 struct ArgsS {
     float *gout;
     const float *mx, *my;
-    const float *force;  // [2][ny][pitch] (walled grids read it directly at Eq. 3.10)
+    const float *force;  // [2][ny][pitch]
     int nx, ny, pitch;
     size_t plane;
     int rows;
-    // output rectangle: columns [xoff + 56 bx, ...) below xend, rows [yoff + rows by,
-    // ...) below yend (the whole grid on a periodic one)
-    int xoff, xend, yoff, yend;
+    // the interior rectangle, columns [xoff + 56 bx, ...) below xend and rows
+    // [yoff + rows by, ...) below yend: the whole grid on a periodic one; on a
+    // walled axis the nodes at least 4 from the walls whose windows (row
+    // tiles) load no column (row) outside the grid, where the walled and the
+    // periodic sweep compute the same values.  The frame around it (walled
+    // axes) runs the walls sweep in tiles of kFrameW columns and erows rows.
+    int xoff, xend, yoff, yend, erows;
+    int nix, nframe;  // interior windows per row of tiles; frame tiles (0 on a periodic grid)
     float rho0, h, dt, b_bar, b_til, b_star;
     float w[4];  // wm1, w0, w1, w2
     int *err;
@@ -119,9 +133,7 @@ struct ArgsS {
     // analogue for fbar), and 3 x the weights of the forcing term in fbar^{+,h}
     // (Eq. 2.34 after Eq. 2.19), f~+ (Eq. 2.20) and f* (Eq. 2.32)
     float hdt, hh, k_bar, k_til, k_star;
-    // walled axes (WALLS instances): the velocities of the W, E, S, N walls (Eq. 3.10)
-    int wx, wy;
-    float uw[4][2];
+    int wx, wy;  // walled axes
 };
 
 // The arguments of one grid: its tensor maps (kernel parameters, or entries
@@ -187,29 +199,6 @@ __device__ __forceinline__ f2 xtaps(const f2 c[3], int sgn, f2 v0, f2 acc)
     return fma2(c[2], make_float2(Rlo, Rhi), acc);
 }
 
-// Next to a wall (Eq. 3.10 grids) an interior node whose upwind tap would
-// reach past the wall takes the central difference alone.  With the value
-// past the wall replaced by the quadratic extrapolation 3 f(0) - 3 f(1) + f(2)
-// of the three nearest values, the mixed weights of Eq. 2.36 give exactly the
-// central difference (the upwind part is exact on quadratics), so every node
-// keeps the same weights and the stencil loops the same code.  ghost_x puts
-// that value into the column past a wall of x, held by a lane outside the
-// grid (or, for an odd width, the padding column of the lane at the east
-// wall); all lanes take part in the shuffles.  gw: the lane holds columns -2
-// and -1; ge: nx and nx+1 (nx even); go: nx-1 and nx (nx odd).
-__device__ __forceinline__ void ghost_x(f2 &v, bool gw, bool ge, bool go)
-{
-    const float d0 = __shfl_down_sync(kFull, v.x, 1);   // columns xc+2, xc+3, xc+4
-    const float d1 = __shfl_down_sync(kFull, v.y, 1);
-    const float d2 = __shfl_down_sync(kFull, v.x, 2);
-    const float u0 = __shfl_up_sync(kFull, v.x, 1);     // columns xc-2, xc-1, xc-3
-    const float u1 = __shfl_up_sync(kFull, v.y, 1);
-    const float u2 = __shfl_up_sync(kFull, v.y, 2);
-    if (gw) v.y = fmaf(3.f, d0 - d1, d2);   // column -1 from columns 0, 1, 2
-    if (ge) v.x = fmaf(3.f, u1 - u0, u2);   // column nx from columns nx-1, nx-2, nx-3
-    if (go) v.y = fmaf(3.f, v.x - u1, u0);  // column nx from columns nx-1, nx-2, nx-3
-}
-
 // The same in y from the lane's own window (rows k-2 .. k+2 as vm2 .. vp2).
 __device__ __forceinline__ f2 ytaps(const f2 c[3], int sgn, f2 vm2, f2 vm1, f2 vp1, f2 vp2, f2 acc)
 {
@@ -217,66 +206,123 @@ __device__ __forceinline__ f2 ytaps(const f2 c[3], int sgn, f2 vm2, f2 vm1, f2 v
     return fma2(c[2], vp2, fma2(c[1], vp1, fma2(c[0], vm1, acc)));
 }
 
+// The frame of a walled grid runs the walls sweep (walls_sweep.cuh) in blocks
+// of one warp, one column per thread: kFrameW output columns per tile.
+constexpr int kFrameNT = kLanes;
+constexpr int kFrameW = kFrameNT - 2 * walls_sweep::kHalo;
+
+// One tile of a launch: its first output column x0, the end of the columns
+// it stores, and its rows [y0, y1).
+struct Tile {
+    int x0, xend, y0, y1;
+};
+
+// Segment s of an axis of a walled grid: 0 the low frame, 1 the interior
+// rectangle, 2 the high frame (on a periodic axis the interior is the whole
+// axis and the frames are empty).
+__host__ __device__ inline void x_segment(const ArgsS &a, int s, int &lo, int &hi)
+{
+    if (!a.wx) {
+        lo = 0;
+        hi = s == 1 ? a.nx : 0;
+        return;
+    }
+    lo = s == 0 ? 0 : (s == 1 ? a.xoff : a.xend);
+    hi = s == 0 ? min(a.xoff, a.xend) : (s == 1 ? a.xend : a.nx);
+}
+
+__host__ __device__ inline void y_segment(const ArgsS &a, int s, int &lo, int &hi)
+{
+    if (!a.wy) {
+        lo = 0;
+        hi = s == 1 ? a.ny : 0;
+        return;
+    }
+    lo = s == 0 ? 0 : (s == 1 ? a.yoff : a.yend);
+    hi = s == 0 ? a.yoff : (s == 1 ? a.yend : a.ny);
+}
+
+// Tile t of the frame (the segment pairs other than interior x interior, in
+// tiles of kFrameW columns and, beside the interior rows, erows rows; the
+// frame rows of a walled y axis are one tile of at most 4 rows).  Returns the
+// number of frame tiles when t is past the last one (then `out` is unset),
+// else -1.
+__host__ __device__ inline int frame_tile(const ArgsS &a, int t, Tile &out)
+{
+    int n = 0;
+    for (int sy = 0; sy < 3; ++sy) {
+        int ylo, yhi;
+        y_segment(a, sy, ylo, yhi);
+        if (yhi <= ylo) continue;
+        const int h = sy == 1 ? a.erows : yhi - ylo;
+        const int nt = (yhi - ylo + h - 1) / h;
+        for (int sx = 0; sx < 3; ++sx) {
+            if (sx == 1 && sy == 1) continue;
+            int xlo, xhi;
+            x_segment(a, sx, xlo, xhi);
+            if (xhi <= xlo) continue;
+            const int nw = (xhi - xlo + kFrameW - 1) / kFrameW;
+            if (t >= n && t < n + nw * nt) {
+                const int u = t - n;
+                out.x0 = xlo + (u % nw) * kFrameW;
+                out.xend = xhi;
+                out.y0 = ylo + (u / nw) * h;
+                out.y1 = min(out.y0 + h, yhi);
+                return -1;
+            }
+            n += nw * nt;
+        }
+    }
+    return n;
+}
+
+// Tile (bx, by) of the interior rectangle.
+__host__ __device__ inline Tile interior_tile(const ArgsS &a, int bx, int by)
+{
+    Tile t;
+    t.x0 = a.xoff + bx * kW;
+    t.xend = a.xend;
+    t.y0 = a.yoff + by * a.rows;
+    t.y1 = min(t.y0 + a.rows, a.yend);
+    return t;
+}
+
 // INC: the incompressible equilibrium of He and Luo (velocity from rho0 u).
 // GRID: how the update's weights are made to sum to zero (update_weights).
 // FORCE: a body-acceleration field (Eqs. 3.3 and 3.12), whose rows arrive by
 // tensor copy with the rows of f~ into a 5-row ring (stage B reads row r-2).
-// WALLS: walled axes (a.wx, a.wy) with Eq. 3.10, by the rules of the scalar
-// walls sweep: wall nodes take no part in stages B and C, their f* and new f~
-// come from Eq. 3.10 at the nearest interior node (the diagonal one at
-// corners, with the W/E wall velocity), and interior nodes whose upwind tap
-// would reach past a wall take the central difference alone (here through a
-// quadratic ghost value, ghost_x).  Rows and columns past a wall arrive as
-// the tensor copy's zero fill and feed no stored value.
-template <bool INC, bool GRID, bool FORCE, bool WALLS>
+template <bool INC, bool GRID, bool FORCE>
 __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin,
                                           const CUtensorMap *tside, const CUtensorMap *tf,
-                                          const CUtensorMap *tfside, int bx, int by,
+                                          const CUtensorMap *tfside, Tile tile,
                                           unsigned char *smem_raw)
 {
     WarpSmem<FORCE> &sm = *reinterpret_cast<WarpSmem<FORCE> *>(smem_raw);
 
     const int l = threadIdx.x;
-    const int x0 = a.xoff + bx * kW;  // first output column
-    const int y0 = a.yoff + by * a.rows;
-    if (y0 >= a.yend) return;              // uniform over the warp
-    const int y1 = min(y0 + a.rows, a.yend);
+    const int x0 = tile.x0;  // first output column
+    const int y0 = tile.y0, y1 = tile.y1;
     const int iters = (y1 - y0) + 2 * kHalo;
     const int xs = x0 - kHalo;             // window start before wrapping
     const int xc = xs + 2 * l;             // the lane's first column
-    const bool wxl = WALLS && a.wx, wyl = WALLS && a.wy;
     const int gx = wrap_index(xc, a.nx);   // even, and gx + 1 < nx
-    const bool store = (l >= 2) && (l < kLanes - 2) && (xc < a.xend);
-    // lanes at a wall of x: west holds columns (0, 1); with nx even east holds
-    // (nx-2, nx-1); with nx odd easto holds (nx-1, nx),
-    // whose interior neighbour x_j = nx-2 sits in the previous lane (the window
-    // that holds column nx-1 shuffles it over: hase)
-    const bool odd = (a.nx & 1) != 0;
-    const bool west = wxl && xc == 0, east = wxl && !odd && xc == a.nx - 2;
-    const bool easto = wxl && odd && xc == a.nx - 1;
-    const bool hase = wxl && odd && xs <= a.nx - 1 && a.nx - 1 < xs + kCols;
-    // the window holds a wall column (warp-uniform: the wall code that needs
-    // every lane, shuffles and warp barriers, runs under these)
-    const bool winx = wxl && ((xs <= 0 && 0 < xs + kCols) || (xs <= a.nx - 1 && a.nx - 1 < xs + kCols));
-    // lanes that hold the ghost column past a wall of x (ghost_x)
-    const bool gw = wxl && xc == -2, ge = wxl && !odd && xc == a.nx, go = easto;
+    const bool store = (l >= 2) && (l < kLanes - 2) && (xc < tile.xend);
 
     // ---- where the lane's pair lands: the main ring, or the side ring filled
-    // from x = nx - 4 (first window) or x = 0 (last window); a walled x axis
-    // has no seam
-    const bool wrap_lo = !wxl && xs < 0, wrap_hi = !wxl && xs + kCols > a.nx;
+    // from x = nx - 4 (first window) or x = 0 (last window)
+    const bool wrap_lo = xs < 0, wrap_hi = xs + kCols > a.nx;
     const int wrap_x = wrap_lo ? a.nx - kHalo : 0;
     uint32_t rd = (uint32_t)offsetof(WarpSmem<FORCE>, ring) + 8u * (uint32_t)l;
     uint32_t pstride = kCols * sizeof(float);  // bytes between populations
     uint32_t frd = (uint32_t)offsetof(WarpSmem<FORCE>, fring) + 8u * (uint32_t)l;
     uint32_t fstride = kCols * sizeof(float);  // bytes between force components
     if (!FORCE) {
-        if (!wxl && xc < 0) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc + kHalo);
-        if (!wxl && xc >= a.nx) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc - a.nx);
+        if (xc < 0) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc + kHalo);
+        if (xc >= a.nx) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc - a.nx);
     } else {
         // side rings of 4 columns; lanes further past the seam read the main
         // ring's zero fill (their values reach no output)
-        const int side = wxl ? -1 : (xc < 0 ? xc + kHalo : (xc >= a.nx && xc < a.nx + kSide ? xc - a.nx : -1));
+        const int side = xc < 0 ? xc + kHalo : (xc >= a.nx && xc < a.nx + kSide ? xc - a.nx : -1);
         if (side >= 0) {
             rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)side;
             pstride = kSide * sizeof(float);
@@ -314,9 +360,8 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
     const bool seam = wrap_lo || wrap_hi;
     const uint32_t tx = FORCE ? kRowBytes + kFRowBytes + (seam ? 9u * kSide * 4u + 2u * kSide * 4u : 0u)
                               : (seam ? 2u * kRowBytes : kRowBytes);
-    // next row to request (a walled y axis: the logical row, whose copies
-    // past the walls are zero-filled)
-    int ld_row = wyl ? y0 - kHalo : wrap_index(y0 - kHalo, a.ny);
+    // next row to request
+    int ld_row = wrap_index(y0 - kHalo, a.ny);
     // rows into f~ slot `slot` and (force field) force slot `fslot`
     auto issue = [&](int slot, int fslot) {
         if (l == 0) {
@@ -337,7 +382,7 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
                 }
             }
         }
-        ld_row = (!wyl && ld_row + 1 == a.ny) ? 0 : ld_row + 1;
+        ld_row = ld_row + 1 == a.ny ? 0 : ld_row + 1;
     };
 
     if (l == 0) {
@@ -353,17 +398,12 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
     for (int i = 0; i < 9; ++i)
 #pragma unroll
         for (int j = 0; j < 5; ++j) Pw[i][j] = Sw[i][j] = bc(0.f);
-    // rows of stage B (y0 - 6 + k) and C (y0 - 8 + k) at iteration k: wrapped
-    // (metric and store rows) and logical (walls)
+    // rows of stage B (y0 - 6 + k) and C (y0 - 8 + k) at iteration k
     int rs = wrap_index(y0 - 6, a.ny), rq = wrap_index(y0 - 8, a.ny);
-    int rbL = y0 - 6, rcL = y0 - 8;
     float myB = __ldg(a.my + rs), myC = __ldg(a.my + rq);
     int slot = 0;          // iteration mod 3
     uint32_t parity = 0;   // mbarrier phase parity of the current slot
     bool timed_out = false;
-    // wall velocities as pairs (both halves alike; corner halves get their own)
-    auto uwp = [&](int side, int k) { return bc(a.uw[side][k]); };
-
     // force of the lane's pair from force slot fs (components x, y)
     auto force_of = [&](int fs, f2 &Fx, f2 &Fy) {
         const unsigned char *src = frd_base + fs * kFRowBytes;
@@ -431,24 +471,6 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
             // centre coefficients: 1 + the centre weights of the differences taken
             const f2 c_y = bc(1.f + nhy * a.w[1]);
             const f2 c_d = add2(c_y, cxB);
-            // next to a wall: the quadratic ghost values past it (ghost_x); the
-            // slots they overwrite (rows -1 and ny, columns past the walls) feed
-            // no stored value otherwise
-            if (WALLS && wyl && rbL == 1) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (cy(i) > 0) Pw[i][p4] = fma2(bc(3.f), sub2(Pw[i][p3], Pw[i][p2]), Pw[i][p1]);
-            }
-            if (WALLS && wyl && rbL == a.ny - 2) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (cy(i) < 0) Pw[i][p0] = fma2(bc(3.f), sub2(Pw[i][p1], Pw[i][p2]), Pw[i][p3]);
-            }
-            if (WALLS && winx) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (cx(i) != 0) ghost_x(Pw[i][p2], gw, ge, go);
-            }
             f2 gs[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -482,50 +504,8 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
                 for (int i = 0; i < 9; ++i) fs[i] = fma2(bst, sub2(ge[i], gs[i]), gs[i]);
                 force_add1(ge, INC ? sub2(rho0, m.drho) : rho0, Fx, Fy, uF, bc(a.k_star), fs);
             }
-            if (WALLS && wyl && rbL == a.ny - 1) {
-                // the N wall row's f*, from the window row ny-2 (Eq. 3.10 on the
-                // physical distribution: no force shift)
-#pragma unroll
-                for (int i = 0; i < 9; ++i) fs[i] = Sw[i][p1];
-                const f2 z = bc(0.f);
-                nee2<INC, false>(fs, rho0, bc(a.inv_rho0), z, z, z, uwp(FDLBM_WALL_N, 0),
-                                 uwp(FDLBM_WALL_N, 1));
-            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) Sw[i][p0] = fs[i];
-            if (WALLS && winx) {
-                // the W (E) wall column's f* from column 1 (nx-2): the same lane,
-                // or for nx odd the previous one (a shuffle over the whole warp:
-                // winx is uniform)
-                f2 t[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const float nb = __shfl_up_sync(kFull, Sw[i][p0].y, 1);
-                    t[i] = west ? bc(Sw[i][p0].y) : (east ? bc(Sw[i][p0].x) : bc(nb));
-                }
-                if (west || east || easto) {
-                    const f2 z = bc(0.f);
-                    const int sd = west ? FDLBM_WALL_W : FDLBM_WALL_E;
-                    nee2<INC, false>(t, rho0, bc(a.inv_rho0), z, z, z, uwp(sd, 0), uwp(sd, 1));
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        if (east) Sw[i][p0].y = t[i].y;
-                        else Sw[i][p0].x = t[i].x;
-                    }
-                }
-            }
-            if (WALLS && wyl && rbL == 1) {
-                // the S wall row's f* into the window slot of row 0
-                f2 t[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) t[i] = Sw[i][p0];
-                const f2 z = bc(0.f);
-                nee2<INC, false>(t, rho0, bc(a.inv_rho0), z, z, z, uwp(FDLBM_WALL_S, 0),
-                                 uwp(FDLBM_WALL_S, 1));
-#pragma unroll
-                for (int i = 0; i < 9; ++i) Sw[i][p1] = t[i];
-            }
-            ++rbL;
         }
         // ------------------------------------------------------------ C (row r-4)
         // f* rows r-6 .. r-2 sit in slots p4, p3, p2, p1, p0 of Sw.
@@ -544,29 +524,10 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
             // the host): one wide multiply-add per store address
             const unsigned roff = (unsigned)qg * (unsigned)a.pitch + (unsigned)xc;
             const unsigned plane32 = (unsigned)a.plane;
-            const bool rowin = !wyl || (rcL >= 1 && rcL <= a.ny - 2);
-            const bool st = store && k >= 8 && rowin;
-            const bool gS = wyl && rcL == 1, gN = wyl && rcL == a.ny - 2;
-            // (the lane at the east wall of an odd grid stores its second value
-            // into the padding column nx, which nothing reads)
+            const bool st = store && k >= 8;
             auto put = [&](unsigned off, int i, f2 v) {
                 *reinterpret_cast<f2 *>(a.gout + (off + (unsigned)i * plane32)) = v;
             };
-            if (WALLS && gS) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (cy(i) > 0) Sw[i][p4] = fma2(bc(3.f), sub2(Sw[i][p3], Sw[i][p2]), Sw[i][p1]);
-            }
-            if (WALLS && gN) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (cy(i) < 0) Sw[i][p0] = fma2(bc(3.f), sub2(Sw[i][p1], Sw[i][p2]), Sw[i][p3]);
-            }
-            if (WALLS && winx) {
-#pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    if (cx(i) != 0) ghost_x(Sw[i][p2], gw, ge, go);
-            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const f2 v0 = Sw[i][p2];
@@ -578,60 +539,6 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
                 if (cy(i) != 0) acc = ytaps(by, cy(i), Sw[i][p4], Sw[i][p3], Sw[i][p1], Sw[i][p0], acc);
                 if (st) put(roff, i, acc);
             }
-            if (WALLS && (winx || gS || gN) && k >= 8) {
-                // Eq. 3.10 on the new f~ (force shift dt/2, the force of x_j),
-                // from the values just stored: first the W (E) column from
-                // column 1 (nx-2), then the S (N) row from row 1 (ny-2); the
-                // corners take the value of the wall column at that row (its
-                // diagonal x_j with the W/E velocity).  The condition is uniform
-                // over the warp, so every lane reaches the warp barriers.
-                __syncwarp();
-                const f2 ir0 = bc(a.inv_rho0), hd = bc(a.hdt);
-                if (st && (west || east || easto)) {
-                    const int jx = west ? 1 : a.nx - 2, bx = west ? 0 : a.nx - 1;
-                    const unsigned oj = (unsigned)qg * (unsigned)a.pitch + (unsigned)jx;
-                    f2 t[9];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) t[i] = bc(a.gout[oj + (unsigned)i * plane32]);
-                    f2 Fx = bc(0.f), Fy = bc(0.f);
-                    if (FORCE) {
-                        Fx = bc(__ldg(a.force + oj));
-                        Fy = bc(__ldg(a.force + a.plane + oj));
-                    }
-                    const int sd = west ? FDLBM_WALL_W : FDLBM_WALL_E;
-                    nee2<INC, FORCE>(t, rho0, ir0, hd, Fx, Fy, uwp(sd, 0), uwp(sd, 1));
-                    const unsigned ob = (unsigned)qg * (unsigned)a.pitch + (unsigned)bx;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) a.gout[ob + (unsigned)i * plane32] = t[i].x;
-                }
-                if (gS || gN) __syncwarp();
-                if ((gS || gN) && store) {
-                    f2 t[9];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        t[i] = *reinterpret_cast<const f2 *>(a.gout + (roff + (unsigned)i * plane32));
-                    f2 Fx = bc(0.f), Fy = bc(0.f);
-                    if (FORCE) {  // (the force field's padding column reads as any finite value)
-                        Fx = __ldg(reinterpret_cast<const float2 *>(a.force + roff));
-                        Fy = __ldg(reinterpret_cast<const float2 *>(a.force + a.plane + roff));
-                    }
-                    float corner[9];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) corner[i] = east ? t[i].y : t[i].x;
-                    const int sd = gS ? FDLBM_WALL_S : FDLBM_WALL_N;
-                    nee2<INC, FORCE>(t, rho0, ir0, hd, Fx, Fy, uwp(sd, 0), uwp(sd, 1));
-                    const unsigned wrow = gS ? 0u : (unsigned)(a.ny - 1);
-                    const unsigned woff = wrow * (unsigned)a.pitch + (unsigned)xc;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        f2 v = t[i];
-                        if (west || easto) v.x = corner[i];
-                        if (east) v.y = corner[i];
-                        put(woff, i, v);
-                    }
-                }
-            }
-            ++rcL;
         }
         // every lane has read the slot: refill it three rows ahead (force slot
         // (k + 3) mod 5, which stage B has just read).  The copy is issued at
@@ -663,42 +570,96 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
     }
 }
 
-template <bool INC, bool GRID, bool FORCE, bool WALLS>
+// The interior: tile (blockIdx.x, blockIdx.y) of the rectangle.
+template <bool INC, bool GRID, bool FORCE>
 __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     k_step_fused_warp(const __grid_constant__ ArgsW w)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    warp_tile<INC, GRID, FORCE, WALLS>(w.s, &w.tin, &w.tside, &w.tf, &w.tfside, blockIdx.x,
-                                       blockIdx.y, smem_raw);
+    const Tile tile = interior_tile(w.s, blockIdx.x, blockIdx.y);
+    if (tile.y0 >= tile.y1) return;  // uniform over the warp
+    warp_tile<INC, GRID, FORCE>(w.s, &w.tin, &w.tside, &w.tf, &w.tfside, tile, smem_raw);
 }
 
 // Shared-memory offset of a batch case's scalars, after the rings.
 template <bool FORCE>
 constexpr size_t kArgsOff = (sizeof(WarpSmem<FORCE>) + 15) / 16 * 16;
 
-// Batched: block blk_off + b is tile (b' - blk_start[c]) of case c = blk_case[b']
-// (tiles_x[c] windows per row of tiles); the case's tensor maps are read from
-// the table in global memory, its scalars from a copy in shared memory.
-template <bool INC, bool GRID, bool FORCE, bool WALLS>
+__device__ __forceinline__ void copy_words(void *dst, const void *src, int bytes)
+{
+    const int *s = static_cast<const int *>(src);
+    int *d = static_cast<int *>(dst);
+    for (int k = threadIdx.x; k < bytes / 4; k += kLanes) d[k] = s[k];
+}
+
+// Batched interiors: block blk_off + b is tile (b' - blk_start[c]) of case
+// c = blk_case[b'] (nix tiles per row of tiles); the case's tensor maps are
+// read from the table in global memory, its scalars from a copy in shared
+// memory.
+template <bool INC, bool GRID, bool FORCE>
 __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
-    kb_step_fused_warp(const ArgsW *args, const int *blk_case, const int *blk_start,
-                       const int *tiles_x, int blk_off)
+    kb_step_fused_warp(const ArgsW *args, const int *blk_case, const int *blk_start, int blk_off)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int b = blk_off + blockIdx.x;
     const int c = blk_case[b];
     const ArgsW &w = args[c];
     ArgsS *sa = reinterpret_cast<ArgsS *>(smem_raw + kArgsOff<FORCE>);
-    static_assert(sizeof(ArgsS) % 4 == 0, "scalars are copied as 32-bit words");
-    {
-        const int *src = reinterpret_cast<const int *>(&w.s);
-        int *dst = reinterpret_cast<int *>(sa);
-        for (int k = threadIdx.x; k < (int)(sizeof(ArgsS) / 4); k += kLanes) dst[k] = src[k];
-    }
+    static_assert(sizeof(ArgsS) % 4 == 0, "argument blocks are copied as 32-bit words");
+    copy_words(sa, &w.s, sizeof(ArgsS));
     __syncwarp();
-    const int lb = b - blk_start[c], ns = tiles_x[c];
-    warp_tile<INC, GRID, FORCE, WALLS>(*sa, &w.tin, &w.tside, &w.tf, &w.tfside, lb % ns, lb / ns,
-                                       smem_raw);
+    const int u = b - blk_start[c];
+    const Tile tile = interior_tile(*sa, u % sa->nix, u / sa->nix);
+    if (tile.y0 >= tile.y1) return;  // uniform over the warp
+    warp_tile<INC, GRID, FORCE>(*sa, &w.tin, &w.tside, &w.tf, &w.tfside, tile, smem_raw);
+}
+
+// The frame of a walled grid: the walls sweep (walls_sweep.cuh, Eq. 3.10
+// inside it) on tiles of kFrameW columns in blocks of one warp, a launch of
+// its own before the interior's.  Its rows are a chain of dependent work
+// (about 1.6 us each for a lone warp), so the tiles are short -- 8 rows beside
+// the interior, 4 in the frame rows of a walled y axis -- and the launch ends
+// after about 16 rows of the sweep, all tiles in one wave.
+using FrameSmem = walls_sweep::Smem<float, kFrameNT>;
+constexpr int kFrameMinBlocks = 12;  // 168 registers, as the 128-column walls sweep
+constexpr size_t kFrameArgsOff = (sizeof(FrameSmem) + 15) / 16 * 16;
+
+template <bool FORCE>
+__device__ __forceinline__ void frame_sweep(const StepArgs<float> &sa, const Tile &tile,
+                                            unsigned char *smem_raw)
+{
+    auto &sm = *reinterpret_cast<FrameSmem *>(smem_raw);
+    walls_sweep::sweep_tile<float, FORCE, kFrameNT, true>(sa, sm, tile.x0, tile.xend, tile.y0, tile.y1);
+}
+
+template <bool FORCE>
+__global__ void __launch_bounds__(kFrameNT, kFrameMinBlocks)
+    k_frame_sweep(const __grid_constant__ ArgsS a, const __grid_constant__ StepArgs<float> sa)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Tile tile;
+    if (frame_tile(a, blockIdx.x, tile) >= 0) return;
+    frame_sweep<FORCE>(sa, tile, smem_raw);
+}
+
+// Batched frames: block blk_off + b is frame tile (b' - frame_start[c]) of
+// case c = blk_case[b']; the case's walls-sweep arguments are copied into
+// shared memory after the rings.
+template <bool FORCE>
+__global__ void __launch_bounds__(kFrameNT, kFrameMinBlocks)
+    kb_frame_sweep(const ArgsW *args, const StepArgs<float> *sargs, const int *blk_case,
+                   const int *frame_start, int blk_off)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int b = blk_off + blockIdx.x;
+    const int c = blk_case[b];
+    Tile tile;
+    if (frame_tile(args[c].s, b - frame_start[c], tile) >= 0) return;
+    StepArgs<float> *ss = reinterpret_cast<StepArgs<float> *>(smem_raw + kFrameArgsOff);
+    static_assert(sizeof(StepArgs<float>) % 4 == 0, "argument blocks are copied as 32-bit words");
+    copy_words(ss, sargs + c, sizeof(StepArgs<float>));
+    __syncwarp();
+    frame_sweep<FORCE>(*ss, tile, smem_raw);
 }
 
 // cuTensorMapEncodeTiled, looked up once through the runtime (no libcuda link).
@@ -727,7 +688,7 @@ bool fused_warp_ok(int nx, int ny, bool wall_x)
 {
     // periodic x: every copy starts on a 16-byte boundary, a window crosses the
     // seam at most once and a lane's pair never straddles it (nx % 4 == 0);
-    // walled x: any width (the lanes at the east wall handle either parity)
+    // walled x: any width (interior windows from column 4, the rest is frame)
     const unsigned long long pitch = (nx + 31ull) / 32ull * 32ull;
     const bool cols = wall_x || nx % 4 == 0;
     return cols && nx >= kCols && ny >= 4 && 9ull * pitch * (unsigned long long)ny < (1ull << 32);
@@ -779,29 +740,99 @@ cudaError_t fused_warp_encode(WarpMaps *m, const float *state0, const float *sta
     return cudaSuccess;
 }
 
-template <bool INC, bool GRID, bool FORCE, bool WALLS>
+template <bool INC, bool GRID, bool FORCE>
 cudaError_t launch_t(const ArgsW &a, dim3 grid, cudaStream_t stream)
 {
     constexpr size_t smem = sizeof(WarpSmem<FORCE>);
-    auto kern = k_step_fused_warp<INC, GRID, FORCE, WALLS>;
+    auto kern = k_step_fused_warp<INC, GRID, FORCE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kLanes, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
-// Call f with the four instance flags of k as compile-time constants.
+template <bool FORCE>
+cudaError_t launch_frame_t(const ArgsS &a, const StepArgs<float> &sa, cudaStream_t stream)
+{
+    constexpr size_t smem = sizeof(FrameSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_frame_sweep<FORCE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_frame_sweep<FORCE><<<a.nframe, kFrameNT, smem, stream>>>(a, sa);
+    return cudaGetLastError();
+}
+
+// Call f with the three instance flags of k as compile-time constants.
 template <class F>
 cudaError_t dispatch(const WarpKind &k, F &&f)
 {
     using T = std::true_type;
     using N = std::false_type;
-    auto w = [&](auto inc, auto gr, auto fo) {
-        return k.walls ? f(inc, gr, fo, T{}) : f(inc, gr, fo, N{});
-    };
-    auto fo = [&](auto inc, auto gr) { return k.force ? w(inc, gr, T{}) : w(inc, gr, N{}); };
+    auto fo = [&](auto inc, auto gr) { return k.force ? f(inc, gr, T{}) : f(inc, gr, N{}); };
     auto gr = [&](auto inc) { return k.grid ? fo(inc, T{}) : fo(inc, N{}); };
     return k.inc ? gr(T{}) : gr(N{});
+}
+
+// The interior rectangle of a grid and its tile counts.  A walled x axis:
+// interior windows start at column 4 (loads from 0) and end while their loads
+// stay below nx (the last one loads [x0 - 4, x0 + 60)), which leaves a frame
+// of 4 columns at the W wall and 4 to 59 at the E wall.  A walled y axis:
+// rows [4, ny-4).  Frame tiles beside the interior rows take the fewest rows
+// of 4, 8, 16, ... (at most FDLBM_FRAME_MAX_ROWS) for which all frame tiles
+// fit one wave of the frame launch: the launch lasts about (rows + 8) rows of
+// the sweep.
+#ifndef FDLBM_FRAME_MAX_ROWS
+#define FDLBM_FRAME_MAX_ROWS 64
+#endif
+static int frame_slots()
+{
+    static const int n = [] {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+        return sms * kFrameMinBlocks;
+    }();
+    return n;
+}
+
+static void split(ArgsS &a)
+{
+    a.xoff = 0;
+    a.xend = a.nx;
+    a.yoff = 0;
+    a.yend = a.ny;
+    a.erows = 4;
+    if (a.wx) {
+        const int n = a.nx >= kCols ? (a.nx - kCols) / kW + 1 : 0;
+        a.xoff = kHalo;
+        a.xend = kHalo + kW * n;
+    }
+    if (a.wy) {
+        a.yoff = std::min(kHalo, a.ny);
+        a.yend = std::max(a.yoff, a.ny - kHalo);
+    }
+    a.nix = a.xend > a.xoff ? (a.xend - a.xoff + kW - 1) / kW : 0;
+    a.nframe = 0;
+    if (a.wx || a.wy) {
+        Tile unused;
+        for (;;) {
+            a.nframe = frame_tile(a, 1 << 30, unused);
+            if (a.nframe <= frame_slots() || 2 * a.erows > FDLBM_FRAME_MAX_ROWS) break;
+            a.erows *= 2;
+        }
+    }
+}
+
+// Rows of interior tiles; interior tiles.
+static int interior_rows(const ArgsS &a)
+{
+    return a.yend > a.yoff ? (a.yend - a.yoff + a.rows - 1) / a.rows : 0;
+}
+
+static int tile_count(const ArgsS &a)
+{
+    return a.nix > 0 ? a.nix * interior_rows(a) : 0;
 }
 
 // The argument block of one grid at ping-pong parity `cur`.
@@ -826,10 +857,6 @@ ArgsW make_args(const StepArgs<float> &s, const WarpMaps &maps, int cur)
     a.pitch = s.pitch;
     a.plane = s.plane;
     a.rows = s.rows;
-    a.xoff = 0;
-    a.xend = s.nx;
-    a.yoff = 0;
-    a.yend = s.ny;
     a.rho0 = s.c.rho0;
     a.h = s.c.h;
     a.dt = s.c.dt;
@@ -850,10 +877,7 @@ ArgsW make_args(const StepArgs<float> &s, const WarpMaps &maps, int cur)
     a.k_star = 3.0f * s.c.c_star;
     a.wx = s.bc_x == FDLBM_WALL;
     a.wy = s.bc_y == FDLBM_WALL;
-    for (int k = 0; k < 4; ++k) {
-        a.uw[k][0] = s.wall_u[k][0];
-        a.uw[k][1] = s.wall_u[k][1];
-    }
+    split(a);
     return w;
 }
 
@@ -865,7 +889,6 @@ WarpKind warp_kind(const StepArgs<float> &s)
     k.inc = s.c.incomp != 0;
     k.grid = !(s.st.wm1 >= 0.55f * std::fabs(s.st.w1));
     k.force = s.force != nullptr;
-    k.walls = s.bc_x == FDLBM_WALL || s.bc_y == FDLBM_WALL;
     return k;
 }
 
@@ -875,10 +898,12 @@ cudaError_t launch_fused_warp(const StepArgs<float> &s, const WarpMaps &maps, in
     if (s.force && !maps.has_force) return cudaErrorInvalidValue;
     const ArgsW a = make_args(s, maps, cur);
     const WarpKind k = warp_kind(s);
-    const dim3 grid((s.nx + kW - 1) / kW, (s.ny + s.rows - 1) / s.rows);
-    return dispatch(k, [&](auto inc, auto gr, auto fo, auto wa) {
-        return launch_t<decltype(inc)::value, decltype(gr)::value, decltype(fo)::value,
-                        decltype(wa)::value>(a, grid, stream);
+    cudaError_t e = cudaSuccess;
+    if (a.s.nframe > 0) e = s.force ? launch_frame_t<true>(a.s, s, stream) : launch_frame_t<false>(a.s, s, stream);
+    if (e != cudaSuccess || tile_count(a.s) <= 0) return e;
+    const dim3 grid(a.s.nix, interior_rows(a.s));
+    return dispatch(k, [&](auto inc, auto gr, auto fo) {
+        return launch_t<decltype(inc)::value, decltype(gr)::value, decltype(fo)::value>(a, grid, stream);
     });
 }
 
@@ -892,23 +917,49 @@ cudaError_t fused_warp_args(void *dst, const StepArgs<float> &s, const WarpMaps 
     return cudaSuccess;
 }
 
-// A batch's tiles [blk_off, blk_off + nblocks) of the table, all of kind k.
+void fused_warp_tiles(const StepArgs<float> &s, int *interior, int *frame)
+{
+    WarpMaps none;
+    std::memset(&none, 0, sizeof none);
+    none.has_force = s.force != nullptr;
+    const ArgsS a = make_args(s, none, 0).s;
+    *interior = tile_count(a);
+    *frame = a.nframe;
+}
+
+// A batch's interior tiles [blk_off, blk_off + nblocks) of the table, all of
+// kind k.
 cudaError_t launch_batched_warp(const void *args, const int *blk_case, const int *blk_start,
-                                const int *tiles_x, int blk_off, int nblocks, WarpKind k,
-                                cudaStream_t stream)
+                                int blk_off, int nblocks, WarpKind k, cudaStream_t stream)
 {
     if (nblocks <= 0) return cudaSuccess;
-    return dispatch(k, [&](auto inc, auto gr, auto fo, auto wa) {
-        constexpr bool I = decltype(inc)::value, G = decltype(gr)::value, F = decltype(fo)::value,
-                       W = decltype(wa)::value;
+    return dispatch(k, [&](auto inc, auto gr, auto fo) {
+        constexpr bool I = decltype(inc)::value, G = decltype(gr)::value, F = decltype(fo)::value;
         constexpr size_t smem = kArgsOff<F> + sizeof(ArgsS);
-        auto kern = kb_step_fused_warp<I, G, F, W>;
+        auto kern = kb_step_fused_warp<I, G, F>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kern<<<nblocks, kLanes, smem, stream>>>(static_cast<const ArgsW *>(args), blk_case, blk_start,
-                                                tiles_x, blk_off);
+                                                blk_off);
         return cudaGetLastError();
     });
+}
+
+// A batch's frame tiles [blk_off, blk_off + nblocks) of the table (cases with
+// a force field or all without); sargs: the cases' StepArgs<float>.
+cudaError_t launch_batched_frame(const void *args, const void *sargs, const int *blk_case,
+                                 const int *frame_start, int blk_off, int nblocks, bool force,
+                                 cudaStream_t stream)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    constexpr size_t smem = kFrameArgsOff + sizeof(StepArgs<float>);
+    auto kern = force ? kb_frame_sweep<true> : kb_frame_sweep<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<nblocks, kFrameNT, smem, stream>>>(static_cast<const ArgsW *>(args),
+                                              static_cast<const StepArgs<float> *>(sargs), blk_case,
+                                              frame_start, blk_off);
+    return cudaGetLastError();
 }
 
 int fused_warp_tile_width() { return kW; }
@@ -917,7 +968,7 @@ int fused_warp_blocks_per_sm()
 {
     int n = 0;
     constexpr size_t smem = sizeof(WarpSmem<false>);
-    auto kern = k_step_fused_warp<false, false, false, false>;
+    auto kern = k_step_fused_warp<false, false, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kLanes, smem) != cudaSuccess) return 0;
     return n;

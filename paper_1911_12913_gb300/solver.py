@@ -331,6 +331,8 @@ class FDLBMBatch:
             opts[c].has_force = int(cs.get("has_force", False))
             opts[c].A = cs.get("A", 0.5)
             opts[c].scheme = {1: B.SCHEME_T2S2_1, 2: B.SCHEME_T2S2_2}[cs.get("scheme", 1)]
+            opts[c].variant = {"auto": B.VARIANT_AUTO, "scalar": B.VARIANT_SCALAR,
+                               "warp": B.VARIANT_WARP}[cs.get("variant", "auto")]
             opts[c].equilibrium = {"standard": B.EQ_STANDARD,
                                    "incompressible": B.EQ_INCOMPRESSIBLE}[cs.get("equilibrium", "standard")]
         nu = np.ascontiguousarray([cs["nu"] for cs in cases], dtype=np.float64)

@@ -36,9 +36,11 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def _mixed_cases():
+def _mixed_cases(precision="fp32"):
     """Cavity (tanh and uniform), channel with force, periodic with force and
-    metrics, periodic without force, and one T2S2-FDLBM2 case."""
+    metrics, periodic without force, and one T2S2-FDLBM2 case; FP32: some
+    walled cases ask for the warp-tile kernel."""
+    W = dict(variant="warp") if precision == "fp32" else {}
     F = 0.01
     cav = I.tanh_axis(16, 1.5)
     per_x = I.periodic_axis(33, 0.0, 1.0)
@@ -59,18 +61,20 @@ def _mixed_cases():
         dict(xa=I.periodic_axis(24, 0.0, 1.0), ya=I.periodic_axis(20, 0.0, 1.0), nu=0.02,
              cfl=0.3, blend=0.2, scheme=2, init="random"),
         # cases the warp-tile kernel takes in FUSED mode (64 columns and more),
-        # of several kernel instances: walls with and without a force field,
-        # periodic with and without one, update weights of either construction
+        # of several kernel instances: walls with and without a force field
+        # (asked for: the automatic choice leaves small walled grids to the
+        # walls sweep), periodic with and without one, update weights of
+        # either construction
         dict(xa=I.tanh_axis(68, 1.5), ya=I.tanh_axis(40, 1.5), nu=0.1 / 100, cfl=0.5, blend=0.1,
-             wall_u=lid, init="random"),
+             wall_u=lid, init="random", **W),
         dict(xa=I.periodic_axis(64, 0.0, 1.0), ya=I.tanh_axis(30, 1.5), nu=math.sqrt(F / 80), cfl=0.5,
-             blend=0.1, has_force=True, force="channel", init="rest"),
+             blend=0.1, has_force=True, force="channel", init="rest", **W),
         dict(xa=I.periodic_axis(68, 0.0, 1.0), ya=I.periodic_axis(30, 0.0, 0.5), nu=0.02, cfl=0.4,
              blend=0.2, has_force=True, force="random", init="random"),
         dict(xa=I.periodic_axis(128, 0.0, 2 * math.pi), ya=I.periodic_axis(45, 0.0, 2 * math.pi),
              nu=0.01, cfl=0.5, blend=0.1, init="random"),
         dict(xa=I.wall_axis(70, 0.0, 1.0), ya=I.wall_axis(26, 0.0, 1.0), nu=0.001, cfl=0.5,
-             blend=0.1, wall_u=[(0, 0.02), (0, -0.01), (0.03, 0), (0.1, 0.0)], init="random"),
+             blend=0.1, wall_u=[(0, 0.02), (0, -0.01), (0.03, 0), (0.1, 0.0)], init="random", **W),
     ]
     return cases
 
@@ -116,7 +120,7 @@ def test_mixed_batch_matches_oracle(precision, tol, autotune, mode):
     only, the default where it applies), per-stage launches of the staged
     kernels, and the persistent cooperative launch (of the fused sweep where
     it applies, one grid barrier per step; of the staged stages otherwise)."""
-    cases = _mixed_cases()
+    cases = _mixed_cases(precision)
     if mode == "persistent-fused":
         cases = [cs for cs in cases if cs.get("scheme", 1) == 1]
     batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=autotune,
@@ -146,20 +150,22 @@ def test_batch_fused_mode_needs_fp32():
     cases and one for the T2S2-FDLBM2 cases; FP64 batches stay staged."""
     cases = _mixed_cases()
     with pytest.raises(Exception, match="EUNSUPPORTED"):
-        FDLBMBatch(cases, precision="fp64", graph_steps=0, autotune=False, mode="fused")
+        FDLBMBatch(_mixed_cases("fp64"), precision="fp64", graph_steps=0, autotune=False, mode="fused")
     b = FDLBMBatch(cases[:5], precision="fp32", graph_steps=0, autotune=False)
     assert b.describe.startswith("batched-fused") and "launches_per_step=1" in b.describe, b.describe
-    assert "warp_tiles=0" in b.describe, b.describe
+    assert "warp_tiles=0 " in b.describe, b.describe
     b = FDLBMBatch(cases[:6], precision="fp32", graph_steps=0, autotune=False)
     assert b.describe.startswith("batched-fused") and "launches_per_step=2" in b.describe, b.describe
-    # the cases of 64 columns and more go to the warp-tile kernel, one launch
-    # per kernel instance (walls / force / weight construction)
+    # the cases of 64 columns and more go to the warp-tile kernel: their
+    # interiors one launch per kernel instance (force / weight construction:
+    # three here), the frames of the walled ones one launch without and one
+    # with a force field; then the walls sweep and the T2S2-FDLBM2 sweep
     b = FDLBMBatch(cases, precision="fp32", graph_steps=0, autotune=False)
-    assert "warp_tiles=0" not in b.describe and "launches_per_step=6" in b.describe, b.describe
+    assert "warp_tiles=0 " not in b.describe and "launches_per_step=7" in b.describe, b.describe
 
 
 def test_batch_case_restrictions():
-    cases = _mixed_cases()[:2]
+    cases = _mixed_cases("fp64")[:2]
     batch = FDLBMBatch(cases, precision="fp64", graph_steps=0, autotune=False)
     L = B.load()
     h = batch.case(0)._h
@@ -217,7 +223,7 @@ def test_persistent_barrier_timeout_is_reported(precision, scheme1_only):
     fdlbm_batch_sync reports them once and clears them, and the context stays
     usable: with the default limit and re-initialised states the same batch
     matches the oracle again."""
-    cases = _mixed_cases()
+    cases = _mixed_cases(precision)
     if scheme1_only:                           # the persistent fused sweep
         cases = [cs for cs in cases if cs.get("scheme", 1) == 1]
     batch = FDLBMBatch(cases, precision=precision, graph_steps=4, autotune=False, mode="persistent")

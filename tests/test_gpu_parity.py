@@ -228,6 +228,13 @@ _WALL_CASES = [
     # and several windows, walls on x only and on y only, row segments 1..5
     ("wall", "wall", 64, 40, 5), ("wall", "wall", 129, 33, 0), ("periodic", "wall", 128, 21, 3),
     ("wall", "periodic", 66, 24, 2), ("wall", "wall", 200, 12, 1), ("wall", "wall", 115, 10, 4),
+    # the warp-tile split into an interior rectangle (periodic code) and a
+    # frame (wall code): interior windows whose row tiles cross a periodic y
+    # seam, and a periodic x seam inside the interior rows; odd widths whose
+    # east wall would fall on a frame window's first lane (nx = 1 mod 56),
+    # with interior windows (281) and without (113)
+    ("wall", "periodic", 300, 30, 4), ("periodic", "wall", 256, 40, 7),
+    ("wall", "wall", 281, 20, 3), ("wall", "wall", 113, 14, 2), ("wall", "wall", 240, 64, 0),
 ]
 
 
