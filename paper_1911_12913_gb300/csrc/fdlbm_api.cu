@@ -443,7 +443,10 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     const bool f32 = o.precision == FDLBM_FP32_DEV;
     // the warp-tile kernel is a T2S2-FDLBM1 kernel; T2S2-FDLBM2 fuses on the scalar layout only
     const bool s1 = o.scheme == FDLBM_SCHEME_T2S2_1;
-    const bool warp_ok = s1 && fused && f32 && fused_warp_ok(g->nx, g->ny, g->bc_x == FDLBM_WALL);
+    // (a batch case, force_staged: the batch's mode picks the kernels; the
+    // variant is the one its FUSED mode runs the case on)
+    const bool warp_ok =
+        s1 && (fused || force_staged) && f32 && fused_warp_ok(g->nx, g->ny, g->bc_x == FDLBM_WALL);
     if (o.variant == FDLBM_VARIANT_WARP && !warp_ok) return FDLBM_EUNSUPPORTED;
     int variant = o.variant;
     // a walled grid on the warp-tile kernel pays a fixed 25-35 us for its frame
