@@ -43,22 +43,39 @@ namespace {
 // transposed x-differences need the metric of the node they gather from, so
 // the rings hold lam' m_x and lam_gs m_x, each multiplied by its writer's own
 // column metric; the transposed y-differences weight the window rows by a
-// window of m_y.  g waits four rows in a per-thread ring for stage C'.
+// window of m_y.  g and the force wait four rows in a per-thread ring for
+// stages B' and C'.  The rows of g, lam' and the force arrive two rows ahead
+// by asynchronous copies (cp.async) into a three-slot ring, each thread its
+// own column, so that no row waits for its loads.
 // One barrier per row, as in the forward sweep (5-slot rings, 5-row unroll):
 // a ring slot is rewritten five rows after it was written, and every reader
-// of it has passed a barrier in between.
+// of it has passed a barrier in between (the copy ring: a slot is refilled one
+// row, and one barrier, after its thread read it).
 
 constexpr int kAdjNT = 128;
 constexpr int kAdjHalo = 4;
 constexpr int kAdjRing = 5;
+constexpr int kAdjIn = 3;   // rows of the copy ring: this one and two ahead
 
 template <class R>
 struct AdjSmem {
     R P[kAdjRing][6][kAdjNT];   // fbar^{+,h} of the x-moving populations
     R L[kAdjRing][6][kAdjNT];   // lam' m_x of the x-moving populations
     R LG[kAdjRing][6][kAdjNT];  // lam_gs m_x of the x-moving populations
-    R G[kAdjRing][9][kAdjNT];   // g (own column only)
+    R G[kAdjRing][11][kAdjNT];  // g and the force (own column only)
+    R IN[kAdjIn][20][kAdjNT];   // rows in flight: g, lam', force (own column)
 };
+
+// Asynchronous global -> shared copy of one value (cp.async, cached in L1).
+template <class R>
+__device__ __forceinline__ void copy_async(R *dst, const R *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(sizeof(R)) : "memory");
+}
+__device__ __forceinline__ void copy_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void copy_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <class R>
 struct AdjArgs {
@@ -99,43 +116,56 @@ __global__ void __launch_bounds__(kAdjNT, sizeof(R) == 4 ? 2 : 1) k_adj_fused(co
     R Mw[kAdjRing];      // m_y of the rows in the windows above
     R Mg[kAdjRing];      // m_y of the rows of Gw
     R fBx[kAdjRing], fBy[kAdjRing];  // force cotangent of stage B, per row
-    R gcur[9], lcur[9], gnxt[9], lnxt[9];
+    R gcur[9], lcur[9];
     int rl = wrap_index(y0 - kAdjHalo, a.ny);   // row of gcur / lcur
+    int rn = rl;                                // next row to copy
     int rs = wrap_index(y0 - 6, a.ny);          // stage B' row at iteration k: y0 - 6 + k
     int rq = wrap_index(y0 - 8, a.ny);          // stage C' row: y0 - 8 + k
-    auto load = [&](R *g, R *l, int row) {
-        const size_t off = (size_t)row * a.pitch + gx;
+    // row `row` into copy slot `slot` (one commit group per row, empty past
+    // the segment, so that the group count stays in step with the rows)
+    auto issue = [&](int slot, bool any) {
+        if (any) {
+            const size_t off = (size_t)rn * a.pitch + gx;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            g[i] = __ldg(a.gin + i * a.plane + off);
-            l[i] = __ldg(p.lam_next + i * a.plane + off);
+            for (int i = 0; i < 9; ++i) {
+                copy_async(&sm.IN[slot][i][t], a.gin + i * a.plane + off);
+                copy_async(&sm.IN[slot][9 + i][t], p.lam_next + i * a.plane + off);
+            }
+            if (FORCE) {
+                copy_async(&sm.IN[slot][18][t], a.force + off);
+                copy_async(&sm.IN[slot][19][t], a.force + a.plane + off);
+            }
+            rn = rn + 1 == a.ny ? 0 : rn + 1;
         }
+        copy_commit();
     };
-    load(gcur, lcur, rl);
     const int iters = (y1 - y0) + 2 * kAdjHalo;
+    issue(0, true);
+    issue(1, 1 < iters);
 
     auto row = [&](auto PHc, int k) {
         constexpr int PH = decltype(PHc)::value;
         constexpr int p0 = PH, p1 = (PH + 4) % 5, p2 = (PH + 3) % 5, p3 = (PH + 2) % 5,
                       p4 = (PH + 1) % 5;
         const int rA = rl;
-        if (k + 1 < iters) {
-            rl = rl + 1 == a.ny ? 0 : rl + 1;
-            load(gnxt, lnxt, rl);
+        rl = rl + 1 == a.ny ? 0 : rl + 1;
+        // the row two ahead into the slot read one row ago; then this row's
+        const int slot = k % kAdjIn;
+        issue((k + 2) % kAdjIn, k + 2 < iters);
+        copy_wait<2>();
+        R Fx = R(0), Fy = R(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            gcur[i] = sm.IN[slot][i][t];
+            lcur[i] = sm.IN[slot][9 + i][t];
         }
-        // rows of stages B' and C', and their global inputs, loaded before the
-        // barrier so that the loads overlap stage A'
+        if (FORCE) {
+            Fx = sm.IN[slot][18][t];
+            Fy = sm.IN[slot][19][t];
+        }
         const int rB = rs, rC = rq;
         rs = rs + 1 == a.ny ? 0 : rs + 1;
         rq = rq + 1 == a.ny ? 0 : rq + 1;
-        R FBx = R(0), FBy = R(0), FCx = R(0), FCy = R(0);
-        if (FORCE) {
-            const size_t fb = (size_t)rB * a.pitch + gx, fc = (size_t)rC * a.pitch + gx;
-            FBx = __ldg(a.force + fb);
-            FBy = __ldg(a.force + a.plane + fb);
-            FCx = __ldg(a.force + fc);
-            FCy = __ldg(a.force + a.plane + fc);
-        }
         const bool doC = k >= 8 && act2;
         const size_t nC = (size_t)rC * a.nx + xc;
         double dFx = 0.0, dFy = 0.0;
@@ -145,12 +175,6 @@ __global__ void __launch_bounds__(kAdjNT, sizeof(R) == 4 ? 2 : 1) k_adj_fused(co
         }
         // ------------------------------------------------------------ A' (row r)
         {
-            R Fx = R(0), Fy = R(0);
-            if (FORCE) {
-                const size_t fo = (size_t)rA * a.pitch + gx;
-                Fx = __ldg(a.force + fo);
-                Fy = __ldg(a.force + a.plane + fo);
-            }
             R drho, jx, jy;
             moments_dev(gcur, drho, jx, jy);
             const R rho = c.rho0 + drho;
@@ -168,6 +192,10 @@ __global__ void __launch_bounds__(kAdjNT, sizeof(R) == 4 ? 2 : 1) k_adj_fused(co
                 Pw[i][p0] = P;
                 Lw[i][p0] = lcur[i];
                 sm.G[p0][i][t] = gcur[i];
+                if (FORCE && i == 0) {
+                    sm.G[p0][9][t] = Fx;
+                    sm.G[p0][10][t] = Fy;
+                }
                 if (xslot(i) >= 0) {
                     sm.P[p0][xslot(i)][t] = P;
                     sm.L[p0][xslot(i)][t] = lcur[i] * mxc;
@@ -207,7 +235,11 @@ __global__ void __launch_bounds__(kAdjNT, sizeof(R) == 4 ? 2 : 1) k_adj_fused(co
                 gs[i] = acc;
                 lS[i] = -c.dt * lt;
             }
-            const R Fx = FBx, Fy = FBy;
+            R Fx = R(0), Fy = R(0);
+            if (FORCE) {
+                Fx = sm.G[p2][9][t];
+                Fy = sm.G[p2][10][t];
+            }
             NodeMap<R> m;
             m.eval(gs, c.rho0, Fx, Fy, c.half_h);
             R lgeq[9], lF[9], lg[9];
@@ -256,7 +288,11 @@ __global__ void __launch_bounds__(kAdjNT, sizeof(R) == 4 ? 2 : 1) k_adj_fused(co
                 lQ[i] = Lw[i][p4];
                 g[i] = sm.G[p4][i][t];
             }
-            const R Fx = FCx, Fy = FCy;
+            R Fx = R(0), Fy = R(0);
+            if (FORCE) {
+                Fx = sm.G[p4][9][t];
+                Fy = sm.G[p4][10][t];
+            }
             NodeMap<R> m;
             m.eval(g, c.rho0, Fx, Fy, c.half_dt);
             R lgeq[9], lF[9], lg[9];
@@ -275,11 +311,6 @@ __global__ void __launch_bounds__(kAdjNT, sizeof(R) == 4 ? 2 : 1) k_adj_fused(co
                 p.dforce[nC] = dFx + (double(lFx) + double(fBx[p2]));
                 p.dforce[N + nC] = dFy + (double(lFy) + double(fBy[p2]));
             }
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            gcur[i] = gnxt[i];
-            lcur[i] = lnxt[i];
         }
     };
     for (int k = 0; k < iters; k += 5) {
