@@ -70,6 +70,9 @@ def parse():
                    help="only time K steps of the 257^2 cavity (FP32, fused walls) and print that")
     p.add_argument("--adjoint-cost", type=int, default=0, metavar="N",
                    help="only time adjoint against forward steps on an N^2 grid and print that")
+    p.add_argument("--no-walled", action="store_true", help="skip the walled-grid throughput cases")
+    p.add_argument("--walled", type=int, default=0, metavar="N",
+                   help="only time the walled-grid cases (cavity (N+1)^2, channel N x (N+1)) and print that")
     return p.parse_args()
 
 
@@ -167,7 +170,8 @@ class Clocks:
 # committed ncu DRAM-traffic record and the sources it was taken from, per kernel
 TRAFFIC = {
     "fused-warp": ("warp_fp32_traffic.json",
-                   ["step_fused_warp.cu", "packed.cuh", "tma.cuh", "lattice.cuh"]),
+                   ["step_fused_warp.cu", "packed.cuh", "tma.cuh", "lattice.cuh", "walls_sweep.cuh",
+                    "walls_nodes.cuh"]),
     "fused": ("fused_fp32_traffic.json", ["step_fused.cu", "lattice.cuh"]),
 }
 
@@ -500,6 +504,54 @@ def adjoint_cost(dev, m, k=200, seed=11):
             "forward_kernel": s.describe, "adjoint_kernels_per_step": 1}
 
 
+def run_walled(stream, n=N_GRID, steps=100, hbm=None):
+    """Walled grids at the throughput size, FP32, the automatic kernel (at this
+    size: the warp-tile interior plus the walls-sweep frame): the lid-driven
+    cavity on (n+1)^2 uniform nodes (lid U = 0.1, Re = 1000, CFL 0.9), and the
+    channel on n x (n+1) nodes (periodic x, walls y), without and with a
+    uniform body force.  Bytes per cell: 72, or 80 with the force field."""
+    import numpy as np
+    import torch
+    import inputs as I
+    from paper_1911_12913_gb300.solver import FDLBM
+
+    hbm = hbm or (peaks().get("hbm_gbs") or 6800.0)
+    pa = I.periodic_axis(n, 0.0, 1.0)
+    wa = I.wall_axis(n, 0.0, 1.0)
+    lid = [(0.0, 0.0), (0.0, 0.0), (0.0, 0.0), (0.1, 0.0)]
+    out = {}
+    for name, xa, force in (("cavity", wa, None), ("channel", pa, None), ("channel_forced", pa, 1e-6)):
+        s = FDLBM(xa, wa, nu=1e-4, cfl=0.9, blend=BLEND, precision="fp32", stream=stream,
+                  wall_u=lid, has_force=force is not None)
+        if force is not None:
+            F = np.zeros((2, wa.n, xa.n))
+            F[0] = force
+            s.set_force(F)
+        one = np.ones((wa.n, xa.n))
+        s.init_fields(one, 0 * one, 0 * one)
+        s.step(10)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.sync()
+        t = e0.elapsed_time(e1) / 1e3 / steps
+        cells = xa.n * wa.n
+        bpc = 80 if force is not None else 72
+        out[name] = {"nodes": [xa.n, wa.n], "kernel": s.describe, "MLUPS": cells / t / 1e6,
+                     "ms_per_step": t * 1e3, "bytes_per_cell": bpc,
+                     "hbm_frac": bpc * cells / t / 1e9 / hbm, "steps": steps,
+                     "launches_per_step": s.kernels_per_step}
+        del s
+        torch.cuda.empty_cache()
+    out["workload"] = (f"walls Eq. 3.10: cavity {n + 1}^2 uniform, lid U=0.1, Re=1000; channel "
+                       f"{n}x{n + 1} periodic x, walls y, unforced and with F=1e-6; CFL 0.9, "
+                       f"blend {BLEND}, FP32, from rest")
+    return out
+
+
 def run_adjoint(dev, n=256, nsteps=2000, iters=6, seed=11):
     """Adjoint cost against the forward step (256^2 and 4096^2, FP32), and the
     inverse problem: recover a hidden smooth body force on a 256^2 periodic grid
@@ -748,6 +800,11 @@ def run_ours(args):
         del s64
         torch.cuda.empty_cache()
 
+    # ---------------- walled grids at the throughput size (cavity, channel)
+    walled = None
+    if not args.no_walled:
+        walled = run_walled(stream, n, hbm=hbm)
+
     # ---------------- 64-case batched sweep (cavity / channel mixes, FP32)
     batched = None
     if not args.no_batched:
@@ -862,7 +919,7 @@ def run_ours(args):
                "config": config(n, "fp32", args.steps), "clocks": clocks,
                "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
                "cpu_baseline": cpu, "fp64": fp64, "fp32_variants": variants, "fp32_forced": forced,
-               "batched": batched, "adjoint": adjoint,
+               "walled": walled, "batched": batched, "adjoint": adjoint,
                "cavity": cavity, "sweep": sweep, "fdlbm2": fdlbm2,
                "mass_drift_rel": mass_drift,
                "parallelism": "replicas" if world > 1 else "single"}
@@ -877,6 +934,11 @@ def main():
         return run_reference(args)
     if args.cavity_steps:
         print(json.dumps(cavity_steps(args.cavity_steps)), flush=True)
+        return 0
+    if args.walled:
+        import torch
+        stream = torch.cuda.current_stream(torch.device("cuda", torch.cuda.current_device()))
+        print(json.dumps(run_walled(stream, args.walled, steps=max(1, args.steps))), flush=True)
         return 0
     if args.adjoint_cost:
         import torch

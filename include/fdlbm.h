@@ -63,19 +63,24 @@ enum { FDLBM_MEM_HOST = 0, FDLBM_MEM_DEVICE = 1 };
  * returns FDLBM_EUNSUPPORTED with it.  fdlbm_moments returns the density and
  * this velocity. */
 enum { FDLBM_EQ_STANDARD = 0, FDLBM_EQ_INCOMPRESSIBLE = 1 };
-/* Fused-kernel variant of T2S2-FDLBM1 on periodic grids (a grid with a walled
- * axis runs the scalar sweep with Eq. 3.10 inside it, and WARP there is
- * unsupported):
+/* Fused-kernel variant of T2S2-FDLBM1 (Sec. 2D, first sequence):
  *  SCALAR  one column per thread, rows loaded through registers (any nx >= 4);
+ *          on a grid with a walled axis, the walls sweep with Eq. 3.10 inside;
  *  WARP    FP32 only, one independent warp per 56-column tile, two adjacent
  *          columns per lane in packed f32x2 arithmetic, x-neighbours by warp
  *          shuffle, rows by bulk tensor copies into a per-warp ring; no
- *          block-level barrier (no force field, nx % 4 == 0, nx >= 64, fewer
- *          than 2^32 values in the state).
+ *          block-level barrier; with or without a force field (nx >= 64, nx %
+ *          4 == 0 on a periodic x axis, fewer than 2^32 values in the state).
+ *          On a grid with a walled axis it covers the interior, the nodes at
+ *          least 4 from every wall whose tiles load nothing outside the grid
+ *          (there the walled and the periodic scheme compute the same values),
+ *          and a second launch of the walls sweep covers the 4-node frame:
+ *          two launches per step (fdlbm_kernels_per_step).
  * AUTO picks WARP where it applies (the fastest measured on GB300 for the
- * periodic 4096^2 throughput case) and SCALAR otherwise.  Asking for a
- * variant that does not apply returns FDLBM_EUNSUPPORTED; the values 2 to 4
- * are not used. */
+ * periodic 4096^2 throughput case), except on walled grids of fewer than
+ * 1.5 M nodes, where the frame launch's fixed cost makes the walls sweep
+ * faster, and SCALAR otherwise.  Asking for a variant that does not apply
+ * returns FDLBM_EUNSUPPORTED; the values 2 to 4 are not used. */
 enum { FDLBM_VARIANT_AUTO = 0, FDLBM_VARIANT_SCALAR = 1, FDLBM_VARIANT_WARP = 5 };
 enum { FDLBM_WALL_W = 0, FDLBM_WALL_E = 1, FDLBM_WALL_S = 2, FDLBM_WALL_N = 3 };
 /* Time-marching scheme (Sec. 2A):

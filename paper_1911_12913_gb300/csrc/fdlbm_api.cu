@@ -799,8 +799,16 @@ int fdlbm_path(fdlbm_t h) { return h ? h->path : -1; }
 int fdlbm_kernels_per_step(fdlbm_t h)
 {
     if (!h) return -1;
-    if (h->path == FDLBM_PATH_FUSED) return 1;
     const bool walls = h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL;
+    if (h->path == FDLBM_PATH_FUSED) {
+        // a walled grid on the warp-tile kernel: the frame's launch and the interior's
+        if (h->precision == FDLBM_FP32_DEV && h->variant == FDLBM_VARIANT_WARP && walls) {
+            int interior = 0, frame = 0;
+            fused_warp_tiles(step_args<float>(h), &interior, &frame);
+            return (interior > 0) + (frame > 0);
+        }
+        return 1;
+    }
     if (h->scheme == FDLBM_SCHEME_T2S2_2) return walls ? 6 : 3;
     return walls ? 5 : 3;
 }
