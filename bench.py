@@ -170,8 +170,7 @@ class Clocks:
 # committed ncu DRAM-traffic record and the sources it was taken from, per kernel
 TRAFFIC = {
     "fused-warp": ("warp_fp32_traffic.json",
-                   ["step_fused_warp.cu", "packed.cuh", "tma.cuh", "lattice.cuh", "walls_sweep.cuh",
-                    "walls_nodes.cuh"]),
+                   ["step_fused_warp.cu", "packed.cuh", "tma.cuh", "lattice.cuh"]),
     "fused": ("fused_fp32_traffic.json", ["step_fused.cu", "lattice.cuh"]),
 }
 
