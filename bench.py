@@ -71,6 +71,7 @@ def parse():
     p.add_argument("--adjoint-cost", type=int, default=0, metavar="N",
                    help="only time adjoint against forward steps on an N^2 grid and print that")
     p.add_argument("--no-walled", action="store_true", help="skip the walled-grid throughput cases")
+    p.add_argument("--fdlbm2", action="store_true", help="only time the T2S2-FDLBM2 cases at --n and print that")
     p.add_argument("--walled", type=int, default=0, metavar="N",
                    help="only time the walled-grid cases (cavity (N+1)^2, channel N x (N+1)) and print that")
     return p.parse_args()
@@ -368,8 +369,9 @@ def run_sweep(dev, stream, sizes=(512, 1024, 2048, 4096)):
 
 # ----------------------------------------------------------------------- T2S2-FDLBM2
 def run_fdlbm2(dev, stream, n=N_GRID):
-    """T2S2-FDLBM2 (Eq. 5.23) on the throughput workload: the fused sweep in FP32
-    and FP64 against the staged kernels in FP32 (extra line, not the headline)."""
+    """T2S2-FDLBM2 (Eq. 5.23) on the throughput workload: the fused sweeps in FP32
+    (the automatic kernel, the warp tile, and the scalar sweep) and FP64 against
+    the staged kernels in FP32 (extra line, not the headline)."""
     import torch
     from paper_1911_12913_gb300.solver import FDLBM
 
@@ -377,10 +379,12 @@ def run_fdlbm2(dev, stream, n=N_GRID):
     ax, f, _ = workload_fields(n)
     grad = [f["dudx"], f["dudy"], f["dvdx"], f["dvdy"]]
     out = {}
-    for name, prec, path, k in (("fused_fp32", "fp32", "fused", 200), ("staged_fp32", "fp32", "staged", 20),
-                                ("fused_fp64", "fp64", "fused", 10)):
+    for name, prec, path, k, var in (("fused_fp32", "fp32", "fused", 200, "auto"),
+                                     ("fused_scalar_fp32", "fp32", "fused", 200, "scalar"),
+                                     ("staged_fp32", "fp32", "staged", 20, "auto"),
+                                     ("fused_fp64", "fp64", "fused", 10, "auto")):
         s = FDLBM(ax, ax, nu=NU, cfl=CFL, blend=BLEND, precision=prec, scheme=2, path=path,
-                  stream=stream)
+                  stream=stream, variant=var)
         s.init_fields(f["rho"], f["ux"], f["uy"], grad)
         s.step(3)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -933,6 +937,11 @@ def main():
         return run_reference(args)
     if args.cavity_steps:
         print(json.dumps(cavity_steps(args.cavity_steps)), flush=True)
+        return 0
+    if args.fdlbm2:
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        print(json.dumps(run_fdlbm2(dev, torch.cuda.current_stream(dev), args.n)), flush=True)
         return 0
     if args.walled:
         import torch

@@ -101,10 +101,10 @@ int choose_rows(int nx, int ny, int precision, int variant, bool walls, int sche
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool f32 = precision == FDLBM_FP32_DEV;
     int per_sm;
-    if (scheme == FDLBM_SCHEME_T2S2_2)
-        per_sm = f32 ? fused_s2_blocks_per_sm<float>() : fused_s2_blocks_per_sm<double>();
-    else if (variant == FDLBM_VARIANT_WARP)
+    if (variant == FDLBM_VARIANT_WARP)
         per_sm = fused_warp_blocks_per_sm();
+    else if (scheme == FDLBM_SCHEME_T2S2_2)
+        per_sm = f32 ? fused_s2_blocks_per_sm<float>() : fused_s2_blocks_per_sm<double>();
     else if (walls)
         per_sm = f32 ? fused_walls_blocks_per_sm<float>() : fused_walls_blocks_per_sm<double>();
     else
@@ -167,8 +167,8 @@ cudaError_t launch_step(fdlbm_ctx *h, cudaStream_t s)
     if (h->precision == FDLBM_FP32_DEV) {
         auto a = step_args<float>(h);
         if (h->path == FDLBM_PATH_STAGED) return launch_staged(a, s);
-        if (h->scheme == FDLBM_SCHEME_T2S2_2) return launch_fused_s2(a, s);
         if (h->variant == FDLBM_VARIANT_WARP) return launch_fused_warp(a, h->wmaps, h->cur, s);
+        if (h->scheme == FDLBM_SCHEME_T2S2_2) return launch_fused_s2(a, s);
         if (walls) return launch_fused_walls(a, s);
         return launch_fused(a, s);
     }
@@ -441,12 +441,15 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     if (path < 0) return FDLBM_EUNSUPPORTED;
     const bool fused = path == FDLBM_PATH_FUSED;
     const bool f32 = o.precision == FDLBM_FP32_DEV;
-    // the warp-tile kernel is a T2S2-FDLBM1 kernel; T2S2-FDLBM2 fuses on the scalar layout only
+    // the warp-tile kernel runs T2S2-FDLBM1 on periodic and walled grids and
+    // T2S2-FDLBM2 on periodic ones (a single grid: batches keep their
+    // T2S2-FDLBM2 cases on the scalar sweep)
     const bool s1 = o.scheme == FDLBM_SCHEME_T2S2_1;
+    const bool s2_warp = o.scheme == FDLBM_SCHEME_T2S2_2 && !walled(g) && !force_staged;
     // (a batch case, force_staged: the batch's mode picks the kernels; the
     // variant is the one its FUSED mode runs the case on)
-    const bool warp_ok =
-        s1 && (fused || force_staged) && f32 && fused_warp_ok(g->nx, g->ny, g->bc_x == FDLBM_WALL);
+    const bool warp_ok = (s1 || s2_warp) && (fused || force_staged) && f32 &&
+                         fused_warp_ok(g->nx, g->ny, g->bc_x == FDLBM_WALL);
     if (o.variant == FDLBM_VARIANT_WARP && !warp_ok) return FDLBM_EUNSUPPORTED;
     int variant = o.variant;
     // a walled grid on the warp-tile kernel pays a fixed 25-35 us for its frame
@@ -907,7 +910,9 @@ const char *fdlbm_describe(fdlbm_t h)
     if (!h) return "NULL handle";
     const char *prec = h->precision == FDLBM_FP32_DEV ? "fp32dev" : "fp64";
     if (h->scheme == FDLBM_SCHEME_T2S2_2) {
-        h->desc = std::string(h->path == FDLBM_PATH_FUSED ? "fused-scheme2 " : "staged-scheme2 ") +
+        h->desc = std::string(h->path == FDLBM_PATH_STAGED         ? "staged-scheme2 "
+                              : h->variant == FDLBM_VARIANT_WARP ? "fused-warp-scheme2 "
+                                                                 : "fused-scheme2 ") +
                   prec;
         if (h->path == FDLBM_PATH_FUSED) h->desc += " rows=" + std::to_string(h->rows);
         if (h->graph_steps) h->desc += " graph_steps=" + std::to_string(h->graph_steps);

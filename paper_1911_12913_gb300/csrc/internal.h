@@ -129,8 +129,11 @@ cudaError_t launch_fused_warp(const StepArgs<float> &a, const WarpMaps &maps, in
                               cudaStream_t s);
 // The instance of the warp-tile kernel a grid needs.
 struct WarpKind {
-    bool inc = false, grid = false, force = false;
-    bool operator==(const WarpKind &o) const { return inc == o.inc && grid == o.grid && force == o.force; }
+    bool inc = false, grid = false, force = false, s2 = false;  // s2: T2S2-FDLBM2
+    bool operator==(const WarpKind &o) const
+    {
+        return inc == o.inc && grid == o.grid && force == o.force && s2 == o.s2;
+    }
 };
 WarpKind warp_kind(const StepArgs<float> &s);
 // Batches: the per-case argument blocks (tensor maps and scalars) in a device

@@ -92,21 +92,34 @@ constexpr uint32_t kSideSlot = 256;              // bytes per side-ring slot (14
 constexpr uint32_t kFSideSlot = 128;             // bytes per force side-ring slot (32 used)
 constexpr uint32_t kFRowBytes = 2u * kCols * sizeof(float);
 
-template <bool FORCE>
+// S2: T2S2-FDLBM2 (Eq. 5.23), whose sweep keeps f^n for the differences of
+// L(f^n) in a per-warp shared ring (FN) and L(f^n) for the update two rows
+// later (LN); the register window holds f~+ (in T2S2-FDLBM1, fbar^{+,h}, with
+// f~+ in the Q ring).  Side rings of 4 columns where a force field or S2
+// needs the room.
+template <bool FORCE, bool S2 = false>
 struct WarpSmem {
+    static constexpr bool kSideRing = FORCE || S2;
     float ring[kStages][9][kCols];                // f~ rows of the window, [pop][window column]
-    // the same rows at the other side of the seam: 64 columns, or with a force
-    // field the 4 columns next to the seam ([pop][4], one 256-byte slot per row)
-    float wrap[kStages][FORCE ? kSideSlot / 4 : 9 * kCols];
+    // the same rows at the other side of the seam: 64 columns, or the 4
+    // columns next to the seam ([pop][4], one 256-byte slot per row)
+    float wrap[kStages][kSideRing ? kSideSlot / 4 : 9 * kCols];
     float fring[FORCE ? kFRing : 1][2][kCols];    // force rows, [component][window column]
     float fwrap[FORCE ? kFRing : 1][kFSideSlot / 4];  // force columns next to the seam, [2][4]
-    f2 Q[kQRing][9][kLanes];                      // f~+ of the lane's two columns
+    f2 Q[S2 ? 1 : kQRing][9][kLanes];             // f~+ of the lane's two columns
+    f2 FN[S2 ? kQRing : 1][8][kLanes];            // S2: f^n of populations 1..8, rows r-4 .. r
+    f2 LN[S2 ? 3 : 1][8][kLanes];                 // S2: scaled L(f^n) of rows r-4 .. r-2
     uint64_t bar[kStages];
 };
 static_assert(offsetof(WarpSmem<false>, wrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
 static_assert(offsetof(WarpSmem<true>, wrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
 static_assert(offsetof(WarpSmem<true>, fring) % 128 == 0, "tensor-copy destinations are 128-B aligned");
 static_assert(offsetof(WarpSmem<true>, fwrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
+using WarpSmemS2 = WarpSmem<false, true>;
+using WarpSmemS2F = WarpSmem<true, true>;
+static_assert(offsetof(WarpSmemS2, wrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
+static_assert(offsetof(WarpSmemS2F, fring) % 128 == 0, "tensor-copy destinations are 128-B aligned");
+static_assert(offsetof(WarpSmemS2F, fwrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
 
 // Scalars and pointers of one step of one grid.
 struct ArgsS {
@@ -133,6 +146,9 @@ struct ArgsS {
     // analogue for fbar), and 3 x the weights of the forcing term in fbar^{+,h}
     // (Eq. 2.34 after Eq. 2.19), f~+ (Eq. 2.20) and f* (Eq. 2.32)
     float hdt, hh, k_bar, k_til, k_star;
+    // S2 (T2S2-FDLBM2): Eq. 2.52 at h = dt for f^n, and 3 x the weight of its
+    // forcing term
+    float b_phys, k_phys;
     int wx, wy;  // walled axes
 };
 
@@ -197,6 +213,20 @@ __device__ __forceinline__ f2 xtaps(const f2 c[3], int sgn, f2 v0, f2 acc)
     acc = fma2(c[0], make_float2(Lhi, v0.x), acc);
     acc = fma2(c[1], make_float2(v0.y, Rlo), acc);
     return fma2(c[2], make_float2(Rlo, Rhi), acc);
+}
+
+// The same from the neighbouring lanes' pairs L (lane l - 1) and R (lane
+// l + 1), read from shared memory instead of shuffled.
+__device__ __forceinline__ f2 xtaps_lr(const f2 c[3], int sgn, f2 L, f2 v0, f2 R, f2 acc)
+{
+    if (sgn > 0) {
+        acc = fma2(c[0], make_float2(v0.y, R.x), acc);
+        acc = fma2(c[1], make_float2(L.y, v0.x), acc);
+        return fma2(c[2], make_float2(L.x, L.y), acc);
+    }
+    acc = fma2(c[0], make_float2(L.y, v0.x), acc);
+    acc = fma2(c[1], make_float2(v0.y, R.x), acc);
+    return fma2(c[2], make_float2(R.x, R.y), acc);
 }
 
 // The same in y from the lane's own window (rows k-2 .. k+2 as vm2 .. vp2).
@@ -291,13 +321,20 @@ __host__ __device__ inline Tile interior_tile(const ArgsS &a, int bx, int by)
 // GRID: how the update's weights are made to sum to zero (update_weights).
 // FORCE: a body-acceleration field (Eqs. 3.3 and 3.12), whose rows arrive by
 // tensor copy with the rows of f~ into a 5-row ring (stage B reads row r-2).
-template <bool INC, bool GRID, bool FORCE>
+// S2: the second sequence of Sec. 2D (T2S2-FDLBM2, h = dt): stage A makes f^n
+// (Eq. 2.52) and f~+ (Eq. 2.20); stage B makes fbar = f~+ - dt xi.grad f~+
+// and f^{n+1} (Eq. 2.52) as stage B of T2S2-FDLBM1 does from fbar^{+,h}, and
+// L(f^n) of its row; stage C adds dt/2 [L(f^n) + L(f^{n+1})] to f~+ (Eq.
+// 5.23), both differences with the update weights of scale -dt/2 m.
+template <bool INC, bool GRID, bool FORCE, bool S2 = false>
 __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin,
                                           const CUtensorMap *tside, const CUtensorMap *tf,
                                           const CUtensorMap *tfside, Tile tile,
                                           unsigned char *smem_raw)
 {
-    WarpSmem<FORCE> &sm = *reinterpret_cast<WarpSmem<FORCE> *>(smem_raw);
+    using Smem = WarpSmem<FORCE, S2>;
+    constexpr bool SIDE = Smem::kSideRing;
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
 
     const int l = threadIdx.x;
     const int x0 = tile.x0;  // first output column
@@ -312,21 +349,21 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
     // from x = nx - 4 (first window) or x = 0 (last window)
     const bool wrap_lo = xs < 0, wrap_hi = xs + kCols > a.nx;
     const int wrap_x = wrap_lo ? a.nx - kHalo : 0;
-    uint32_t rd = (uint32_t)offsetof(WarpSmem<FORCE>, ring) + 8u * (uint32_t)l;
+    uint32_t rd = (uint32_t)offsetof(Smem, ring) + 8u * (uint32_t)l;
     uint32_t pstride = kCols * sizeof(float);  // bytes between populations
-    uint32_t frd = (uint32_t)offsetof(WarpSmem<FORCE>, fring) + 8u * (uint32_t)l;
+    uint32_t frd = (uint32_t)offsetof(Smem, fring) + 8u * (uint32_t)l;
     uint32_t fstride = kCols * sizeof(float);  // bytes between force components
-    if (!FORCE) {
-        if (xc < 0) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc + kHalo);
-        if (xc >= a.nx) rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)(xc - a.nx);
+    if (!SIDE) {
+        if (xc < 0) rd = (uint32_t)offsetof(Smem, wrap) + 4u * (uint32_t)(xc + kHalo);
+        if (xc >= a.nx) rd = (uint32_t)offsetof(Smem, wrap) + 4u * (uint32_t)(xc - a.nx);
     } else {
         // side rings of 4 columns; lanes further past the seam read the main
         // ring's zero fill (their values reach no output)
         const int side = xc < 0 ? xc + kHalo : (xc >= a.nx && xc < a.nx + kSide ? xc - a.nx : -1);
         if (side >= 0) {
-            rd = (uint32_t)offsetof(WarpSmem<FORCE>, wrap) + 4u * (uint32_t)side;
+            rd = (uint32_t)offsetof(Smem, wrap) + 4u * (uint32_t)side;
             pstride = kSide * sizeof(float);
-            frd = (uint32_t)offsetof(WarpSmem<FORCE>, fwrap) + 4u * (uint32_t)side;
+            frd = (uint32_t)offsetof(Smem, fwrap) + 4u * (uint32_t)side;
             fstride = kSide * sizeof(float);
         }
     }
@@ -336,7 +373,8 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
     // ---- constants: the x weights carry -h m_x (stage B) and -dt m_x (stage C)
     const f2 rho0 = bc(a.rho0);
     const f2 mx2 = make_float2(__ldg(a.mx + gx), __ldg(a.mx + (gx + 1 < a.nx ? gx + 1 : gx)));
-    const f2 nhx = mul2(bc(-a.h), mx2), ndx = mul2(bc(-a.dt), mx2);
+    // (S2: the update's two differences at scale -dt/2)
+    const f2 nhx = mul2(bc(-a.h), mx2), ndx = mul2(bc(S2 ? -a.hdt : -a.dt), mx2);
     const f2 axB[3] = {mul2(nhx, bc(a.w[0])), mul2(nhx, bc(a.w[2])), mul2(nhx, bc(a.w[3]))};
     // stage C: taps on the weight grid of each column and the centre as minus
     // their sum, so that the x weights of the update sum to exactly zero
@@ -352,14 +390,15 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
     }
     const f2 cxB = mul2(nhx, bc(a.w[1]));
     const f2 c_xB = add2(bc(1.f), cxB);
-    const f2 bbar = bc(a.b_bar), btil = bc(a.b_til);
+    const f2 bbar = bc(S2 ? a.b_phys : a.b_bar), btil = bc(a.b_til);
 
     const uint32_t bar0 = smem_addr(&sm.bar[0]);
     const uint32_t ring0 = smem_addr(&sm.ring[0][0][0]), wrap0 = smem_addr(&sm.wrap[0][0]);
     const uint32_t fring0 = smem_addr(&sm.fring[0][0][0]), fwrap0 = smem_addr(&sm.fwrap[0][0]);
     const bool seam = wrap_lo || wrap_hi;
-    const uint32_t tx = FORCE ? kRowBytes + kFRowBytes + (seam ? 9u * kSide * 4u + 2u * kSide * 4u : 0u)
-                              : (seam ? 2u * kRowBytes : kRowBytes);
+    const uint32_t tx = SIDE ? kRowBytes + (seam ? 9u * kSide * 4u : 0u) +
+                                   (FORCE ? kFRowBytes + (seam ? 2u * kSide * 4u : 0u) : 0u)
+                             : (seam ? 2u * kRowBytes : kRowBytes);
     // next row to request
     int ld_row = wrap_index(y0 - kHalo, a.ny);
     // rows into f~ slot `slot` and (force field) force slot `fslot`
@@ -370,15 +409,16 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx)
                          : "memory");
             tensor_copy_3d(ring0 + (uint32_t)slot * kRowBytes, tin, xs, ld_row, 0, bar);
-            if (!FORCE) {
+            if (!SIDE) {
                 if (seam)
                     tensor_copy_3d(wrap0 + (uint32_t)slot * kRowBytes, tin, wrap_x, ld_row, 0, bar);
             } else {
-                tensor_copy_3d(fring0 + (uint32_t)fslot * kFRowBytes, tf, xs, ld_row, 0, bar);
+                if (FORCE) tensor_copy_3d(fring0 + (uint32_t)fslot * kFRowBytes, tf, xs, ld_row, 0, bar);
                 if (seam) {
                     tensor_copy_3d(wrap0 + (uint32_t)slot * kSideSlot, tside, wrap_x, ld_row, 0, bar);
-                    tensor_copy_3d(fwrap0 + (uint32_t)fslot * kFSideSlot, tfside, wrap_x, ld_row, 0,
-                                   bar);
+                    if (FORCE)
+                        tensor_copy_3d(fwrap0 + (uint32_t)fslot * kFSideSlot, tfside, wrap_x, ld_row, 0,
+                                       bar);
                 }
             }
         }
@@ -402,12 +442,13 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
     int rs = wrap_index(y0 - 6, a.ny), rq = wrap_index(y0 - 8, a.ny);
     float myB = __ldg(a.my + rs), myC = __ldg(a.my + rq);
     int slot = 0;          // iteration mod 3
+    int lw = 0;            // S2: LN slot written at this iteration (mod 3); read: the next one
     uint32_t parity = 0;   // mbarrier phase parity of the current slot
     bool timed_out = false;
     // force of the lane's pair from force slot fs (components x, y)
     auto force_of = [&](int fs, f2 &Fx, f2 &Fy) {
         const unsigned char *src = frd_base + fs * kFRowBytes;
-        if (FORCE && fstride != kCols * sizeof(float)) src = frd_base + fs * kFSideSlot;
+        if (SIDE && fstride != kCols * sizeof(float)) src = frd_base + fs * kFSideSlot;
         Fx = *reinterpret_cast<const f2 *>(src);
         Fy = *reinterpret_cast<const f2 *>(src + fstride);
     };
@@ -420,19 +461,24 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
         if (!mbar_wait_bounded(&sm.bar[slot], parity)) timed_out = true;
         {
             const unsigned char *src =
-                rd_base + slot * (FORCE && pstride != kCols * sizeof(float) ? kSideSlot : kRowBytes);
+                rd_base + slot * (SIDE && pstride != kCols * sizeof(float) ? kSideSlot : kRowBytes);
             f2 g[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i)
-                g[i] = *reinterpret_cast<const f2 *>(src + i * (FORCE ? pstride : kCols * sizeof(float)));
+                g[i] = *reinterpret_cast<const f2 *>(src + i * (SIDE ? pstride : kCols * sizeof(float)));
             f2 geq[9];
             if (!FORCE) {
                 equilibrium2_j(INC ? moments2_j_incomp(g, bc(a.inv_rho0)) : moments2_j(g, rho0), geq);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const f2 neq = sub2(geq[i], g[i]);
-                    Pw[i][p0] = fma2(bbar, neq, g[i]);
-                    sm.Q[PH][i][l] = fma2(btil, neq, g[i]);
+                    if (!S2) {
+                        Pw[i][p0] = fma2(bbar, neq, g[i]);
+                        sm.Q[PH][i][l] = fma2(btil, neq, g[i]);
+                    } else {
+                        Pw[i][p0] = fma2(btil, neq, g[i]);                        // f~+
+                        if (i > 0) sm.FN[PH][i - 1][l] = fma2(bbar, neq, g[i]);  // f^n
+                    }
                 }
             } else {
                 f2 Fx, Fy;
@@ -453,17 +499,23 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
                 }
                 // Eq. 3.12 at the equilibrium of Eq. 3.2 (at rho0 under the
                 // incompressible one)
-                force_add2(geq, INC ? sub2(rho0, m.drho) : rho0, Fx, Fy, uF, bc(a.k_bar),
+                force_add2(geq, INC ? sub2(rho0, m.drho) : rho0, Fx, Fy, uF, bc(S2 ? a.k_phys : a.k_bar),
                            bc(a.k_til), P, Qv);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
-                    Pw[i][p0] = P[i];
-                    sm.Q[PH][i][l] = Qv[i];
+                    if (!S2) {
+                        Pw[i][p0] = P[i];
+                        sm.Q[PH][i][l] = Qv[i];
+                    } else {
+                        Pw[i][p0] = Qv[i];
+                        if (i > 0) sm.FN[PH][i - 1][l] = P[i];
+                    }
                 }
             }
         }
         // ------------------------------------------------------------ B (row r-2)
         {
+            const float myb = myB;
             const float nhy = -a.h * myB;
             rs = rs + 1 == a.ny ? 0 : rs + 1;
             myB = __ldg(a.my + rs);
@@ -506,13 +558,38 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
             }
 #pragma unroll
             for (int i = 0; i < 9; ++i) Sw[i][p0] = fs[i];
+            if (S2) {
+                // -dt/2 (m_x D_x + m_y D_y) f^n of row r-2 (Eq. 5.23's L(f^n),
+                // scaled as the update's other difference), from the f^n ring:
+                // y from the lane's own column, x from the neighbouring lanes'
+                // pairs; stored for stage C two rows on
+                float tl[3], cl;
+                update_weights<GRID>(-a.hdt * myb, a.w, tl, cl);
+                const f2 byl[3] = {bc(tl[0]), bc(tl[1]), bc(tl[2])};
+                const f2 c_yl = bc(cl), c_dl = add2(c_yl, cxC);
+                const int lm = (l + kLanes - 1) & (kLanes - 1), lp = (l + 1) & (kLanes - 1);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    const f2 v0 = sm.FN[p2][i - 1][l];
+                    f2 acc;
+                    if (cx(i) != 0 && cy(i) != 0) acc = mul2(c_dl, v0);
+                    else if (cx(i) != 0) acc = mul2(cxC, v0);
+                    else acc = mul2(c_yl, v0);
+                    if (cx(i) != 0)
+                        acc = xtaps_lr(axC, cx(i), sm.FN[p2][i - 1][lm], v0, sm.FN[p2][i - 1][lp], acc);
+                    if (cy(i) != 0)
+                        acc = ytaps(byl, cy(i), sm.FN[p4][i - 1][l], sm.FN[p3][i - 1][l],
+                                    sm.FN[p1][i - 1][l], sm.FN[p0][i - 1][l], acc);
+                    sm.LN[lw][i - 1][l] = acc;
+                }
+            }
         }
         // ------------------------------------------------------------ C (row r-4)
         // f* rows r-6 .. r-2 sit in slots p4, p3, p2, p1, p0 of Sw.
         {
             const int qg = rq;
             rq = rq + 1 == a.ny ? 0 : rq + 1;
-            const float ndy = -a.dt * myC;
+            const float ndy = (S2 ? -a.hdt : -a.dt) * myC;
             myC = __ldg(a.my + rq);
             // the y weights of the update, summing to zero exactly
             float ty[3], cyw;
@@ -531,7 +608,11 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const f2 v0 = Sw[i][p2];
-                f2 acc = sm.Q[p4][i][l];
+                // T2S2-FDLBM1: f~+ from its ring; S2: f~+ of row r-4 from the
+                // window and its L(f^n) term, stored two rows ago
+                f2 acc;
+                if (!S2) acc = sm.Q[p4][i][l];
+                else acc = i == 0 ? Pw[0][p4] : add2(Pw[i][p4], sm.LN[lw == 2 ? 0 : lw + 1][i - 1][l]);
                 if (cx(i) != 0 && cy(i) != 0) acc = fma2(c_d, v0, acc);
                 else if (cx(i) != 0) acc = fma2(cxC, v0, acc);
                 else if (cy(i) != 0) acc = fma2(c_y, v0, acc);
@@ -550,6 +631,7 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
             slot = 0;
             parity ^= 1u;
         }
+        if (S2) lw = lw == 2 ? 0 : lw + 1;
     };
 
     for (int k = 0; k < iters; k += 5) {
@@ -571,14 +653,14 @@ __device__ __forceinline__ void warp_tile(const ArgsS &a, const CUtensorMap *tin
 }
 
 // The interior: tile (blockIdx.x, blockIdx.y) of the rectangle.
-template <bool INC, bool GRID, bool FORCE>
+template <bool INC, bool GRID, bool FORCE, bool S2>
 __global__ void __launch_bounds__(kLanes, FDLBM_WARP_MIN_BLOCKS)
     k_step_fused_warp(const __grid_constant__ ArgsW w)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const Tile tile = interior_tile(w.s, blockIdx.x, blockIdx.y);
     if (tile.y0 >= tile.y1) return;  // uniform over the warp
-    warp_tile<INC, GRID, FORCE>(w.s, &w.tin, &w.tside, &w.tf, &w.tfside, tile, smem_raw);
+    warp_tile<INC, GRID, FORCE, S2>(w.s, &w.tin, &w.tside, &w.tf, &w.tfside, tile, smem_raw);
 }
 
 // Shared-memory offset of a batch case's scalars, after the rings.
@@ -728,7 +810,7 @@ cudaError_t fused_warp_encode(WarpMaps *m, const float *state0, const float *sta
     const float *st[2] = {state0, state1};
     for (int b = 0; b < 2; ++b) {
         cudaError_t e = encode(m->state[b], st[b], nx, ny, pitch, plane, 9, kCols);
-        if (e == cudaSuccess && force) e = encode(m->side[b], st[b], nx, ny, pitch, plane, 9, kSide);
+        if (e == cudaSuccess) e = encode(m->side[b], st[b], nx, ny, pitch, plane, 9, kSide);
         if (e != cudaSuccess) return e;
     }
     m->has_force = force != nullptr;
@@ -740,11 +822,11 @@ cudaError_t fused_warp_encode(WarpMaps *m, const float *state0, const float *sta
     return cudaSuccess;
 }
 
-template <bool INC, bool GRID, bool FORCE>
+template <bool INC, bool GRID, bool FORCE, bool S2>
 cudaError_t launch_t(const ArgsW &a, dim3 grid, cudaStream_t stream)
 {
-    constexpr size_t smem = sizeof(WarpSmem<FORCE>);
-    auto kern = k_step_fused_warp<INC, GRID, FORCE>;
+    constexpr size_t smem = sizeof(WarpSmem<FORCE, S2>);
+    auto kern = k_step_fused_warp<INC, GRID, FORCE, S2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<grid, kLanes, smem, stream>>>(a);
@@ -842,8 +924,8 @@ ArgsW make_args(const StepArgs<float> &s, const WarpMaps &maps, int cur)
     std::memset(&w, 0, sizeof w);
     const bool force = s.force != nullptr;
     std::memcpy(&w.tin, maps.state[cur], sizeof(CUtensorMap));
+    std::memcpy(&w.tside, maps.side[cur], sizeof(CUtensorMap));
     if (force) {
-        std::memcpy(&w.tside, maps.side[cur], sizeof(CUtensorMap));
         std::memcpy(&w.tf, maps.force, sizeof(CUtensorMap));
         std::memcpy(&w.tfside, maps.force_side, sizeof(CUtensorMap));
     }
@@ -875,6 +957,8 @@ ArgsW make_args(const StepArgs<float> &s, const WarpMaps &maps, int cur)
     a.k_bar = 3.0f * s.c.c_bar;
     a.k_til = 3.0f * s.c.c_til;
     a.k_star = 3.0f * s.c.c_star;
+    a.b_phys = s.c.b_phys;
+    a.k_phys = 3.0f * s.c.c_phys;
     a.wx = s.bc_x == FDLBM_WALL;
     a.wy = s.bc_y == FDLBM_WALL;
     split(a);
@@ -889,6 +973,7 @@ WarpKind warp_kind(const StepArgs<float> &s)
     k.inc = s.c.incomp != 0;
     k.grid = !(s.st.wm1 >= 0.55f * std::fabs(s.st.w1));
     k.force = s.force != nullptr;
+    k.s2 = s.scheme == FDLBM_SCHEME_T2S2_2;
     return k;
 }
 
@@ -903,7 +988,8 @@ cudaError_t launch_fused_warp(const StepArgs<float> &s, const WarpMaps &maps, in
     if (e != cudaSuccess || tile_count(a.s) <= 0) return e;
     const dim3 grid(a.s.nix, interior_rows(a.s));
     return dispatch(k, [&](auto inc, auto gr, auto fo) {
-        return launch_t<decltype(inc)::value, decltype(gr)::value, decltype(fo)::value>(a, grid, stream);
+        constexpr bool I = decltype(inc)::value, G = decltype(gr)::value, F = decltype(fo)::value;
+        return k.s2 ? launch_t<I, G, F, true>(a, grid, stream) : launch_t<I, G, F, false>(a, grid, stream);
     });
 }
 
@@ -933,6 +1019,7 @@ cudaError_t launch_batched_warp(const void *args, const int *blk_case, const int
                                 int blk_off, int nblocks, WarpKind k, cudaStream_t stream)
 {
     if (nblocks <= 0) return cudaSuccess;
+    if (k.s2) return cudaErrorInvalidValue;  // batches run T2S2-FDLBM2 on the scalar sweep
     return dispatch(k, [&](auto inc, auto gr, auto fo) {
         constexpr bool I = decltype(inc)::value, G = decltype(gr)::value, F = decltype(fo)::value;
         constexpr size_t smem = kArgsOff<F> + sizeof(ArgsS);
@@ -968,7 +1055,7 @@ int fused_warp_blocks_per_sm()
 {
     int n = 0;
     constexpr size_t smem = sizeof(WarpSmem<false>);
-    auto kern = k_step_fused_warp<false, false, false>;
+    auto kern = k_step_fused_warp<false, false, false, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kLanes, smem) != cudaSuccess) return 0;
     return n;

@@ -106,7 +106,7 @@ def test_workspace_and_validation_without_gpu(B):
     o.path = B.PATH_STAGED
     assert L.fdlbm_workspace_bytes(ctypes.byref(grid), ctypes.byref(o)) > n32
     # walled grids take the fused path (Eq. 3.10 inside the sweep), for both
-    # schemes; the warp-tile kernel does not run T2S2-FDLBM2
+    # schemes; the warp-tile kernel runs T2S2-FDLBM2 on periodic grids only
     wa = I.wall_axis(20, 0.0, 1.0)
     wgrid, keep2 = B.make_grid(xa, wa)
     o.path = B.PATH_FUSED
@@ -115,7 +115,7 @@ def test_workspace_and_validation_without_gpu(B):
     assert L.fdlbm_workspace_bytes(ctypes.byref(wgrid), ctypes.byref(o)) > 0
     h = ctypes.c_void_p()
     o.variant = B.VARIANT_WARP
-    assert L.fdlbm_create(ctypes.byref(grid), None, 0.01, 0.5, 0.1, ctypes.byref(o),
+    assert L.fdlbm_create(ctypes.byref(wgrid), None, 0.01, 0.5, 0.1, ctypes.byref(o),
                           ctypes.byref(h)) == -5
     o.variant = B.VARIANT_AUTO
     # invalid arguments are rejected before any device work

@@ -50,12 +50,14 @@ def _mean_flow_run(n, steps, precision, **kw):
 # blend 0.1 takes the Sterbenz-ordered weights of the warp-tile kernel's
 # update, blend 0.3 the weight-grid ones
 @pytest.mark.parametrize("variant,blend,scheme", [("warp", 0.1, 1), ("warp", 0.3, 1), ("scalar", 0.1, 1),
-                                                  ("scalar", 0.3, 1), ("auto", 0.1, 2)])
+                                                  ("scalar", 0.3, 1), ("auto", 0.1, 2), ("auto", 0.3, 2),
+                                                  ("scalar", 0.1, 2)])
 def test_fp32_momentum_mass_conserved_over_20000_steps(variant, blend, scheme):
     desc, dm, dj = _mean_flow_run(256, 20000, "fp32", blend=blend, variant=variant, scheme=scheme)
     print(f"{desc} blend {blend}: relative change after 20000 steps: mass {dm:.2e}, "
           f"momentum ({dj[0]:.2e}, {dj[1]:.2e})")
-    expect = {"warp": "fused-warp", "scalar": "fused", "auto": "fused-scheme2"}[variant]
+    expect = {("warp", 1): "fused-warp", ("scalar", 1): "fused", ("auto", 2): "fused-warp-scheme2",
+              ("scalar", 2): "fused-scheme2"}[variant, scheme]
     assert desc.split()[0] == expect, desc
     assert dj.max() < 2e-5
     assert dm < 1e-6

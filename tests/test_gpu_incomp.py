@@ -146,19 +146,22 @@ def test_incomp_walls(precision, tol, path, bcx, bcy, nx, ny, rows):
                   label=f"{s.describe} {bcx}/{bcy} {nx}x{ny}")
 
 
-@pytest.mark.parametrize("walls,precision,tol", [(True, "fp64", FP64_TOL), (False, "fp64", FP64_TOL),
-                                                 (True, "fp32", FP32_L2)])
-def test_incomp_scheme2(walls, precision, tol):
+@pytest.mark.parametrize("walls,precision,tol,nx", [(True, "fp64", FP64_TOL, 24), (False, "fp64", FP64_TOL, 24),
+                                                    (True, "fp32", FP32_L2, 24), (False, "fp32", FP32_L2, 128)])
+def test_incomp_scheme2(walls, precision, tol, nx):
     """T2S2-FDLBM2 with the incompressible equilibrium: the staged kernels on an
-    FP64 channel, the fused sweeps on an FP32 channel and a periodic grid."""
-    nx, ny = 24, 20
+    FP64 channel, the fused sweeps on an FP32 channel and a periodic grid, and
+    the warp-tile kernel on a periodic FP32 grid of 128 columns."""
+    ny = 20
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.tanh_axis(ny - 1, 1.5) if walls else I.periodic_axis(ny, 0.0, 0.8)
     force = 1e-3 * np.random.default_rng(4).uniform(-1, 1, size=(2, ny, nx))
     s, o = _pair(xa, ya, nu=0.02, cfl=0.3, beta=0.2, force=force, scheme=2, precision=precision,
                  wall_u=[(0, 0), (0, 0), (0, 0), (0.05, 0.0)] if walls else None)
     staged = walls and precision == "fp64"
-    assert s.describe.startswith("staged-scheme2" if staged else "fused-scheme2"), s.describe
+    warp = not walls and precision == "fp32" and nx >= 64
+    assert s.describe.startswith("staged-scheme2" if staged else
+                                 "fused-warp-scheme2" if warp else "fused-scheme2"), s.describe
     _init_both(s, o, I.random_fields(nx, ny, 5, drho=0.05))
     s.step(15)
     o.step(15)

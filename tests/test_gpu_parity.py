@@ -373,20 +373,28 @@ def test_t2s2_fdlbm2_periodic_force_metrics(precision, tol, path):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_L2)])
+@pytest.mark.parametrize("variant", ["scalar", "auto"])
 @pytest.mark.parametrize("nx,ny,rows,force", [(133, 37, 0, False), (250, 21, 1, True), (4, 9, 0, True),
-                                              (128, 64, 5, False), (500, 13, 3, False)])
-def test_t2s2_fdlbm2_fused_ragged(precision, tol, nx, ny, rows, force):
-    """The fused T2S2-FDLBM2 sweep on ragged strips and row segments (tile
-    heights 1, 3, 5 and automatic, a grid narrower than the halo), with and
-    without a force field, random metrics: 1 + 11 steps against the oracle."""
+                                              (128, 64, 5, False), (500, 13, 3, False),
+                                              (68, 45, 2, True), (256, 21, 1, True), (1024, 9, 0, False),
+                                              (112, 30, 4, True)])
+def test_t2s2_fdlbm2_fused_ragged(precision, tol, variant, nx, ny, rows, force):
+    """The fused T2S2-FDLBM2 sweeps on ragged strips and row segments (tile
+    heights 1-5 and automatic, a grid narrower than the halo), with and
+    without a force field, random metrics: 1 + 11 steps against the oracle.
+    variant auto: the warp-tile kernel for FP32 widths of 64 and more that
+    are multiples of 4 (one window with its seam copies, a width that is a
+    multiple of the 56-column window, several windows), else the scalar
+    sweep."""
     xa = I.periodic_axis(nx, 0.0, 1.0)
     ya = I.periodic_axis(ny, 0.0, 0.7)
     xa.metric = I.random_metric(nx, 11, base=nx, spread=0.4)
     ya.metric = I.random_metric(ny, 12, base=ny / 0.7, spread=0.4)
     F = 1e-3 * np.random.default_rng(nx + ny).uniform(-1, 1, size=(2, ny, nx)) if force else None
     s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, has_force=force, precision=precision, scheme=2,
-              rows_per_cta=rows)
-    assert s.describe.startswith("fused-scheme2"), s.describe
+              rows_per_cta=rows, variant=variant)
+    warp = variant == "auto" and precision == "fp32" and nx >= 64 and nx % 4 == 0
+    assert s.describe.startswith("fused-warp-scheme2" if warp else "fused-scheme2"), s.describe
     o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=F, scheme=2)
     if force:
         s.set_force(F)
@@ -608,6 +616,7 @@ def test_fp32_field_io_matches_fp64(precision, where):
 @pytest.mark.parametrize("precision,tol,scheme,eq,force", [("fp32", 1e-8, 1, "standard", False),
                                                            ("fp64", FP64_TOL, 1, "standard", False),
                                                            ("fp32", 1e-8, 2, "standard", False),
+                                                           ("fp32", 1e-8, 2, "standard", True),
                                                            ("fp64", FP64_TOL, 2, "standard", False),
                                                            ("fp32", 1e-8, 1, "incompressible", False),
                                                            ("fp32", 1e-8, 1, "standard", True)])
