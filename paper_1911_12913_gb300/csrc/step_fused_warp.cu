@@ -106,11 +106,15 @@ struct WarpSmem {
     float wrap[kStages][kSideRing ? kSideSlot / 4 : 9 * kCols];
     float fring[FORCE ? kFRing : 1][2][kCols];    // force rows, [component][window column]
     float fwrap[FORCE ? kFRing : 1][kFSideSlot / 4];  // force columns next to the seam, [2][4]
-    f2 Q[S2 ? 1 : kQRing][9][kLanes];             // f~+ of the lane's two columns
-    f2 FN[S2 ? kQRing : 1][8][kLanes];            // S2: f^n of populations 1..8, rows r-4 .. r
-    f2 LN[S2 ? 3 : 1][8][kLanes];                 // S2: scaled L(f^n) of rows r-4 .. r-2
+    // (the members an instance does not use shrink to one element, so that
+    // they cost no occupancy)
+    f2 Q[S2 ? 1 : kQRing][S2 ? 1 : 9][S2 ? 1 : kLanes];  // f~+ of the lane's two columns
+    f2 FN[S2 ? kQRing : 1][S2 ? 8 : 1][S2 ? kLanes : 1];  // S2: f^n of populations 1..8, rows r-4 .. r
+    f2 LN[S2 ? 3 : 1][S2 ? 8 : 1][S2 ? kLanes : 1];       // S2: scaled L(f^n) of rows r-4 .. r-2
     uint64_t bar[kStages];
 };
+static_assert(sizeof(WarpSmem<false>) <= 26u * 1024u && sizeof(WarpSmem<true>) <= 23u * 1024u,
+              "T2S2-FDLBM1 instances keep 8 warps per SM");
 static_assert(offsetof(WarpSmem<false>, wrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
 static_assert(offsetof(WarpSmem<true>, wrap) % 128 == 0, "tensor-copy destinations are 128-B aligned");
 static_assert(offsetof(WarpSmem<true>, fring) % 128 == 0, "tensor-copy destinations are 128-B aligned");
