@@ -249,15 +249,5 @@ __device__ __forceinline__ void force_add1(const f2 geq[9], f2 rf, f2 Fx, f2 Fy,
     one(8, sub2(nuF, d), 2);
 }
 
-// sign(c) * D_m f at the centre from f(k-2..k+2); w = {wm1, w0, w1, w2} of
-// make_stencil (lattice.cuh).
-__device__ __forceinline__ f2 stencil2(const float w[4], int sgn, f2 vm2, f2 vm1, f2 v0, f2 vp1,
-                                       f2 vp2)
-{
-    if (sgn > 0)
-        return fma2(bc(w[3]), vm2, fma2(bc(w[2]), vm1, fma2(bc(w[1]), v0, mul2(bc(w[0]), vp1))));
-    return fma2(bc(w[3]), vp2, fma2(bc(w[2]), vp1, fma2(bc(w[1]), v0, mul2(bc(w[0]), vm1))));
-}
-
 }  // namespace packed
 }  // namespace fdlbm

@@ -78,50 +78,6 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2)
 // when every block has passed the barrier after that counter's last use.  A
 // barrier that times out sets every case's error flag and the block leaves;
 // the others then time out at their next barrier.
-// Persistent batched: all tiles of all cases for nsteps steps in one
-// cooperative launch (all blocks resident).  Within a step the blocks fetch
-// tiles from a global counter, as the hardware would hand out the blocks of
-// one launch; one grid barrier separates consecutive steps, since a step reads
-// the state the previous one wrote around its tile.  Steps alternate between
-// two counters: block 0 clears the next step's counter at the start of a step,
-// when every block has passed the barrier after that counter's last use.  A
-// barrier that times out sets every case's error flag and the block leaves;
-// the others then time out at their next barrier.
-// One tile of the persistent batch, out of line: the tile sweep then gets the
-// registers of the batched kernel, and the step loop of the caller keeps only
-// a few values live across the call.  The case's argument block goes to
-// dynamic shared memory after the sweep's rings.
-template <class R>
-__device__ __noinline__ void persistent_tile(const StepArgs<R> *cases, const int *blk_case,
-                                             const int *blk_start, const int *tiles_x, int b)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<R> &sm = *reinterpret_cast<Smem<R> *>(smem_raw);
-    unsigned char *abuf = smem_raw + kArgOffset<R>;
-    static_assert(sizeof(StepArgs<R>) % 4 == 0, "argument block is copied as 32-bit words");
-    const int c = blk_case[b];
-    {
-        const int *src = reinterpret_cast<const int *>(cases + c);
-        int *dst = reinterpret_cast<int *>(abuf);
-        for (int q = threadIdx.x; q < (int)(sizeof(StepArgs<R>) / 4); q += blockDim.x) dst[q] = src[q];
-    }
-    __syncthreads();
-    const StepArgs<R> &a = *reinterpret_cast<const StepArgs<R> *>(abuf);
-    const int lb = b - blk_start[c], ns = tiles_x[c];
-    const int y0 = (lb / ns) * a.rows;
-    if (y0 < a.ny)  // uniform over the block
-        sweep_tile<R, true, false>(a, sm, (lb % ns) * (NT - 2 * kHalo), y0);
-}
-
-// Persistent batched: all tiles of all cases for nsteps steps in one
-// cooperative launch (all blocks resident).  Within a step the blocks fetch
-// tiles from a global counter, as the hardware would hand out the blocks of
-// one launch; one grid barrier separates consecutive steps, since a step reads
-// the state the previous one wrote around its tile.  Steps alternate between
-// two counters: block 0 clears the next step's counter at the start of a step,
-// when every block has passed the barrier after that counter's last use.  A
-// barrier that times out sets every case's error flag and the block leaves;
-// the others then time out at their next barrier.
 template <class R>
 __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2)
     kp_step_fused_walls(const BatchTables t, GridBarrier *bar, int parity0, int nsteps,
