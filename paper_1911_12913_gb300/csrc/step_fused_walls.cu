@@ -26,10 +26,10 @@ constexpr size_t kPersistSmem = kArgOffset<R> + sizeof(StepArgs<R>);
 
 // PF (metric and force a row ahead): the single-grid and batched FP32 sweeps,
 // whose registers allow it.
-template <class R, bool FORCE, bool PF = sizeof(R) == 4>
+template <class R, bool FORCE, bool PF = sizeof(R) == 4, bool TAIL = false>
 __device__ __forceinline__ void sweep_tile(const StepArgs<R> &a, Smem<R> &sm, int x0, int y0)
 {
-    walls_sweep::sweep_tile<R, FORCE, NT, PF>(a, sm, x0, a.nx, y0, min(y0 + a.rows, a.ny));
+    walls_sweep::sweep_tile<R, FORCE, NT, PF, TAIL>(a, sm, x0, a.nx, y0, min(y0 + a.rows, a.ny));
 }
 
 template <class R, bool FORCE>
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 3 : 2)
             const int lb = b - t.blk_start[c], ns = t.tiles_x[c];
             const int y0 = (lb / ns) * a.rows;
             if (y0 < a.ny)  // uniform over the block
-                sweep_tile<R, true, false>(a, sm, (lb % ns) * (NT - 2 * kHalo), y0);
+                sweep_tile<R, true, false, true>(a, sm, (lb % ns) * (NT - 2 * kHalo), y0);
         }
         if (!grid_barrier(bar, gen, spin_limit)) {
             if (threadIdx.x == 0) {

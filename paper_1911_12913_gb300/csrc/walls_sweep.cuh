@@ -298,7 +298,10 @@ struct SweepW {
 };
 
 // One tile: output columns x0 .. x0 + NT - 9 below xhi and rows y0 .. y1 - 1.
-template <class R, bool FORCE, int NT, bool PF = false>
+// TAIL: the rows past the last full group of five in a separate copy of the
+// row phases (twice the code: faster only where instruction fetch does not
+// limit, the persistent batch kernel).
+template <class R, bool FORCE, int NT, bool PF = false, bool TAIL = false>
 __device__ __forceinline__ void sweep_tile(const StepArgs<R> &a, Smem<R, NT> &sm, int x0, int xhi,
                                            int y0, int y1)
 {
@@ -333,15 +336,30 @@ __device__ __forceinline__ void sweep_tile(const StepArgs<R> &a, Smem<R, NT> &sm
         sw.force_at(sw.rA, sw.F0[0], sw.F0[1]);
     }
     const int iters = (y1 - y0) + 2 * kHalo;
-    // one copy of each phase of the unrolled row (the rows past the segment's
-    // end skipped by uniform guards): half the code of a separate tail, which
-    // matters to the instruction cache
-    for (int k = 0; k < iters; k += kRing) {
-        sw.template row<0>(k + 1 < iters, k >= 4, k >= 8);
-        if (k + 1 < iters) sw.template row<1>(k + 2 < iters, k + 1 >= 4, k + 1 >= 8);
-        if (k + 2 < iters) sw.template row<2>(k + 3 < iters, k + 2 >= 4, k + 2 >= 8);
-        if (k + 3 < iters) sw.template row<3>(k + 4 < iters, k + 3 >= 4, k + 3 >= 8);
-        if (k + 4 < iters) sw.template row<4>(k + 5 < iters, k + 4 >= 4, k + 4 >= 8);
+    if constexpr (TAIL) {
+        int k = 0;
+        for (; k + kRing <= iters; k += kRing) {
+            sw.template row<0>(k + 1 < iters, k >= 4, k >= 8);
+            sw.template row<1>(k + 2 < iters, k + 1 >= 4, k + 1 >= 8);
+            sw.template row<2>(k + 3 < iters, k + 2 >= 4, k + 2 >= 8);
+            sw.template row<3>(k + 4 < iters, k + 3 >= 4, k + 3 >= 8);
+            sw.template row<4>(k + 5 < iters, k + 4 >= 4, k + 4 >= 8);
+        }
+        if (k < iters) sw.template row<0>(k + 1 < iters, true, k >= 8);
+        if (k + 1 < iters) sw.template row<1>(k + 2 < iters, true, k + 1 >= 8);
+        if (k + 2 < iters) sw.template row<2>(k + 3 < iters, true, k + 2 >= 8);
+        if (k + 3 < iters) sw.template row<3>(k + 4 < iters, true, k + 3 >= 8);
+    } else {
+        // one copy of each phase of the unrolled row (the rows past the
+        // segment's end skipped by uniform guards): half the code of a separate
+        // tail, which matters to the instruction cache
+        for (int k = 0; k < iters; k += kRing) {
+            sw.template row<0>(k + 1 < iters, k >= 4, k >= 8);
+            if (k + 1 < iters) sw.template row<1>(k + 2 < iters, k + 1 >= 4, k + 1 >= 8);
+            if (k + 2 < iters) sw.template row<2>(k + 3 < iters, k + 2 >= 4, k + 2 >= 8);
+            if (k + 3 < iters) sw.template row<3>(k + 4 < iters, k + 3 >= 4, k + 3 >= 8);
+            if (k + 4 < iters) sw.template row<4>(k + 5 < iters, k + 4 >= 4, k + 4 >= 8);
+        }
     }
 }
 
