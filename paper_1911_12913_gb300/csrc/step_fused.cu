@@ -221,16 +221,18 @@ __global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 4 : 2) k_step_fused(const
     // iteration k loads row y0-4+k; stage B from k = 4, stage C from k = 8.
     // Full blocks of five rows first (one straight-line body, which lets the
     // compiler hoist the next row's loads), then the remaining 0..4 rows.
-    // one copy of each phase of the unrolled row (the rows past the segment's
-    // end skipped by uniform guards): half the code of a separate tail, which
-    // matters to the instruction cache
-    for (int k = 0; k < iters; k += kRing) {
+    int k = 0;
+    for (; k + kRing <= iters; k += kRing) {
         sw.template row<0>(k + 1 < iters, k >= 4, k >= 8);
-        if (k + 1 < iters) sw.template row<1>(k + 2 < iters, k + 1 >= 4, k + 1 >= 8);
-        if (k + 2 < iters) sw.template row<2>(k + 3 < iters, k + 2 >= 4, k + 2 >= 8);
-        if (k + 3 < iters) sw.template row<3>(k + 4 < iters, k + 3 >= 4, k + 3 >= 8);
-        if (k + 4 < iters) sw.template row<4>(k + 5 < iters, k + 4 >= 4, k + 4 >= 8);
+        sw.template row<1>(k + 2 < iters, k + 1 >= 4, k + 1 >= 8);
+        sw.template row<2>(k + 3 < iters, k + 2 >= 4, k + 2 >= 8);
+        sw.template row<3>(k + 4 < iters, k + 3 >= 4, k + 3 >= 8);
+        sw.template row<4>(k + 5 < iters, k + 4 >= 4, k + 4 >= 8);
     }
+    if (k < iters) sw.template row<0>(k + 1 < iters, true, k >= 8);
+    if (k + 1 < iters) sw.template row<1>(k + 2 < iters, true, k + 1 >= 8);
+    if (k + 2 < iters) sw.template row<2>(k + 3 < iters, true, k + 2 >= 8);
+    if (k + 3 < iters) sw.template row<3>(k + 4 < iters, true, k + 3 >= 8);
 }
 
 }  // namespace
