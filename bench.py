@@ -512,7 +512,8 @@ def run_walled(stream, n=N_GRID, steps=100, hbm=None):
     size: the warp-tile interior plus the walls-sweep frame): the lid-driven
     cavity on (n+1)^2 uniform nodes (lid U = 0.1, Re = 1000, CFL 0.9), and the
     channel on n x (n+1) nodes (periodic x, walls y), without and with a
-    uniform body force.  Bytes per cell: 72, or 80 with the force field."""
+    uniform body force, and the cavity in T2S2-FDLBM2.  Bytes per cell: 72,
+    or 80 with the force field."""
     import numpy as np
     import torch
     import inputs as I
@@ -523,9 +524,10 @@ def run_walled(stream, n=N_GRID, steps=100, hbm=None):
     wa = I.wall_axis(n, 0.0, 1.0)
     lid = [(0.0, 0.0), (0.0, 0.0), (0.0, 0.0), (0.1, 0.0)]
     out = {}
-    for name, xa, force in (("cavity", wa, None), ("channel", pa, None), ("channel_forced", pa, 1e-6)):
+    for name, xa, force, scheme in (("cavity", wa, None, 1), ("channel", pa, None, 1),
+                                    ("channel_forced", pa, 1e-6, 1), ("cavity_fdlbm2", wa, None, 2)):
         s = FDLBM(xa, wa, nu=1e-4, cfl=0.9, blend=BLEND, precision="fp32", stream=stream,
-                  wall_u=lid, has_force=force is not None)
+                  wall_u=lid, has_force=force is not None, scheme=scheme)
         if force is not None:
             F = np.zeros((2, wa.n, xa.n))
             F[0] = force
@@ -549,9 +551,9 @@ def run_walled(stream, n=N_GRID, steps=100, hbm=None):
                      "launches_per_step": s.kernels_per_step}
         del s
         torch.cuda.empty_cache()
-    out["workload"] = (f"walls Eq. 3.10: cavity {n + 1}^2 uniform, lid U=0.1, Re=1000; channel "
-                       f"{n}x{n + 1} periodic x, walls y, unforced and with F=1e-6; CFL 0.9, "
-                       f"blend {BLEND}, FP32, from rest")
+    out["workload"] = (f"walls Eq. 3.10: cavity {n + 1}^2 uniform, lid U=0.1, Re=1000 (T2S2-FDLBM1 "
+                       f"and T2S2-FDLBM2); channel {n}x{n + 1} periodic x, walls y, unforced and with "
+                       f"F=1e-6; CFL 0.9, blend {BLEND}, FP32, from rest")
     return out
 
 

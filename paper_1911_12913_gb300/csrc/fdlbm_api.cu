@@ -441,11 +441,10 @@ fdlbm_status handle_prepare(const fdlbm_grid *g, const fdlbm_metrics *metrics, d
     if (path < 0) return FDLBM_EUNSUPPORTED;
     const bool fused = path == FDLBM_PATH_FUSED;
     const bool f32 = o.precision == FDLBM_FP32_DEV;
-    // the warp-tile kernel runs T2S2-FDLBM1 on periodic and walled grids and
-    // T2S2-FDLBM2 on periodic ones (a single grid: batches keep their
-    // T2S2-FDLBM2 cases on the scalar sweep)
+    // the warp-tile kernel runs both schemes, on periodic and walled grids (a
+    // single grid: batches keep their T2S2-FDLBM2 cases on the scalar sweep)
     const bool s1 = o.scheme == FDLBM_SCHEME_T2S2_1;
-    const bool s2_warp = o.scheme == FDLBM_SCHEME_T2S2_2 && !walled(g) && !force_staged;
+    const bool s2_warp = o.scheme == FDLBM_SCHEME_T2S2_2 && !force_staged;
     // (a batch case, force_staged: the batch's mode picks the kernels; the
     // variant is the one its FUSED mode runs the case on)
     const bool warp_ok = (s1 || s2_warp) && (fused || force_staged) && f32 &&
@@ -915,6 +914,9 @@ const char *fdlbm_describe(fdlbm_t h)
                                                                  : "fused-scheme2 ") +
                   prec;
         if (h->path == FDLBM_PATH_FUSED) h->desc += " rows=" + std::to_string(h->rows);
+        if (h->path == FDLBM_PATH_FUSED && h->variant == FDLBM_VARIANT_WARP &&
+            (h->bc_x == FDLBM_WALL || h->bc_y == FDLBM_WALL))
+            h->desc += " walls";
         if (h->graph_steps) h->desc += " graph_steps=" + std::to_string(h->graph_steps);
         if (h->incomp) h->desc += " incompressible";
         return h->desc.c_str();

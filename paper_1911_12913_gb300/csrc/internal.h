@@ -127,6 +127,17 @@ cudaError_t fused_warp_encode(WarpMaps *m, const float *state0, const float *sta
                               const float *force, int nx, int ny, int pitch, size_t plane);
 cudaError_t launch_fused_warp(const StepArgs<float> &a, const WarpMaps &maps, int cur,
                               cudaStream_t s);
+// Frame geometry of a walled grid split between the warp-tile kernel (the
+// interior rectangle [xoff, xend) x [yoff, yend)) and a walls sweep in blocks
+// of one warp (nframe tiles, erows rows beside the interior rows).
+struct FrameGeom {
+    int nx, ny, wx, wy;
+    int xoff, xend, yoff, yend, erows, nframe;
+};
+// step_fused_s2.cu: the frame of a walled T2S2-FDLBM2 grid (FP32).
+cudaError_t launch_frame_s2(const FrameGeom &g, const StepArgs<float> &a, cudaStream_t s);
+int frame_s2_blocks_per_sm();
+
 // The instance of the warp-tile kernel a grid needs.
 struct WarpKind {
     bool inc = false, grid = false, force = false, s2 = false;  // s2: T2S2-FDLBM2

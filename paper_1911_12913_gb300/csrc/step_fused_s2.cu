@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "frame.cuh"
 #include "walls_nodes.cuh"
 
 namespace fdlbm {
@@ -496,20 +497,20 @@ struct SweepS2W {
     }
 };
 
-// One tile of the walls sweep: output columns x0 .. x0 + NT - 9, rows y0 .. y0 +
-// a.rows - 1 (periodic axes wrap, walled axes clamp).
+// One tile of the walls sweep: output columns x0 .. x0 + NT - 9 below xhi,
+// rows y0 .. y1 - 1 (periodic axes wrap, walled axes clamp).
 template <class R, bool FORCE, int NT>
-__device__ __forceinline__ void sweep_tile_s2(const StepArgs<R> &a, Smem2<R, NT> &sm, int x0, int y0)
+__device__ __forceinline__ void sweep_tile_s2(const StepArgs<R> &a, Smem2<R, NT> &sm, int x0, int xhi,
+                                              int y0, int y1)
 {
     const int t = threadIdx.x;
     const int xc = x0 - kHalo2 + t;
-    const int y1 = min(y0 + a.rows, a.ny);
     const bool wx = a.bc_x == FDLBM_WALL, wy = a.bc_y == FDLBM_WALL;
     const bool inside = !wx || (xc >= 0 && xc < a.nx);
     const int gx = wx ? min(max(xc, 0), a.nx - 1) : wrap_index(xc, a.nx);
     const bool colint = !wx || (xc >= 1 && xc <= a.nx - 2);
     const bool colB = (t >= 2) && (t < NT - 2) && inside && colint;
-    const bool colC = (t >= kHalo2) && (t < NT - kHalo2) && xc < a.nx && inside && colint;
+    const bool colC = (t >= kHalo2) && (t < NT - kHalo2) && xc < min(a.nx, xhi) && inside && colint;
     SweepS2W<R, FORCE, NT> sw{a,
                               sm,
                               t,
@@ -543,7 +544,7 @@ __global__ void __launch_bounds__(NT, 2) k_step_fused_s2_walls(const StepArgs<R>
     Smem2<R, NT> &sm = *reinterpret_cast<Smem2<R, NT> *>(smem_raw);
     const int y0 = blockIdx.y * a.rows;
     if (y0 >= a.ny) return;  // uniform over the block
-    sweep_tile_s2<R, FORCE, NT>(a, sm, blockIdx.x * (NT - 2 * kHalo2), y0);
+    sweep_tile_s2<R, FORCE, NT>(a, sm, blockIdx.x * (NT - 2 * kHalo2), a.nx, y0, min(y0 + a.rows, a.ny));
 }
 
 // Batched: block b is tile (b + blk_off - blk_start[c]) of case c =
@@ -571,7 +572,21 @@ __global__ void __launch_bounds__(NT, 2)
     const int lb = b - blk_start[c], ns = strips[c];
     const int y0 = (lb / ns) * a.rows;
     if (y0 >= a.ny) return;  // uniform over the block
-    sweep_tile_s2<R, true, NT>(a, sm, (lb % ns) * (NT - 2 * kHalo2), y0);
+    sweep_tile_s2<R, true, NT>(a, sm, (lb % ns) * (NT - 2 * kHalo2), a.nx, y0, min(y0 + a.rows, a.ny));
+}
+
+// The frame of a walled FP32 grid whose interior runs the warp-tile kernel
+// (T2S2-FDLBM2): this walls sweep in blocks of one warp on the frame tiles.
+using FrameSmem2 = Smem2<float, frame::kFrameNT>;
+
+template <bool FORCE>
+__global__ void __launch_bounds__(frame::kFrameNT) k_frame_sweep_s2(const FrameGeom g, const StepArgs<float> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FrameSmem2 &sm = *reinterpret_cast<FrameSmem2 *>(smem_raw);
+    frame::Tile tile;
+    if (frame::frame_tile(g, blockIdx.x, tile) >= 0) return;
+    sweep_tile_s2<float, FORCE, frame::kFrameNT>(a, sm, tile.x0, tile.xend, tile.y0, tile.y1);
 }
 
 template <class R, bool FORCE>
@@ -648,5 +663,27 @@ template cudaError_t launch_fused_s2<float>(const StepArgs<float> &, cudaStream_
 template cudaError_t launch_fused_s2<double>(const StepArgs<double> &, cudaStream_t);
 template int fused_s2_blocks_per_sm<float>();
 template int fused_s2_blocks_per_sm<double>();
+
+cudaError_t launch_frame_s2(const FrameGeom &g, const StepArgs<float> &a, cudaStream_t s)
+{
+    if (g.nframe <= 0) return cudaSuccess;
+    constexpr size_t smem = sizeof(FrameSmem2);
+    auto kern = a.force ? k_frame_sweep_s2<true> : k_frame_sweep_s2<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<g.nframe, frame::kFrameNT, smem, s>>>(g, a);
+    return cudaGetLastError();
+}
+
+int frame_s2_blocks_per_sm()
+{
+    int n = 0;
+    constexpr size_t smem = sizeof(FrameSmem2);
+    cudaFuncSetAttribute(k_frame_sweep_s2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_frame_sweep_s2<true>, frame::kFrameNT, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
 
 }  // namespace fdlbm

@@ -61,6 +61,7 @@
 #include "internal.h"
 #include "packed.cuh"
 #include "tma.cuh"
+#include "frame.cuh"
 #include "walls_sweep.cuh"
 
 namespace fdlbm {
@@ -240,75 +241,11 @@ __device__ __forceinline__ f2 ytaps(const f2 c[3], int sgn, f2 vm2, f2 vm1, f2 v
     return fma2(c[2], vp2, fma2(c[1], vp1, fma2(c[0], vm1, acc)));
 }
 
-// The frame of a walled grid runs the walls sweep (walls_sweep.cuh) in blocks
-// of one warp, one column per thread: kFrameW output columns per tile.
-constexpr int kFrameNT = kLanes;
-constexpr int kFrameW = kFrameNT - 2 * walls_sweep::kHalo;
-
-// One tile of a launch: its first output column x0, the end of the columns
-// it stores, and its rows [y0, y1).
-struct Tile {
-    int x0, xend, y0, y1;
-};
-
-// Segment s of an axis of a walled grid: 0 the low frame, 1 the interior
-// rectangle, 2 the high frame (on a periodic axis the interior is the whole
-// axis and the frames are empty).
-__host__ __device__ inline void x_segment(const ArgsS &a, int s, int &lo, int &hi)
-{
-    if (!a.wx) {
-        lo = 0;
-        hi = s == 1 ? a.nx : 0;
-        return;
-    }
-    lo = s == 0 ? 0 : (s == 1 ? a.xoff : a.xend);
-    hi = s == 0 ? min(a.xoff, a.xend) : (s == 1 ? a.xend : a.nx);
-}
-
-__host__ __device__ inline void y_segment(const ArgsS &a, int s, int &lo, int &hi)
-{
-    if (!a.wy) {
-        lo = 0;
-        hi = s == 1 ? a.ny : 0;
-        return;
-    }
-    lo = s == 0 ? 0 : (s == 1 ? a.yoff : a.yend);
-    hi = s == 0 ? a.yoff : (s == 1 ? a.yend : a.ny);
-}
-
-// Tile t of the frame (the segment pairs other than interior x interior, in
-// tiles of kFrameW columns and, beside the interior rows, erows rows; the
-// frame rows of a walled y axis are one tile of at most 4 rows).  Returns the
-// number of frame tiles when t is past the last one (then `out` is unset),
-// else -1.
-__host__ __device__ inline int frame_tile(const ArgsS &a, int t, Tile &out)
-{
-    int n = 0;
-    for (int sy = 0; sy < 3; ++sy) {
-        int ylo, yhi;
-        y_segment(a, sy, ylo, yhi);
-        if (yhi <= ylo) continue;
-        const int h = sy == 1 ? a.erows : yhi - ylo;
-        const int nt = (yhi - ylo + h - 1) / h;
-        for (int sx = 0; sx < 3; ++sx) {
-            if (sx == 1 && sy == 1) continue;
-            int xlo, xhi;
-            x_segment(a, sx, xlo, xhi);
-            if (xhi <= xlo) continue;
-            const int nw = (xhi - xlo + kFrameW - 1) / kFrameW;
-            if (t >= n && t < n + nw * nt) {
-                const int u = t - n;
-                out.x0 = xlo + (u % nw) * kFrameW;
-                out.xend = xhi;
-                out.y0 = ylo + (u / nw) * h;
-                out.y1 = min(out.y0 + h, yhi);
-                return -1;
-            }
-            n += nw * nt;
-        }
-    }
-    return n;
-}
+using frame::kFrameNT;
+using frame::kFrameW;
+using frame::Tile;
+using frame::frame_tile;
+static_assert(kFrameNT == kLanes && kFrameW == kFrameNT - 2 * walls_sweep::kHalo, "frame tiles");
 
 // Tile (bx, by) of the interior rectangle.
 __host__ __device__ inline Tile interior_tile(const ArgsS &a, int bx, int by)
@@ -870,19 +807,21 @@ cudaError_t dispatch(const WarpKind &k, F &&f)
 #ifndef FDLBM_FRAME_MAX_ROWS
 #define FDLBM_FRAME_MAX_ROWS 64
 #endif
-static int frame_slots()
+// One wave of the frame launch: 12 blocks per SM for the T2S2-FDLBM1 walls
+// sweep (168 registers), fewer for the T2S2-FDLBM2 one.
+static int frame_slots(bool s2)
 {
-    static const int n = [] {
-        int dev = 0, sms = 0;
+    static const int sms = [] {
+        int dev = 0, n = 0;
         cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-            sms = 152;
-        return sms * kFrameMinBlocks;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        return n;
     }();
-    return n;
+    static const int per_sm_s2 = std::max(1, frame_s2_blocks_per_sm());
+    return sms * (s2 ? per_sm_s2 : kFrameMinBlocks);
 }
 
-static void split(ArgsS &a)
+static void split(ArgsS &a, bool s2)
 {
     a.xoff = 0;
     a.xend = a.nx;
@@ -904,7 +843,7 @@ static void split(ArgsS &a)
         Tile unused;
         for (;;) {
             a.nframe = frame_tile(a, 1 << 30, unused);
-            if (a.nframe <= frame_slots() || 2 * a.erows > FDLBM_FRAME_MAX_ROWS) break;
+            if (a.nframe <= frame_slots(s2) || 2 * a.erows > FDLBM_FRAME_MAX_ROWS) break;
             a.erows *= 2;
         }
     }
@@ -965,7 +904,7 @@ ArgsW make_args(const StepArgs<float> &s, const WarpMaps &maps, int cur)
     a.k_phys = 3.0f * s.c.c_phys;
     a.wx = s.bc_x == FDLBM_WALL;
     a.wy = s.bc_y == FDLBM_WALL;
-    split(a);
+    split(a, s.scheme == FDLBM_SCHEME_T2S2_2);
     return w;
 }
 
@@ -988,7 +927,13 @@ cudaError_t launch_fused_warp(const StepArgs<float> &s, const WarpMaps &maps, in
     const ArgsW a = make_args(s, maps, cur);
     const WarpKind k = warp_kind(s);
     cudaError_t e = cudaSuccess;
-    if (a.s.nframe > 0) e = s.force ? launch_frame_t<true>(a.s, s, stream) : launch_frame_t<false>(a.s, s, stream);
+    if (a.s.nframe > 0 && k.s2) {
+        const FrameGeom g{a.s.nx, a.s.ny, a.s.wx, a.s.wy, a.s.xoff, a.s.xend, a.s.yoff, a.s.yend, a.s.erows,
+                          a.s.nframe};
+        e = launch_frame_s2(g, s, stream);
+    } else if (a.s.nframe > 0) {
+        e = s.force ? launch_frame_t<true>(a.s, s, stream) : launch_frame_t<false>(a.s, s, stream);
+    }
     if (e != cudaSuccess || tile_count(a.s) <= 0) return e;
     const dim3 grid(a.s.nix, interior_rows(a.s));
     return dispatch(k, [&](auto inc, auto gr, auto fo) {

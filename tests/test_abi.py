@@ -106,7 +106,7 @@ def test_workspace_and_validation_without_gpu(B):
     o.path = B.PATH_STAGED
     assert L.fdlbm_workspace_bytes(ctypes.byref(grid), ctypes.byref(o)) > n32
     # walled grids take the fused path (Eq. 3.10 inside the sweep), for both
-    # schemes; the warp-tile kernel runs T2S2-FDLBM2 on periodic grids only
+    # schemes; the warp-tile kernel is FP32 only
     wa = I.wall_axis(20, 0.0, 1.0)
     wgrid, keep2 = B.make_grid(xa, wa)
     o.path = B.PATH_FUSED
@@ -115,8 +115,10 @@ def test_workspace_and_validation_without_gpu(B):
     assert L.fdlbm_workspace_bytes(ctypes.byref(wgrid), ctypes.byref(o)) > 0
     h = ctypes.c_void_p()
     o.variant = B.VARIANT_WARP
+    o.precision = B.FP64
     assert L.fdlbm_create(ctypes.byref(wgrid), None, 0.01, 0.5, 0.1, ctypes.byref(o),
                           ctypes.byref(h)) == -5
+    o.precision = B.FP32_DEV
     o.variant = B.VARIANT_AUTO
     # invalid arguments are rejected before any device work
     L.fdlbm_default_opts(ctypes.byref(o))

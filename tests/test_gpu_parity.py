@@ -287,22 +287,31 @@ def test_fused_walls_match_oracle(precision, tol, variant, force_on, bcx, bcy, n
                   label=f"{s.describe} {bcx}/{bcy} {nx}x{ny}")
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", FP64_TOL), ("fp32", FP32_L2)])
+@pytest.mark.parametrize("precision,tol,variant", [("fp64", FP64_TOL, "scalar"), ("fp32", FP32_L2, "scalar"),
+                                                   ("fp32", FP32_L2, "warp")])
 @pytest.mark.parametrize("bcx,bcy,nx,ny,rows", _WALL_CASES)
-def test_fused_walls_scheme2_match_oracle(precision, tol, bcx, bcy, nx, ny, rows):
-    """The fused T2S2-FDLBM2 sweep with Eq. 3.10 inside it (f^n, f^{n+1} and the
-    new f~ extrapolated to the walls) on the walled grids of the T2S2-FDLBM1
-    walls test: moving walls on every side, a force field, random state, 12
-    steps against the oracle's second sequence."""
+def test_fused_walls_scheme2_match_oracle(precision, tol, variant, bcx, bcy, nx, ny, rows):
+    """The fused T2S2-FDLBM2 sweeps with Eq. 3.10 inside them (f^n, f^{n+1} and
+    the new f~ extrapolated to the walls) on the walled grids of the
+    T2S2-FDLBM1 walls test: moving walls on every side, a force field, random
+    state, 12 steps against the oracle's second sequence.  variant warp: the
+    warp-tile kernel on the interior and the T2S2-FDLBM2 walls sweep on the
+    4-node frame (widths of 64 and more)."""
+    if variant == "warp" and not _warp_walls_ok(bcx, nx):
+        pytest.skip("narrower than the warp-tile window, or a periodic width not a multiple of 4")
     xa = _axis(bcx, nx, 81, 1.0)
     ya = _axis(bcy, ny, 82, 0.8)
     rng = np.random.default_rng(nx * 1000 + ny + 7)
     force = 1e-3 * rng.uniform(-1, 1, size=(2, ny, nx))
     wall_u = [tuple(0.05 * rng.uniform(-1, 1, size=2)) for _ in range(4)]
     s = FDLBM(xa, ya, nu=0.02, cfl=0.4, blend=0.2, precision=precision, has_force=True,
-              wall_u=wall_u, rows_per_cta=rows, path="fused", scheme=2)
-    assert s.describe.startswith("fused-scheme2"), s.describe
-    assert s.kernels_per_step == 1
+              wall_u=wall_u, rows_per_cta=rows, path="fused", scheme=2, variant=variant)
+    if variant == "warp":
+        assert s.describe.startswith("fused-warp-scheme2") and s.describe.endswith("walls"), s.describe
+        assert s.kernels_per_step == 2
+    else:
+        assert s.describe.startswith("fused-scheme2"), s.describe
+        assert s.kernels_per_step == 1
     o = O.Oracle(xa, ya, nu=0.02, dt=s.dt, beta=0.2, force=force, wall_u=wall_u, scheme=2)
     s.set_force(force)
     _init_both(s, o, I.random_fields(nx, ny, 190 + nx))
