@@ -221,6 +221,19 @@ double fdlbm_tau(fdlbm_t h);             /* nu / cs^2 */
 long long fdlbm_steps_done(fdlbm_t h);   /* steps enqueued since creation */
 int fdlbm_path(fdlbm_t h);               /* FDLBM_PATH_FUSED or FDLBM_PATH_STAGED */
 int fdlbm_kernels_per_step(fdlbm_t h);   /* kernel launches fdlbm_step makes per step */
+/* The tiles of the warp-tile kernel's step on a grid (FDLBM_VARIANT_WARP), for
+ * the tile height `rows` (> 0) and `scheme` (FDLBM_SCHEME_*): first the
+ * interior windows in launch order, then, on a walled grid, the frame tiles,
+ * 5 ints each: kind (0: interior, the warp tile, 56 output columns; 1: frame,
+ * the walls sweep in one-warp blocks, 24 output columns), x0 (first output
+ * column), the end of the columns the tile stores, y0, y1 (rows [y0, y1)).
+ * The interior covers the nodes at least 4 from every wall whose tiles load
+ * nothing outside the grid (Eq. 3.10 and the central differences next to a
+ * wall reach no further), the frame the rest.  Host only, no device work:
+ * *count receives the number of tiles and at most cap are written to tiles.
+ * EINVAL for bad arguments, EUNSUPPORTED where the warp-tile kernel does not
+ * apply. */
+fdlbm_status fdlbm_tile_plan(const fdlbm_grid *g, int rows, int scheme, int *tiles, int cap, int *count);
 const char *fdlbm_last_error(fdlbm_t h); /* never NULL */
 /* Short description of the kernel the handle runs per step, e.g.
  * "fused-warp fp32dev rows=121" (never NULL; valid until the handle is destroyed). */

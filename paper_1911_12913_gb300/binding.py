@@ -79,6 +79,8 @@ SIGNATURES = [
     ("fdlbm_steps_done", ctypes.c_longlong, [_H]),
     ("fdlbm_path", ctypes.c_int, [_H]),
     ("fdlbm_kernels_per_step", ctypes.c_int, [_H]),
+    ("fdlbm_tile_plan", ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("fdlbm_last_error", ctypes.c_char_p, [_H]),
     ("fdlbm_describe", ctypes.c_char_p, [_H]),
     ("fdlbm_status_string", ctypes.c_char_p, [ctypes.c_int]),

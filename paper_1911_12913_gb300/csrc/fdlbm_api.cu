@@ -798,6 +798,17 @@ double fdlbm_dt(fdlbm_t h) { return h ? h->dt : -1.0; }
 double fdlbm_tau(fdlbm_t h) { return h ? h->tau : -1.0; }
 long long fdlbm_steps_done(fdlbm_t h) { return h ? h->steps : -1; }
 int fdlbm_path(fdlbm_t h) { return h ? h->path : -1; }
+fdlbm_status fdlbm_tile_plan(const fdlbm_grid *g, int rows, int scheme, int *tiles, int cap, int *count)
+{
+    if (!grid_ok(g) || rows <= 0 || cap < 0 || !count || (cap > 0 && !tiles) ||
+        (scheme != FDLBM_SCHEME_T2S2_1 && scheme != FDLBM_SCHEME_T2S2_2))
+        return FDLBM_EINVAL;
+    if (!fused_warp_ok(g->nx, g->ny, g->bc_x == FDLBM_WALL)) return FDLBM_EUNSUPPORTED;
+    *count = warp_tile_plan(g->nx, g->ny, g->bc_x == FDLBM_WALL, g->bc_y == FDLBM_WALL, rows,
+                            scheme == FDLBM_SCHEME_T2S2_2, tiles, cap);
+    return FDLBM_OK;
+}
+
 int fdlbm_kernels_per_step(fdlbm_t h)
 {
     if (!h) return -1;

@@ -161,6 +161,10 @@ cudaError_t launch_batched_frame(const void *args, const void *sargs, const int 
 // Interior tiles (warp-tile launch) and frame tiles (walls-sweep launch, 0 on
 // a periodic grid) of one grid at its tile height.
 void fused_warp_tiles(const StepArgs<float> &s, int *interior, int *frame);
+// The same tiles as a list (5 ints each: kind 0 interior / 1 frame, x0, end of
+// the stored columns, y0, y1); host only.  Returns the count (entries past cap
+// are not written).
+int warp_tile_plan(int nx, int ny, bool wx, bool wy, int rows, bool s2, int *out, int cap);
 int fused_warp_tile_width();
 int fused_warp_blocks_per_sm();
 // step_fused_walls.cu (scalar sweep with walled axes and Eq. 3.10 inside)

@@ -998,6 +998,42 @@ cudaError_t launch_batched_frame(const void *args, const void *sargs, const int 
     return cudaGetLastError();
 }
 
+// The tiles of one grid's warp-tile step, host side only: interior windows
+// (kind 0: x0, store end, y0, y1) in launch order, then frame tiles (kind 1).
+int warp_tile_plan(int nx, int ny, bool wx, bool wy, int rows, bool s2, int *out, int cap)
+{
+    ArgsS a;
+    std::memset(&a, 0, sizeof a);
+    a.nx = nx;
+    a.ny = ny;
+    a.wx = wx;
+    a.wy = wy;
+    a.rows = std::max(1, std::min(rows, ny));
+    split(a, s2);
+    int n = 0;
+    auto put = [&](int kind, const Tile &t) {
+        if (n < cap && out) {
+            int *o = out + 5 * n;
+            o[0] = kind;
+            o[1] = t.x0;
+            o[2] = t.xend;
+            o[3] = t.y0;
+            o[4] = t.y1;
+        }
+        ++n;
+    };
+    for (int by = 0; by < interior_rows(a); ++by)
+        for (int bx = 0; bx < a.nix; ++bx) {
+            const Tile t = interior_tile(a, bx, by);
+            if (t.y0 < t.y1) put(0, t);
+        }
+    for (int t = 0; t < a.nframe; ++t) {
+        Tile tile;
+        if (frame_tile(a, t, tile) < 0) put(1, tile);
+    }
+    return n;
+}
+
 int fused_warp_tile_width() { return kW; }
 
 int fused_warp_blocks_per_sm()
