@@ -87,9 +87,12 @@ enum { FDLBM_WALL_W = 0, FDLBM_WALL_E = 1, FDLBM_WALL_S = 2, FDLBM_WALL_N = 3 };
  *  T2S2_1  f~(n+1) = f~+ + dt L(f*), f* at t_n + A dt (Eq. 2.23; A = 0 gives T1S2);
  *  T2S2_2  f~(n+1) = f~+ + dt/2 [L(f^n) + L(f^{n+1})] with the characteristic
  *          estimate of f^{n+1} over h = dt (Eq. 5.23, second sequence of Sec. 2D).
- *          Runs on its own fused sweeps (periodic grids in both precisions,
- *          walled grids in FP32) and on the staged kernels (walled grids in
- *          FP64, or opts.path = FDLBM_PATH_STAGED); A is ignored. */
+ *          Runs on its own fused sweeps (FP32 grids of 64 columns and more:
+ *          the warp-tile kernel, with the walls sweep on the 4-node frame of a
+ *          walled grid; otherwise the scalar sweeps, periodic grids in both
+ *          precisions and walled grids in FP32) and on the staged kernels
+ *          (walled grids in FP64, or opts.path = FDLBM_PATH_STAGED); A is
+ *          ignored. */
 enum { FDLBM_SCHEME_T2S2_1 = 0, FDLBM_SCHEME_T2S2_2 = 1 };
 
 /* Tensor-product grid (Sec. 3, Eqs. 3.9 and 3.11).  A periodic axis stores its
