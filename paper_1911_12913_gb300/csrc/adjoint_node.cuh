@@ -32,12 +32,13 @@ struct NodeMap {
         ux = jx * inv;
         uy = jy * inv;
         const R usq = R(1.5) * (ux * ux + uy * uy);
+        const R uF = ux * Fx + uy * Fy;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             eu[i] = xi_dot<R>(i, ux, uy);
             t[i] = eu[i] * (R(3) + R(4.5) * eu[i]) - usq;
             feq[i] = wq<R>(i) * rho0 + wq<R>(i) * (drho + rho * t[i]);
-            s[i] = (R(cx(i)) - ux) * Fx + (R(cy(i)) - uy) * Fy;
+            s[i] = xi_dot<R>(i, Fx, Fy) - uF;  // (xi_i - u).F
         }
     }
 
@@ -47,24 +48,30 @@ struct NodeMap {
                         R &lFy) const
     {
         R lux = R(0), luy = R(0), lrho = R(0), ldrho = R(0), lusq = R(0);
+        // the cotangents of s_i = (xi_i - u).F summed first: sum ls, sum xi ls
+        R ls0 = R(0), lsx = R(0), lsy = R(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             // F_i = 3 s_i feq_i
             const R lgeq = lgeq_in[i] + R(3) * s[i] * lF[i];
             const R ls = R(3) * feq[i] * lF[i];
-            lux -= Fx * ls;
-            luy -= Fy * ls;
-            lFx += (R(cx(i)) - ux) * ls;
-            lFy += (R(cy(i)) - uy) * ls;
+            ls0 += ls;
+            lsx += R(cx(i)) * ls;
+            lsy += R(cy(i)) * ls;
             // geq_i = w_i (drho + rho t_i), t_i = eu_i (3 + 4.5 eu_i) - usq
-            ldrho += wq<R>(i) * lgeq;
-            lrho += wq<R>(i) * t[i] * lgeq;
-            const R lt = wq<R>(i) * rho * lgeq;
+            const R wl = wq<R>(i) * lgeq;
+            ldrho += wl;
+            lrho += t[i] * wl;
+            const R lt = rho * wl;
             const R leu = (R(3) + R(9) * eu[i]) * lt;
             lusq -= lt;
             lux += R(cx(i)) * leu;
             luy += R(cy(i)) * leu;
         }
+        lux -= Fx * ls0;
+        luy -= Fy * ls0;
+        lFx += lsx - ux * ls0;
+        lFy += lsy - uy * ls0;
         // usq = 1.5 (ux^2 + uy^2)
         lux += R(3) * ux * lusq;
         luy += R(3) * uy * lusq;
